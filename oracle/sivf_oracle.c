@@ -1,0 +1,617 @@
+/*
+ * SIVF oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU model of the streaming IVF-Flat index
+ * of "SIVF: GPU-Resident IVF Index for Streaming Vector Search"
+ * (arxiv 2601.11808).  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load it.  It shares no code,
+ * header, table or helper with the CUDA library; the product path never
+ * calls it.
+ *
+ * Floating point: every distance is FP64, summed over coordinates in index
+ * order j = 0..d-1, each term (double(a_j) - double(b_j))^2.  The file is
+ * compiled with -ffp-contract=off so that a*b+c is two roundings on every
+ * host (x86-64 and aarch64 give the same bits).
+ *
+ * What each part follows (paper sections / algorithms):
+ *   - coarse assignment and probe selection: the IVF coarse quantizer of
+ *     Sec. 3.3 (nearest centroid by L2; the paper is silent on ties -- ties go
+ *     to the lowest centroid index);
+ *   - list scan and top-k: Algorithm 3 and the search complexity of
+ *     Sec. 3.5.2 (exact scan of every live member of the probed lists; the
+ *     metric is squared L2; ties go to the lower id; missing results are
+ *     padded with (+inf, -1));
+ *   - delete-then-insert overwrite: the data model paragraph of Sec. 3;
+ *   - idempotent delete: Algorithm 4 and Theorem 3;
+ *   - slab bookkeeping (which slab a vector lands in, when a slab is taken
+ *     from or returned to the pool): Algorithm 1 (a list fills its head slab
+ *     and takes a new slab only when the head is absent or full) and
+ *     Algorithm 4 (a slab whose live count reaches zero goes back to the
+ *     pool).  Slab *identities* are not modelled, only per-list sequences
+ *     of slab records {fill, live}, so the model is independent of how a
+ *     free stack orders its slabs.
+ *   - batch semantics (a reading; the paper gives per-vector operations
+ *     only): add(batch) = (1) keep the last occurrence of each id, (2) all-
+ *     or-nothing admission: slab demand, computed on the state before the
+ *     batch, must fit in the free slabs and in each list's directory
+ *     capacity, (3) remove every kept id that is currently live, (4) append
+ *     the kept ids in batch order.  remove(batch) removes each live id once;
+ *     absent ids are no-ops.
+ *   - reduced-precision encodings used by the precision path: bfloat16 with
+ *     round-to-nearest-even, and FP8 E4M3 (OCP "fn" variant: bias 7, no
+ *     infinities, max finite 448) with round-to-nearest-even and saturation
+ *     to +-448, applied to v = x * inv_scale rounded to FP32.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { O_OK = 0, O_E_ARG = 1, O_E_NOMEM = 2, O_E_STATE = 3 };
+
+typedef struct {
+    int32_t fill; /* slots ever written in this slab (monotone until freed) */
+    int32_t live; /* live vectors in this slab */
+    int32_t list; /* owning list, -1 once returned to the pool */
+} orec;
+
+typedef struct {
+    int64_t n, cap;  /* members, in insertion order */
+    int64_t *ids;
+    float *x;        /* n * d */
+    int64_t *rec;    /* slab record of each member */
+    int32_t *slot;   /* slot of each member inside its slab */
+    int64_t nrec, reccap;
+    int64_t *recs;   /* this list's slab records, oldest first; last = head */
+} olist;
+
+typedef struct oivf {
+    int d, nlist, C;
+    int64_t n_max, n_slabs, dir_cap;
+    float *cent;
+    int have_cent;
+    olist *lists;
+    int32_t *where;  /* id -> list, or -1 */
+    orec *recs;
+    int64_t nrecs, recs_cap;
+    int64_t free_slabs;
+    int64_t ntotal;
+} oivf;
+
+/* ------------------------------------------------------------------ */
+/* small helpers                                                        */
+/* ------------------------------------------------------------------ */
+
+static double sqdist(const float *a, const float *b, int d)
+{
+    double acc = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = (double)a[j] - (double)b[j];
+        acc += t * t;
+    }
+    return acc;
+}
+
+static void *xrealloc(void *p, size_t n)
+{
+    void *q = realloc(p, n ? n : 1);
+    if (!q) abort();
+    return q;
+}
+
+typedef struct {
+    double d;
+    int64_t key; /* centroid index or vector id */
+} dk;
+
+static int cmp_dk(const void *a, const void *b)
+{
+    const dk *x = (const dk *)a, *y = (const dk *)b;
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return 0;
+}
+
+int oivf_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* lifetime                                                             */
+/* ------------------------------------------------------------------ */
+
+oivf *oivf_create(int d, int nlist, int C, int64_t n_max, int64_t n_slabs,
+                  int64_t dir_cap)
+{
+    if (d <= 0 || nlist <= 0 || C <= 0 || n_max <= 0 || n_slabs <= 0 ||
+        dir_cap <= 0)
+        return NULL;
+    oivf *o = (oivf *)calloc(1, sizeof(oivf));
+    o->d = d;
+    o->nlist = nlist;
+    o->C = C;
+    o->n_max = n_max;
+    o->n_slabs = n_slabs;
+    o->dir_cap = dir_cap;
+    o->cent = (float *)calloc((size_t)nlist * d, sizeof(float));
+    o->lists = (olist *)calloc((size_t)nlist, sizeof(olist));
+    o->where = (int32_t *)malloc((size_t)n_max * sizeof(int32_t));
+    for (int64_t i = 0; i < n_max; ++i) o->where[i] = -1;
+    o->free_slabs = n_slabs;
+    return o;
+}
+
+void oivf_destroy(oivf *o)
+{
+    if (!o) return;
+    for (int l = 0; l < o->nlist; ++l) {
+        olist *L = &o->lists[l];
+        free(L->ids);
+        free(L->x);
+        free(L->rec);
+        free(L->slot);
+        free(L->recs);
+    }
+    free(o->lists);
+    free(o->cent);
+    free(o->where);
+    free(o->recs);
+    free(o);
+}
+
+int oivf_set_centroids(oivf *o, const float *c)
+{
+    memcpy(o->cent, c, (size_t)o->nlist * o->d * sizeof(float));
+    o->have_cent = 1;
+    return O_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* coarse quantizer                                                     */
+/* ------------------------------------------------------------------ */
+
+/* nearest centroid; strict '<' over ascending index keeps the lowest index
+ * on ties */
+static int32_t nearest(const oivf *o, const float *x)
+{
+    int32_t best = 0;
+    double bd = sqdist(x, o->cent, o->d);
+    for (int c = 1; c < o->nlist; ++c) {
+        double dc = sqdist(x, o->cent + (size_t)c * o->d, o->d);
+        if (dc < bd) {
+            bd = dc;
+            best = c;
+        }
+    }
+    return best;
+}
+
+int oivf_assign(const oivf *o, const float *x, int64_t n, int32_t *out)
+{
+    if (!o->have_cent) return O_E_STATE;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) out[i] = nearest(o, x + (size_t)i * o->d);
+    return O_OK;
+}
+
+/* the P nearest centroids of q, ascending by (distance, index) */
+static void probes_of(const oivf *o, const float *q, int P, int32_t *out,
+                      dk *tmp)
+{
+    for (int c = 0; c < o->nlist; ++c) {
+        tmp[c].d = sqdist(q, o->cent + (size_t)c * o->d, o->d);
+        tmp[c].key = c;
+    }
+    qsort(tmp, (size_t)o->nlist, sizeof(dk), cmp_dk);
+    for (int p = 0; p < P; ++p) out[p] = (int32_t)tmp[p].key;
+}
+
+int oivf_probe(const oivf *o, const float *q, int64_t nq, int P, int32_t *out)
+{
+    if (!o->have_cent) return O_E_STATE;
+    if (P < 1 || P > o->nlist) return O_E_ARG;
+#pragma omp parallel
+    {
+        dk *tmp = (dk *)malloc((size_t)o->nlist * sizeof(dk));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < nq; ++i)
+            probes_of(o, q + (size_t)i * o->d, P, out + (size_t)i * P, tmp);
+        free(tmp);
+    }
+    return O_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* search                                                               */
+/* ------------------------------------------------------------------ */
+
+/* exact scan of every member of the given lists, then the k smallest by
+ * (distance, id); fewer than k candidates are padded with (+inf, -1) */
+static void scan_lists(const oivf *o, const float *q, const int32_t *probes,
+                       int P, int k, double *dist, int64_t *ids)
+{
+    int64_t ncand = 0;
+    for (int p = 0; p < P; ++p) {
+        int32_t l = probes[p];
+        if (l >= 0 && l < o->nlist) ncand += o->lists[l].n;
+    }
+    dk *cand = (dk *)malloc((size_t)(ncand ? ncand : 1) * sizeof(dk));
+    int64_t m = 0;
+    for (int p = 0; p < P; ++p) {
+        int32_t l = probes[p];
+        if (l < 0 || l >= o->nlist) continue;
+        /* a list probed twice is scanned once */
+        int dup = 0;
+        for (int pp = 0; pp < p; ++pp)
+            if (probes[pp] == l) dup = 1;
+        if (dup) continue;
+        const olist *L = &o->lists[l];
+        for (int64_t i = 0; i < L->n; ++i) {
+            cand[m].d = sqdist(q, L->x + (size_t)i * o->d, o->d);
+            cand[m].key = L->ids[i];
+            ++m;
+        }
+    }
+    qsort(cand, (size_t)m, sizeof(dk), cmp_dk);
+    for (int j = 0; j < k; ++j) {
+        if (j < m) {
+            dist[j] = cand[j].d;
+            ids[j] = cand[j].key;
+        } else {
+            dist[j] = INFINITY;
+            ids[j] = -1;
+        }
+    }
+    free(cand);
+}
+
+int oivf_search_with_probes(const oivf *o, const float *q, int64_t nq, int k,
+                            int P, const int32_t *probes, double *dist,
+                            int64_t *ids)
+{
+    if (k < 1 || P < 1) return O_E_ARG;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < nq; ++i)
+        scan_lists(o, q + (size_t)i * o->d, probes + (size_t)i * P, P, k,
+                   dist + (size_t)i * k, ids + (size_t)i * k);
+    return O_OK;
+}
+
+int oivf_search(const oivf *o, const float *q, int64_t nq, int k, int P,
+                double *dist, int64_t *ids)
+{
+    if (!o->have_cent) return O_E_STATE;
+    if (k < 1 || P < 1 || P > o->nlist) return O_E_ARG;
+#pragma omp parallel
+    {
+        dk *tmp = (dk *)malloc((size_t)o->nlist * sizeof(dk));
+        int32_t *pr = (int32_t *)malloc((size_t)P * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < nq; ++i) {
+            const float *qi = q + (size_t)i * o->d;
+            probes_of(o, qi, P, pr, tmp);
+            scan_lists(o, qi, pr, P, k, dist + (size_t)i * k,
+                       ids + (size_t)i * k);
+        }
+        free(pr);
+        free(tmp);
+    }
+    return O_OK;
+}
+
+/* brute-force k nearest live vectors (every list scanned) */
+int oivf_exact_knn(const oivf *o, const float *q, int64_t nq, int k,
+                   double *dist, int64_t *ids)
+{
+    if (k < 1) return O_E_ARG;
+    int32_t *all = (int32_t *)malloc((size_t)o->nlist * sizeof(int32_t));
+    for (int l = 0; l < o->nlist; ++l) all[l] = l;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < nq; ++i)
+        scan_lists(o, q + (size_t)i * o->d, all, o->nlist, k,
+                   dist + (size_t)i * k, ids + (size_t)i * k);
+    free(all);
+    return O_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* slab bookkeeping model (Algorithms 1 and 4)                          */
+/* ------------------------------------------------------------------ */
+
+static int64_t new_record(oivf *o, int32_t list)
+{
+    if (o->nrecs == o->recs_cap) {
+        o->recs_cap = o->recs_cap ? 2 * o->recs_cap : 1024;
+        o->recs = (orec *)xrealloc(o->recs, (size_t)o->recs_cap * sizeof(orec));
+    }
+    int64_t u = o->nrecs++;
+    o->recs[u].fill = 0;
+    o->recs[u].live = 0;
+    o->recs[u].list = list;
+    olist *L = &o->lists[list];
+    if (L->nrec == L->reccap) {
+        L->reccap = L->reccap ? 2 * L->reccap : 8;
+        L->recs = (int64_t *)xrealloc(L->recs, (size_t)L->reccap * sizeof(int64_t));
+    }
+    L->recs[L->nrec++] = u;
+    o->free_slabs -= 1;
+    return u;
+}
+
+/* Algorithm 4: clear the member, decrement its slab's live count and give
+ * the slab back to the pool when nothing live remains in it. */
+static void erase(oivf *o, int64_t id)
+{
+    int32_t l = o->where[id];
+    olist *L = &o->lists[l];
+    int64_t p = 0;
+    while (L->ids[p] != id) ++p;
+    int64_t u = L->rec[p];
+    int64_t tail = L->n - p - 1;
+    memmove(L->ids + p, L->ids + p + 1, (size_t)tail * sizeof(int64_t));
+    memmove(L->x + (size_t)p * o->d, L->x + (size_t)(p + 1) * o->d,
+            (size_t)tail * o->d * sizeof(float));
+    memmove(L->rec + p, L->rec + p + 1, (size_t)tail * sizeof(int64_t));
+    memmove(L->slot + p, L->slot + p + 1, (size_t)tail * sizeof(int32_t));
+    L->n -= 1;
+    o->where[id] = -1;
+    o->ntotal -= 1;
+    o->recs[u].live -= 1;
+    if (o->recs[u].live == 0) {
+        int64_t r = 0;
+        while (L->recs[r] != u) ++r;
+        memmove(L->recs + r, L->recs + r + 1,
+                (size_t)(L->nrec - r - 1) * sizeof(int64_t));
+        L->nrec -= 1;
+        o->recs[u].list = -1;
+        o->free_slabs += 1;
+    }
+}
+
+/* Algorithm 1 (Insert): write into the head slab while it has a free slot,
+ * otherwise take a fresh slab from the pool and make it the head. */
+static void append(oivf *o, int32_t l, int64_t id, const float *x)
+{
+    olist *L = &o->lists[l];
+    int64_t u = -1;
+    if (L->nrec > 0) {
+        int64_t h = L->recs[L->nrec - 1];
+        if (o->recs[h].fill < o->C) u = h;
+    }
+    if (u < 0) u = new_record(o, l);
+    int32_t slot = o->recs[u].fill;
+    o->recs[u].fill += 1;
+    o->recs[u].live += 1;
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 64;
+        L->ids = (int64_t *)xrealloc(L->ids, (size_t)L->cap * sizeof(int64_t));
+        L->x = (float *)xrealloc(L->x, (size_t)L->cap * o->d * sizeof(float));
+        L->rec = (int64_t *)xrealloc(L->rec, (size_t)L->cap * sizeof(int64_t));
+        L->slot = (int32_t *)xrealloc(L->slot, (size_t)L->cap * sizeof(int32_t));
+    }
+    L->ids[L->n] = id;
+    memcpy(L->x + (size_t)L->n * o->d, x, (size_t)o->d * sizeof(float));
+    L->rec[L->n] = u;
+    L->slot[L->n] = slot;
+    L->n += 1;
+    o->where[id] = l;
+    o->ntotal += 1;
+}
+
+int oivf_add(oivf *o, const int64_t *ids, const float *x, int64_t n,
+             int64_t *n_added)
+{
+    if (n_added) *n_added = 0;
+    if (!o->have_cent) return O_E_STATE;
+    if (n < 0) return O_E_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (ids[i] < 0 || ids[i] >= o->n_max) return O_E_ARG;
+    if (n == 0) return O_OK;
+
+    /* (1) the last occurrence of every id wins */
+    int64_t *last = (int64_t *)malloc((size_t)o->n_max * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) last[ids[i]] = i;
+    char *win = (char *)malloc((size_t)n);
+    for (int64_t i = 0; i < n; ++i) win[i] = (last[ids[i]] == i);
+    free(last);
+
+    int32_t *lab = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    oivf_assign(o, x, n, lab);
+
+    /* (2) admission on the state before the batch */
+    int64_t *cnt = (int64_t *)calloc((size_t)o->nlist, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i)
+        if (win[i]) cnt[lab[i]] += 1;
+    int64_t demand = 0;
+    int status = O_OK;
+    for (int l = 0; l < o->nlist; ++l) {
+        if (!cnt[l]) continue;
+        const olist *L = &o->lists[l];
+        int64_t avail = 0;
+        if (L->nrec > 0) avail = o->C - o->recs[L->recs[L->nrec - 1]].fill;
+        int64_t need = cnt[l] > avail ? (cnt[l] - avail + o->C - 1) / o->C : 0;
+        if (L->nrec + need > o->dir_cap) status = O_E_NOMEM;
+        demand += need;
+    }
+    if (demand > o->free_slabs) status = O_E_NOMEM;
+    free(cnt);
+    if (status != O_OK) {
+        free(win);
+        free(lab);
+        return status;
+    }
+
+    /* (3) delete-then-insert: every kept id that is live is removed first */
+    for (int64_t i = 0; i < n; ++i)
+        if (win[i] && o->where[ids[i]] >= 0) erase(o, ids[i]);
+
+    /* (4) append in batch order */
+    int64_t added = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!win[i]) continue;
+        append(o, lab[i], ids[i], x + (size_t)i * o->d);
+        ++added;
+    }
+    free(win);
+    free(lab);
+    if (n_added) *n_added = added;
+    return O_OK;
+}
+
+int oivf_remove(oivf *o, const int64_t *ids, int64_t n, int64_t *n_removed)
+{
+    if (n_removed) *n_removed = 0;
+    if (n < 0) return O_E_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (ids[i] < 0 || ids[i] >= o->n_max) return O_E_ARG;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (o->where[ids[i]] < 0) continue; /* absent: no-op (Theorem 3) */
+        erase(o, ids[i]);
+        ++cnt;
+    }
+    if (n_removed) *n_removed = cnt;
+    return O_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* introspection                                                        */
+/* ------------------------------------------------------------------ */
+
+int64_t oivf_ntotal(const oivf *o) { return o->ntotal; }
+int64_t oivf_free_slabs(const oivf *o) { return o->free_slabs; }
+int32_t oivf_list_of(const oivf *o, int64_t id)
+{
+    return (id >= 0 && id < o->n_max) ? o->where[id] : -1;
+}
+int64_t oivf_list_size(const oivf *o, int l) { return o->lists[l].n; }
+int64_t oivf_list_nslabs(const oivf *o, int l) { return o->lists[l].nrec; }
+
+/* members of list l in insertion order, with the slab sequence number (the
+ * position of their slab in the list's slab sequence, oldest = 0) and slot */
+void oivf_list_members(const oivf *o, int l, int64_t *ids, int32_t *slab_seq,
+                       int32_t *slot)
+{
+    const olist *L = &o->lists[l];
+    for (int64_t i = 0; i < L->n; ++i) {
+        if (ids) ids[i] = L->ids[i];
+        if (slot) slot[i] = L->slot[i];
+        if (slab_seq) {
+            int32_t r = 0;
+            while (L->recs[r] != L->rec[i]) ++r;
+            slab_seq[i] = r;
+        }
+    }
+}
+
+void oivf_list_vectors(const oivf *o, int l, float *x)
+{
+    const olist *L = &o->lists[l];
+    memcpy(x, L->x, (size_t)L->n * o->d * sizeof(float));
+}
+
+/* fill and live count of each slab of list l, oldest first */
+void oivf_list_slabs(const oivf *o, int l, int32_t *fill, int32_t *live)
+{
+    const olist *L = &o->lists[l];
+    for (int64_t r = 0; r < L->nrec; ++r) {
+        fill[r] = o->recs[L->recs[r]].fill;
+        live[r] = o->recs[L->recs[r]].live;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* reduced-precision encodings                                          */
+/* ------------------------------------------------------------------ */
+
+static uint32_t f2u(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+/* bfloat16: keep the top 16 bits of the FP32 pattern, rounding the dropped
+ * 16 bits to nearest, ties to even; NaN stays a quiet NaN */
+void oivf_to_bf16(const float *in, uint16_t *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t u = f2u(in[i]);
+        if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) {
+            out[i] = (uint16_t)((u >> 16) | 0x0040u);
+            continue;
+        }
+        uint32_t upper = u >> 16, lower = u & 0xffffu;
+        if (lower > 0x8000u || (lower == 0x8000u && (upper & 1u))) upper += 1;
+        out[i] = (uint16_t)upper;
+    }
+}
+
+void oivf_from_bf16(const uint16_t *in, float *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t u = (uint32_t)in[i] << 16;
+        memcpy(&out[i], &u, 4);
+    }
+}
+
+/* value of an E4M3 code: sign, 4 exponent bits (bias 7), 3 mantissa bits;
+ * exponent field 0 is subnormal (m/8 * 2^-6); S.1111.111 is NaN */
+static double e4m3_value(uint8_t c)
+{
+    int s = c >> 7, e = (c >> 3) & 15, m = c & 7;
+    double v;
+    if (e == 15 && m == 7) return NAN;
+    if (e == 0)
+        v = ldexp((double)m / 8.0, -6);
+    else
+        v = ldexp(1.0 + (double)m / 8.0, e - 7);
+    return s ? -v : v;
+}
+
+void oivf_from_e4m3(const uint8_t *in, double *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = e4m3_value(in[i]);
+}
+
+/* E4M3 encoding of v = fl32(x * inv_scale): the nearest code value, ties to
+ * the code with an even mantissa, |v| above the largest finite value
+ * saturates to +-448.  Found by plain search over the 127 non-negative
+ * finite codes (obviously correct, slow). */
+void oivf_to_e4m3(const float *in, float inv_scale, uint8_t *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float vf = (float)((double)in[i] * (double)inv_scale);
+        double v = (double)vf;
+        if (isnan(v)) {
+            out[i] = 0x7f;
+            continue;
+        }
+        uint8_t sign = (v < 0 || (v == 0 && signbit(v))) ? 0x80 : 0;
+        double a = fabs(v);
+        uint8_t best = 0;
+        double bd = INFINITY;
+        for (int c = 0; c <= 0x7e; ++c) {
+            double cv = e4m3_value((uint8_t)c);
+            double dd = fabs(cv - a);
+            if (dd < bd || (dd == bd && (c & 1) == 0 && (best & 1) == 1)) {
+                bd = dd;
+                best = (uint8_t)c;
+            }
+        }
+        if (a >= 448.0) best = 0x7e;
+        out[i] = (uint8_t)(sign | best);
+    }
+}

@@ -1,0 +1,143 @@
+"""Seeded synthetic inputs shaped like the paper's sliding-window workloads.
+
+This module only draws random numbers; it holds none of the index's
+arithmetic.  Both the CUDA path and the CPU oracle take their inputs from
+here, so the two always see the same vectors.
+
+Every stream is cut into fixed blocks of ``BLOCK`` vectors and block ``b`` of
+stream ``s`` is drawn from ``PCG64(SeedSequence([seed, s, b]))``; a vector's
+value therefore depends only on its position in the stream, never on how a
+caller batches it.  Streams: 0 = mixture centers, 1 = database vectors,
+2 = queries, 3 = extra centroids (sample points, used when there are more
+lists than mixture components).
+
+The paper's datasets (SIFT1M, GIST1M, Deep1B, T2I-1B, DINO10B) are not
+available; these mixtures stand in for them with the same dimensions and
+value ranges (SIFT-like: d=128 integers in [0, 255]; Deep-like: d=96, unit
+norm).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BLOCK = 4096
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    d: int
+    n_comp: int          # mixture components
+    kind: str            # "uniform_box" | "sift" | "sphere"
+    sigma: float
+    nlist: int
+    slab_size: int
+    window: int          # live vectors in the sliding window
+    step: int            # vectors inserted (and oldest deleted) per step
+    n_queries: int
+    k: int
+    nprobes: tuple = field(default=(8,))
+    seed: int = 0
+
+
+# the five workload shapes (sizes, distributions and index parameters)
+CONFIGS = {
+    "tiny_window": Workload("tiny_window", d=32, n_comp=64, kind="uniform_box",
+                            sigma=0.1, nlist=64, slab_size=32, window=20_000,
+                            step=2_000, n_queries=200, k=10, nprobes=(8,)),
+    "sift_window": Workload("sift_window", d=128, n_comp=1024, kind="sift",
+                            sigma=20.0, nlist=1024, slab_size=64,
+                            window=1_000_000, step=10_000, n_queries=10_000,
+                            k=10, nprobes=(8, 32, 128)),
+    "deep_precision": Workload("deep_precision", d=96, n_comp=4096,
+                               kind="sphere", sigma=0.02, nlist=4096,
+                               slab_size=32, window=10_000_000, step=0,
+                               n_queries=10_000, k=100, nprobes=(64,)),
+    "mixed_batches": Workload("mixed_batches", d=128, n_comp=64,
+                              kind="uniform_box", sigma=0.1, nlist=2048,
+                              slab_size=64, window=5_000_000, step=0,
+                              n_queries=4096, k=10,
+                              nprobes=(8, 16, 32, 64, 128)),
+    "serving": Workload("serving", d=128, n_comp=16384, kind="uniform_box",
+                        sigma=0.1, nlist=16384, slab_size=128,
+                        window=100_000_000, step=0, n_queries=256, k=10,
+                        nprobes=(32,)),
+}
+
+
+def _rng(seed: int, stream: int, block: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(
+        np.random.SeedSequence([int(seed), int(stream), int(block)])))
+
+
+def centers(w: Workload) -> np.ndarray:
+    """Mixture centers, float32 [n_comp, d]."""
+    g = _rng(w.seed, 0, 0)
+    if w.kind == "uniform_box":
+        c = g.uniform(-1.0, 1.0, size=(w.n_comp, w.d))
+    elif w.kind == "sift":
+        c = g.uniform(0.0, 255.0, size=(w.n_comp, w.d))
+    elif w.kind == "sphere":
+        c = g.standard_normal(size=(w.n_comp, w.d))
+        c /= np.linalg.norm(c, axis=1, keepdims=True)
+    else:
+        raise ValueError(w.kind)
+    return c.astype(np.float32)
+
+
+def _draw(w: Workload, ctr: np.ndarray, stream: int, start: int,
+          n: int) -> np.ndarray:
+    out = np.empty((n, w.d), np.float32)
+    pos = 0
+    b0, b1 = start // BLOCK, (start + n + BLOCK - 1) // BLOCK
+    for b in range(b0, b1):
+        g = _rng(w.seed, stream, b)
+        comp = g.integers(0, w.n_comp, size=BLOCK)
+        noise = g.standard_normal(size=(BLOCK, w.d))
+        blk = ctr[comp].astype(np.float64) + w.sigma * noise
+        if w.kind == "sift":
+            blk = np.clip(np.rint(blk), 0.0, 255.0)
+        elif w.kind == "sphere":
+            blk /= np.linalg.norm(blk, axis=1, keepdims=True)
+        lo = max(start, b * BLOCK) - b * BLOCK
+        hi = min(start + n, (b + 1) * BLOCK) - b * BLOCK
+        out[pos:pos + hi - lo] = blk[lo:hi]
+        pos += hi - lo
+    return out
+
+
+def vectors(w: Workload, start: int, n: int, ctr: np.ndarray | None = None
+            ) -> np.ndarray:
+    """Database vectors [start, start+n) of the stream, float32 [n, d]."""
+    return _draw(w, centers(w) if ctr is None else ctr, 1, start, n)
+
+
+def queries(w: Workload, start: int, n: int, ctr: np.ndarray | None = None
+            ) -> np.ndarray:
+    """Queries [start, start+n) from the same mixture, float32 [n, d]."""
+    return _draw(w, centers(w) if ctr is None else ctr, 2, start, n)
+
+
+def index_centroids(w: Workload, ctr: np.ndarray | None = None) -> np.ndarray:
+    """Coarse centroids handed to set_centroids: the mixture centers, then
+    (when there are more lists than components) sample points of stream 3."""
+    ctr = centers(w) if ctr is None else ctr
+    if w.nlist <= w.n_comp:
+        return np.ascontiguousarray(ctr[: w.nlist])
+    extra = _draw(w, ctr, 3, 0, w.nlist - w.n_comp)
+    return np.concatenate([ctr, extra], axis=0)
+
+
+def stream_ids(start: int, n: int, n_max: int) -> np.ndarray:
+    """Dense ids of stream positions [start, start+n): position mod n_max."""
+    return (np.arange(start, start + n, dtype=np.int64) % int(n_max))
+
+
+def small(name: str = "tiny_window", **over) -> Workload:
+    """A named workload with some fields overridden (for tests)."""
+    base = CONFIGS[name]
+    fields = dict(base.__dict__)
+    fields.update(over)
+    return Workload(**fields)

@@ -1,0 +1,428 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against exact rational arithmetic, brute force
+written with numpy, a plain set model of the add/remove semantics, torch's
+own bfloat16 / float8 casts, or closed forms.  A plausible mistake in the
+oracle (a dropped coordinate, a wrong sign, ties to the wrong index, a top-k
+off by one, a slab never returned to the pool, ...) fails at least one of
+them; ``test_oracle_mutants.py`` plants such mistakes to show it.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleIVF, OracleError
+
+
+# ---------------------------------------------------------------- helpers
+def exact_sq(a, b):
+    """Exact squared L2 distance of two float32 vectors (rational)."""
+    return sum((Fraction(float(x)) - Fraction(float(y))) ** 2
+               for x, y in zip(a, b))
+
+
+def exact_nearest(x, cent):
+    ds = [exact_sq(x, c) for c in cent]
+    m = min(ds)
+    return ds.index(m)          # first index at the minimum
+
+
+def exact_probes(q, cent, P):
+    ds = [(exact_sq(q, c), i) for i, c in enumerate(cent)]
+    ds.sort()
+    return [i for _, i in ds[:P]]
+
+
+def brute_knn(q, x, ids, k):
+    """k nearest by (float64 distance, id) -- numpy brute force."""
+    q64, x64 = q.astype(np.float64), x.astype(np.float64)
+    out_d = np.full((len(q), k), np.inf)
+    out_i = np.full((len(q), k), -1, np.int64)
+    for r in range(len(q)):
+        dd = ((x64 - q64[r]) ** 2).sum(axis=1)
+        order = np.lexsort((ids, dd))[:k]
+        out_d[r, :len(order)] = dd[order]
+        out_i[r, :len(order)] = ids[order]
+    return out_d, out_i
+
+
+def grid_points(rng, n, d, lo=-4, hi=4, denom=1):
+    return (rng.integers(lo, hi + 1, size=(n, d)) / denom).astype(np.float32)
+
+
+# ------------------------------------------------------- coarse quantizer
+@pytest.mark.parametrize("d,denom", [(1, 1), (2, 1), (3, 2), (4, 8)])
+def test_assign_matches_exact_rational_argmin(d, denom):
+    """Small integer / dyadic grids: many exact ties, all resolved to the
+    lowest centroid index, as the rational argmin does."""
+    rng = np.random.default_rng(100 + d)
+    cent = grid_points(rng, 9, d, denom=denom)
+    x = grid_points(rng, 300, d, denom=denom)
+    o = OracleIVF(d, len(cent), n_max=1000)
+    o.set_centroids(cent)
+    got = o.assign(x)
+    want = [exact_nearest(v, cent) for v in x]
+    assert list(got) == want
+    # ties really occur in this sample
+    n_ties = sum(1 for v in x
+                 if sorted(exact_sq(v, c) for c in cent)[:2][0]
+                 == sorted(exact_sq(v, c) for c in cent)[:2][1])
+    assert n_ties > 0
+
+
+def test_assign_general_floats_exact_rational():
+    rng = np.random.default_rng(7)
+    cent = rng.standard_normal((16, 4)).astype(np.float32)
+    x = rng.standard_normal((200, 4)).astype(np.float32)
+    o = OracleIVF(4, 16, n_max=1000)
+    o.set_centroids(cent)
+    assert list(o.assign(x)) == [exact_nearest(v, cent) for v in x]
+
+
+def test_assign_duplicate_centroids_lowest_index():
+    cent = np.array([[1, 1], [0, 0], [1, 1], [0, 0]], np.float32)
+    o = OracleIVF(2, 4, n_max=10)
+    o.set_centroids(cent)
+    assert list(o.assign([[1, 1], [0.1, 0], [0.9, 1.0]])) == [0, 1, 0]
+
+
+@pytest.mark.parametrize("P", [1, 3, 9])
+def test_probe_matches_exact_rational_order(P):
+    rng = np.random.default_rng(11 + P)
+    cent = grid_points(rng, 9, 2)
+    q = grid_points(rng, 100, 2)
+    o = OracleIVF(2, 9, n_max=10)
+    o.set_centroids(cent)
+    got = o.probe(q, P)
+    for r in range(len(q)):
+        assert list(got[r]) == exact_probes(q[r], cent, P)
+
+
+# ------------------------------------------------------------------ search
+def _filled(d=8, nlist=12, n=600, seed=3, integer=False, C=8):
+    rng = np.random.default_rng(seed)
+    if integer:
+        cent = grid_points(rng, nlist, d, -3, 3)
+        x = grid_points(rng, n, d, -3, 3)
+    else:
+        cent = rng.standard_normal((nlist, d)).astype(np.float32)
+        x = rng.standard_normal((n, d)).astype(np.float32)
+    ids = rng.permutation(10 * n)[:n].astype(np.int64)
+    o = OracleIVF(d, nlist, C, n_max=10 * n, n_slabs=10 * n)
+    o.set_centroids(cent)
+    o.add(ids, x)
+    return o, cent, x, ids, rng
+
+
+@pytest.mark.parametrize("integer", [False, True])
+def test_full_probe_equals_brute_force(integer):
+    """nprobe = nlist scans every list: IVF search is exact kNN."""
+    o, cent, x, ids, rng = _filled(integer=integer)
+    q = (grid_points(rng, 50, 8, -3, 3) if integer
+         else rng.standard_normal((50, 8)).astype(np.float32))
+    for k in (1, 7, 30):
+        d_o, i_o = o.search(q, k, o.nlist)
+        d_b, i_b = brute_knn(q, x, ids, k)
+        np.testing.assert_array_equal(i_o, i_b)
+        np.testing.assert_allclose(d_o, d_b, rtol=1e-12)
+        d_e, i_e = o.exact_knn(q, k)
+        np.testing.assert_array_equal(i_e, i_b)
+
+
+def test_partial_probe_equals_brute_force_over_probed_lists():
+    o, cent, x, ids, rng = _filled(seed=5)
+    q = rng.standard_normal((40, 8)).astype(np.float32)
+    P, k = 3, 10
+    d_o, i_o = o.search(q, k, P)
+    for r in range(len(q)):
+        probed = exact_probes(q[r], cent, P)
+        members = np.concatenate([o.list_members(l)[0] for l in probed])
+        pos = {int(v): j for j, v in enumerate(ids)}
+        xs = x[[pos[int(m)] for m in members]]
+        d_b, i_b = brute_knn(q[r:r + 1], xs, members, k)
+        np.testing.assert_array_equal(i_o[r], i_b[0])
+        np.testing.assert_allclose(d_o[r], d_b[0], rtol=1e-12)
+
+
+def test_pad_when_fewer_than_k():
+    o = OracleIVF(2, 2, 4, n_max=10, n_slabs=10)
+    o.set_centroids([[0, 0], [10, 10]])
+    o.add([3, 4], [[1, 0], [0, 2]])
+    d, i = o.search([[0, 0]], 5, 1)
+    assert list(i[0]) == [3, 4, -1, -1, -1]
+    assert d[0, 0] == 1 and d[0, 1] == 4 and np.isinf(d[0, 2:]).all()
+
+
+def test_ties_in_topk_go_to_lower_id():
+    o = OracleIVF(1, 1, 4, n_max=100, n_slabs=10)
+    o.set_centroids([[0]])
+    o.add([50, 7, 9, 3], [[2], [-2], [1], [-1]])
+    d, i = o.search([[0]], 3, 1)
+    assert list(i[0]) == [3, 9, 7] and list(d[0]) == [1, 1, 4]
+
+
+def test_search_with_probes_matches_search():
+    o, cent, x, ids, rng = _filled(seed=9)
+    q = rng.standard_normal((30, 8)).astype(np.float32)
+    pr = o.probe(q, 4)
+    a = o.search(q, 6, 4)
+    b = o.search_with_probes(q, 6, pr)
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[0], b[0])
+
+
+def test_golden_tiny_1d():
+    """Hand-worked example of tests/golden/tiny_1d.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tiny_1d.txt")
+    sec, data = None, {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        if line.startswith("["):
+            sec = line.strip("[]")
+            data[sec] = []
+            continue
+        data[sec].append([float(t) for t in line.split()])
+    cent = np.array(data["centroids"], np.float32)
+    pts = data["points"]
+    o = OracleIVF(1, len(cent), 2, n_max=100, n_slabs=100)
+    o.set_centroids(cent)
+    ids = np.array([int(p[0]) for p in pts])
+    x = np.array([[p[1]] for p in pts], np.float32)
+    o.add(ids, x)
+    for p in pts:
+        assert o.list_of(int(p[0])) == int(p[2])
+    for row in data["search"]:
+        qv, k, P = row[0], int(row[1]), int(row[2])
+        want_ids = [int(v) for v in row[3:3 + k]]
+        want_d = row[3 + k:3 + 2 * k]
+        d, i = o.search([[qv]], k, P)
+        assert list(i[0]) == want_ids
+        assert list(d[0]) == want_d
+
+
+# ---------------------------------------------- add / remove semantics
+class SetModel:
+    """Plain dictionary model of the add / remove semantics."""
+
+    def __init__(self):
+        self.vec = {}
+
+    def add(self, ids, x):
+        for i, v in zip(ids, x):     # later occurrences overwrite earlier
+            self.vec[int(i)] = v
+
+    def remove(self, ids):
+        n = 0
+        for i in ids:
+            if int(i) in self.vec:
+                del self.vec[int(i)]
+                n += 1
+        return n
+
+
+def test_random_ops_match_set_model_and_invariants():
+    rng = np.random.default_rng(21)
+    d, L, C, nmax = 4, 7, 4, 120
+    cent = grid_points(rng, L, d, -2, 2)
+    o = OracleIVF(d, L, C, n_max=nmax, n_slabs=1000)
+    o.set_centroids(cent)
+    m = SetModel()
+    for step in range(60):
+        if rng.random() < 0.6:
+            n = int(rng.integers(0, 25))
+            ids = rng.integers(0, nmax, size=n)     # duplicates + overwrites
+            x = grid_points(rng, n, d, -2, 2)
+            got = o.add(ids, x)
+            assert got == len(set(ids.tolist()))
+            m.add(ids, x)
+        else:
+            n = int(rng.integers(0, 25))
+            ids = rng.integers(0, nmax, size=n)
+            assert o.remove(ids) == m.remove(ids)
+        assert o.ntotal == len(m.vec)
+        seen = []
+        used = 0
+        for l in range(L):
+            mids, seq, slot = o.list_members(l)
+            seen += mids.tolist()
+            fill, live = o.list_slabs(l)
+            used += len(fill)
+            # every slab but the head is full; live counts match members
+            assert (fill[:-1] == C).all() if len(fill) else True
+            assert (live >= 1).all() and live.sum() == len(mids)
+            assert np.bincount(seq, minlength=len(fill)).tolist() == live.tolist()
+            pairs = set(zip(seq.tolist(), slot.tolist()))
+            assert len(pairs) == len(mids)                 # no slot twice
+            assert all(s < fill[q] for q, s in zip(seq, slot))
+            xs = o.list_vectors(l)
+            for i, v in zip(mids, xs):
+                np.testing.assert_array_equal(v, m.vec[int(i)])
+                assert exact_nearest(v, cent) == l
+        assert sorted(seen) == sorted(m.vec)              # each id once
+        assert used + o.free_slabs == 1000
+
+
+def test_duplicate_in_batch_last_wins():
+    o = OracleIVF(1, 2, 4, n_max=10, n_slabs=10)
+    o.set_centroids([[0], [10]])
+    assert o.add([5, 5, 6], [[0.5], [9.5], [1]]) == 2
+    assert o.list_of(5) == 1 and o.list_of(6) == 0
+    assert list(o.list_members(0)[0]) == [6]
+
+
+def test_overwrite_is_delete_then_insert():
+    o = OracleIVF(1, 2, 4, n_max=10, n_slabs=10)
+    o.set_centroids([[0], [10]])
+    o.add([1, 2, 3], [[0], [1], [2]])
+    o.add([2], [[11]])
+    assert list(o.list_members(0)[0]) == [1, 3]
+    assert list(o.list_members(1)[0]) == [2]
+    d, i = o.search([[1]], 3, 2)
+    assert list(i[0]) == [1, 3, 2] and list(d[0]) == [1, 1, 100]
+
+
+def test_remove_idempotent_and_absent_ids():
+    o, cent, x, ids, rng = _filled(seed=13)
+    n0 = o.ntotal
+    drop = ids[:100]
+    assert o.remove(np.concatenate([drop, drop])) == 100
+    assert o.remove(drop) == 0
+    assert o.ntotal == n0 - 100
+    q = rng.standard_normal((20, 8)).astype(np.float32)
+    _, i = o.search(q, 50, o.nlist)
+    assert not set(i.ravel().tolist()) & set(drop.tolist())
+
+
+def test_out_of_range_ids_rejected_without_change():
+    o = OracleIVF(1, 1, 4, n_max=10, n_slabs=10)
+    o.set_centroids([[0]])
+    o.add([1], [[0]])
+    with pytest.raises(OracleError) as e:
+        o.add([2, 10], [[0], [0]])
+    assert e.value.status == oracle.E_ARG and o.ntotal == 1
+    with pytest.raises(OracleError):
+        o.remove([1, -1])
+    assert o.ntotal == 1
+
+
+def test_untrained_is_state_error():
+    o = OracleIVF(1, 1, 4, n_max=10, n_slabs=10)
+    with pytest.raises(OracleError) as e:
+        o.add([1], [[0]])
+    assert e.value.status == oracle.E_STATE
+
+
+# ------------------------------------------------------ slab bookkeeping
+@pytest.mark.parametrize("n,C", [(1, 4), (4, 4), (5, 4), (100, 32), (64, 32)])
+def test_slab_count_closed_form(n, C):
+    o = OracleIVF(1, 1, C, n_max=1000, n_slabs=1000)
+    o.set_centroids([[0]])
+    o.add(np.arange(n), np.zeros((n, 1)))
+    fill, live = o.list_slabs(0)
+    nsl = -(-n // C)
+    assert len(fill) == nsl and o.free_slabs == 1000 - nsl
+    want = [C] * (nsl - 1) + [n - C * (nsl - 1)]
+    assert fill.tolist() == want and live.tolist() == want
+
+
+def test_delete_all_returns_every_slab():
+    o, *_ = _filled(seed=17)
+    ids = np.arange(o.n_max)
+    o.remove(ids)
+    assert o.ntotal == 0 and o.free_slabs == o.n_slabs
+    for l in range(o.nlist):
+        assert len(o.list_slabs(l)[0]) == 0
+
+
+def test_sliding_window_frees_oldest_slab():
+    C = 8
+    o = OracleIVF(1, 1, C, n_max=1000, n_slabs=100)
+    o.set_centroids([[0]])
+    o.add(np.arange(40), np.zeros((40, 1)))          # 5 full slabs
+    free0 = o.free_slabs
+    o.remove(np.arange(7))                           # oldest slab: 1 live
+    assert o.free_slabs == free0
+    o.remove([7])                                    # now empty -> pool
+    assert o.free_slabs == free0 + 1
+    for step in range(10):                           # steady window
+        base = 40 + C * step
+        o.add(np.arange(base, base + C), np.zeros((C, 1)))
+        o.remove(np.arange(base - 32, base - 32 + C))
+        assert o.free_slabs == free0 + 1
+
+
+def test_admission_is_all_or_nothing():
+    C = 4
+    o = OracleIVF(1, 2, C, n_max=100, n_slabs=3)
+    o.set_centroids([[0], [10]])
+    o.add([0, 1, 2], [[0], [0], [0]])                # list 0: fill 3/4
+    # list 0 needs ceil((6-1)/4) = 2 more slabs, list 1 needs 1: 3 > 2 free
+    with pytest.raises(OracleError) as e:
+        o.add(range(10, 17), [[0]] * 6 + [[10]])
+    assert e.value.status == oracle.E_NOMEM
+    assert o.ntotal == 3 and o.free_slabs == 2
+    o.add(range(10, 15), [[0]] * 5)                  # needs exactly 1
+    assert o.free_slabs == 1 and o.ntotal == 8
+
+
+def test_directory_capacity_limits_a_list():
+    o = OracleIVF(1, 2, 2, n_max=100, n_slabs=50, dir_cap=3)
+    o.set_centroids([[0], [10]])
+    o.add(range(6), [[0]] * 6)                       # 3 slabs in list 0
+    with pytest.raises(OracleError) as e:
+        o.add([20], [[0]])
+    assert e.value.status == oracle.E_NOMEM
+    o.add([21], [[10]])                              # list 1 still fine
+
+
+# ------------------------------------------------------------ encodings
+def test_bf16_matches_torch_rne():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([
+        rng.standard_normal(20000).astype(np.float32) * 1e3,
+        np.array([0.0, -0.0, 1.0, -1.5, 3.0e38, -3.4e38, 1e-40, np.inf,
+                  -np.inf], np.float32),
+        # exact halfway cases, both parities
+        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 2.0 + 2 ** -7],
+                 np.float32)])
+    got = oracle.to_bf16(x)
+    want = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy()
+    np.testing.assert_array_equal(got, want.view(np.uint16))
+    back = oracle.from_bf16(got)
+    np.testing.assert_array_equal(
+        back, torch.from_numpy(x).to(torch.bfloat16).float().numpy())
+
+
+def test_e4m3_matches_torch_in_range_and_saturates():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([
+        rng.uniform(-440, 440, 20000), rng.standard_normal(20000),
+        rng.standard_normal(2000) * 1e-2,
+        # halfway points between neighbouring codes
+        [1.0625, 1.1875, 17.0, 0.001953125 * 1.5, 2 ** -10]]).astype(np.float32)
+    got = oracle.to_e4m3(x, 1.0)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    np.testing.assert_array_equal(got, want)
+    big = np.array([448.0, 500.0, 1e6, -1e9], np.float32)
+    assert oracle.to_e4m3(big, 1.0).tolist() == [0x7e, 0x7e, 0x7e, 0xfe]
+    # scaling: v = fl32(x * inv_scale)
+    y = rng.standard_normal(1000).astype(np.float32) * 300
+    inv = np.float32(1.0 / 0.75)
+    np.testing.assert_array_equal(oracle.to_e4m3(y, inv),
+                                  oracle.to_e4m3((y * inv).astype(np.float32), 1.0))
+
+
+def test_e4m3_decode_all_codes_matches_torch():
+    torch = pytest.importorskip("torch")
+    codes = np.array([c for c in range(256) if c not in (0x7f, 0xff)], np.uint8)
+    got = oracle.from_e4m3(codes)
+    want = torch.from_numpy(codes).view(torch.float8_e4m3fn).double().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert got.max() == 448.0 and got[got > 0].min() == 2.0 ** -9
