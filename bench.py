@@ -1,0 +1,435 @@
+"""Benchmark of the streaming IVF-Flat hot path on GB300.
+
+One step = one pass of the whole hot path over one batch of the SIFT-shaped
+sliding window (1,000,000 live vectors, d=128, nlist=1024, slab 64):
+insert 10,000 new vectors (coarse assignment + slot claim + append), delete
+the 10,000 oldest (address-table lookup, bit clear, slab reclaim), and search
+10,000 fresh queries (coarse probe selection, list scan, top-10) at the
+smallest nprobe of {8, 16, 32, 64, 128} whose recall@10 reaches 0.95.
+
+Prints one JSON line.  `value` is queries per second of whole steps (each
+step also absorbs its insert and delete batch); the components give search
+QPS alone, insert and delete vectors/s and the p99 update latency.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sivf|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the index on its
+own GPU (the path has no cross-GPU exchange); rank 0 reports the sum of
+queries over the max time.  `--impl reference` times the FP64 CPU oracle on
+the host cores on a bounded sample of the same steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_11808_gb300 import workloads as W  # noqa: E402
+
+METRIC = "QPS@recall@10=0.95; insert/delete vec/s; p99 update ms (1×GB300)"
+NPROBES = (8, 16, 32, 64, 128)
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="sivf", choices=["sivf", "reference"])
+    p.add_argument("--workload", default="sift_window")
+    p.add_argument("--nprobe", type=int, default=0, help="0 = calibrate for recall 0.95")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi clock / throttle samples taken during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9])
+                          if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]),
+                "samples": len(rows), "reasons": reasons}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------- data
+def make_data(w: W.Workload, n_steps: int, n_calib: int, rank: int):
+    ctr = W.centers(w)
+    cent = W.index_centroids(w, ctr)
+    # each replica draws its own stream and queries (weak scaling)
+    wr = W.small(w.name, seed=w.seed + rank) if rank else w
+    ctr_r = ctr
+    total = w.window + n_steps * w.step
+    X = W.vectors(wr, 0, total, ctr_r)
+    Q = W.queries(wr, 0, n_steps * w.n_queries + n_calib, ctr_r)
+    return cent, X, Q
+
+
+def oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps):
+    """FP64 oracle on the host cores: full window built with all cores
+    (untimed), then `steps` bounded samples of a step (n_ins inserts, n_del
+    deletes of the oldest, n_q queries), each scaled to the full step."""
+    import oracle
+    cores = oracle.num_threads(os.cpu_count() or 1)
+    S = int(1.25 * (w.window // w.slab_size + 2 * w.nlist))
+    o = oracle.OracleIVF(w.d, w.nlist, w.slab_size, n_max, S)
+    o.set_centroids(cent)
+    t0 = time.time()
+    for b in range(0, w.window, 100_000):
+        o.add(W.stream_ids(b, 100_000, n_max), X[b:b + 100_000])
+    build_s = time.time() - t0
+    per_step = []
+    for s in range(steps):
+        new = w.window + s * n_ins
+        t0 = time.time()
+        o.add(W.stream_ids(new, n_ins, n_max), X[new:new + n_ins])
+        t_ins = time.time() - t0
+        t0 = time.time()
+        o.remove(W.stream_ids(s * n_del, n_del, n_max))
+        t_del = time.time() - t0
+        t0 = time.time()
+        o.search(Q[s * n_q:(s + 1) * n_q], w.k, nprobe)
+        t_q = time.time() - t0
+        per_step.append((t_ins * w.step / n_ins, t_del * w.step / n_del,
+                         t_q * w.n_queries / n_q))
+    a = np.array(per_step)
+    step_s = a.sum(axis=1)
+    return {
+        "qps": float(w.n_queries / np.mean(step_s)),
+        "search_qps": float(w.n_queries / np.mean(a[:, 2])),
+        "insert_vec_s": float(w.step / np.mean(a[:, 0])),
+        "delete_vec_s": float(w.step / np.mean(a[:, 1])),
+        "p99_update_ms": float(np.percentile((a[:, 0] + a[:, 1]) * 1e3, 99)),
+        "cores": cores, "build_s": build_s, "step_s": step_s.tolist(),
+    }
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = W.CONFIGS[args.workload]
+    nprobe = args.nprobe or 8
+    n_ins, n_del, n_q = 1000, 1000, 200
+    steps = args.steps + args.warmup
+    cent, X, Q = make_data(w, 2, 0, 0)
+    n_max = w.window + 4 * w.step
+    t0 = time.time()
+    r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps)
+    wall = time.time() - t0
+    sample = (f"oracle index holding the full {w.window:,}-vector window (built with "
+              f"{r['cores']} threads, untimed); per step {n_ins} inserts, {n_del} deletes "
+              f"of the oldest and {n_q} queries (k={w.k}, nprobe={nprobe}), each scaled to "
+              f"the full step ({w.step} / {w.step} / {w.n_queries})")
+    st = r["step_s"][args.warmup:]
+    val = float(w.n_queries / np.mean(st))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "queries/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(float(np.mean(st)) * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, nprobe),
+        "components": {k: r[k] for k in ("search_qps", "insert_vec_s", "delete_vec_s",
+                                           "p99_update_ms")},
+        "cpu_baseline": {"value": round(val, 3), "unit": "queries/s", "cores": r["cores"],
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 1),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, nprobe):
+    return {"workload": w.name, "window": w.window, "d": w.d, "nlist": w.nlist,
+            "slab": w.slab_size, "insert_per_step": w.step, "delete_per_step": w.step,
+            "queries_per_step": w.n_queries, "k": w.k, "nprobe": nprobe,
+            "scan_dtype": "fp32",
+            "l2": "inputs larger than L2: 512 MB index, fresh insert/query batches "
+                  "every step",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2601_11808_gb300 import build as B
+    B.build()
+    from paper_2601_11808_gb300 import sivf
+
+    w = W.CONFIGS[args.workload]
+    K, Wm = args.steps, args.warmup
+    n_steps = Wm + 2 * K + 1
+    n_calib = 1000
+    cent, X, Q = make_data(w, n_steps, n_calib, rank)
+    n_max = w.window + (n_steps + 2) * w.step
+    S = int(1.25 * (w.window // w.slab_size + 2 * w.nlist))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S)
+    g.set_centroids(torch.from_numpy(cent).to(dev))
+    for b in range(0, w.window, 100_000):
+        g.add(torch.from_numpy(W.stream_ids(b, 100_000, n_max)).to(dev),
+              torch.from_numpy(X[b:b + 100_000]).to(dev))
+    g.sync()
+
+    # nprobe for recall@10 >= 0.95 against exact search (nprobe = nlist)
+    Qc = torch.from_numpy(Q[-n_calib:]).to(dev)
+    _, gt = g.search(Qc, w.k, w.nlist)
+    gt = gt.cpu().numpy()
+    recalls = {}
+    nprobe = args.nprobe
+    for P in ([args.nprobe] if args.nprobe else NPROBES):
+        _, got = g.search(Qc, w.k, P)
+        got = got.cpu().numpy()
+        recalls[P] = float(np.mean([len(set(a) & set(b)) / w.k
+                                    for a, b in zip(got.tolist(), gt.tolist())]))
+        if not nprobe and recalls[P] >= 0.95:
+            nprobe = P
+    nprobe = nprobe or NPROBES[-1]
+
+    # step inputs resident in HBM before the timed region
+    def step_inputs(s):
+        new = w.window + s * w.step
+        return (torch.from_numpy(W.stream_ids(new, w.step, n_max)).to(dev),
+                torch.from_numpy(X[new:new + w.step]).to(dev),
+                torch.from_numpy(W.stream_ids(s * w.step, w.step, n_max)).to(dev),
+                torch.from_numpy(Q[s * w.n_queries:(s + 1) * w.n_queries]).to(dev))
+
+    dist_out = torch.empty((w.n_queries, w.k), dtype=torch.float32, device=dev)
+    lab_out = torch.empty((w.n_queries, w.k), dtype=torch.int64, device=dev)
+    g.reserve(w.step, w.step, w.n_queries, w.k, nprobe)
+    inputs = [step_inputs(s) for s in range(Wm + K)]
+
+    def run_step(ins_ids, ins_x, del_ids, q, ev=None):
+        if ev:
+            ev[0].record(stream)
+        g.add(ins_ids, ins_x)
+        if ev:
+            ev[1].record(stream)
+        g.remove(del_ids)
+        if ev:
+            ev[2].record(stream)
+        g.search(q, w.k, nprobe, dist=dist_out, labels=lab_out)
+        if ev:
+            ev[3].record(stream)
+
+    for s in range(Wm):
+        run_step(*inputs[s])
+    torch.cuda.synchronize()
+    g.sync()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    st0 = g.stats()
+    launches0 = g.profile_read("all")[0]
+    g.profile(True)
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(K):
+        run_step(*inputs[Wm + s], ev=evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    st1 = g.stats()
+    launches = g.profile_read("all")[0] - launches0
+    scan_n, scan_ms = g.profile_read("scan")
+    prof = {k: g.profile_read(k) for k in ("coarse", "insert", "remove", "group", "scan",
+                                           "merge")}
+    g.profile(False)
+    assert g.sync() >= 0
+
+    ins_ms = np.array([a[0].elapsed_time(a[1]) for a in evs])
+    del_ms = np.array([a[1].elapsed_time(a[2]) for a in evs])
+    srch_ms = np.array([a[2].elapsed_time(a[3]) for a in evs])
+    upd = ins_ms + del_ms
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K * w.n_queries / (total_ms / 1e3)
+
+    # roofline of the list scan (dominant kernel): algorithmic flops of the
+    # direct form, 3 d per (query, live vector) pair the scans scored
+    pairs = st1["pairs_scanned"] - st0["pairs_scanned"]
+    sbytes = st1["slab_bytes_scanned"] - st0["slab_bytes_scanned"]
+    flops = 3.0 * w.d * pairs
+    achieved = flops / (scan_ms / 1e3) / 1e12 if scan_ms > 0 else 0.0
+    pk = peaks()
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": None, "kernel": "k_scan (list scan, FP32 direct form)",
+                "launches": scan_n, "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
+                "flops_per_launch": flops / max(scan_n, 1),
+                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz; the direct "
+                             "form issues 2 instructions per 3 flops, so its ceiling is 0.75",
+                "hbm_view": {"algorithmic_bytes_per_launch": sbytes / max(scan_n, 1),
+                             "gbs": round(sbytes / (scan_ms / 1e3) / 1e9, 1) if scan_ms else 0,
+                             "peak_gbs": pk.get("hbm_gbs")}}
+    kernel_ms = {k: round(v[1] / K, 4) for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": round(total_ms / K, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded 1,024-component Gaussian mixture shaped like SIFT "
+                "(d=128, integers 0..255); stands in for SIFT1M",
+        "config": config_of(w, nprobe),
+        "components": {
+            "search_qps": round(world * K * w.n_queries / (srch_ms.sum() / 1e3), 1),
+            "insert_vec_s": round(world * K * w.step / (ins_ms.sum() / 1e3), 1),
+            "delete_vec_s": round(world * K * w.step / (del_ms.sum() / 1e3), 1),
+            "p50_update_ms": round(float(np.percentile(upd, 50)), 4),
+            "p99_update_ms": round(float(np.percentile(upd, 99)), 4),
+            "insert_ms": round(float(ins_ms.mean()), 4),
+            "delete_ms": round(float(del_ms.mean()), 4),
+            "search_ms": round(float(srch_ms.mean()), 4),
+            "recall_at_10": recalls.get(nprobe), "recall_by_nprobe": recalls,
+            "kernel_ms_per_step": kernel_ms,
+        },
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs from pinned memory and D2H of its results inside the timed region
+    if not args.no_e2e:
+        host = []
+        for s in range(Wm + K, Wm + 2 * K):
+            t = [x.cpu().pin_memory() for x in step_inputs(s)]
+            host.append(t)
+        dev_in = [torch.empty_like(x, device=dev) for x in host[0]]
+        hd = torch.empty((w.n_queries, w.k), dtype=torch.float32).pin_memory()
+        hl = torch.empty((w.n_queries, w.k), dtype=torch.int64).pin_memory()
+        h2d = sum(x.numel() * x.element_size() for x in host[0])
+        d2h = hd.numel() * 4 + hl.numel() * 8
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(K):
+            for dst, src in zip(dev_in, host[s]):
+                dst.copy_(src, non_blocking=True)
+            run_step(*dev_in)
+            hd.copy_(dist_out, non_blocking=True)
+            hl.copy_(lab_out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": round(world * K * w.n_queries / (e2e_ms / 1e3), 3),
+                       "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g.close()
+        del inputs
+        torch.cuda.empty_cache()
+        n_ins, n_del, n_q = 1000, 1000, 200
+        r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2)
+        line["cpu_baseline"] = {
+            "value": round(r["qps"], 3), "unit": "queries/s", "cores": r["cores"],
+            "kind": "oracle",
+            "sample": (f"FP64 oracle holding the full {w.window:,}-vector window (built with "
+                       f"{r['cores']} threads in {r['build_s']:.1f} s, untimed); 2 steps of "
+                       f"{n_ins} inserts, {n_del} deletes of the oldest and {n_q} queries "
+                       f"(k={w.k}, nprobe={nprobe}), each scaled to the full step"),
+            "components": {k: round(r[k], 3) for k in ("search_qps", "insert_vec_s",
+                                                       "delete_vec_s", "p99_update_ms")},
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,280 @@
+/*
+ * sivf.h -- C ABI of libsivf, a GB300 (sm_103a) streaming IVF-Flat index
+ * whose inverted lists are chains of fixed-size slabs, after
+ * "SIVF: GPU-Resident IVF Index for Streaming Vector Search"
+ * (arxiv 2601.11808).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments marked [device] are device pointers in the index's
+ *    CUDA device; arrays marked [host] are host memory.  The caller owns
+ *    every array it passes; the library never frees or keeps them past the
+ *    call's stream work.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it and the call returns without waiting,
+ *    except where an argument marked "forces a sync" is non-NULL.
+ *  - Layouts are row-major and dense: a [n, d] float array holds vector i
+ *    at elements i*d .. i*d+d-1.  Vectors are float32; ids are int64 in
+ *    the dense id space [0, n_max) (the paper's data model, Sec. 3).
+ *  - Distances are squared L2 (the paper writes d(q, x); squared L2 is the
+ *    IVF-Flat convention it builds on), returned in float32.
+ *  - Every call checks its host-visible arguments first and returns
+ *    SIVF_E_ARG without enqueuing anything when one is wrong.  Conditions
+ *    only the device can see (an id out of range inside a device array, a
+ *    full slab pool) reject the whole batch on the device: no state
+ *    changes, and the status is reported by the call itself when it syncs,
+ *    otherwise by the next sivf_sync().
+ *  - A device loop that hits its bound (a corrupt directory) records a
+ *    sticky error and returns; nothing traps.  Every later call returns
+ *    SIVF_E_CORRUPT.
+ *  - One index is driven by one host thread at a time.  Calls on the same
+ *    stream are ordered; the library does not order calls across streams.
+ *  - Scratch memory grows on demand with cudaMalloc; call sivf_reserve()
+ *    first when the calls will be captured into a CUDA graph.
+ */
+#ifndef SIVF_H
+#define SIVF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sivf_index sivf_index;
+
+typedef enum {
+    SIVF_OK = 0,
+    SIVF_E_ARG = 1,      /* bad argument (host check, or an id out of range) */
+    SIVF_E_NOMEM = 2,    /* slab pool, list directory or device memory full  */
+    SIVF_E_STATE = 3,    /* set_centroids has not been called                */
+    SIVF_E_CUDA = 4,     /* a CUDA call failed                               */
+    SIVF_E_CORRUPT = 5,  /* a bounded device walk hit its bound (sticky)     */
+    SIVF_E_TIMEOUT = 6   /* a bounded device wait ran out (sticky)           */
+} sivf_status;
+
+typedef enum {
+    SIVF_FP32 = 0,       /* exact FP32 scan of the FP32 payload              */
+    SIVF_BF16 = 1,       /* BF16 scan on tensor cores + FP32 re-rank         */
+    SIVF_FP8E4M3 = 2     /* FP8 E4M3 scan (per-list scale) + FP32 re-rank    */
+} sivf_scan_dtype;
+
+typedef struct {
+    int d;               /* dimension, 4 <= d <= 256, d % 4 == 0            */
+    int nlist;           /* inverted lists, 1 <= nlist <= 65536             */
+    int slab_size;       /* slab capacity C: 32, 64 or 128, C * d <= 20480   */
+    int64_t n_max;       /* size of the dense id space [0, n_max)            */
+    int64_t n_slabs;     /* slabs in the pre-allocated pool (the paper's S)  */
+    int64_t dir_cap;     /* most slabs one list may hold (0 = n_slabs)       */
+    uint32_t scan_dtypes;/* extra payload copies: bit (1<<SIVF_BF16) and/or
+                            bit (1<<SIVF_FP8E4M3); the FP32 copy always exists */
+} sivf_config;
+
+typedef struct {
+    int64_t ntotal;      /* live vectors                                     */
+    int64_t free_slabs;  /* slabs on the free stack                          */
+    int64_t used_slabs;  /* slabs held by lists                              */
+    uint32_t error_bits; /* sticky device error word (0 = healthy)           */
+    int32_t last_status; /* status of the last add/remove batch (sivf_status)*/
+    int64_t last_count;  /* vectors added / removed by that batch            */
+    int64_t bytes_device;/* device memory held by the index                  */
+    int64_t pairs_scanned;      /* (query, live vector) pairs the list scans
+                                   have scored since creation (FP32 path)    */
+    int64_t slab_bytes_scanned; /* slab payload + id bytes the list scans
+                                   streamed since creation, one read per
+                                   (list, query tile)                        */
+} sivf_stats_t;
+
+/*
+ * sivf_create -- allocate an empty index and its slab pool on the current
+ * CUDA device (Sec. 3.1: a monolithic pre-allocated pool of S slabs of C
+ * vectors, per-list heads, a free stack and the address translation table).
+ * `cfg` [host] is read once.  On success *out receives the handle.
+ * Errors: SIVF_E_ARG (bad config), SIVF_E_NOMEM (cudaMalloc failed).
+ */
+sivf_status sivf_create(const sivf_config *cfg, sivf_index **out);
+
+/* sivf_destroy -- synchronize the device and free everything the index
+ * holds.  NULL is accepted. */
+sivf_status sivf_destroy(sivf_index *index);
+
+/*
+ * sivf_set_centroids -- load the coarse quantizer (Sec. 3.3: the lists are
+ * the cells of nearest-centroid assignment).  `c` [device] is [nlist, d]
+ * float32.  The index must be empty (SIVF_E_STATE otherwise).  Also sets
+ * every list's FP8 inverse scale to 448 / (2 * max_j |c_lj|) (1.0 when the
+ * centroid is zero); sivf_set_list_scales overrides it.
+ */
+sivf_status sivf_set_centroids(sivf_index *index, const float *c, void *stream);
+
+/*
+ * sivf_set_list_scales -- per-list FP8 E4M3 inverse scales: list l stores
+ * code(fl32(x_j * inv_scale[l])) and decodes x_j ~ code / inv_scale[l].
+ * `inv_scale` [device] is [nlist] float32, each finite and > 0.  Must be
+ * called while the index is empty.
+ */
+sivf_status sivf_set_list_scales(sivf_index *index, const float *inv_scale,
+                                 void *stream);
+
+/*
+ * sivf_reserve -- pre-allocate the scratch of `stream` for batches up to the
+ * given sizes so that later calls on that stream allocate nothing (needed
+ * before CUDA-graph capture).  Scratch is per stream: calls on different
+ * streams never share it.
+ */
+sivf_status sivf_reserve(sivf_index *index, int64_t max_add, int64_t max_remove,
+                         int64_t max_queries, int max_k, int max_nprobe,
+                         void *stream);
+
+/*
+ * sivf_add -- batched insert (Algorithm 2, redone as a conflict-free batch).
+ *   ids [device] int64[n], x [device] float32[n, d].
+ * Semantics of one batch:
+ *   1. the last occurrence of each id wins;
+ *   2. each kept vector goes to its nearest centroid's list, ties to the
+ *      lowest list index (the assignment equals an FP64 argmin bit-exactly);
+ *   3. admission, all or nothing: the slab demand of the batch, computed on
+ *      the state before it, must fit the free slabs and every list's
+ *      directory capacity, else SIVF_E_NOMEM (Sec. 3.2 fail-fast) and
+ *      nothing changes; an id outside [0, n_max) gives SIVF_E_ARG, also with
+ *      nothing changed;
+ *   4. kept ids that are live are deleted first (delete-then-insert, Sec. 3);
+ *   5. kept vectors are appended to their lists in batch order: a list fills
+ *      its head slab, then takes fresh slabs from the free stack.  Each
+ *      vector is published by setting its validity bit after its payload,
+ *      id and address-table entry are written (Theorem 1).
+ * n_added [host, optional]: if non-NULL the call forces a sync, stores the
+ * number of kept ids and returns the batch status.
+ */
+sivf_status sivf_add(sivf_index *index, const int64_t *ids, const float *x,
+                     int64_t n, void *stream, int64_t *n_added);
+
+/*
+ * sivf_remove -- batched delete (Algorithm 4: address-table lookup, atomic
+ * clear of the validity bit, live-count decrement; a slab whose live count
+ * reaches zero leaves its list and returns to the free stack).  No
+ * compaction.  Absent and repeated ids are no-ops (Theorem 3).
+ *   ids [device] int64[n]; an id outside [0, n_max) rejects the batch with
+ *   SIVF_E_ARG and nothing changes.
+ * n_removed [host, optional]: if non-NULL the call forces a sync, stores the
+ * number of ids actually removed and returns the batch status.
+ */
+sivf_status sivf_remove(sivf_index *index, const int64_t *ids, int64_t n,
+                        void *stream, int64_t *n_removed);
+
+/*
+ * sivf_search -- batched k-NN (Algorithm 3 redone list-centrically): coarse
+ * selection of the nprobe nearest lists (the exact FP64 top-nprobe set, ties
+ * to the lowest index), a scan of every live slot of those lists, and a
+ * top-k per query in ascending (distance, id) order.
+ *   q [device] float32[nq, d]; dist [device] float32[nq, k];
+ *   labels [device] int64[nq, k].  Missing results are (+inf, -1).
+ *   1 <= k <= 1024 (and small enough that a slab pair plus 8 queries' best
+ *   k fit in shared memory: SIVF_E_ARG otherwise); 1 <= nprobe <=
+ *   min(nlist, 1024).
+ * dtype SIVF_FP32 scans the FP32 payload with direct-form distances.
+ * SIVF_BF16 / SIVF_FP8E4M3 scan the reduced copy (which must have been
+ * enabled at create) on tensor cores, keep the best 4k candidates per query
+ * and re-rank them with exact FP32 distances.
+ */
+sivf_status sivf_search(sivf_index *index, const float *q, int64_t nq, int k,
+                        int nprobe, sivf_scan_dtype dtype, float *dist,
+                        int64_t *labels, void *stream);
+
+/*
+ * sivf_search_with_probes -- the fine scan and top-k of sivf_search with
+ * caller-given lists: probes [device] int32[nq, nprobe] (entries outside
+ * [0, nlist) are skipped; a list given twice is scanned once).
+ */
+sivf_status sivf_search_with_probes(sivf_index *index, const float *q,
+                                    int64_t nq, int k, int nprobe,
+                                    const int32_t *probes, sivf_scan_dtype dtype,
+                                    float *dist, int64_t *labels, void *stream);
+
+/*
+ * sivf_assign -- the coarse assignment step of sivf_add alone:
+ * labels [device] int32[n] = argmin_l ||x_i - c_l||^2, ties to the lowest l.
+ */
+sivf_status sivf_assign(sivf_index *index, const float *x, int64_t n,
+                        int32_t *labels, void *stream);
+
+/*
+ * sivf_probe -- the coarse selection step of sivf_search alone:
+ * probes [device] int32[nq, nprobe] holds the nprobe nearest lists of each
+ * query in ascending list index (the set equals the FP64 top-nprobe by
+ * (distance, index)).
+ */
+sivf_status sivf_probe(sivf_index *index, const float *q, int64_t nq,
+                       int nprobe, int32_t *probes, void *stream);
+
+/*
+ * sivf_sync -- wait for the stream and return the status of the last
+ * add/remove batch (or a sticky error); *count [host, optional] receives the
+ * vectors that batch added or removed.
+ */
+sivf_status sivf_sync(sivf_index *index, void *stream, int64_t *count);
+
+/* sivf_stats -- forces a sync; fills `out` [host]. */
+sivf_status sivf_stats(sivf_index *index, void *stream, sivf_stats_t *out);
+
+/*
+ * sivf_dump -- copy the bookkeeping state to host arrays for invariant
+ * checks (forces a sync).  Any pointer may be NULL to skip that array.
+ *   list_nslabs [host] int32[nlist]; list_head [host] int32[nlist];
+ *   list_dir [host] int32[nlist * dir_cap] (row l holds list l's slabs in
+ *     chain order, oldest first);
+ *   slab_meta [host] int32[n_slabs * 3]: {list, fill, live} per slab;
+ *   slab_bits [host] uint32[n_slabs * slab_size / 32]: validity bitmaps;
+ *   slab_ids [host] int64[n_slabs * slab_size];
+ *   att [host] int64[n_max]: (slab << 32) | slot, or -1;
+ *   free_stack [host] int32[n_slabs], *n_free [host].
+ */
+sivf_status sivf_dump(sivf_index *index, void *stream, int32_t *list_nslabs,
+                      int32_t *list_head, int32_t *list_dir, int32_t *slab_meta,
+                      uint32_t *slab_bits, int64_t *slab_ids, int64_t *att,
+                      int32_t *free_stack, int64_t *n_free);
+
+/*
+ * sivf_dump_payload -- copy slab payload rows to host (forces a sync):
+ * the FP32 rows [n_slabs * slab_size, d] (x32, optional), the BF16 copy as
+ * uint16 (xb16, optional), the FP8 copy as uint8 (x8, optional) and the
+ * per-list FP8 inverse scales float32[nlist] (inv_scale, optional).
+ */
+sivf_status sivf_dump_payload(sivf_index *index, void *stream, float *x32,
+                              uint16_t *xb16, uint8_t *x8, float *inv_scale);
+
+/*
+ * sivf_list_sizes -- live vectors of every list (forces a sync):
+ * sizes [host] int32[nlist].
+ */
+sivf_status sivf_list_sizes(sivf_index *index, void *stream, int32_t *sizes);
+
+/*
+ * sivf_profile -- tracing.  enable != 0 starts recording a CUDA event pair
+ * on the launching stream around every kernel group the index enqueues
+ * (forces a device sync and clears earlier records); enable == 0 stops.
+ * Not for use while a stream is being captured into a graph.
+ */
+sivf_status sivf_profile(sivf_index *index, int enable);
+
+/*
+ * sivf_profile_read -- forces a device sync.  For `kernel` one of "coarse"
+ * (approximate-distance GEMM + exact selection), "insert", "remove",
+ * "group" (pairs grouped by list), "scan" (the list scan), "merge" (per-query
+ * top-k): *launches = kernels launched in that group while recording and
+ * *total_ms = the summed event time.  For "all": *launches = every kernel
+ * the index has launched since creation, *total_ms = 0.
+ */
+sivf_status sivf_profile_read(sivf_index *index, const char *kernel,
+                              int64_t *launches, double *total_ms);
+
+/* sivf_last_error -- text of the last error on this index (never NULL). */
+const char *sivf_last_error(const sivf_index *index);
+
+/* sivf_version -- library version string. */
+const char *sivf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIVF_H */

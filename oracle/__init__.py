@@ -69,6 +69,7 @@ def load_lib(path: str):
         "oivf_to_e4m3": (None, [p, f32, p, i64]),
         "oivf_from_e4m3": (None, [p, p, i64]),
         "oivf_num_threads": (i32, [i32]),
+        "oivf_dists": (None, [p, p, i64, i32, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -252,6 +253,15 @@ class OracleIVF:
         """list of every id in [0, n_max), -1 where absent."""
         return np.array([self.list_of(i) for i in range(self.n_max)],
                         dtype=np.int32)
+
+
+def dists(q, x) -> np.ndarray:
+    """FP64 squared distances of one query to each row of x."""
+    q = _f32(q).reshape(-1)
+    x = _f32(x).reshape(-1, q.shape[0])
+    out = np.zeros(x.shape[0], np.float64)
+    _load().oivf_dists(_ptr(q), _ptr(x), x.shape[0], q.shape[0], _ptr(out))
+    return out
 
 
 # -- encodings -----------------------------------------------------------

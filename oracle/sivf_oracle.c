@@ -486,6 +486,12 @@ int oivf_remove(oivf *o, const int64_t *ids, int64_t n, int64_t *n_removed)
     return O_OK;
 }
 
+/* FP64 squared distances of q to n vectors (the definition, one by one) */
+void oivf_dists(const float *q, const float *x, int64_t n, int d, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = sqdist(q, x + (size_t)i * d, d);
+}
+
 /* ------------------------------------------------------------------ */
 /* introspection                                                        */
 /* ------------------------------------------------------------------ */

@@ -1,0 +1,410 @@
+// Coarse quantizer of the index (Sec. 3.3, "the coarse lists returned by
+// the quantizer"): nearest centroid for insert (A1) and the nprobe nearest
+// centroids for search (A4).
+//
+// The result must equal the FP64 definition  argmin_c sum_j (x_j - c_j)^2
+// (ties to the lowest index) bit for bit.  The fast part is an FP32 GEMM
+//     Dt[i][c] = fl(||c||^2 - 2 x_i.c)
+// which differs from the exact  Q = ||c||^2 - 2 x.c  (= D - ||x||^2) by at
+// most
+//     E = 2 * ( u (fl||c||^2 + |Dt|) + 2 gamma_d ||x|| ||c|| )
+// (u = 2^-24, gamma_d = d u / (1 - d u); the dot product error of any
+// summation order is gamma_d sum_j |x_j c_j| <= gamma_d ||x|| ||c||; the
+// factor 2 covers the roundings of the bound arithmetic itself).  The
+// selection then works on intervals [Dt - E, Dt + E]:
+//   T  = the P-th smallest upper bound,
+//   S  = { c : lower bound <= T }         (contains the whole top-P set),
+//   c in S is *sure* when UB_c <= T and fewer than P others have a lower
+//   bound <= UB_c; the remaining places go to the best of the other members
+//   of S by their FP64 distance, computed in the same order and with the
+//   same roundings as the definition (no fused multiply-add).
+// Only near-ties ever reach the FP64 step.
+#include <float.h>
+#include <math.h>
+
+#include "device_utils.cuh"
+#include "kernels.cuh"
+
+namespace sivf {
+
+// ------------------------------------------------------------ centroid prep
+__global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
+                                 float *__restrict__ cn, float *__restrict__ cnrm_up,
+                                 float *__restrict__ inv_scale8)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L) return;
+    const float *v = cent + (size_t)c * d;
+    double s = 0.0, mx = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = (double)v[j];
+        s = __dadd_rn(s, __dmul_rn(t, t));
+        mx = fmax(mx, fabs(t));
+    }
+    cn[c] = __double2float_rn(s);
+    cnrm_up[c] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+    if (inv_scale8) inv_scale8[c] = mx > 0.0 ? (float)(448.0 / (2.0 * mx)) : 1.0f;
+}
+
+// ----------------------------------------------------- FP32 tile GEMM (SIMT)
+// out[i][c] = fl(cn[c] - 2 * sum_j x[i][j] * cent[c][j]) for i < m, c < L.
+// 128 x 128 tiles, 256 threads, 8 x 8 outputs per thread, k-tiles of 16.
+constexpr int GBM = 128, GBN = 128, GBK = 16;
+
+__global__ __launch_bounds__(256) void k_coarse_gemm(const float *__restrict__ x, int m,
+                                                     int d, const float *__restrict__ cent,
+                                                     const float *__restrict__ cn, int L,
+                                                     float *__restrict__ out)
+{
+    __shared__ __align__(16) float As[GBK][GBM];
+    __shared__ __align__(16) float Bs[GBK][GBN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int row0 = blockIdx.y * GBM, col0 = blockIdx.x * GBN;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    for (int k0 = 0; k0 < d; k0 += GBK) {
+        for (int e = tid; e < GBM * GBK / 4; e += 256) {
+            int r = e / (GBK / 4), c4 = e % (GBK / 4);
+            int gk = k0 + c4 * 4;
+            int gr = row0 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < m && gk < d) v = *reinterpret_cast<const float4 *>(x + (size_t)gr * d + gk);
+            As[c4 * 4 + 0][r] = v.x;
+            As[c4 * 4 + 1][r] = v.y;
+            As[c4 * 4 + 2][r] = v.z;
+            As[c4 * 4 + 3][r] = v.w;
+            int gc = col0 + r;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gc < L && gk < d) w = *reinterpret_cast<const float4 *>(cent + (size_t)gc * d + gk);
+            Bs[c4 * 4 + 0][r] = w.x;
+            Bs[c4 * 4 + 1][r] = w.y;
+            Bs[c4 * 4 + 2][r] = w.z;
+            Bs[c4 * 4 + 3][r] = w.w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + tx * 4]);
+            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int r = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            int c = col0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            if (c < L) out[(size_t)r * L + c] = fmaf(-2.f, acc[i][j], cn[c]);
+        }
+    }
+}
+
+// ------------------------------------------------------- exact selection
+constexpr int SEL_NT = 256;
+constexpr int SEL_SCAP = 1024;   // candidate capacity before the slow path
+
+struct SelArgs {
+    const float *D;        // [m, L] approximate distances (row stride L)
+    int m, L, P, d;
+    const float *x;        // [m, d] rows being assigned / queries
+    const float *cent;     // [L, d]
+    const float *cn;       // [L]
+    const float *cnrm_up;  // [L]
+    float gamma2;          // 2 * gamma_d
+    int32_t *out;          // [m, P]
+    uint32_t *err;
+};
+
+// FP64 distance in the order and with the roundings of the definition
+__device__ __forceinline__ double exact_dist(const float *__restrict__ a,
+                                             const float *__restrict__ b, int d)
+{
+    double acc = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = __dsub_rn((double)a[j], (double)b[j]);
+        acc = __dadd_rn(acc, __dmul_rn(t, t));
+    }
+    return acc;
+}
+
+// Bound E of |Dt - Q|.  Written with explicit-rounding intrinsics so that
+// every evaluation for the same inputs gives the same bits (no contraction).
+__device__ __forceinline__ float bound_of(float Dt, float cnc, float cnrm, float xn,
+                                          float gamma2)
+{
+    const float u = 5.9604645e-08f;  // 2^-24
+    float t1 = __fmul_rn(u, __fadd_rn(cnc, fabsf(Dt)));
+    float t2 = __fmul_rn(__fmul_rn(gamma2, xn), cnrm);
+    return __fadd_rn(__fmul_rn(2.f, __fadd_rn(t1, t2)), 1e-30f);
+}
+__device__ __forceinline__ float upper_of(float Dt, float E) { return __fadd_rn(Dt, E); }
+__device__ __forceinline__ float lower_of(float Dt, float E) { return __fsub_rn(Dt, E); }
+
+// block-wide helpers for SEL_NT threads
+__device__ float block_min(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < SEL_NT / 32 ? red[l] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (l == 0) red[0] = v;
+    }
+    __syncthreads();
+    float r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
+{
+    const int row = blockIdx.x;
+    if (row >= a.m) return;
+    const int tid = threadIdx.x;
+    const float *Dr = a.D + (size_t)row * a.L;
+    const float *xr = a.x + (size_t)row * a.d;
+
+    __shared__ float red[32];
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t s_prefix, s_rank;
+    __shared__ int s_ns, s_nsure, s_nb, s_nsel;
+    __shared__ float sLB[SEL_SCAP], sUB[SEL_SCAP];
+    __shared__ int sIdx[SEL_SCAP];
+    __shared__ unsigned char sSure[SEL_SCAP];
+    __shared__ double sDx[SEL_SCAP];
+    __shared__ int sSel[kMaxK];
+
+    // ||x|| upper bound from an FP64 sum
+    double part = 0.0;
+    for (int j = tid; j < a.d; j += SEL_NT) part += (double)xr[j] * (double)xr[j];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __shared__ double dred[SEL_NT / 32];
+    if ((tid & 31) == 0) dred[tid >> 5] = part;
+    __syncthreads();
+    double xs = 0.0;
+    for (int w = 0; w < SEL_NT / 32; ++w) xs += dred[w];
+    const float xn = __double2float_ru(sqrt(xs) * (1.0 + 1e-12));
+
+    // T = P-th smallest upper bound
+    float T;
+    if (a.P == 1) {
+        float v = INFINITY;
+        for (int c = tid; c < a.L; c += SEL_NT) {
+            float Dt = Dr[c];
+            v = fminf(v, upper_of(Dt, bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2)));
+        }
+        T = block_min(v, red);
+    } else {
+        if (tid == 0) {
+            s_prefix = 0;
+            s_rank = (uint32_t)a.P;
+        }
+        uint32_t mask = 0;
+        for (int pass = 0; pass < 4; ++pass) {
+            const int shift = 24 - 8 * pass;
+            hist[tid] = 0;  // SEL_NT == 256 bins
+            __syncthreads();
+            const uint32_t prefix = s_prefix;
+            for (int c = tid; c < a.L; c += SEL_NT) {
+                float Dt = Dr[c];
+                uint32_t k = fkey(upper_of(Dt, bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2)));
+                if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid < 32) {
+                // lane l owns bins 8l .. 8l+7
+                uint32_t loc[8], s = 0;
+                for (int b = 0; b < 8; ++b) {
+                    loc[b] = hist[tid * 8 + b];
+                    s += loc[b];
+                }
+                uint32_t incl = s;
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (tid >= o) incl += t;
+                }
+                uint32_t excl = incl - s, need = s_rank;
+                bool mine = excl < need && incl >= need;
+                if (mine) {
+                    uint32_t cum = excl;
+                    for (int b = 0; b < 8; ++b) {
+                        if (cum + loc[b] >= need) {
+                            s_prefix = prefix | ((uint32_t)(tid * 8 + b) << shift);
+                            s_rank = need - cum;
+                            break;
+                        }
+                        cum += loc[b];
+                    }
+                }
+            }
+            mask |= 255u << shift;
+            __syncthreads();
+        }
+        T = fkey_inv(s_prefix);
+    }
+
+    // candidate set S
+    if (tid == 0) {
+        s_ns = 0;
+        s_nsure = 0;
+        s_nb = 0;
+        s_nsel = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < a.L; c += SEL_NT) {
+        float Dt = Dr[c];
+        float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
+        if (lower_of(Dt, E) <= T) {
+            int p = atomicAdd(&s_ns, 1);
+            if (p < SEL_SCAP) {
+                sLB[p] = lower_of(Dt, E);
+                sUB[p] = upper_of(Dt, E);
+                sIdx[p] = c;
+            }
+        }
+    }
+    __syncthreads();
+    const int ns = s_ns;
+    int32_t *outr = a.out + (size_t)row * a.P;
+
+    if (ns <= SEL_SCAP) {
+        // sure members
+        for (int p = tid; p < ns; p += SEL_NT) {
+            float ub = sUB[p];
+            int cnt = 0;
+            for (int q = 0; q < ns; ++q) cnt += (q != p && sLB[q] <= ub);
+            bool sure = ub <= T && cnt < a.P;
+            sSure[p] = sure;
+            if (sure) {
+                int s = atomicAdd(&s_nsel, 1);
+                if (s < kMaxK) sSel[s] = sIdx[p];
+            }
+        }
+        __syncthreads();
+        const int nsure = s_nsel;
+        const int r = a.P - nsure;
+        if (r > 0) {
+            // boundary members: exact FP64 distances, then rank among them
+            const int nb = ns - nsure;
+            if (nb > r) {
+                for (int p = tid; p < ns; p += SEL_NT)
+                    if (!sSure[p]) sDx[p] = exact_dist(xr, a.cent + (size_t)sIdx[p] * a.d, a.d);
+                __syncthreads();
+            }
+            for (int p = tid; p < ns; p += SEL_NT) {
+                if (sSure[p]) continue;
+                bool take = true;
+                if (nb > r) {
+                    const double Dc = sDx[p];
+                    const int c = sIdx[p];
+                    int rank = 0;
+                    for (int q = 0; q < ns; ++q) {
+                        if (q == p || sSure[q]) continue;
+                        rank += (sDx[q] < Dc || (sDx[q] == Dc && sIdx[q] < c));
+                    }
+                    take = rank < r;
+                }
+                if (take) {
+                    int s = atomicAdd(&s_nsel, 1);
+                    if (s < kMaxK) sSel[s] = sIdx[p];
+                }
+            }
+        }
+        __syncthreads();
+    } else if (tid == 0) {
+        // pathological: more than SEL_SCAP candidates (e.g. many identical
+        // centroids).  Exact FP64 selection by insertion into a sorted
+        // array of P (distance, index) pairs, scanning lists in index order.
+        double *hd = sDx;  // P <= SEL_SCAP entries
+        int n = 0;
+        for (int c = 0; c < a.L; ++c) {
+            float Dt = Dr[c];
+            float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
+            if (lower_of(Dt, E) > T) continue;
+            double Dc = exact_dist(xr, a.cent + (size_t)c * a.d, a.d);
+            if (n == a.P && !(Dc < hd[n - 1])) continue;  // index order keeps ties
+            int pos = n < a.P ? n : a.P - 1;
+            while (pos > 0 && Dc < hd[pos - 1]) {
+                hd[pos] = hd[pos - 1];
+                sSel[pos] = sSel[pos - 1];
+                --pos;
+            }
+            hd[pos] = Dc;
+            sSel[pos] = c;
+            if (n < a.P) ++n;
+        }
+        s_nsel = n;
+    }
+    __syncthreads();
+
+    // write the selected set in ascending list index
+    const int nsel = min(s_nsel, a.P);
+    if (s_nsel != a.P && tid == 0) atomicOr(a.err, ERR_SELECT);
+    for (int s = tid; s < a.P; s += SEL_NT) {
+        if (s >= nsel) {
+            outr[s] = -1;
+            continue;
+        }
+        int c = sSel[s], pos = 0;
+        for (int q = 0; q < nsel; ++q) pos += sSel[q] < c;
+        outr[pos] = c;
+    }
+}
+
+// ------------------------------------------------------------ host drivers
+void centroid_prep(sivf_index *ix, cudaStream_t st)
+{
+    ix->launches += 1;
+    k_centroid_norms<<<(ix->nlist + 127) / 128, 128, 0, st>>>(
+        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8);
+}
+
+// rows [0, m) of x -> out[m, P]; `Dbuf` holds at least rows_per_chunk * L
+// floats.
+void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
+                 float *Dbuf, int64_t rows_per_chunk, cudaStream_t st)
+{
+    const int L = ix->nlist, d = ix->d;
+    const double u = 5.9604644775390625e-08;
+    const double gd = d * u / (1.0 - d * u);
+    for (int64_t r0 = 0; r0 < m; r0 += rows_per_chunk) {
+        int mc = (int)std::min<int64_t>(rows_per_chunk, m - r0);
+        dim3 g((L + GBN - 1) / GBN, (mc + GBM - 1) / GBM);
+        const int tok = prof_begin(ix, PROF_COARSE, 2, st);
+        k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
+        SelArgs a;
+        a.D = Dbuf;
+        a.m = mc;
+        a.L = L;
+        a.P = P;
+        a.d = d;
+        a.x = x + r0 * d;
+        a.cent = ix->cent;
+        a.cn = ix->cnorm;
+        a.cnrm_up = ix->cnrm_up;
+        a.gamma2 = (float)(2.0 * gd * (1.0 + 1e-6));
+        a.out = out + r0 * P;
+        a.err = ix->err;
+        k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
+        prof_end(ix, tok, st);
+    }
+}
+
+}  // namespace sivf

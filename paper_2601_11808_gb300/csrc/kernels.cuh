@@ -1,0 +1,58 @@
+// Host-side drivers of the kernels, one per step of the hot path.  Each
+// enqueues its kernels on `st` and returns; scratch pointers come from the
+// caller's arena.
+#pragma once
+
+#include <algorithm>
+
+#include "sivf_internal.cuh"
+
+namespace sivf {
+
+// ---- coarse quantizer (coarse.cu)
+void centroid_prep(sivf_index *ix, cudaStream_t st);
+// exact top-P set of each row of x, in ascending list index; Dbuf holds
+// rows_per_chunk * nlist floats
+void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
+                 float *Dbuf, int64_t rows_per_chunk, cudaStream_t st);
+
+// ---- insert / delete (mutate.cu)
+struct InsertScratch {
+    int32_t *lab;        // [n] list of each vector
+    int32_t *rloc;       // [n] rank among winners of its list in its block
+    int32_t *touched;    // [nlist]
+    int32_t *bcnt;       // [nlist] vectors per touched list
+    PlanEntry *plan;     // [nlist]
+    int32_t *affected;   // [nlist]
+};
+void insert_batch(sivf_index *ix, const int64_t *ids, const float *x, int64_t n,
+                  const InsertScratch &s, cudaStream_t st);
+void remove_batch(sivf_index *ix, const int64_t *ids, int64_t n, int32_t *affected,
+                  cudaStream_t st);
+
+// ---- search (scan.cu)
+struct SearchScratch {
+    int32_t *lcnt;       // [nlist] (query, list) pairs per list
+    int32_t *loff;       // [nlist + 1]
+    int32_t *ibase;      // [nlist + 1] first work item of each list
+    int32_t *nch;        // [nlist] slab chunks of each list
+    int32_t *prank;      // [nq * P] rank of the pair inside its list group
+    int32_t *qlist;      // [nq * P] pairs grouped by list (q * P + p)
+    float *part_d;       // [nq * P * CH * K]
+    int64_t *part_i;     // [nq * P * CH * K]
+};
+struct SearchPlan {
+    int tq;              // queries per work item
+    int ch;              // most slab chunks per list
+    int slabs_per_chunk; // slabs per chunk before splitting stops
+    int K;               // candidates kept per (query, item)
+};
+SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K);
+bool scan_fits(const sivf_index *ix, int K);   // shared memory for k = K
+void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
+                bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
+void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
+                const SearchPlan &pl, const SearchScratch &s, int k, float *dist,
+                int64_t *labels, cudaStream_t st);
+
+}  // namespace sivf

@@ -1,0 +1,586 @@
+// List scan and top-k of the search (Algorithm 3, redone list-centrically).
+//
+// Algorithm 3 gives one warp to one query and walks each probed list's slab
+// chain.  Here the (query, list) pairs of a whole batch are first grouped by
+// list, and one CTA scans one list for a tile of up to TQ queries: every slab
+// of the list is read from HBM once per tile instead of once per query, and
+// the list's slabs come from its directory, so the next slabs are fetched
+// (whole, by one bulk copy each, into shared memory) while the current one
+// is being scored.  Distances are the direct form sum_j (q_j - x_j)^2 in
+// FP32 (the paper's metric, squared L2).  A slot is read only when its
+// validity bit is set (Theorem 2).  Each (query, list tile) keeps its best K
+// (distance, id) pairs; a final merge per query keeps the best k of all
+// probed lists, ties to the lower id, padded with (+inf, -1).
+#include <math.h>
+
+#include "device_utils.cuh"
+#include "kernels.cuh"
+
+namespace sivf {
+
+// ------------------------------------------------------ grouping by list
+__global__ void k_srch_hist(const int32_t *__restrict__ probes, int64_t nq, int P, int L,
+                            bool dedupe, int32_t *__restrict__ lcnt,
+                            int32_t *__restrict__ prank)
+{
+    int64_t n = nq * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int l = probes[e];
+        bool ok = l >= 0 && l < L;
+        if (ok && dedupe) {
+            int64_t q0 = (e / P) * P;
+            for (int64_t f = q0; f < e; ++f)
+                if (probes[f] == l) {
+                    ok = false;
+                    break;
+                }
+        }
+        prank[e] = ok ? atomicAdd(&lcnt[l], 1) : -1;
+    }
+}
+
+// One block: exclusive scans over the lists of the pair counts and of the
+// work items (query tiles x slab chunks).
+__global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ lcnt,
+                                                    const int32_t *__restrict__ nslabs,
+                                                    const int32_t *__restrict__ list_live,
+                                                    int L, int tq, int ch, int spc,
+                                                    int64_t slab_bytes,
+                                                    int32_t *__restrict__ loff,
+                                                    int32_t *__restrict__ ibase,
+                                                    int32_t *__restrict__ nch, Ctl *ctl,
+                                                    int64_t *stat)
+{
+    __shared__ int32_t sa[1024], sb[1024];
+    const int tid = threadIdx.x;
+    const int per = (L + 1023) / 1024;
+    const int b0 = tid * per, b1 = min(L, b0 + per);
+    int32_t ca = 0, cb = 0;
+    unsigned long long pairs = 0, bytes = 0;
+    for (int l = b0; l < b1; ++l) {
+        int m = lcnt[l], ns = nslabs[l];
+        int nt = (m + tq - 1) / tq;
+        int c = (m > 0 && ns > 0) ? min(ch, max(1, (ns + spc - 1) / spc)) : 0;
+        c = min(c, ns);
+        nch[l] = c;
+        ca += m;
+        cb += nt * c;
+        if (c) {
+            pairs += (unsigned long long)m * (unsigned long long)max(list_live[l], 0);
+            bytes += (unsigned long long)nt * ns * slab_bytes;
+        }
+    }
+    if (pairs) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 1), pairs);
+    if (bytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 2), bytes);
+    sa[tid] = ca;
+    sb[tid] = cb;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int32_t va = tid >= o ? sa[tid - o] : 0, vb = tid >= o ? sb[tid - o] : 0;
+        __syncthreads();
+        sa[tid] += va;
+        sb[tid] += vb;
+        __syncthreads();
+    }
+    int32_t ea = sa[tid] - ca, eb = sb[tid] - cb;
+    for (int l = b0; l < b1; ++l) {
+        int m = lcnt[l];
+        loff[l] = ea;
+        ibase[l] = eb;
+        ea += m;
+        eb += ((m + tq - 1) / tq) * nch[l];
+    }
+    if (tid == 1023) {
+        loff[L] = sa[1023];
+        ibase[L] = sb[1023];
+        ctl->nitems = sb[1023];
+        ctl->nscan = sa[1023];
+    }
+}
+
+__global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, int P,
+                               const int32_t *__restrict__ prank,
+                               const int32_t *__restrict__ loff, int32_t *__restrict__ qlist)
+{
+    int64_t n = nq * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int r = prank[e];
+        if (r >= 0) qlist[loff[probes[e]] + r] = (int32_t)e;
+    }
+}
+
+// ------------------------------------------------------------ the scan
+constexpr int SCAN_NT = 256;
+constexpr int NST = 2;  // slab stages in flight
+
+struct ScanArgs {
+    const float *q;
+    int64_t nq;
+    int P, K, M, CH;
+    const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
+    float *part_d;
+    int64_t *part_i;
+    // index
+    const float *x32;
+    const int64_t *ids;
+    const uint32_t *bits;
+    const SlabMeta *meta;
+    const int32_t *nslabs, *dir;
+    int64_t n_slabs, dir_cap;
+    int L, d;
+    Ctl *ctl;
+    uint32_t *err;
+};
+
+__host__ __device__ constexpr int scan_next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// shared memory carve-up, identical on host and device
+struct ScanSmem {
+    size_t qs, xs, idb, bd, bi, misc, total;
+};
+__host__ __device__ inline ScanSmem scan_smem(int TQ, int C, int d, int M)
+{
+    ScanSmem s;
+    const size_t DP = d + 4;
+    s.qs = 0;
+    s.xs = s.qs + (size_t)TQ * DP * 4;
+    s.idb = s.xs + (size_t)NST * C * d * 4;
+    s.bd = s.idb + (size_t)NST * C * 8;
+    s.bi = s.bd + (size_t)TQ * M * 4;
+    s.bi = (s.bi + 15) & ~(size_t)15;
+    s.misc = s.bi + (size_t)TQ * M * 8;
+    s.total = s.misc + 256;
+    return s;
+}
+
+template <int TQ, int C>
+__global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
+{
+    constexpr int QW = TQ >= 32 ? TQ / 32 : 1;
+    constexpr int SW = 8 / QW;
+    constexpr int RQ = TQ / (8 * QW);
+    constexpr int RX = C / (4 * SW);
+    constexpr int W = C / 32;
+    static_assert(RQ >= 1 && RX >= 1, "tile shape");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int d = a.d, DP = d + 4, M = a.M, K = a.K;
+    const ScanSmem L = scan_smem(TQ, C, d, M);
+    float *Qs = reinterpret_cast<float *>(smem + L.qs);
+    float *Xs = reinterpret_cast<float *>(smem + L.xs);
+    int64_t *IDs = reinterpret_cast<int64_t *>(smem + L.idb);
+    float *BD = reinterpret_cast<float *>(smem + L.bd);
+    int64_t *BI = reinterpret_cast<int64_t *>(smem + L.bi);
+    unsigned char *misc = smem + L.misc;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);            // [NST]
+    int *s_item = reinterpret_cast<int *>(misc + 8 * NST);
+    int *s_abort = s_item + 1;
+    int *stage_slab = s_item + 2;                                   // [NST]
+    __shared__ int32_t s_qpair[TQ];                                 // pair of each row
+    __shared__ int s_cc[TQ];                                        // candidates per row
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wq = warp % QW, ws = warp / QW;
+    const int qy = lane & 7, sx = lane >> 3;
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&mbar[s], 1);
+        fence_mbar_init();
+        *s_abort = 0;
+    }
+    __syncthreads();
+
+    const uint32_t slab_bytes = (uint32_t)(C * d * 4);
+    uint32_t g_cons = 0, g_issue = 0;  // slabs consumed / issued by this CTA
+
+    auto issue = [&](int stage, int s) {
+        // called by thread 0 only
+        bool ok = s >= 0 && s < a.n_slabs;
+        if (!ok) atomicOr(a.err, ERR_BAD_SLAB);
+        stage_slab[stage] = ok ? s : -1;
+        if (ok) {
+            mbar_arrive_expect_tx(&mbar[stage], slab_bytes + C * 8);
+            bulk_g2s(Xs + (size_t)stage * C * d, a.x32 + (size_t)s * C * d, slab_bytes,
+                     &mbar[stage]);
+            bulk_g2s(IDs + (size_t)stage * C, a.ids + (size_t)s * C, C * 8, &mbar[stage]);
+        } else {
+            mbar_arrive(&mbar[stage]);
+        }
+    };
+
+    for (;;) {
+        if (tid == 0) *s_item = atomicAdd(&a.ctl->next_item, 1);
+        __syncthreads();
+        const int item = *s_item;
+        if (item >= a.ctl->nitems || *s_abort) break;
+
+        // decode item -> list, query tile, slab chunk
+        int lo = 0, hi = a.L;  // largest l with ibase[l] <= item
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (a.ibase[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int l = lo;
+        const int nc = a.nch[l];
+        const int rel = item - a.ibase[l];
+        const int tile = rel / nc, chunk = rel % nc;
+        const int mcount = a.lcnt[l];
+        const int m = min(TQ, mcount - tile * TQ);
+        int ns_total = a.nslabs[l];
+        if (ns_total > a.dir_cap) {
+            if (tid == 0) atomicOr(a.err, ERR_DIR_BOUND);
+            ns_total = (int)a.dir_cap;
+        }
+        const int s0 = (int)((int64_t)ns_total * chunk / nc);
+        const int s1 = (int)((int64_t)ns_total * (chunk + 1) / nc);
+        const int ns = s1 - s0;
+        const int32_t *dirl = a.dir + (size_t)l * a.dir_cap;
+
+        // stage the first slabs while the query tile is gathered
+        if (tid == 0) {
+            for (int t = 0; t < NST && t < ns; ++t) {
+                issue((g_issue % NST), dirl[s0 + t]);
+                ++g_issue;
+            }
+        }
+        const int qb = a.loff[l] + tile * TQ;
+        for (int r = tid; r < TQ; r += SCAN_NT) {
+            s_qpair[r] = r < m ? a.qlist[qb + r] : -1;
+            s_cc[r] = 0;
+        }
+        __syncthreads();
+        for (int e = tid; e < TQ * (d / 4); e += SCAN_NT) {
+            int r = e / (d / 4), j4 = e % (d / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int pr = s_qpair[r];
+            if (pr >= 0)
+                v = *reinterpret_cast<const float4 *>(a.q + (size_t)(pr / a.P) * d + 4 * j4);
+            *reinterpret_cast<float4 *>(Qs + (size_t)r * DP + 4 * j4) = v;
+        }
+        for (int e = tid; e < TQ * M; e += SCAN_NT) {
+            BD[e] = INFINITY;
+            BI[e] = -1;
+        }
+        __syncthreads();
+
+        for (int idx = 0; idx < ns; ++idx) {
+            const int stage = g_cons % NST;
+            const uint32_t parity = (g_cons / NST) & 1u;
+            if (!mbar_wait_bounded(&mbar[stage], parity, a.err)) *s_abort = 1;
+            ++g_cons;
+            const int s = stage_slab[stage];
+            if (s >= 0 && !*s_abort) {
+                const float *xs = Xs + (size_t)stage * C * d;
+                const int64_t *ib = IDs + (size_t)stage * C;
+                float acc[RQ][RX];
+#pragma unroll
+                for (int i = 0; i < RQ; ++i)
+#pragma unroll
+                    for (int r = 0; r < RX; ++r) acc[i][r] = 0.f;
+                const float *qrow = Qs + (size_t)(wq * 8 * RQ + qy) * DP;
+                const float *xrow = xs + (size_t)(ws * 4 * RX + sx) * d;
+#pragma unroll 2
+                for (int j = 0; j < d; j += 4) {
+                    float4 qv[RQ], xv[RX];
+#pragma unroll
+                    for (int i = 0; i < RQ; ++i)
+                        qv[i] = *reinterpret_cast<const float4 *>(qrow + (size_t)i * 8 * DP + j);
+#pragma unroll
+                    for (int r = 0; r < RX; ++r)
+                        xv[r] = *reinterpret_cast<const float4 *>(xrow + (size_t)r * 4 * d + j);
+#pragma unroll
+                    for (int i = 0; i < RQ; ++i)
+#pragma unroll
+                        for (int r = 0; r < RX; ++r) {
+                            float t0 = qv[i].x - xv[r].x, t1 = qv[i].y - xv[r].y;
+                            float t2 = qv[i].z - xv[r].z, t3 = qv[i].w - xv[r].w;
+                            float v = acc[i][r];
+                            v = fmaf(t0, t0, v);
+                            v = fmaf(t1, t1, v);
+                            v = fmaf(t2, t2, v);
+                            v = fmaf(t3, t3, v);
+                            acc[i][r] = v;
+                        }
+                }
+                uint32_t bw[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) bw[w] = __ldg(a.bits + (size_t)s * W + w);
+#pragma unroll
+                for (int i = 0; i < RQ; ++i) {
+                    const int qr = wq * 8 * RQ + qy + 8 * i;
+                    if (qr >= m) continue;
+                    const float kd = BD[qr * M + K - 1];
+                    const int64_t ki = BI[qr * M + K - 1];
+#pragma unroll
+                    for (int r = 0; r < RX; ++r) {
+                        const int slot = ws * 4 * RX + sx + 4 * r;
+                        if (!((bw[slot >> 5] >> (slot & 31)) & 1u)) continue;
+                        const float dd = acc[i][r];
+                        if (dd < kd || (dd == kd && ib[slot] < ki)) {
+                            int pos = atomicAdd(&s_cc[qr], 1);
+                            BD[qr * M + K + pos] = dd;
+                            BI[qr * M + K + pos] = ib[slot];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // the stage is free: fetch the slab NST ahead into it
+            if (tid == 0 && idx + NST < ns && !*s_abort) {
+                fence_proxy_async_smem();
+                issue(g_issue % NST, dirl[s0 + idx + NST]);
+                ++g_issue;
+            }
+            // merge candidates of each query into its best K (one warp per
+            // query): bitonic sort of the M entries in shared memory
+            for (int qr = warp; qr < m; qr += SCAN_NT / 32) {
+                const int n_c = s_cc[qr];
+                if (n_c == 0) continue;
+                float *bd = BD + (size_t)qr * M;
+                int64_t *bi = BI + (size_t)qr * M;
+                for (int e = K + n_c + lane; e < M; e += 32) {
+                    bd[e] = INFINITY;
+                    bi[e] = -1;
+                }
+                __syncwarp();
+                for (int size = 2; size <= M; size <<= 1)
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int t = lane; t < M / 2; t += 32) {
+                            int pos = 2 * t - (t & (stride - 1));
+                            int par = pos + stride;
+                            bool up = (pos & size) == 0;
+                            float d0 = bd[pos], d1 = bd[par];
+                            int64_t i0 = bi[pos], i1 = bi[par];
+                            bool gt = dk_less(d1, i1, d0, i0);
+                            if (gt == up) {
+                                bd[pos] = d1;
+                                bd[par] = d0;
+                                bi[pos] = i1;
+                                bi[par] = i0;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                if (lane == 0) s_cc[qr] = 0;
+            }
+            __syncthreads();
+        }
+
+        // write the best K of each query of the tile
+        for (int e = tid; e < m * K; e += SCAN_NT) {
+            int r = e / K, j = e % K;
+            int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
+            a.part_d[base + j] = BD[r * M + j];
+            a.part_i[base + j] = BI[r * M + j];
+        }
+        __syncthreads();
+    }
+    // after an abort, give copies still in flight a bounded chance to land
+    // before the CTA (and its shared memory) goes away
+    if (tid == 0)
+        while (g_cons < g_issue) {
+            mbar_wait_bounded(&mbar[g_cons % NST], (g_cons / NST) & 1u, a.err, 100000u);
+            ++g_cons;
+        }
+}
+
+// ------------------------------------------------------- per-query merge
+constexpr int MERGE_NT = 128;
+constexpr int MERGE_RUNS_PER_LANE = 64;
+
+__global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ probes,
+                                                    const int32_t *__restrict__ prank,
+                                                    const int32_t *__restrict__ nch, int64_t nq,
+                                                    int P, int CH, int K, int k,
+                                                    const float *__restrict__ part_d,
+                                                    const int64_t *__restrict__ part_i,
+                                                    float *__restrict__ dist,
+                                                    int64_t *__restrict__ labels)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)MERGE_NT + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    // runs owned by this lane: (p, chunk) pairs numbered r = p * CH + chunk,
+    // r = lane, lane + 32, ...; cursor per run kept in local memory
+    int cur[MERGE_RUNS_PER_LANE];
+    int nrun = 0;
+    const int R = P * CH;
+    for (int r = lane; r < R && nrun < MERGE_RUNS_PER_LANE; r += 32) {
+        int p = r / CH, c = r % CH;
+        bool ok = prank[q * P + p] >= 0 && c < nch[probes[q * P + p]];
+        cur[nrun++] = ok ? 0 : K;
+    }
+    auto head = [&](int j, float &hd, int64_t &hi) {
+        int r = lane + 32 * j;
+        if (cur[j] >= K) {
+            hd = INFINITY;
+            hi = -1;
+            return;
+        }
+        int64_t e = ((q * P + r / CH) * (int64_t)CH + r % CH) * K + cur[j];
+        hd = part_d[e];
+        hi = part_i[e];
+        if (hi < 0) hd = INFINITY;
+    };
+    float bd = INFINITY;
+    int64_t bi = -1;
+    int bj = -1;
+    auto rescan = [&]() {
+        bd = INFINITY;
+        bi = -1;
+        bj = -1;
+        for (int j = 0; j < nrun; ++j) {
+            float hd;
+            int64_t hi;
+            head(j, hd, hi);
+            if (hi >= 0 && (bj < 0 || dk_less(hd, hi, bd, bi))) {
+                bd = hd;
+                bi = hi;
+                bj = j;
+            }
+        }
+    };
+    rescan();
+    for (int o = 0; o < k; ++o) {
+        float wd = bd;
+        int64_t wi = bi;
+        int wl = bj >= 0 ? lane : 32;
+        for (int s = 16; s > 0; s >>= 1) {
+            float od = __shfl_xor_sync(0xffffffffu, wd, s);
+            int64_t oi = __shfl_xor_sync(0xffffffffu, wi, s);
+            int ol = __shfl_xor_sync(0xffffffffu, wl, s);
+            bool take = ol < 32 && (wl >= 32 || dk_less(od, oi, wd, wi));
+            if (take) {
+                wd = od;
+                wi = oi;
+                wl = ol;
+            }
+        }
+        if (lane == 0) {
+            dist[q * k + o] = wl < 32 ? wd : INFINITY;
+            labels[q * k + o] = wl < 32 ? wi : -1;
+        }
+        if (wl == lane) {
+            ++cur[bj];
+            rescan();
+        }
+    }
+}
+
+// --------------------------------------------------------------- drivers
+template <int TQ, int C>
+static void launch_scan(sivf_index *ix, const ScanArgs &a, size_t smem, int grid,
+                        cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_scan<TQ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+        attr = true;
+    }
+    const int tok = prof_begin(ix, PROF_SCAN, 1, st);
+    k_scan<TQ, C><<<grid, SCAN_NT, smem, st>>>(a);
+    prof_end(ix, tok, st);
+}
+
+SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
+{
+    SearchPlan pl;
+    const int C = ix->C, d = ix->d;
+    const double pairs_per_list = (double)nq * P / ix->nlist;
+    int tq = pairs_per_list >= 48 ? 64 : pairs_per_list >= 24 ? 32 : pairs_per_list >= 12 ? 16 : 8;
+    const int M = scan_next_pow2(K + C);
+    while (tq > 8 && scan_smem(tq, C, d, M).total > 220 * 1024) tq >>= 1;
+    pl.tq = tq;
+    pl.K = K;
+    // enough work items for every SM: split lists into slab chunks when the
+    // query tiles alone are too few
+    const double touched = std::min<double>(ix->nlist, (double)nq * P);
+    const double tiles = std::max(touched, (double)nq * P / tq);
+    const double want = 4.0 * 152;
+    int ch = tiles >= want ? 1 : (int)std::min<double>(kMaxChunks, std::ceil(want / tiles));
+    ch = std::min(ch, std::max(1, 2048 / P));  // runs per query the merge can hold
+    pl.ch = std::max(1, ch);
+    pl.slabs_per_chunk = 2;
+    return pl;
+}
+
+bool scan_fits(const sivf_index *ix, int K)
+{
+    return scan_smem(8, ix->C, ix->d, scan_next_pow2(K + ix->C)).total <= 220 * 1024;
+}
+
+void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
+                bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st)
+{
+    const int L = ix->nlist;
+    cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
+    int64_t n = nq * P;
+    int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    const int tg = prof_begin(ix, PROF_GROUP, 3, st);
+    k_srch_hist<<<std::max(g, 1), 256, 0, st>>>(probes, nq, P, L, dedupe, s.lcnt, s.prank);
+    const int64_t slab_bytes = (int64_t)ix->C * (ix->d * 4 + 8);
+    k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
+                                    pl.slabs_per_chunk, slab_bytes, s.loff, s.ibase, s.nch,
+                                    ix->ctl, ix->stat);
+    k_srch_scatter<<<std::max(g, 1), 256, 0, st>>>(probes, nq, P, s.prank, s.loff, s.qlist);
+    prof_end(ix, tg, st);
+
+    ScanArgs a;
+    a.q = q;
+    a.nq = nq;
+    a.P = P;
+    a.K = pl.K;
+    a.M = scan_next_pow2(pl.K + ix->C);
+    a.CH = pl.ch;
+    a.qlist = s.qlist;
+    a.loff = s.loff;
+    a.lcnt = s.lcnt;
+    a.ibase = s.ibase;
+    a.nch = s.nch;
+    a.part_d = s.part_d;
+    a.part_i = s.part_i;
+    a.x32 = ix->x32;
+    a.ids = ix->ids;
+    a.bits = ix->bits;
+    a.meta = ix->meta;
+    a.nslabs = ix->nslabs;
+    a.dir = ix->dir;
+    a.n_slabs = ix->n_slabs;
+    a.dir_cap = ix->dir_cap;
+    a.L = L;
+    a.d = ix->d;
+    a.ctl = ix->ctl;
+    a.err = ix->err;
+    const size_t smem = scan_smem(pl.tq, ix->C, ix->d, a.M).total;
+    const int grid = 152;  // persistent: one CTA per SM
+#define SIVF_SCAN_CASE(TQ_, C_) \
+    if (pl.tq == TQ_ && ix->C == C_) return launch_scan<TQ_, C_>(ix, a, smem, grid, st);
+    SIVF_SCAN_CASE(8, 32) SIVF_SCAN_CASE(16, 32) SIVF_SCAN_CASE(32, 32) SIVF_SCAN_CASE(64, 32)
+    SIVF_SCAN_CASE(8, 64) SIVF_SCAN_CASE(16, 64) SIVF_SCAN_CASE(32, 64) SIVF_SCAN_CASE(64, 64)
+    SIVF_SCAN_CASE(8, 128) SIVF_SCAN_CASE(16, 128) SIVF_SCAN_CASE(32, 128)
+    SIVF_SCAN_CASE(64, 128)
+#undef SIVF_SCAN_CASE
+}
+
+void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
+                const SearchPlan &pl, const SearchScratch &s, int k, float *dist,
+                int64_t *labels, cudaStream_t st)
+{
+    int64_t warps = nq;
+    int64_t blocks = (warps * 32 + MERGE_NT - 1) / MERGE_NT;
+    const int tok = prof_begin(ix, PROF_MERGE, 1, st);
+    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(probes, s.prank, s.nch, nq, P, pl.ch, pl.K, k,
+                                                  s.part_d, s.part_i, dist, labels);
+    prof_end(ix, tok, st);
+}
+
+}  // namespace sivf

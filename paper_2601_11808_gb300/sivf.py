@@ -1,0 +1,427 @@
+"""ctypes binding of libsivf (include/sivf.h).
+
+The module-level functions carry the C names and only marshal arguments:
+torch tensors become device pointers, the torch current stream becomes the
+``cudaStream_t``.  Every step of the index runs in the CUDA library; there is
+no fallback.  If ``libsivf.so`` has not been built, loading fails loudly.
+
+``Index`` is a small convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsivf.so")
+
+OK, E_ARG, E_NOMEM, E_STATE, E_CUDA, E_CORRUPT, E_TIMEOUT = range(7)
+STATUS_NAMES = ["OK", "E_ARG", "E_NOMEM", "E_STATE", "E_CUDA", "E_CORRUPT",
+                "E_TIMEOUT"]
+FP32, BF16, FP8E4M3 = 0, 1, 2
+DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
+
+# every symbol include/sivf.h declares
+EXPORTS = [
+    "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
+    "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
+    "sivf_search_with_probes", "sivf_assign", "sivf_probe", "sivf_sync",
+    "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
+    "sivf_profile", "sivf_profile_read", "sivf_last_error", "sivf_version",
+]
+
+
+class sivf_config(C.Structure):
+    _fields_ = [("d", C.c_int), ("nlist", C.c_int), ("slab_size", C.c_int),
+                ("n_max", C.c_int64), ("n_slabs", C.c_int64),
+                ("dir_cap", C.c_int64), ("scan_dtypes", C.c_uint32)]
+
+
+class sivf_stats_t(C.Structure):
+    _fields_ = [("ntotal", C.c_int64), ("free_slabs", C.c_int64),
+                ("used_slabs", C.c_int64), ("error_bits", C.c_uint32),
+                ("last_status", C.c_int32), ("last_count", C.c_int64),
+                ("bytes_device", C.c_int64), ("pairs_scanned", C.c_int64),
+                ("slab_bytes_scanned", C.c_int64)]
+
+
+class SivfError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"sivf {name}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libsivf.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"{p} is missing: build it with paper_2601_11808_gb300.build.build()")
+        lib = C.CDLL(p)
+        vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+        sig = {
+            "sivf_create": (i32, [C.POINTER(sivf_config), C.POINTER(vp)]),
+            "sivf_destroy": (i32, [vp]),
+            "sivf_set_centroids": (i32, [vp, vp, vp]),
+            "sivf_set_list_scales": (i32, [vp, vp, vp]),
+            "sivf_reserve": (i32, [vp, i64, i64, i64, i32, i32, vp]),
+            "sivf_add": (i32, [vp, vp, vp, i64, vp, C.POINTER(i64)]),
+            "sivf_remove": (i32, [vp, vp, i64, vp, C.POINTER(i64)]),
+            "sivf_search": (i32, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
+            "sivf_search_with_probes": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
+            "sivf_assign": (i32, [vp, vp, i64, vp, vp]),
+            "sivf_probe": (i32, [vp, vp, i64, i32, vp, vp]),
+            "sivf_sync": (i32, [vp, vp, C.POINTER(i64)]),
+            "sivf_stats": (i32, [vp, vp, C.POINTER(sivf_stats_t)]),
+            "sivf_dump": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64)]),
+            "sivf_dump_payload": (i32, [vp, vp, vp, vp, vp, vp]),
+            "sivf_list_sizes": (i32, [vp, vp, vp]),
+            "sivf_profile": (i32, [vp, i32]),
+            "sivf_profile_read": (i32, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)]),
+            "sivf_last_error": (C.c_char_p, [vp]),
+            "sivf_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------ marshalling
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _check(lib, h, st: int):
+    if st != OK:
+        msg = lib.sivf_last_error(h) if h else b""
+        raise SivfError(st, (msg or b"").decode())
+
+
+def _dev(t, dtype):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor")
+    return t
+
+
+# ------------------------------------------------- C-named entry points
+def sivf_version() -> str:
+    return load().sivf_version().decode()
+
+
+def sivf_create(d, nlist, slab_size, n_max, n_slabs, dir_cap=0, scan_dtypes=0) -> int:
+    lib = load()
+    cfg = sivf_config(int(d), int(nlist), int(slab_size), int(n_max), int(n_slabs),
+                      int(dir_cap), int(scan_dtypes))
+    h = C.c_void_p()
+    _check(lib, None, lib.sivf_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def sivf_destroy(h) -> None:
+    load().sivf_destroy(h)
+
+
+def sivf_set_centroids(h, c, stream=None) -> None:
+    import torch
+    lib = load()
+    _check(lib, h, lib.sivf_set_centroids(h, _ptr(_dev(c, torch.float32)), _stream(stream)))
+
+
+def sivf_set_list_scales(h, inv_scale, stream=None) -> None:
+    import torch
+    lib = load()
+    _check(lib, h, lib.sivf_set_list_scales(h, _ptr(_dev(inv_scale, torch.float32)),
+                                            _stream(stream)))
+
+
+def sivf_reserve(h, max_add=0, max_remove=0, max_queries=0, max_k=0, max_nprobe=0,
+                 stream=None) -> None:
+    lib = load()
+    _check(lib, h, lib.sivf_reserve(h, max_add, max_remove, max_queries, max_k,
+                                    max_nprobe, _stream(stream)))
+
+
+def sivf_add(h, ids, x, stream=None, sync=False):
+    import torch
+    lib = load()
+    _dev(ids, torch.int64)
+    _dev(x, torch.float32)
+    out = C.c_int64(0)
+    st = lib.sivf_add(h, _ptr(ids), _ptr(x), ids.numel(), _stream(stream),
+                      C.byref(out) if sync else None)
+    _check(lib, h, st)
+    return out.value if sync else None
+
+
+def sivf_remove(h, ids, stream=None, sync=False):
+    import torch
+    lib = load()
+    _dev(ids, torch.int64)
+    out = C.c_int64(0)
+    st = lib.sivf_remove(h, _ptr(ids), ids.numel(), _stream(stream),
+                         C.byref(out) if sync else None)
+    _check(lib, h, st)
+    return out.value if sync else None
+
+
+def sivf_search(h, q, k, nprobe, dtype=FP32, dist=None, labels=None, stream=None):
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    nq = q.shape[0]
+    if dist is None:
+        dist = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+    if labels is None:
+        labels = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+    st = lib.sivf_search(h, _ptr(q), nq, k, nprobe, int(dtype), _ptr(dist), _ptr(labels),
+                         _stream(stream))
+    _check(lib, h, st)
+    return dist, labels
+
+
+def sivf_search_with_probes(h, q, k, probes, dtype=FP32, dist=None, labels=None,
+                            stream=None):
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    _dev(probes, torch.int32)
+    nq = q.shape[0]
+    if dist is None:
+        dist = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+    if labels is None:
+        labels = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+    st = lib.sivf_search_with_probes(h, _ptr(q), nq, k, probes.shape[1], _ptr(probes),
+                                     int(dtype), _ptr(dist), _ptr(labels), _stream(stream))
+    _check(lib, h, st)
+    return dist, labels
+
+
+def sivf_assign(h, x, labels=None, stream=None):
+    import torch
+    lib = load()
+    _dev(x, torch.float32)
+    if labels is None:
+        labels = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+    _check(lib, h, lib.sivf_assign(h, _ptr(x), x.shape[0], _ptr(labels), _stream(stream)))
+    return labels
+
+
+def sivf_probe(h, q, nprobe, probes=None, stream=None):
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    if probes is None:
+        probes = torch.empty((q.shape[0], nprobe), dtype=torch.int32, device=q.device)
+    _check(lib, h, lib.sivf_probe(h, _ptr(q), q.shape[0], nprobe, _ptr(probes),
+                                  _stream(stream)))
+    return probes
+
+
+def sivf_sync(h, stream=None) -> int:
+    """Wait for the stream; raise on a rejected batch, return its count."""
+    lib = load()
+    out = C.c_int64(0)
+    _check(lib, h, lib.sivf_sync(h, _stream(stream), C.byref(out)))
+    return out.value
+
+
+def sivf_stats(h, stream=None) -> dict:
+    lib = load()
+    s = sivf_stats_t()
+    _check(lib, h, lib.sivf_stats(h, _stream(stream), C.byref(s)))
+    return {f: getattr(s, f) for f, _ in sivf_stats_t._fields_}
+
+
+def sivf_dump(h, nlist, n_slabs, slab_size, n_max, dir_cap, stream=None) -> dict:
+    lib = load()
+    W = slab_size // 32
+    out = {
+        "list_nslabs": np.zeros(nlist, np.int32),
+        "list_head": np.zeros(nlist, np.int32),
+        "list_dir": np.zeros((nlist, dir_cap), np.int32),
+        "slab_meta": np.zeros((n_slabs, 3), np.int32),
+        "slab_bits": np.zeros((n_slabs, W), np.uint32),
+        "slab_ids": np.zeros((n_slabs, slab_size), np.int64),
+        "att": np.zeros(n_max, np.int64),
+        "free_stack": np.zeros(n_slabs, np.int32),
+    }
+    nfree = C.c_int64(0)
+    st = lib.sivf_dump(h, _stream(stream), *[_ptr(out[k]) for k in (
+        "list_nslabs", "list_head", "list_dir", "slab_meta", "slab_bits", "slab_ids",
+        "att", "free_stack")], C.byref(nfree))
+    _check(lib, h, st)
+    out["n_free"] = nfree.value
+    out["free_stack"] = out["free_stack"][: nfree.value]
+    return out
+
+
+def sivf_dump_payload(h, n_slabs, slab_size, d, nlist, x32=True, bf16=False, fp8=False,
+                      stream=None) -> dict:
+    lib = load()
+    rows = n_slabs * slab_size
+    out = {"x32": np.zeros((rows, d), np.float32) if x32 else None,
+           "xb16": np.zeros((rows, d), np.uint16) if bf16 else None,
+           "x8": np.zeros((rows, d), np.uint8) if fp8 else None,
+           "inv_scale": np.zeros(nlist, np.float32)}
+    st = lib.sivf_dump_payload(h, _stream(stream), _ptr(out["x32"]), _ptr(out["xb16"]),
+                               _ptr(out["x8"]), _ptr(out["inv_scale"]))
+    _check(lib, h, st)
+    return out
+
+
+def sivf_list_sizes(h, nlist, stream=None) -> np.ndarray:
+    lib = load()
+    out = np.zeros(nlist, np.int32)
+    _check(lib, h, lib.sivf_list_sizes(h, _stream(stream), _ptr(out)))
+    return out
+
+
+def sivf_profile(h, enable: bool) -> None:
+    lib = load()
+    _check(lib, h, lib.sivf_profile(h, int(bool(enable))))
+
+
+def sivf_profile_read(h, kernel: str):
+    """(launches, total_ms) of a kernel group recorded since sivf_profile."""
+    lib = load()
+    n, ms = C.c_int64(0), C.c_double(0.0)
+    _check(lib, h, lib.sivf_profile_read(h, kernel.encode(), C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+# ---------------------------------------------------------- convenience
+class Index:
+    """Owning wrapper: one device index, calls on the torch current stream."""
+
+    def __init__(self, d, nlist, slab_size=32, n_max=1 << 20, n_slabs=None, dir_cap=0,
+                 scan_dtypes=()):
+        self.d, self.nlist, self.slab_size = int(d), int(nlist), int(slab_size)
+        self.n_max = int(n_max)
+        self.n_slabs = int(n_slabs if n_slabs is not None else
+                           2 * (self.n_max // self.slab_size + self.nlist))
+        mask = 0
+        for t in scan_dtypes:
+            mask |= 1 << DTYPES[t]
+        self.scan_dtypes = tuple(scan_dtypes)
+        self.h = sivf_create(self.d, self.nlist, self.slab_size, self.n_max, self.n_slabs,
+                             dir_cap, mask)
+        self.dir_cap = int(dir_cap) if dir_cap else self.n_slabs
+
+    def close(self):
+        if getattr(self, "h", None):
+            sivf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_centroids(self, c, stream=None):
+        sivf_set_centroids(self.h, c, stream)
+
+    def set_list_scales(self, inv_scale, stream=None):
+        sivf_set_list_scales(self.h, inv_scale, stream)
+
+    def reserve(self, max_add=0, max_remove=0, max_queries=0, max_k=0, max_nprobe=0,
+                stream=None):
+        sivf_reserve(self.h, max_add, max_remove, max_queries, max_k, max_nprobe, stream)
+
+    def add(self, ids, x, stream=None, sync=False):
+        return sivf_add(self.h, ids, x, stream, sync)
+
+    def remove(self, ids, stream=None, sync=False):
+        return sivf_remove(self.h, ids, stream, sync)
+
+    def search(self, q, k, nprobe, dtype="fp32", stream=None, dist=None, labels=None):
+        return sivf_search(self.h, q, k, nprobe, DTYPES[dtype], dist, labels, stream)
+
+    def search_with_probes(self, q, k, probes, dtype="fp32", stream=None):
+        return sivf_search_with_probes(self.h, q, k, probes, DTYPES[dtype], None, None,
+                                       stream)
+
+    def assign(self, x, stream=None):
+        return sivf_assign(self.h, x, None, stream)
+
+    def probe(self, q, nprobe, stream=None):
+        return sivf_probe(self.h, q, nprobe, None, stream)
+
+    def sync(self, stream=None):
+        return sivf_sync(self.h, stream)
+
+    def stats(self, stream=None):
+        return sivf_stats(self.h, stream)
+
+    def dump(self, stream=None):
+        return sivf_dump(self.h, self.nlist, self.n_slabs, self.slab_size, self.n_max,
+                         self.dir_cap, stream)
+
+    def list_sizes(self, stream=None):
+        return sivf_list_sizes(self.h, self.nlist, stream)
+
+    def profile(self, enable=True):
+        sivf_profile(self.h, enable)
+
+    def profile_read(self, kernel):
+        return sivf_profile_read(self.h, kernel)
+
+    def dump_payload(self, bf16=False, fp8=False, stream=None):
+        return sivf_dump_payload(self.h, self.n_slabs, self.slab_size, self.d, self.nlist,
+                                 True, bf16, fp8, stream)
+
+
+# ------------------------------------------------------------ host logic
+def slab_header_overhead(d: int, slab_size: int = 32, header_bytes: int = 128,
+                         payload_bytes: int = 4) -> float:
+    """Fraction of slab memory spent on the per-slab header: the space model
+    of Sec. 3.5.3 (metadata amortised over C vectors of d floats)."""
+    return header_bytes / (slab_size * d * payload_bytes)
+
+
+def merge_topk_host(dists, ids, k: int):
+    """Merge per-shard top-k lists (shape [shards, nq, k']) into one top-k by
+    (distance, id), the gather step of the paper's scatter-gather search
+    (Sec. 4.2).  Padding (+inf, -1) sorts last."""
+    d = np.concatenate(list(dists), axis=1)
+    i = np.concatenate(list(ids), axis=1)
+    key_i = np.where(i < 0, np.iinfo(np.int64).max, i)
+    out_d = np.empty((d.shape[0], k), d.dtype)
+    out_i = np.empty((d.shape[0], k), np.int64)
+    for r in range(d.shape[0]):
+        order = np.lexsort((key_i[r], d[r]))[:k]
+        out_d[r] = d[r][order]
+        out_i[r] = i[r][order]
+    return out_d, out_i
