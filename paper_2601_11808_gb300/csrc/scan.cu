@@ -480,11 +480,11 @@ template <int TQ, int C>
 static void launch_scan(sivf_index *ix, const ScanArgs &a, size_t smem, int grid,
                         cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
+    static size_t attr = 48 * 1024;
+    if (smem > attr) {
         cudaFuncSetAttribute(k_scan<TQ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        attr = true;
+                             (int)smem);
+        attr = smem;
     }
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     k_scan<TQ, C><<<grid, SCAN_NT, smem, st>>>(a);
