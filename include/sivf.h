@@ -182,6 +182,33 @@ sivf_status sivf_search(sivf_index *index, const float *q, int64_t nq, int k,
                         int64_t *labels, void *stream);
 
 /*
+ * sivf_search_noalloc -- the FP32 search of sivf_search for callers that
+ * cannot let a library allocate device memory during a call (a serving
+ * process whose memory pool owns the whole device, a latency-critical loop
+ * that must stay out of the allocator).  The paper has no counterpart; it
+ * is an interface addition of this library.
+ *   Same arguments, layouts, results and errors as sivf_search with
+ *   dtype SIVF_FP32; the caller passes q [device], dist [device] and
+ *   labels [device] as there.
+ *   No cudaMalloc or cudaFree happens inside the call: every scratch buffer
+ *   comes from one array of SIVF_NOALLOC_SCRATCH_BYTES bytes declared in
+ *   the library's device code, held by every GPU that loads the library
+ *   until the process exits.  A batch whose scratch does not fit (roughly
+ *   nq * nprobe * k * 12 bytes plus nlist-sized tables) is refused with
+ *   SIVF_E_ARG and a message giving the bytes it needs.
+ *   The first call on a device looks the array's device address up (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture begins.
+ *   All calls share the array and it keeps the last call's contents; calls
+ *   whose work overlaps on the GPU (other streams, other indexes on the
+ *   same device) race on it and must be ordered by the caller.
+ */
+#define SIVF_NOALLOC_SCRATCH_BYTES (32u << 20)
+sivf_status sivf_search_noalloc(sivf_index *index, const float *q, int64_t nq,
+                                int k, int nprobe, float *dist, int64_t *labels,
+                                void *stream);
+
+/*
  * sivf_search_with_probes -- the fine scan and top-k of sivf_search with
  * caller-given lists: probes [device] int32[nq, nprobe] (entries outside
  * [0, nlist) are skipped; a list given twice is scanned once).

@@ -28,7 +28,7 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
     "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
-    "sivf_search_with_probes", "sivf_assign", "sivf_probe", "sivf_sync",
+    "sivf_search_with_probes", "sivf_search_noalloc", "sivf_assign", "sivf_probe", "sivf_sync",
     "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
     "sivf_profile", "sivf_profile_read", "sivf_last_error", "sivf_version",
 ]
@@ -81,6 +81,7 @@ def load(path: str | None = None):
             "sivf_remove": (i32, [vp, vp, i64, vp, C.POINTER(i64)]),
             "sivf_search": (i32, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
             "sivf_search_with_probes": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
+            "sivf_search_noalloc": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
             "sivf_assign": (i32, [vp, vp, i64, vp, vp]),
             "sivf_probe": (i32, [vp, vp, i64, i32, vp, vp]),
             "sivf_sync": (i32, [vp, vp, C.POINTER(i64)]),
@@ -207,6 +208,24 @@ def sivf_search(h, q, k, nprobe, dtype=FP32, dist=None, labels=None, stream=None
         labels = torch.empty((nq, k), dtype=torch.int64, device=q.device)
     st = lib.sivf_search(h, _ptr(q), nq, k, nprobe, int(dtype), _ptr(dist), _ptr(labels),
                          _stream(stream))
+    _check(lib, h, st)
+    return dist, labels
+
+
+def sivf_search_noalloc(h, q, k, nprobe, dist, labels, stream=None):
+    """FP32 search that allocates no device memory during the call: the
+    caller passes the output tensors (dist float32 [nq, k], labels int64
+    [nq, k]); the library takes its scratch from a fixed device array."""
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    _dev(dist, torch.float32)
+    _dev(labels, torch.int64)
+    nq = q.shape[0]
+    if tuple(dist.shape) != (nq, k) or tuple(labels.shape) != (nq, k):
+        raise ValueError("dist and labels must be [nq, k]")
+    st = lib.sivf_search_noalloc(h, _ptr(q), nq, k, nprobe, _ptr(dist), _ptr(labels),
+                                 _stream(stream))
     _check(lib, h, st)
     return dist, labels
 
