@@ -366,7 +366,7 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
     if (plo) *plo = pl;
     size_t parts = (size_t)nq * P * pl.ch * pl.K;
     return coarse_bytes(ix, nq) + (size_t)nq * P * 4 * 3 + (size_t)(L + 1) * 4 * 4 +
-           parts * 12 + 10 * 256;
+           parts * 12 + (size_t)nq * 4 + 11 * 256;
 }
 
 static int64_t query_chunk(const sivf_index *ix, int P, int k)
@@ -487,6 +487,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.qlist = b.take<int32_t>((size_t)m * P);
         sc.part_d = b.take<float>((size_t)m * P * pl.ch * pl.K);
         sc.part_i = b.take<int64_t>((size_t)m * P * pl.ch * pl.K);
+        sc.thr = b.take<float>((size_t)m);
         const int64_t rows = coarse_rows(ix, m);
         float *Dbuf = b.take<float>((size_t)rows * L);
         CUDA_TRY(ix, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));

@@ -40,6 +40,7 @@ struct SearchScratch {
     int32_t *qlist;      // [nq * P] pairs grouped by list (q * P + p)
     float *part_d;       // [nq * P * CH * K]
     int64_t *part_i;     // [nq * P * CH * K]
+    float *thr;          // [nq] shared bound of each query's k-th distance
 };
 struct SearchPlan {
     int tq;              // queries per work item

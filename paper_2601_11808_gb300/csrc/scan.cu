@@ -122,6 +122,7 @@ struct ScanArgs {
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
     float *part_d;
     int64_t *part_i;
+    float *thr;          // [nq] shared upper bound of each query's k-th distance
     // index
     const float *x32;
     const int64_t *ids;
@@ -139,6 +140,14 @@ __host__ __device__ constexpr int scan_next_pow2(int v)
     int p = 1;
     while (p < v) p <<= 1;
     return p;
+}
+
+// Entries per row of the best-K + candidate buffer: the best K, then room
+// for two slabs of candidates (merged by rank, at most 256 entries); for
+// larger K a power of two that the bitonic fallback can sort.
+__host__ __device__ constexpr int scan_buf_len(int K, int C)
+{
+    return K + 2 * C <= 256 ? ((K + 2 * C + 15) & ~15) : scan_next_pow2(K + C);
 }
 
 // shared memory carve-up, identical on host and device
@@ -160,6 +169,166 @@ __host__ __device__ inline ScanSmem scan_smem(int TQ, int C, int d, int M)
     return s;
 }
 
+// Merge one query's candidates into its best list (one warp).  Every
+// element of the union finds its rank by counting the elements that precede
+// it in (distance, id) order -- candidates by a broadcast scan, best entries
+// by binary search -- and then all elements land at once.  best[0, nb) is
+// sorted, cand[K, K + nc) is not; ids are distinct, so ranks are too.
+template <int EPL>
+__device__ __forceinline__ void warp_rank_merge(float *bd, int64_t *bi, int K, int nb, int nc,
+                                                int lane)
+{
+    const int n = nb + nc;
+    float vd[EPL];
+    int64_t vi[EPL];
+    int pos[EPL];
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+        const int e = lane + 32 * t;
+        pos[t] = K;
+        if (e >= n) continue;
+        const int src = e < nb ? e : K + (e - nb);
+        const float dv = bd[src];
+        const int64_t iv = bi[src];
+        vd[t] = dv;
+        vi[t] = iv;
+        int r = 0;
+        for (int j = 0; j < nc; ++j) r += dk_less(bd[K + j], bi[K + j], dv, iv);
+        if (e < nb) {
+            r += e;
+        } else {
+            int lo = 0, hi = nb;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (dk_less(bd[mid], bi[mid], dv, iv)) lo = mid + 1;
+                else hi = mid;
+            }
+            r += lo;
+        }
+        pos[t] = r;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < EPL; ++t)
+        if (pos[t] < K) {
+            bd[pos[t]] = vd[t];
+            bi[pos[t]] = vi[t];
+        }
+    __syncwarp();
+}
+
+// Fallback for large buffers: bitonic sort of all M entries (pads first).
+__device__ void warp_bitonic_merge(float *bd, int64_t *bi, int K, int nb, int nc, int M,
+                                   int lane)
+{
+    for (int e = nb + lane; e < K; e += 32) {
+        bd[e] = INFINITY;
+        bi[e] = -1;
+    }
+    for (int e = K + nc + lane; e < M; e += 32) {
+        bd[e] = INFINITY;
+        bi[e] = -1;
+    }
+    __syncwarp();
+    for (int size = 2; size <= M; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < M / 2; t += 32) {
+                const int pos = 2 * t - (t & (stride - 1));
+                const int par = pos + stride;
+                const bool up = (pos & size) == 0;
+                const float d0 = bd[pos], d1 = bd[par];
+                const int64_t i0 = bi[pos], i1 = bi[par];
+                // pads (id -1) sort after every real entry
+                const bool lt = (i1 >= 0 && i0 < 0) ||
+                                (i1 >= 0 && i0 >= 0 && dk_less(d1, i1, d0, i0));
+                if (lt == up) {
+                    bd[pos] = d1;
+                    bd[par] = d0;
+                    bi[pos] = i1;
+                    bi[par] = i0;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// Ascending (distance, id) bitonic sort of 32*E elements held E per lane
+// (element i = lane + 32 e); pads are (+inf, -1).
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int64_t (&id)[E], int lane)
+{
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+        for (int st = size >> 1; st > 0; st >>= 1)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                const bool up = (i & size) == 0;
+                if (st >= 32) {
+                    const int pe = e ^ (st >> 5);
+                    if (pe > e) {
+                        const bool sw = up ? dk_less(v[pe], id[pe], v[e], id[e])
+                                           : dk_less(v[e], id[e], v[pe], id[pe]);
+                        if (sw) {
+                            const float tv = v[e];
+                            v[e] = v[pe];
+                            v[pe] = tv;
+                            const int64_t ti = id[e];
+                            id[e] = id[pe];
+                            id[pe] = ti;
+                        }
+                    }
+                } else {
+                    const float ov = __shfl_xor_sync(0xffffffffu, v[e], st);
+                    const int64_t oi = __shfl_xor_sync(0xffffffffu, id[e], st);
+                    const bool lower = (lane & st) == 0;
+                    const bool take = (lower == up) ? dk_less(ov, oi, v[e], id[e])
+                                                    : dk_less(v[e], id[e], ov, oi);
+                    if (take) {
+                        v[e] = ov;
+                        id[e] = oi;
+                    }
+                }
+            }
+}
+
+// Direct-form distances of the first RQA row groups of a thread's tile:
+// acc[i][r] = sum_j (q_{i}[j] - x_{r}[j])^2, FP32, j in steps of 4.
+template <int RQA, int RQ, int RX>
+__device__ __forceinline__ void dist_tile(float (&acc)[RQ][RX], const float *__restrict__ qrow,
+                                          const float *__restrict__ xrow, int d, int DP)
+{
+#pragma unroll
+    for (int i = 0; i < RQA; ++i)
+#pragma unroll
+        for (int r = 0; r < RX; ++r) acc[i][r] = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < d; j += 4) {
+        float4 qv[RQA], xv[RX];
+#pragma unroll
+        for (int i = 0; i < RQA; ++i)
+            qv[i] = *reinterpret_cast<const float4 *>(qrow + (size_t)i * 8 * DP + j);
+#pragma unroll
+        for (int r = 0; r < RX; ++r)
+            xv[r] = *reinterpret_cast<const float4 *>(xrow + (size_t)r * 4 * d + j);
+#pragma unroll
+        for (int i = 0; i < RQA; ++i)
+#pragma unroll
+            for (int r = 0; r < RX; ++r) {
+                const float t0 = qv[i].x - xv[r].x, t1 = qv[i].y - xv[r].y;
+                const float t2 = qv[i].z - xv[r].z, t3 = qv[i].w - xv[r].w;
+                float v = acc[i][r];
+                v = fmaf(t0, t0, v);
+                v = fmaf(t1, t1, v);
+                v = fmaf(t2, t2, v);
+                v = fmaf(t3, t3, v);
+                acc[i][r] = v;
+            }
+    }
+}
+
 template <int TQ, int C>
 __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
 {
@@ -172,6 +341,7 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
 
     extern __shared__ __align__(128) unsigned char smem[];
     const int d = a.d, DP = d + 4, M = a.M, K = a.K;
+    const int CB = M - K;  // candidate buffer capacity (>= C)
     const ScanSmem L = scan_smem(TQ, C, d, M);
     float *Qs = reinterpret_cast<float *>(smem + L.qs);
     float *Xs = reinterpret_cast<float *>(smem + L.xs);
@@ -179,16 +349,20 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
     float *BD = reinterpret_cast<float *>(smem + L.bd);
     int64_t *BI = reinterpret_cast<int64_t *>(smem + L.bi);
     unsigned char *misc = smem + L.misc;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);            // [NST]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);  // [NST]
     int *s_item = reinterpret_cast<int *>(misc + 8 * NST);
     int *s_abort = s_item + 1;
-    int *stage_slab = s_item + 2;                                   // [NST]
-    __shared__ int32_t s_qpair[TQ];                                 // pair of each row
-    __shared__ int s_cc[TQ];                                        // candidates per row
+    int *stage_slab = s_item + 2;                         // [NST]
+    __shared__ int32_t s_qpair[TQ];   // (query, probe) pair of each row
+    __shared__ int s_cc[TQ];          // candidates waiting per row
+    __shared__ int s_nb[TQ];          // valid best entries per row
+    __shared__ float s_kd[TQ];        // admission threshold per row
+    __shared__ int64_t s_ki[TQ];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int wq = warp % QW, ws = warp / QW;
     const int qy = lane & 7, sx = lane >> 3;
+    const int64_t NOID = 0x7fffffffffffffffLL;
 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&mbar[s], 1);
@@ -215,6 +389,40 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
         }
     };
 
+    // merge the waiting candidates of row qr (one warp), then refresh the
+    // row's threshold from its own K-th entry and the query's shared bound
+    auto merge_row = [&](int qr) {
+        float *bd = BD + (size_t)qr * M;
+        int64_t *bi = BI + (size_t)qr * M;
+        const int nb = s_nb[qr], nc = s_cc[qr];
+        if (nc > 0) {
+            if (nb + nc <= 128) warp_rank_merge<4>(bd, bi, K, nb, nc, lane);
+            else if (nb + nc <= 256) warp_rank_merge<8>(bd, bi, K, nb, nc, lane);
+            else warp_bitonic_merge(bd, bi, K, nb, nc, M, lane);
+        }
+        const int nb2 = min(K, nb + nc);
+        if (lane == 0) {
+            s_nb[qr] = nb2;
+            s_cc[qr] = 0;
+            float kd = s_kd[qr];
+            int64_t ki = s_ki[qr];
+            const int q = s_qpair[qr] / a.P;
+            if (nb2 == K && dk_less(bd[K - 1], bi[K - 1], kd, ki)) {
+                kd = bd[K - 1];
+                ki = bi[K - 1];
+                atomicMin(reinterpret_cast<int *>(a.thr) + q, __float_as_int(kd));
+            }
+            const float g = __ldcg(a.thr + q);
+            if (g < kd) {
+                kd = g;
+                ki = NOID;
+            }
+            s_kd[qr] = kd;
+            s_ki[qr] = ki;
+        }
+        __syncwarp();
+    };
+
     for (;;) {
         if (tid == 0) *s_item = atomicAdd(&a.ctl->next_item, 1);
         __syncthreads();
@@ -224,23 +432,24 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
         // decode item -> list, query tile, slab chunk
         int lo = 0, hi = a.L;  // largest l with ibase[l] <= item
         while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
+            const int mid = (lo + hi) >> 1;
             if (a.ibase[mid] <= item) lo = mid;
             else hi = mid;
         }
         const int l = lo;
-        const int nc = a.nch[l];
+        const int nc_l = a.nch[l];
         const int rel = item - a.ibase[l];
-        const int tile = rel / nc, chunk = rel % nc;
+        const int tile = rel / nc_l, chunk = rel % nc_l;
         const int mcount = a.lcnt[l];
-        const int m = min(TQ, mcount - tile * TQ);
+        const int r0 = tile * TQ;                     // tiles filled from the front;
+        const int m = min(TQ, mcount - r0);           // the last one skips empty groups
         int ns_total = a.nslabs[l];
         if (ns_total > a.dir_cap) {
             if (tid == 0) atomicOr(a.err, ERR_DIR_BOUND);
             ns_total = (int)a.dir_cap;
         }
-        const int s0 = (int)((int64_t)ns_total * chunk / nc);
-        const int s1 = (int)((int64_t)ns_total * (chunk + 1) / nc);
+        const int s0 = (int)((int64_t)ns_total * chunk / nc_l);
+        const int s1 = (int)((int64_t)ns_total * (chunk + 1) / nc_l);
         const int ns = s1 - s0;
         const int32_t *dirl = a.dir + (size_t)l * a.dir_cap;
 
@@ -251,84 +460,93 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
                 ++g_issue;
             }
         }
-        const int qb = a.loff[l] + tile * TQ;
+        const int qb = a.loff[l] + r0;
         for (int r = tid; r < TQ; r += SCAN_NT) {
-            s_qpair[r] = r < m ? a.qlist[qb + r] : -1;
+            const int pr = r < m ? a.qlist[qb + r] : -1;
+            s_qpair[r] = pr;
             s_cc[r] = 0;
+            s_nb[r] = 0;
+            s_kd[r] = pr >= 0 ? __ldcg(a.thr + pr / a.P) : INFINITY;
+            s_ki[r] = NOID;
         }
         __syncthreads();
         for (int e = tid; e < TQ * (d / 4); e += SCAN_NT) {
-            int r = e / (d / 4), j4 = e % (d / 4);
+            const int r = e / (d / 4), j4 = e % (d / 4);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            int pr = s_qpair[r];
+            const int pr = s_qpair[r];
             if (pr >= 0)
                 v = *reinterpret_cast<const float4 *>(a.q + (size_t)(pr / a.P) * d + 4 * j4);
             *reinterpret_cast<float4 *>(Qs + (size_t)r * DP + 4 * j4) = v;
         }
-        for (int e = tid; e < TQ * M; e += SCAN_NT) {
-            BD[e] = INFINITY;
-            BI[e] = -1;
-        }
         __syncthreads();
 
+        const bool warp_active = wq * 8 * RQ < m;  // some row of this warp is real
         for (int idx = 0; idx < ns; ++idx) {
             const int stage = g_cons % NST;
             const uint32_t parity = (g_cons / NST) & 1u;
             if (!mbar_wait_bounded(&mbar[stage], parity, a.err)) *s_abort = 1;
             ++g_cons;
             const int s = stage_slab[stage];
-            if (s >= 0 && !*s_abort) {
+            if (s >= 0 && warp_active && !*s_abort) {
                 const float *xs = Xs + (size_t)stage * C * d;
                 const int64_t *ib = IDs + (size_t)stage * C;
                 float acc[RQ][RX];
-#pragma unroll
-                for (int i = 0; i < RQ; ++i)
-#pragma unroll
-                    for (int r = 0; r < RX; ++r) acc[i][r] = 0.f;
                 const float *qrow = Qs + (size_t)(wq * 8 * RQ + qy) * DP;
                 const float *xrow = xs + (size_t)(ws * 4 * RX + sx) * d;
-#pragma unroll 2
-                for (int j = 0; j < d; j += 4) {
-                    float4 qv[RQ], xv[RX];
-#pragma unroll
-                    for (int i = 0; i < RQ; ++i)
-                        qv[i] = *reinterpret_cast<const float4 *>(qrow + (size_t)i * 8 * DP + j);
-#pragma unroll
-                    for (int r = 0; r < RX; ++r)
-                        xv[r] = *reinterpret_cast<const float4 *>(xrow + (size_t)r * 4 * d + j);
-#pragma unroll
-                    for (int i = 0; i < RQ; ++i)
-#pragma unroll
-                        for (int r = 0; r < RX; ++r) {
-                            float t0 = qv[i].x - xv[r].x, t1 = qv[i].y - xv[r].y;
-                            float t2 = qv[i].z - xv[r].z, t3 = qv[i].w - xv[r].w;
-                            float v = acc[i][r];
-                            v = fmaf(t0, t0, v);
-                            v = fmaf(t1, t1, v);
-                            v = fmaf(t2, t2, v);
-                            v = fmaf(t3, t3, v);
-                            acc[i][r] = v;
-                        }
-                }
+                // only the row groups that hold queries are computed
+                const int nact = min(RQ, (m - wq * 8 * RQ + 7) / 8);
+                if (nact >= RQ) dist_tile<RQ, RQ, RX>(acc, qrow, xrow, d, DP);
+                else if (nact == 1) dist_tile<1, RQ, RX>(acc, qrow, xrow, d, DP);
+                else if (nact == 2) dist_tile<(RQ >= 2 ? 2 : 1), RQ, RX>(acc, qrow, xrow, d, DP);
+                else dist_tile<(RQ >= 3 ? 3 : 1), RQ, RX>(acc, qrow, xrow, d, DP);
                 uint32_t bw[W];
 #pragma unroll
                 for (int w = 0; w < W; ++w) bw[w] = __ldg(a.bits + (size_t)s * W + w);
+                if (idx == 0) {
+                    // first slab of the tile: every distance goes to the row's
+                    // candidate area, indexed by slot (sorted below)
+#pragma unroll
+                    for (int i = 0; i < RQ; ++i) {
+                        const int qr = wq * 8 * RQ + qy + 8 * i;
+                        if (qr >= m) continue;
+#pragma unroll
+                        for (int r = 0; r < RX; ++r) {
+                            const int slot = ws * 4 * RX + sx + 4 * r;
+                            const bool live = (bw[slot >> 5] >> (slot & 31)) & 1u;
+                            BD[(size_t)qr * M + K + slot] = live ? acc[i][r] : INFINITY;
+                            BI[(size_t)qr * M + K + slot] = live ? ib[slot] : -1;
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int i = 0; i < RQ; ++i) {
                     const int qr = wq * 8 * RQ + qy + 8 * i;
                     if (qr >= m) continue;
-                    const float kd = BD[qr * M + K - 1];
-                    const int64_t ki = BI[qr * M + K - 1];
+                    const float kd = s_kd[qr];
+                    const int64_t ki = s_ki[qr];
 #pragma unroll
                     for (int r = 0; r < RX; ++r) {
                         const int slot = ws * 4 * RX + sx + 4 * r;
                         if (!((bw[slot >> 5] >> (slot & 31)) & 1u)) continue;
                         const float dd = acc[i][r];
                         if (dd < kd || (dd == kd && ib[slot] < ki)) {
-                            int pos = atomicAdd(&s_cc[qr], 1);
-                            BD[qr * M + K + pos] = dd;
-                            BI[qr * M + K + pos] = ib[slot];
+                            const int pos = atomicAdd(&s_cc[qr], 1);
+                            BD[(size_t)qr * M + K + pos] = dd;
+                            BI[(size_t)qr * M + K + pos] = ib[slot];
                         }
+                    }
+                }
+                }
+            } else if (idx == 0) {
+                // an inactive warp or a skipped slab leaves its rows empty
+#pragma unroll
+                for (int i = 0; i < RQ; ++i) {
+                    const int qr = wq * 8 * RQ + qy + 8 * i;
+                    if (qr >= m) continue;
+#pragma unroll
+                    for (int r = 0; r < RX; ++r) {
+                        BD[(size_t)qr * M + K + ws * 4 * RX + sx + 4 * r] = INFINITY;
+                        BI[(size_t)qr * M + K + ws * 4 * RX + sx + 4 * r] = -1;
                     }
                 }
             }
@@ -339,47 +557,59 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
                 issue(g_issue % NST, dirl[s0 + idx + NST]);
                 ++g_issue;
             }
-            // merge candidates of each query into its best K (one warp per
-            // query): bitonic sort of the M entries in shared memory
-            for (int qr = warp; qr < m; qr += SCAN_NT / 32) {
-                const int n_c = s_cc[qr];
-                if (n_c == 0) continue;
-                float *bd = BD + (size_t)qr * M;
-                int64_t *bi = BI + (size_t)qr * M;
-                for (int e = K + n_c + lane; e < M; e += 32) {
-                    bd[e] = INFINITY;
-                    bi[e] = -1;
-                }
-                __syncwarp();
-                for (int size = 2; size <= M; size <<= 1)
-                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                        for (int t = lane; t < M / 2; t += 32) {
-                            int pos = 2 * t - (t & (stride - 1));
-                            int par = pos + stride;
-                            bool up = (pos & size) == 0;
-                            float d0 = bd[pos], d1 = bd[par];
-                            int64_t i0 = bi[pos], i1 = bi[par];
-                            bool gt = dk_less(d1, i1, d0, i0);
-                            if (gt == up) {
-                                bd[pos] = d1;
-                                bd[par] = d0;
-                                bi[pos] = i1;
-                                bi[par] = i0;
-                            }
-                        }
-                        __syncwarp();
+            const bool last = idx + 1 == ns;
+            if (idx == 0) {
+                // exact best K of the first slab of every row: one warp per
+                // row sorts the row's C distances in registers (the slab's
+                // stage is already being refilled: ids come from the row)
+                constexpr int E = C / 32;
+                for (int qr = warp; qr < m; qr += SCAN_NT / 32) {
+                    float v[E];
+                    int64_t id[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int slot = lane + 32 * e;
+                        v[e] = BD[(size_t)qr * M + K + slot];
+                        id[e] = BI[(size_t)qr * M + K + slot];
                     }
-                if (lane == 0) s_cc[qr] = 0;
+                    warp_bitonic_sort<E>(v, id, lane);
+                    const float kd0 = s_kd[qr];
+                    const int64_t ki0 = s_ki[qr];
+                    int nb = 0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int i = lane + 32 * e;
+                        const bool keep = id[e] >= 0 && i < K && dk_less(v[e], id[e], kd0, ki0);
+                        nb += __popc(__ballot_sync(0xffffffffu, keep));
+                        if (keep) {
+                            BD[(size_t)qr * M + i] = v[e];
+                            BI[(size_t)qr * M + i] = id[e];
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        s_nb[qr] = nb;
+                        s_cc[qr] = 0;
+                    }
+                    __syncwarp();
+                    merge_row(qr);  // nothing to merge: refreshes the threshold
+                }
+            } else {
+                // merge rows whose buffer could overflow on the next slab (all
+                // rows after the last slab)
+                for (int qr = warp; qr < m; qr += SCAN_NT / 32)
+                    if (s_cc[qr] > 0 && (last || s_cc[qr] > CB - C)) merge_row(qr);
             }
             __syncthreads();
         }
 
-        // write the best K of each query of the tile
+        // the best K of each row of the tile (padded with (+inf, -1))
         for (int e = tid; e < m * K; e += SCAN_NT) {
-            int r = e / K, j = e % K;
-            int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
-            a.part_d[base + j] = BD[r * M + j];
-            a.part_i[base + j] = BI[r * M + j];
+            const int r = e / K, j = e % K;
+            const int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
+            const bool ok = j < s_nb[r];
+            a.part_d[base + j] = ok ? BD[(size_t)r * M + j] : INFINITY;
+            a.part_i[base + j] = ok ? BI[(size_t)r * M + j] : -1;
         }
         __syncthreads();
     }
@@ -497,7 +727,7 @@ SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
     const int C = ix->C, d = ix->d;
     const double pairs_per_list = (double)nq * P / ix->nlist;
     int tq = pairs_per_list >= 48 ? 64 : pairs_per_list >= 24 ? 32 : pairs_per_list >= 12 ? 16 : 8;
-    const int M = scan_next_pow2(K + C);
+    const int M = scan_buf_len(K, C);
     while (tq > 8 && scan_smem(tq, C, d, M).total > 220 * 1024) tq >>= 1;
     pl.tq = tq;
     pl.K = K;
@@ -515,7 +745,7 @@ SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
 
 bool scan_fits(const sivf_index *ix, int K)
 {
-    return scan_smem(8, ix->C, ix->d, scan_next_pow2(K + ix->C)).total <= 220 * 1024;
+    return scan_smem(8, ix->C, ix->d, scan_buf_len(K, ix->C)).total <= 220 * 1024;
 }
 
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
@@ -523,6 +753,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
 {
     const int L = ix->nlist;
     cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
+    cudaMemsetAsync(s.thr, 0x7f, sizeof(float) * nq, st);  // 3.4e38: no bound yet
     int64_t n = nq * P;
     int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     const int tg = prof_begin(ix, PROF_GROUP, 3, st);
@@ -539,7 +770,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
     a.nq = nq;
     a.P = P;
     a.K = pl.K;
-    a.M = scan_next_pow2(pl.K + ix->C);
+    a.M = scan_buf_len(pl.K, ix->C);
     a.CH = pl.ch;
     a.qlist = s.qlist;
     a.loff = s.loff;
@@ -548,6 +779,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
     a.nch = s.nch;
     a.part_d = s.part_d;
     a.part_i = s.part_i;
+    a.thr = s.thr;
     a.x32 = ix->x32;
     a.ids = ix->ids;
     a.bits = ix->bits;
