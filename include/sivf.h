@@ -67,7 +67,8 @@ typedef struct {
     int64_t n_slabs;     /* slabs in the pre-allocated pool (the paper's S)  */
     int64_t dir_cap;     /* most slabs one list may hold (0 = n_slabs)       */
     uint32_t scan_dtypes;/* extra payload copies: bit (1<<SIVF_BF16) and/or
-                            bit (1<<SIVF_FP8E4M3); the FP32 copy always exists */
+                            bit (1<<SIVF_FP8E4M3), which need d % 16 == 0;
+                            the FP32 copy always exists                     */
 } sivf_config;
 
 typedef struct {
@@ -174,12 +175,26 @@ sivf_status sivf_remove(sivf_index *index, const int64_t *ids, int64_t n,
  *   min(nlist, 1024).
  * dtype SIVF_FP32 scans the FP32 payload with direct-form distances.
  * SIVF_BF16 / SIVF_FP8E4M3 scan the reduced copy (which must have been
- * enabled at create) on tensor cores, keep the best 4k candidates per query
- * and re-rank them with exact FP32 distances.
+ * enabled at create; d % 16 == 0) on tensor cores, keep the best 4k
+ * candidates per query (k <= 32) and re-rank them with exact FP32
+ * direct-form distances from the FP32 payload.
  */
 sivf_status sivf_search(sivf_index *index, const float *q, int64_t nq, int k,
                         int nprobe, sivf_scan_dtype dtype, float *dist,
                         int64_t *labels, void *stream);
+
+/*
+ * sivf_search_candidates -- the first stage of a reduced-precision search
+ * alone: the `kc` best candidates of each query by the reduced-precision
+ * distance ||q||^2 + ||x||^2 - 2 s q^.x^ over the nprobe nearest lists
+ * (q^, x^ the BF16 / FP8 roundings; FP32 accumulation), ascending, ties to
+ * the lower slot.  dist [device] float32[nq, kc] holds those approximate
+ * distances, labels [device] int64[nq, kc] the ids; padding (+inf, -1).
+ * 1 <= kc <= 128; dtype SIVF_BF16 or SIVF_FP8E4M3.
+ */
+sivf_status sivf_search_candidates(sivf_index *index, const float *q, int64_t nq,
+                                   int kc, int nprobe, sivf_scan_dtype dtype,
+                                   float *dist, int64_t *labels, void *stream);
 
 /*
  * sivf_search_noalloc -- the FP32 search of sivf_search for callers that

@@ -224,7 +224,8 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
         !(C == 32 || C == 64 || C == 128) || cfg->n_max < 1 || cfg->n_max > ((int64_t)1 << 40) ||
         cfg->n_slabs < 1 || cfg->n_slabs > INT32_MAX || cfg->dir_cap < 0 ||
         (cfg->scan_dtypes & ~((1u << SIVF_BF16) | (1u << SIVF_FP8E4M3))) ||
-        (size_t)2 * C * d * 4 > kMaxStageBytes)
+        (size_t)2 * C * d * 4 > kMaxStageBytes ||
+        (cfg->scan_dtypes && d % 16))
         return SIVF_E_ARG;
     sivf_index *ix = new (std::nothrow) sivf_index();
     if (!ix) return SIVF_E_NOMEM;
@@ -288,6 +289,8 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
     k_init_pool<<<(unsigned)std::min<size_t>((S + 255) / 256, 152 * 64), 256>>>(
         ix->free_list, ix->meta, (int64_t)S);
     if (cudaDeviceSynchronize() != cudaSuccess) return bad(SIVF_E_CUDA);
+    if ((ix->xb16 || ix->x8) && !tc_make_maps(ix)) return bad(SIVF_E_CUDA);
+    ix->tmaps_ready = true;
     *out = ix;
     return SIVF_OK;
 }
@@ -365,8 +368,8 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
     SearchPlan pl = plan_search(ix, nq, P, k);
     if (plo) *plo = pl;
     size_t parts = (size_t)nq * P * pl.ch * pl.K;
-    return coarse_bytes(ix, nq) + (size_t)nq * P * 4 * 3 + (size_t)(L + 1) * 4 * 4 +
-           parts * 12 + (size_t)nq * 4 + 11 * 256;
+    return coarse_bytes(ix, nq) + (size_t)nq * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
+           parts * 12 + (size_t)nq * 4 + (size_t)nq * pl.K * 12 + 14 * 256;
 }
 
 static int64_t query_chunk(const sivf_index *ix, int P, int k)
@@ -452,28 +455,62 @@ sivf_status sivf_remove(sivf_index *ix, const int64_t *ids, int64_t n, void *str
     return SIVF_OK;
 }
 
+// plan of the reduced-precision scan: tiles of 64 queries, K' candidates
+static SearchPlan plan_tc(const sivf_index *ix, int64_t nq, int P, int Kc)
+{
+    SearchPlan pl;
+    pl.tq = 64;
+    pl.K = Kc;
+    const double touched = std::min<double>(ix->nlist, (double)nq * P);
+    const double tiles = std::max(touched, (double)nq * P / 64);
+    const double want = 4.0 * 152;
+    int ch = tiles >= want ? 1 : (int)std::min<double>(kMaxChunks, std::ceil(want / tiles));
+    ch = std::min(ch, std::max(1, 2048 / P));
+    pl.ch = std::max(1, ch);
+    pl.slabs_per_chunk = 4;
+    return pl;
+}
+
+// reduced-precision candidates: the re-rank depth K' = 4k, at most 128
+static int rerank_depth(int k) { return std::min(128, 4 * k); }
+
 static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k, int nprobe,
                                const int32_t *probes_in, sivf_scan_dtype dtype, float *dist,
-                               int64_t *labels, void *stream)
+                               int64_t *labels, void *stream, int cand_only = 0)
 {
     if (!ix) return SIVF_E_ARG;
     if (nq < 0 || k < 1 || k > kMaxK || nprobe < 1 ||
         (!probes_in && (nprobe > ix->nlist || nprobe > kMaxK)) ||
         (probes_in && nprobe > kMaxK) || (nq > 0 && (!q || !dist || !labels)))
         return fail(ix, SIVF_E_ARG, "bad search arguments");
-    if (dtype != SIVF_FP32) return fail(ix, SIVF_E_ARG, "scan dtype not available");
+    if (dtype != SIVF_FP32 && dtype != SIVF_BF16 && dtype != SIVF_FP8E4M3)
+        return fail(ix, SIVF_E_ARG, "unknown scan dtype");
+    const bool tc = dtype != SIVF_FP32;
+    if (tc && ((dtype == SIVF_BF16 && !ix->xb16) || (dtype == SIVF_FP8E4M3 && !ix->x8)))
+        return fail(ix, SIVF_E_ARG, "that reduced-precision copy was not enabled at create");
+    const int Kc = tc ? (cand_only ? k : rerank_depth(k)) : k;
+    if (tc && (4 * k > 128 && !cand_only)) return fail(ix, SIVF_E_ARG, "k > 32 for a reduced-precision scan");
+    if (tc && (Kc > 128 || !tc_fits(ix, Kc)))
+        return fail(ix, SIVF_E_ARG, "k too large for the reduced-precision scan");
     if (!probes_in && !ix->have_centroids) return fail(ix, SIVF_E_STATE, "set_centroids first");
     sivf_status st = check_health(ix);
     if (st) return st;
     if (nq == 0) return SIVF_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int P = nprobe, L = ix->nlist;
-    if (!scan_fits(ix, k)) return fail(ix, SIVF_E_ARG, "k too large for this slab shape");
-    const int64_t qc = query_chunk(ix, P, k);
+    if (!tc && !scan_fits(ix, k)) return fail(ix, SIVF_E_ARG, "k too large for this slab shape");
+    const int64_t qc = query_chunk(ix, P, std::max(k, Kc));
     for (int64_t q0 = 0; q0 < nq; q0 += qc) {
         const int64_t m = std::min(qc, nq - q0);
         SearchPlan pl;
-        size_t need = search_bytes(ix, m, k, P, &pl);
+        size_t need = search_bytes(ix, m, Kc, P, &pl);
+        if (tc) {
+            pl = plan_tc(ix, m, P, Kc);
+            need = std::max(need, coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 +
+                                      (size_t)(L + 1) * 4 * 4 +
+                                      (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 +
+                                      (size_t)m * pl.K * 12 + 14 * 256);
+        }
         Ctx *c;
         if ((st = get_ctx(ix, stream, need, &c))) return st;
         Bump b{c->scratch};
@@ -485,9 +522,12 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.nch = b.take<int32_t>(L);
         sc.prank = b.take<int32_t>((size_t)m * P);
         sc.qlist = b.take<int32_t>((size_t)m * P);
+        sc.pnch = b.take<int32_t>((size_t)m * P);
         sc.part_d = b.take<float>((size_t)m * P * pl.ch * pl.K);
         sc.part_i = b.take<int64_t>((size_t)m * P * pl.ch * pl.K);
         sc.thr = b.take<float>((size_t)m);
+        float *cand_d = b.take<float>((size_t)m * pl.K);
+        int64_t *cand_s = b.take<int64_t>((size_t)m * pl.K);
         const int64_t rows = coarse_rows(ix, m);
         float *Dbuf = b.take<float>((size_t)rows * L);
         CUDA_TRY(ix, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));
@@ -497,8 +537,31 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
                                          cudaMemcpyDeviceToDevice, s));
         else
             coarse_topP(ix, qq, m, P, probes, Dbuf, rows, s);
-        scan_lists(ix, qq, m, P, probes, probes_in != nullptr, pl, sc, s);
-        merge_topk(ix, m, P, probes, pl, sc, k, dist + q0 * k, labels + q0 * k, s);
+        if (!tc) {
+            scan_lists(ix, qq, m, P, probes, probes_in != nullptr, pl, sc, s);
+            merge_topk(ix, m, P, probes, pl, sc, k, dist + q0 * k, labels + q0 * k, s);
+        } else {
+            // phase 1: every query's nearest list alone sets a tight bound on
+            // its K'-th distance; phase 2 scans the other lists under it
+            const int esz = dtype == SIVF_BF16 ? 2 : 1;
+            const int64_t sb = (int64_t)ix->C * ix->d * esz;
+            CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
+            const int split = P > 1 ? 1 : P;
+            group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
+            scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+            if (split < P) {
+                group_pairs(ix, m, P, split, P, probes, probes_in != nullptr, pl, sc, sb, s);
+                scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+            }
+            if (cand_only) {
+                merge_topk(ix, m, P, probes, pl, sc, Kc, dist + q0 * k,
+                           reinterpret_cast<int64_t *>(labels + q0 * k), s);
+                slots_to_ids(ix, labels + q0 * k, m * k, s);
+            } else {
+                merge_topk(ix, m, P, probes, pl, sc, Kc, cand_d, cand_s, s);
+                rerank(ix, qq, m, Kc, cand_d, cand_s, k, dist + q0 * k, labels + q0 * k, s);
+            }
+        }
         CUDA_TRY(ix, cudaGetLastError());
     }
     return SIVF_OK;
@@ -508,6 +571,14 @@ sivf_status sivf_search(sivf_index *ix, const float *q, int64_t nq, int k, int n
                         sivf_scan_dtype dtype, float *dist, int64_t *labels, void *stream)
 {
     return search_impl(ix, q, nq, k, nprobe, nullptr, dtype, dist, labels, stream);
+}
+
+sivf_status sivf_search_candidates(sivf_index *ix, const float *q, int64_t nq, int kc,
+                                   int nprobe, sivf_scan_dtype dtype, float *dist,
+                                   int64_t *labels, void *stream)
+{
+    if (dtype == SIVF_FP32) return fail(ix, SIVF_E_ARG, "candidates need a reduced-precision dtype");
+    return search_impl(ix, q, nq, kc, nprobe, nullptr, dtype, dist, labels, stream, 1);
 }
 
 sivf_status sivf_search_with_probes(sivf_index *ix, const float *q, int64_t nq, int k,
@@ -632,7 +703,7 @@ sivf_status sivf_profile_read(sivf_index *ix, const char *kernel, int64_t *launc
 {
     if (!ix || !kernel) return fail(ix, SIVF_E_ARG, "null argument");
     static const char *names[PROF_NKIND] = {"coarse", "insert", "remove", "group", "scan",
-                                            "merge"};
+                                            "merge", "rerank"};
     int kind = -1;
     for (int k = 0; k < PROF_NKIND; ++k)
         if (!strcmp(kernel, names[k])) kind = k;

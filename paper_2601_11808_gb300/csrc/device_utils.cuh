@@ -122,4 +122,46 @@ __device__ __forceinline__ float fkey_inv(uint32_t k)
     return __uint_as_float(u);
 }
 
+// Ascending (distance, id) bitonic sort of 32*E elements held E per lane
+// (element i = lane + 32 e); pads are (+inf, -1).
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int64_t (&id)[E], int lane)
+{
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+        for (int st = size >> 1; st > 0; st >>= 1)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                const bool up = (i & size) == 0;
+                if (st >= 32) {
+                    const int pe = e ^ (st >> 5);
+                    if (pe > e) {
+                        const bool sw = up ? dk_less(v[pe], id[pe], v[e], id[e])
+                                           : dk_less(v[e], id[e], v[pe], id[pe]);
+                        if (sw) {
+                            const float tv = v[e];
+                            v[e] = v[pe];
+                            v[pe] = tv;
+                            const int64_t ti = id[e];
+                            id[e] = id[pe];
+                            id[pe] = ti;
+                        }
+                    }
+                } else {
+                    const float ov = __shfl_xor_sync(0xffffffffu, v[e], st);
+                    const int64_t oi = __shfl_xor_sync(0xffffffffu, id[e], st);
+                    const bool lower = (lane & st) == 0;
+                    const bool take = (lower == up) ? dk_less(ov, oi, v[e], id[e])
+                                                    : dk_less(v[e], id[e], ov, oi);
+                    if (take) {
+                        v[e] = ov;
+                        id[e] = oi;
+                    }
+                }
+            }
+}
+
 }  // namespace sivf

@@ -41,6 +41,7 @@ struct SearchScratch {
     float *part_d;       // [nq * P * CH * K]
     int64_t *part_i;     // [nq * P * CH * K]
     float *thr;          // [nq] shared bound of each query's k-th distance
+    int32_t *pnch;       // [nq * P] slab chunks scanned for each pair (0: none)
 };
 struct SearchPlan {
     int tq;              // queries per work item
@@ -52,8 +53,20 @@ SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K);
 bool scan_fits(const sivf_index *ix, int K);   // shared memory for k = K
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
+void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_t *probes,
+                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, int64_t slab_bytes,
+                 cudaStream_t st);
 void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
                 const SearchPlan &pl, const SearchScratch &s, int k, float *dist,
                 int64_t *labels, cudaStream_t st);
+
+// ---- reduced-precision scan + re-rank (scan_tc.cu)
+bool tc_make_maps(sivf_index *ix);
+bool tc_fits(const sivf_index *ix, int Kc);
+void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
+                   const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
+void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);
+void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
+            const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
 
 }  // namespace sivf

@@ -19,17 +19,20 @@
 namespace sivf {
 
 // ------------------------------------------------------ grouping by list
-__global__ void k_srch_hist(const int32_t *__restrict__ probes, int64_t nq, int P, int L,
-                            bool dedupe, int32_t *__restrict__ lcnt,
+// pairs (q, p) with p in [p0, p1): rank of each pair inside its list group
+__global__ void k_srch_hist(const int32_t *__restrict__ probes, int64_t nq, int P, int p0,
+                            int p1, int L, bool dedupe, int32_t *__restrict__ lcnt,
                             int32_t *__restrict__ prank)
 {
-    int64_t n = nq * P;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int l = probes[e];
+    const int np = p1 - p0;
+    const int64_t n = nq * np;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = (t / np) * P + p0 + t % np;
+        const int l = probes[e];
         bool ok = l >= 0 && l < L;
         if (ok && dedupe) {
-            int64_t q0 = (e / P) * P;
+            const int64_t q0 = (e / P) * P;
             for (int64_t f = q0; f < e; ++f)
                 if (probes[f] == l) {
                     ok = false;
@@ -96,18 +99,30 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
         ibase[L] = sb[1023];
         ctl->nitems = sb[1023];
         ctl->nscan = sa[1023];
+        ctl->next_item = 0;
     }
 }
 
-__global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, int P,
-                               const int32_t *__restrict__ prank,
-                               const int32_t *__restrict__ loff, int32_t *__restrict__ qlist)
+// pairs grouped by list; pnch = slab chunks the pair's list is split into
+// (0: the pair is not scanned)
+__global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, int P, int p0,
+                               int p1, const int32_t *__restrict__ prank,
+                               const int32_t *__restrict__ loff, const int32_t *__restrict__ nch,
+                               int32_t *__restrict__ qlist, int32_t *__restrict__ pnch)
 {
-    int64_t n = nq * P;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int r = prank[e];
-        if (r >= 0) qlist[loff[probes[e]] + r] = (int32_t)e;
+    const int np = p1 - p0;
+    const int64_t n = nq * np;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = (t / np) * P + p0 + t % np;
+        const int r = prank[e];
+        if (r >= 0) {
+            const int l = probes[e];
+            qlist[loff[l] + r] = (int32_t)e;
+            pnch[e] = nch[l];
+        } else {
+            pnch[e] = 0;
+        }
     }
 }
 
@@ -250,48 +265,6 @@ __device__ void warp_bitonic_merge(float *bd, int64_t *bi, int K, int nb, int nc
             }
             __syncwarp();
         }
-}
-
-// Ascending (distance, id) bitonic sort of 32*E elements held E per lane
-// (element i = lane + 32 e); pads are (+inf, -1).
-template <int E>
-__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int64_t (&id)[E], int lane)
-{
-    constexpr int N = 32 * E;
-#pragma unroll
-    for (int size = 2; size <= N; size <<= 1)
-#pragma unroll
-        for (int st = size >> 1; st > 0; st >>= 1)
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane + 32 * e;
-                const bool up = (i & size) == 0;
-                if (st >= 32) {
-                    const int pe = e ^ (st >> 5);
-                    if (pe > e) {
-                        const bool sw = up ? dk_less(v[pe], id[pe], v[e], id[e])
-                                           : dk_less(v[e], id[e], v[pe], id[pe]);
-                        if (sw) {
-                            const float tv = v[e];
-                            v[e] = v[pe];
-                            v[pe] = tv;
-                            const int64_t ti = id[e];
-                            id[e] = id[pe];
-                            id[pe] = ti;
-                        }
-                    }
-                } else {
-                    const float ov = __shfl_xor_sync(0xffffffffu, v[e], st);
-                    const int64_t oi = __shfl_xor_sync(0xffffffffu, id[e], st);
-                    const bool lower = (lane & st) == 0;
-                    const bool take = (lower == up) ? dk_less(ov, oi, v[e], id[e])
-                                                    : dk_less(v[e], id[e], ov, oi);
-                    if (take) {
-                        v[e] = ov;
-                        id[e] = oi;
-                    }
-                }
-            }
 }
 
 // Direct-form distances of the first RQA row groups of a thread's tile:
@@ -626,9 +599,7 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
 constexpr int MERGE_NT = 128;
 constexpr int MERGE_RUNS_PER_LANE = 64;
 
-__global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ probes,
-                                                    const int32_t *__restrict__ prank,
-                                                    const int32_t *__restrict__ nch, int64_t nq,
+__global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ pnch, int64_t nq,
                                                     int P, int CH, int K, int k,
                                                     const float *__restrict__ part_d,
                                                     const int64_t *__restrict__ part_i,
@@ -645,7 +616,7 @@ __global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ 
     const int R = P * CH;
     for (int r = lane; r < R && nrun < MERGE_RUNS_PER_LANE; r += 32) {
         int p = r / CH, c = r % CH;
-        bool ok = prank[q * P + p] >= 0 && c < nch[probes[q * P + p]];
+        bool ok = c < pnch[q * P + p];
         cur[nrun++] = ok ? 0 : K;
     }
     auto head = [&](int j, float &hd, int64_t &hi) {
@@ -748,22 +719,30 @@ bool scan_fits(const sivf_index *ix, int K)
     return scan_smem(8, ix->C, ix->d, scan_buf_len(K, ix->C)).total <= 220 * 1024;
 }
 
+void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_t *probes,
+                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, int64_t slab_bytes,
+                 cudaStream_t st)
+{
+    const int L = ix->nlist;
+    cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
+    const int64_t n = nq * (p1 - p0);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+    const int tg = prof_begin(ix, PROF_GROUP, 3, st);
+    k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
+    k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
+                                    pl.slabs_per_chunk, slab_bytes, s.loff, s.ibase, s.nch,
+                                    ix->ctl, ix->stat);
+    k_srch_scatter<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
+                                      s.pnch);
+    prof_end(ix, tg, st);
+}
+
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st)
 {
     const int L = ix->nlist;
-    cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
     cudaMemsetAsync(s.thr, 0x7f, sizeof(float) * nq, st);  // 3.4e38: no bound yet
-    int64_t n = nq * P;
-    int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-    const int tg = prof_begin(ix, PROF_GROUP, 3, st);
-    k_srch_hist<<<std::max(g, 1), 256, 0, st>>>(probes, nq, P, L, dedupe, s.lcnt, s.prank);
-    const int64_t slab_bytes = (int64_t)ix->C * (ix->d * 4 + 8);
-    k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
-                                    pl.slabs_per_chunk, slab_bytes, s.loff, s.ibase, s.nch,
-                                    ix->ctl, ix->stat);
-    k_srch_scatter<<<std::max(g, 1), 256, 0, st>>>(probes, nq, P, s.prank, s.loff, s.qlist);
-    prof_end(ix, tg, st);
+    group_pairs(ix, nq, P, 0, P, probes, dedupe, pl, s, (int64_t)ix->C * (ix->d * 4 + 8), st);
 
     ScanArgs a;
     a.q = q;
@@ -810,8 +789,8 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
     int64_t warps = nq;
     int64_t blocks = (warps * 32 + MERGE_NT - 1) / MERGE_NT;
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
-    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(probes, s.prank, s.nch, nq, P, pl.ch, pl.K, k,
-                                                  s.part_d, s.part_i, dist, labels);
+    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(s.pnch, nq, P, pl.ch, pl.K, k, s.part_d,
+                                                  s.part_i, dist, labels);
     prof_end(ix, tok, st);
 }
 

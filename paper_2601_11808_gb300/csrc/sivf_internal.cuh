@@ -69,7 +69,7 @@ struct PlanEntry {       // per list touched by an insert batch
 
 // Kernel groups timed by the profiler (sivf_profile / sivf_profile_read).
 enum ProfKind { PROF_COARSE = 0, PROF_INSERT, PROF_REMOVE, PROF_GROUP, PROF_SCAN,
-                PROF_MERGE, PROF_NKIND };
+                PROF_MERGE, PROF_RERANK, PROF_NKIND };
 
 struct ProfEvent {
     int kind;
@@ -112,6 +112,10 @@ struct sivf_index {
     int32_t *list_live;            // [nlist] live vectors per list
     int32_t *dir;                  // [nlist, dir_cap] slabs of each list
     float *inv_scale8;             // [nlist] FP8 inverse scale
+    // TMA descriptors (CUtensorMap, 128 bytes) of the BF16 / FP8 copies
+    alignas(64) unsigned char tmap_bf16[128];
+    alignas(64) unsigned char tmap_fp8[128];
+    bool tmaps_ready;
 
     // address translation table (Sec. 3.4)
     int64_t *att;                  // [n_max] (slab << 32) | slot, or -1

@@ -28,7 +28,8 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
     "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
-    "sivf_search_with_probes", "sivf_search_noalloc", "sivf_assign", "sivf_probe", "sivf_sync",
+    "sivf_search_with_probes", "sivf_search_noalloc", "sivf_search_candidates",
+    "sivf_assign", "sivf_probe", "sivf_sync",
     "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
     "sivf_profile", "sivf_profile_read", "sivf_last_error", "sivf_version",
 ]
@@ -82,6 +83,7 @@ def load(path: str | None = None):
             "sivf_search": (i32, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
             "sivf_search_with_probes": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
             "sivf_search_noalloc": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
+            "sivf_search_candidates": (i32, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
             "sivf_assign": (i32, [vp, vp, i64, vp, vp]),
             "sivf_probe": (i32, [vp, vp, i64, i32, vp, vp]),
             "sivf_sync": (i32, [vp, vp, C.POINTER(i64)]),
@@ -208,6 +210,21 @@ def sivf_search(h, q, k, nprobe, dtype=FP32, dist=None, labels=None, stream=None
         labels = torch.empty((nq, k), dtype=torch.int64, device=q.device)
     st = lib.sivf_search(h, _ptr(q), nq, k, nprobe, int(dtype), _ptr(dist), _ptr(labels),
                          _stream(stream))
+    _check(lib, h, st)
+    return dist, labels
+
+
+def sivf_search_candidates(h, q, kc, nprobe, dtype=BF16, stream=None):
+    """The kc best reduced-precision candidates of each query (approximate
+    distances and ids), before the FP32 re-rank."""
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    nq = q.shape[0]
+    dist = torch.empty((nq, kc), dtype=torch.float32, device=q.device)
+    labels = torch.empty((nq, kc), dtype=torch.int64, device=q.device)
+    st = lib.sivf_search_candidates(h, _ptr(q), nq, kc, nprobe, int(dtype), _ptr(dist),
+                                    _ptr(labels), _stream(stream))
     _check(lib, h, st)
     return dist, labels
 
@@ -387,6 +404,9 @@ class Index:
 
     def search(self, q, k, nprobe, dtype="fp32", stream=None, dist=None, labels=None):
         return sivf_search(self.h, q, k, nprobe, DTYPES[dtype], dist, labels, stream)
+
+    def search_candidates(self, q, kc, nprobe, dtype="bf16", stream=None):
+        return sivf_search_candidates(self.h, q, kc, nprobe, DTYPES[dtype], stream)
 
     def search_with_probes(self, q, k, probes, dtype="fp32", stream=None):
         return sivf_search_with_probes(self.h, q, k, probes, DTYPES[dtype], None, None,
