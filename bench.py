@@ -6,6 +6,9 @@ insert 10,000 new vectors (coarse assignment + slot claim + append), delete
 the 10,000 oldest (address-table lookup, bit clear, slab reclaim), and search
 10,000 fresh queries (coarse probe selection, list scan, top-10) at the
 smallest nprobe of {8, 16, 32, 64, 128} whose recall@10 reaches 0.95.
+Each scan form is measured (FP32 direct form; BF16 and FP8 scans on the
+tensor cores with an FP32 re-rank of the best 4k); the headline is the
+fastest form that reaches recall 0.95, and every form is reported.
 
 Prints one JSON line.  `value` is queries per second of whole steps (each
 step also absorbs its insert and delete batch); the components give search
@@ -51,6 +54,9 @@ def parse():
     p.add_argument("--nprobe", type=int, default=0, help="0 = calibrate for recall 0.95")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--forms", default="fp32,bf16,fp8",
+                   help="scan forms to measure; the fastest that reaches recall 0.95 "
+                        "is the headline")
     return p.parse_args()
 
 
@@ -177,8 +183,8 @@ def run_reference(args):
     nprobe = args.nprobe or 8
     n_ins, n_del, n_q = 1000, 1000, 200
     steps = args.steps + args.warmup
-    cent, X, Q = make_data(w, 2, 0, 0)
-    n_max = w.window + 4 * w.step
+    cent, X, Q = make_data(w, (steps * n_ins) // w.step + 1, 0, 0)
+    n_max = w.window + (steps * n_ins // w.step + 3) * w.step
     t0 = time.time()
     r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps)
     wall = time.time() - t0
@@ -205,11 +211,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_of(w, nprobe):
+def config_of(w, nprobe, form="fp32"):
     return {"workload": w.name, "window": w.window, "d": w.d, "nlist": w.nlist,
             "slab": w.slab_size, "insert_per_step": w.step, "delete_per_step": w.step,
             "queries_per_step": w.n_queries, "k": w.k, "nprobe": nprobe,
-            "scan_dtype": "fp32",
+            "scan_dtype": form if form == "fp32" else f"{form} scan + fp32 re-rank of 4k",
             "l2": "inputs larger than L2: 512 MB index, fresh insert/query batches "
                   "every step",
             "parallelism": "replicas"}
@@ -231,8 +237,9 @@ def main():
     from paper_2601_11808_gb300 import sivf
 
     w = W.CONFIGS[args.workload]
+    forms = [f for f in args.forms.split(",") if f]
     K, Wm = args.steps, args.warmup
-    n_steps = Wm + 2 * K + 1
+    n_steps = Wm + (len(forms) + 1) * K + 1
     n_calib = 1000
     cent, X, Q = make_data(w, n_steps, n_calib, rank)
     n_max = w.window + (n_steps + 2) * w.step
@@ -240,29 +247,32 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S)
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S,
+                   scan_dtypes=tuple(f for f in forms if f != "fp32"))
     g.set_centroids(torch.from_numpy(cent).to(dev))
     for b in range(0, w.window, 100_000):
         g.add(torch.from_numpy(W.stream_ids(b, 100_000, n_max)).to(dev),
               torch.from_numpy(X[b:b + 100_000]).to(dev))
     g.sync()
 
-    # nprobe for recall@10 >= 0.95 against exact search (nprobe = nlist)
+    # per form: the smallest nprobe with recall@10 >= 0.95 against exact
+    # search (nprobe = nlist, FP32)
     Qc = torch.from_numpy(Q[-n_calib:]).to(dev)
     _, gt = g.search(Qc, w.k, w.nlist)
     gt = gt.cpu().numpy()
-    recalls = {}
-    nprobe = args.nprobe
-    for P in ([args.nprobe] if args.nprobe else NPROBES):
-        _, got = g.search(Qc, w.k, P)
-        got = got.cpu().numpy()
-        recalls[P] = float(np.mean([len(set(a) & set(b)) / w.k
+    calib = {}
+    for f in forms:
+        rec, chosen = {}, None
+        for P in ([args.nprobe] if args.nprobe else NPROBES):
+            _, got = g.search(Qc, w.k, P, f)
+            got = got.cpu().numpy()
+            rec[P] = float(np.mean([len(set(a) & set(b)) / w.k
                                     for a, b in zip(got.tolist(), gt.tolist())]))
-        if not nprobe and recalls[P] >= 0.95:
-            nprobe = P
-    nprobe = nprobe or NPROBES[-1]
+            if chosen is None and rec[P] >= 0.95:
+                chosen = P
+        calib[f] = {"recall_by_nprobe": rec, "nprobe": chosen or NPROBES[-1],
+                    "meets_target": chosen is not None}
 
-    # step inputs resident in HBM before the timed region
     def step_inputs(s):
         new = w.window + s * w.step
         return (torch.from_numpy(W.stream_ids(new, w.step, n_max)).to(dev),
@@ -272,10 +282,9 @@ def main():
 
     dist_out = torch.empty((w.n_queries, w.k), dtype=torch.float32, device=dev)
     lab_out = torch.empty((w.n_queries, w.k), dtype=torch.int64, device=dev)
-    g.reserve(w.step, w.step, w.n_queries, w.k, nprobe)
-    inputs = [step_inputs(s) for s in range(Wm + K)]
+    g.reserve(w.step, w.step, w.n_queries, w.k, max(c["nprobe"] for c in calib.values()))
 
-    def run_step(ins_ids, ins_x, del_ids, q, ev=None):
+    def run_step(form, nprobe, ins_ids, ins_x, del_ids, q, ev=None):
         if ev:
             ev[0].record(stream)
         g.add(ins_ids, ins_x)
@@ -284,105 +293,132 @@ def main():
         g.remove(del_ids)
         if ev:
             ev[2].record(stream)
-        g.search(q, w.k, nprobe, dist=dist_out, labels=lab_out)
+        g.search(q, w.k, nprobe, form, dist=dist_out, labels=lab_out)
         if ev:
             ev[3].record(stream)
 
+    step_no = 0
     for s in range(Wm):
-        run_step(*inputs[s])
+        for f in forms:
+            run_step(f, calib[f]["nprobe"], *step_inputs(step_no))
+        step_no += 1
     torch.cuda.synchronize()
     g.sync()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    st0 = g.stats()
-    launches0 = g.profile_read("all")[0]
-    g.profile(True)
-    clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for s in range(K):
-        run_step(*inputs[Wm + s], ev=evs[s])
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if world > 1:
-        torch.distributed.barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    st1 = g.stats()
-    launches = g.profile_read("all")[0] - launches0
-    scan_n, scan_ms = g.profile_read("scan")
-    prof = {k: g.profile_read(k) for k in ("coarse", "insert", "remove", "group", "scan",
-                                           "merge")}
-    g.profile(False)
-    assert g.sync() >= 0
+    results = {}
+    for f in forms:
+        P = calib[f]["nprobe"]
+        inputs = [step_inputs(step_no + s) for s in range(K)]
+        step_no += K
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        st0 = g.stats()
+        launches0 = g.profile_read("all")[0]
+        g.profile(True)
+        clocks = Clocks(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(K):
+            run_step(f, P, *inputs[s], ev=evs[s])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms = t0.elapsed_time(t1)
+        st1 = g.stats()
+        launches = g.profile_read("all")[0] - launches0
+        prof = {k: g.profile_read(k) for k in ("coarse", "insert", "remove", "group", "scan",
+                                               "merge", "rerank")}
+        g.profile(False)
+        g.sync()
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ins_ms = np.array([a[0].elapsed_time(a[1]) for a in evs])
+        del_ms = np.array([a[1].elapsed_time(a[2]) for a in evs])
+        srch_ms = np.array([a[2].elapsed_time(a[3]) for a in evs])
+        upd = ins_ms + del_ms
+        results[f] = {
+            "qps": world * K * w.n_queries / (total_ms / 1e3), "total_ms": total_ms,
+            "search_qps": world * K * w.n_queries / (srch_ms.sum() / 1e3),
+            "insert_vec_s": world * K * w.step / (ins_ms.sum() / 1e3),
+            "delete_vec_s": world * K * w.step / (del_ms.sum() / 1e3),
+            "p50_update_ms": float(np.percentile(upd, 50)),
+            "p99_update_ms": float(np.percentile(upd, 99)),
+            "insert_ms": float(ins_ms.mean()), "delete_ms": float(del_ms.mean()),
+            "search_ms": float(srch_ms.mean()),
+            "kernel_ms_per_step": {k: round(v[1] / K, 4) for k, v in prof.items()},
+            "scan": prof["scan"], "launches": launches, "clocks": clk,
+            "pairs": st1["pairs_scanned"] - st0["pairs_scanned"],
+            "sbytes": st1["slab_bytes_scanned"] - st0["slab_bytes_scanned"],
+        }
 
-    ins_ms = np.array([a[0].elapsed_time(a[1]) for a in evs])
-    del_ms = np.array([a[1].elapsed_time(a[2]) for a in evs])
-    srch_ms = np.array([a[2].elapsed_time(a[3]) for a in evs])
-    upd = ins_ms + del_ms
-
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K * w.n_queries / (total_ms / 1e3)
-
-    # roofline of the list scan (dominant kernel): algorithmic flops of the
-    # direct form, 3 d per (query, live vector) pair the scans scored
-    pairs = st1["pairs_scanned"] - st0["pairs_scanned"]
-    sbytes = st1["slab_bytes_scanned"] - st0["slab_bytes_scanned"]
-    flops = 3.0 * w.d * pairs
-    achieved = flops / (scan_ms / 1e3) / 1e12 if scan_ms > 0 else 0.0
+    ok = [f for f in forms if calib[f]["meets_target"]] or forms
+    head = max(ok, key=lambda f: results[f]["qps"])
+    r = results[head]
+    nprobe = calib[head]["nprobe"]
     pk = peaks()
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
-                "traffic": None, "kernel": "k_scan (list scan, FP32 direct form)",
-                "launches": scan_n, "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
-                "flops_per_launch": flops / max(scan_n, 1),
-                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz; the direct "
-                             "form issues 2 instructions per 3 flops, so its ceiling is 0.75",
-                "hbm_view": {"algorithmic_bytes_per_launch": sbytes / max(scan_n, 1),
-                             "gbs": round(sbytes / (scan_ms / 1e3) / 1e9, 1) if scan_ms else 0,
-                             "peak_gbs": pk.get("hbm_gbs")}}
-    kernel_ms = {k: round(v[1] / K, 4) for k, v in prof.items()}
+    scan_n, scan_ms = r["scan"]
+    if head == "fp32":
+        flops = 3.0 * w.d * r["pairs"]
+        achieved = flops / (scan_ms / 1e3) / 1e12 if scan_ms > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": round(achieved, 3),
+                    "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                    "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz; the direct "
+                                 "form issues 2 instructions per 3 flops, so its ceiling is 0.75",
+                    "kernel": "k_scan (FP32 direct form)"}
+    else:
+        gbs = r["sbytes"] / (scan_ms / 1e3) / 1e9 if scan_ms > 0 else 0.0
+        roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.get("hbm_gbs"),
+                    "unit": "GB/s", "frac": round(gbs / pk.get("hbm_gbs", 6695.5), 4),
+                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "kernel": f"k_scan_tc<{head}> (tcgen05 scan of the {head} copy)",
+                    "tensor_view": {"tflops": round(2.0 * w.d * r["pairs"] / (scan_ms / 1e3) / 1e12, 2),
+                                    "peak_bf16_tflops": pk.get("bf16_tflops")}}
+    roofline.update({"traffic": None, "launches": scan_n,
+                     "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
+                     "algorithmic_bytes_per_launch": r["sbytes"] / max(scan_n, 1),
+                     "flops_per_launch": (3.0 if head == "fp32" else 2.0) * w.d * r["pairs"]
+                     / max(scan_n, 1)})
 
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": world,
-        "steps": K, "warmup": Wm, "ms_per_step": round(total_ms / K, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "metric": METRIC, "value": round(r["qps"], 3), "unit": "queries/s", "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": round(r["total_ms"] / K, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if head == "fp32" else f"{head}+f32",
         "data": "synthetic: seeded 1,024-component Gaussian mixture shaped like SIFT "
                 "(d=128, integers 0..255); stands in for SIFT1M",
-        "config": config_of(w, nprobe),
+        "config": config_of(w, nprobe, head),
         "components": {
-            "search_qps": round(world * K * w.n_queries / (srch_ms.sum() / 1e3), 1),
-            "insert_vec_s": round(world * K * w.step / (ins_ms.sum() / 1e3), 1),
-            "delete_vec_s": round(world * K * w.step / (del_ms.sum() / 1e3), 1),
-            "p50_update_ms": round(float(np.percentile(upd, 50)), 4),
-            "p99_update_ms": round(float(np.percentile(upd, 99)), 4),
-            "insert_ms": round(float(ins_ms.mean()), 4),
-            "delete_ms": round(float(del_ms.mean()), 4),
-            "search_ms": round(float(srch_ms.mean()), 4),
-            "recall_at_10": recalls.get(nprobe), "recall_by_nprobe": recalls,
-            "kernel_ms_per_step": kernel_ms,
+            **{k: round(r[k], 4) for k in ("search_qps", "insert_vec_s", "delete_vec_s",
+                                           "p50_update_ms", "p99_update_ms", "insert_ms",
+                                           "delete_ms", "search_ms")},
+            "recall_at_10": calib[head]["recall_by_nprobe"][nprobe],
+            "kernel_ms_per_step": r["kernel_ms_per_step"],
+            "forms": {f: {"qps": round(results[f]["qps"], 1),
+                          "search_qps": round(results[f]["search_qps"], 1),
+                          "nprobe": calib[f]["nprobe"],
+                          "meets_recall_0.95": calib[f]["meets_target"],
+                          "recall_by_nprobe": calib[f]["recall_by_nprobe"],
+                          "scan_ms": round(results[f]["scan"][1] / K, 4)} for f in forms},
         },
-        "gpu_launches": int(launches),
+        "gpu_launches": int(r["launches"]),
         "roofline": roofline,
-        "clocks": clk,
+        "clocks": r["clocks"],
     }
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs from pinned memory and D2H of its results inside the timed region
     if not args.no_e2e:
         host = []
-        for s in range(Wm + K, Wm + 2 * K):
-            t = [x.cpu().pin_memory() for x in step_inputs(s)]
-            host.append(t)
+        for s in range(K):
+            host.append([x.cpu().pin_memory() for x in step_inputs(step_no + s)])
+        step_no += K
         dev_in = [torch.empty_like(x, device=dev) for x in host[0]]
         hd = torch.empty((w.n_queries, w.k), dtype=torch.float32).pin_memory()
         hl = torch.empty((w.n_queries, w.k), dtype=torch.int64).pin_memory()
@@ -395,7 +431,7 @@ def main():
         for s in range(K):
             for dst, src in zip(dev_in, host[s]):
                 dst.copy_(src, non_blocking=True)
-            run_step(*dev_in)
+            run_step(head, nprobe, *dev_in)
             hd.copy_(dist_out, non_blocking=True)
             hl.copy_(lab_out, non_blocking=True)
         e1.record(stream)
@@ -411,19 +447,18 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g.close()
-        del inputs
         torch.cuda.empty_cache()
         n_ins, n_del, n_q = 1000, 1000, 200
-        r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2)
+        rr = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2)
         line["cpu_baseline"] = {
-            "value": round(r["qps"], 3), "unit": "queries/s", "cores": r["cores"],
+            "value": round(rr["qps"], 3), "unit": "queries/s", "cores": rr["cores"],
             "kind": "oracle",
             "sample": (f"FP64 oracle holding the full {w.window:,}-vector window (built with "
-                       f"{r['cores']} threads in {r['build_s']:.1f} s, untimed); 2 steps of "
+                       f"{rr['cores']} threads in {rr['build_s']:.1f} s, untimed); 2 steps of "
                        f"{n_ins} inserts, {n_del} deletes of the oldest and {n_q} queries "
                        f"(k={w.k}, nprobe={nprobe}), each scaled to the full step"),
-            "components": {k: round(r[k], 3) for k in ("search_qps", "insert_vec_s",
-                                                       "delete_vec_s", "p99_update_ms")},
+            "components": {k: round(rr[k], 3) for k in ("search_qps", "insert_vec_s",
+                                                        "delete_vec_s", "p99_update_ms")},
         }
     if rank == 0:
         print(json.dumps(line), flush=True)

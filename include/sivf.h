@@ -243,8 +243,8 @@ sivf_status sivf_assign(sivf_index *index, const float *x, int64_t n,
 /*
  * sivf_probe -- the coarse selection step of sivf_search alone:
  * probes [device] int32[nq, nprobe] holds the nprobe nearest lists of each
- * query in ascending list index (the set equals the FP64 top-nprobe by
- * (distance, index)).
+ * query; the set equals the FP64 top-nprobe by (distance, index), listed
+ * nearest first by the FP32 approximate distance (ties to the lower index).
  */
 sivf_status sivf_probe(sivf_index *index, const float *q, int64_t nq,
                        int nprobe, int32_t *probes, void *stream);

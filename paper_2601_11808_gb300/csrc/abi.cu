@@ -369,7 +369,8 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
     if (plo) *plo = pl;
     size_t parts = (size_t)nq * P * pl.ch * pl.K;
     return coarse_bytes(ix, nq) + (size_t)nq * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
-           parts * 12 + (size_t)nq * 4 + (size_t)nq * pl.K * 12 + 14 * 256;
+           parts * 12 + (size_t)nq * 4 * 3 + (size_t)nq * pl.K * 12 +
+           ((size_t)nq * P + L) * pl.ch * 8 + 18 * 256;
 }
 
 static int64_t query_chunk(const sivf_index *ix, int P, int k)
@@ -508,8 +509,9 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             pl = plan_tc(ix, m, P, Kc);
             need = std::max(need, coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 +
                                       (size_t)(L + 1) * 4 * 4 +
-                                      (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 +
-                                      (size_t)m * pl.K * 12 + 14 * 256);
+                                      (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 +
+                                      (size_t)m * pl.K * 12 +
+                                      ((size_t)m * P + L) * pl.ch * 8 + 18 * 256);
         }
         Ctx *c;
         if ((st = get_ctx(ix, stream, need, &c))) return st;
@@ -526,6 +528,9 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.part_d = b.take<float>((size_t)m * P * pl.ch * pl.K);
         sc.part_i = b.take<int64_t>((size_t)m * P * pl.ch * pl.K);
         sc.thr = b.take<float>((size_t)m);
+        sc.items = b.take<int2>(((size_t)m * P + L) * pl.ch);
+        sc.qn = b.take<float>((size_t)m);
+        sc.qsc = b.take<float>((size_t)m);
         float *cand_d = b.take<float>((size_t)m * pl.K);
         int64_t *cand_s = b.take<int64_t>((size_t)m * pl.K);
         const int64_t rows = coarse_rows(ix, m);
@@ -546,6 +551,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             const int esz = dtype == SIVF_BF16 ? 2 : 1;
             const int64_t sb = (int64_t)ix->C * ix->d * esz;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
+            query_prep(ix, qq, m, sc.qn, sc.qsc, s);
             const int split = P > 1 ? 1 : P;
             group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
             scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);

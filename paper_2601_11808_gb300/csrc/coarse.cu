@@ -354,7 +354,8 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
     }
     __syncthreads();
 
-    // write the selected set in ascending list index
+    // write the selected set nearest first: ascending approximate distance,
+    // ties to the lower list index (the set itself is the exact one)
     const int nsel = min(s_nsel, a.P);
     if (s_nsel != a.P && tid == 0) atomicOr(a.err, ERR_SELECT);
     for (int s = tid; s < a.P; s += SEL_NT) {
@@ -362,8 +363,14 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
             outr[s] = -1;
             continue;
         }
-        int c = sSel[s], pos = 0;
-        for (int q = 0; q < nsel; ++q) pos += sSel[q] < c;
+        const int c = sSel[s];
+        const float dc = Dr[c];
+        int pos = 0;
+        for (int q = 0; q < nsel; ++q) {
+            const int c2 = sSel[q];
+            const float d2 = Dr[c2];
+            pos += d2 < dc || (d2 == dc && c2 < c);
+        }
         outr[pos] = c;
     }
 }

@@ -42,6 +42,9 @@ struct SearchScratch {
     int64_t *part_i;     // [nq * P * CH * K]
     float *thr;          // [nq] shared bound of each query's k-th distance
     int32_t *pnch;       // [nq * P] slab chunks scanned for each pair (0: none)
+    int2 *items;         // [(nq * P + nlist) * CH] work items (list, tile << 8 | chunk)
+    float *qn;           // [nq] ||q||^2 (reduced-precision scans)
+    float *qsc;          // [nq] FP8 inverse scale of each query
 };
 struct SearchPlan {
     int tq;              // queries per work item
@@ -62,6 +65,8 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
 
 // ---- reduced-precision scan + re-rank (scan_tc.cu)
 bool tc_make_maps(sivf_index *ix);
+void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
+                cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
                    const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);

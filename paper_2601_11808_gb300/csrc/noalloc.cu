@@ -69,6 +69,7 @@ size_t need_bytes(const sivf_index *ix, int64_t nq, int P, const sivf::SearchPla
     add((size_t)nq * P * pl.ch * pl.K * 8);   // part_i
     add((size_t)nq * 4);              // thr
     add((size_t)nq * P * 4);          // pnch
+    add(((size_t)nq * P + L) * pl.ch * 8);   // items
     add((size_t)rows * L * 4);        // coarse distances
     return b;
 }
@@ -139,6 +140,7 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
     sc.part_i = c.take<int64_t>((size_t)nq * P * pl.ch * pl.K);
     sc.thr = c.take<float>((size_t)nq);
     sc.pnch = c.take<int32_t>((size_t)nq * P);
+    sc.items = c.take<int2>(((size_t)nq * P + L) * pl.ch);
     float *Dbuf = c.take<float>((size_t)rows * L);
     if (!c.ok()) return fail(SIVF_E_ARG, "scratch carve-up overflow");
 

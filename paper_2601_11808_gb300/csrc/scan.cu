@@ -52,7 +52,8 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
                                                     int64_t slab_bytes,
                                                     int32_t *__restrict__ loff,
                                                     int32_t *__restrict__ ibase,
-                                                    int32_t *__restrict__ nch, Ctl *ctl,
+                                                    int32_t *__restrict__ nch,
+                                                    int2 *__restrict__ items, Ctl *ctl,
                                                     int64_t *stat)
 {
     __shared__ int32_t sa[1024], sb[1024];
@@ -88,11 +89,13 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
     }
     int32_t ea = sa[tid] - ca, eb = sb[tid] - cb;
     for (int l = b0; l < b1; ++l) {
-        int m = lcnt[l];
+        const int m = lcnt[l], c = nch[l], nt = (m + tq - 1) / tq;
         loff[l] = ea;
         ibase[l] = eb;
+        // work items of list l: (list, tile << 8 | chunk)
+        for (int t = 0; t < nt * c; ++t) items[eb + t] = make_int2(l, ((t / c) << 8) | (t % c));
         ea += m;
-        eb += ((m + tq - 1) / tq) * nch[l];
+        eb += nt * c;
     }
     if (tid == 1023) {
         loff[L] = sa[1023];
@@ -135,6 +138,7 @@ struct ScanArgs {
     int64_t nq;
     int P, K, M, CH;
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
+    const int2 *items;
     float *part_d;
     int64_t *part_i;
     float *thr;          // [nq] shared upper bound of each query's k-th distance
@@ -402,17 +406,11 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
         const int item = *s_item;
         if (item >= a.ctl->nitems || *s_abort) break;
 
-        // decode item -> list, query tile, slab chunk
-        int lo = 0, hi = a.L;  // largest l with ibase[l] <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.ibase[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int l = lo;
+        // item -> list, query tile, slab chunk
+        const int2 it = a.items[item];
+        const int l = it.x;
         const int nc_l = a.nch[l];
-        const int rel = item - a.ibase[l];
-        const int tile = rel / nc_l, chunk = rel % nc_l;
+        const int tile = it.y >> 8, chunk = it.y & 255;
         const int mcount = a.lcnt[l];
         const int r0 = tile * TQ;                     // tiles filled from the front;
         const int m = min(TQ, mcount - r0);           // the last one skips empty groups
@@ -731,7 +729,7 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
     k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
     k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
                                     pl.slabs_per_chunk, slab_bytes, s.loff, s.ibase, s.nch,
-                                    ix->ctl, ix->stat);
+                                    s.items, ix->ctl, ix->stat);
     k_srch_scatter<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
                                       s.pnch);
     prof_end(ix, tg, st);
@@ -759,6 +757,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
     a.part_d = s.part_d;
     a.part_i = s.part_i;
     a.thr = s.thr;
+    a.items = s.items;
     a.x32 = ix->x32;
     a.ids = ix->ids;
     a.bits = ix->bits;

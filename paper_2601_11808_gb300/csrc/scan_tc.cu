@@ -31,13 +31,14 @@ namespace sivf {
 constexpr int TC_N = 64;        // queries per tile (MMA N)
 constexpr int TC_M = 128;       // rows per A tile (MMA M)
 constexpr int TC_NT = 256;
-constexpr int TC_DMP = TC_M + 4;  // padded row of the distance matrix
 
 struct TcArgs {
     const float *q;
     int64_t nq;
     int P, K, M, CH;
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
+    const int2 *items;
+    const float *qn, *qsc;
     float *part_d;
     int64_t *part_i;  // global slot (slab * C + slot) of each candidate
     float *thr;
@@ -51,67 +52,128 @@ struct TcArgs {
     uint32_t *err;
 };
 
+constexpr int TC_NST = 3;       // A-tile stages in flight
+constexpr int TC_META = 256;    // slabs whose ids and bitmaps are staged at once
+
 struct TcSmem {
-    size_t a, b, dm, bd, bs, gs, misc, total;
+    size_t a, b, bd, bs, msl, mbits, misc, total;
 };
 __host__ __device__ inline TcSmem tc_smem(int KC, int M)
 {
     TcSmem s;
-    s.a = 0;                                            // 2 stages x KC x 16 KB
-    s.b = s.a + (size_t)2 * KC * TC_M * 128;            // KC x 64 rows x 128 B
-    s.dm = s.b + (size_t)KC * TC_N * 128;
-    s.bd = s.dm + (size_t)TC_N * TC_DMP * 4;
+    s.a = 0;                                             // TC_NST x KC x 16 KB
+    s.b = s.a + (size_t)TC_NST * KC * TC_M * 128;        // KC x 64 rows x 128 B
+    s.bd = s.b + (size_t)KC * TC_N * 128;
     s.bs = s.bd + (size_t)TC_N * M * 4;
-    s.gs = s.bs + (size_t)TC_N * M * 4;
-    s.misc = s.gs + (size_t)TC_M * 4;
-    s.total = s.misc + 1024 + 1024;                     // + base alignment slack
+    s.msl = s.bs + (size_t)TC_N * M * 4;
+    s.mbits = s.msl + (size_t)TC_META * 4;
+    s.misc = s.mbits + (size_t)TC_META * 4 * 4;
+    s.total = s.misc + 1024 + 1024;                      // + base alignment slack
     return s;
 }
 
-// rank merge for (distance, 32-bit slot) entries, as warp_rank_merge
-template <int EPL>
-__device__ __forceinline__ void rank_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
-                                             int lane)
+// (distance, slot) order with pads (+inf, INT_MAX) last
+__device__ __forceinline__ bool ds_less(float a, int32_t sa, float b, int32_t sb)
 {
-    const int n = nb + nc;
-    float vd[EPL];
-    int32_t vs[EPL];
-    int pos[EPL];
+    return a < b || (a == b && sa < sb);
+}
+
+// Ascending bitonic sort of 32*E (distance, slot) pairs held E per lane.
+template <int E>
+__device__ __forceinline__ void warp_sort32(float (&v)[E], int32_t (&s)[E], int lane)
+{
+    constexpr int N = 32 * E;
 #pragma unroll
-    for (int t = 0; t < EPL; ++t) {
-        const int e = lane + 32 * t;
-        pos[t] = K;
-        if (e >= n) continue;
-        const int src = e < nb ? e : K + (e - nb);
-        const float dv = bd[src];
-        const int32_t sv = bs[src];
-        vd[t] = dv;
-        vs[t] = sv;
-        int r = 0;
-        for (int j = 0; j < nc; ++j) {
-            const float cd = bd[K + j];
-            r += cd < dv || (cd == dv && bs[K + j] < sv);
-        }
-        if (e < nb) {
-            r += e;
-        } else {
-            int lo = 0, hi = nb;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (bd[mid] < dv || (bd[mid] == dv && bs[mid] < sv)) lo = mid + 1;
-                else hi = mid;
+    for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+        for (int st = size >> 1; st > 0; st >>= 1)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                const bool up = (i & size) == 0;
+                if (st >= 32) {
+                    const int pe = e ^ (st >> 5);
+                    if (pe > e) {
+                        const bool sw = up ? ds_less(v[pe], s[pe], v[e], s[e])
+                                           : ds_less(v[e], s[e], v[pe], s[pe]);
+                        if (sw) {
+                            const float tv = v[e];
+                            v[e] = v[pe];
+                            v[pe] = tv;
+                            const int32_t ts = s[e];
+                            s[e] = s[pe];
+                            s[pe] = ts;
+                        }
+                    }
+                } else {
+                    const float ov = __shfl_xor_sync(0xffffffffu, v[e], st);
+                    const int32_t os = __shfl_xor_sync(0xffffffffu, s[e], st);
+                    const bool lower = (lane & st) == 0;
+                    const bool take = (lower == up) ? ds_less(ov, os, v[e], s[e])
+                                                    : ds_less(v[e], s[e], ov, os);
+                    if (take) {
+                        v[e] = ov;
+                        s[e] = os;
+                    }
+                }
             }
-            r += lo;
+}
+
+// Merge nc unsorted candidates (bd/bs[K, K+nc)) into the sorted best list
+// (bd/bs[0, nb)), keeping the K smallest: the candidates are sorted in
+// registers, written back in order, and every output position finds its
+// split between the two sorted runs by binary search (merge path).
+template <int EC>
+__device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc, int lane)
+{
+    float v[EC];
+    int32_t sv[EC];
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = i < nc ? bd[K + i] : INFINITY;
+        sv[e] = i < nc ? bs[K + i] : 0x7fffffff;
+    }
+    warp_sort32<EC>(v, sv, lane);
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+        const int i = lane + 32 * e;
+        if (i < nc) {
+            bd[K + i] = v[e];
+            bs[K + i] = sv[e];
         }
-        pos[t] = r;
+    }
+    __syncwarp();
+    const int n = min(K, nb + nc);
+    constexpr int OPL = 4;  // outputs per lane (K <= 128)
+    float ov[OPL];
+    int32_t os[OPL];
+#pragma unroll
+    for (int t = 0; t < OPL; ++t) {
+        const int o = lane + 32 * t;
+        if (o >= n) continue;
+        // smallest i in [lo, hi] with: taking i best and o - i candidates
+        int lo = max(0, o - nc), hi = min(o, nb);
+        while (lo < hi) {
+            const int i = (lo + hi) >> 1;          // i best, o - i candidates before o
+            const int j = o - i - 1;               // last candidate taken
+            if (ds_less(bd[K + j], bs[K + j], bd[i], bs[i])) hi = i;
+            else lo = i + 1;
+        }
+        const int i = lo, j = o - lo;
+        const bool from_best = i < nb && (j >= nc || !ds_less(bd[K + j], bs[K + j], bd[i], bs[i]));
+        ov[t] = from_best ? bd[i] : bd[K + j];
+        os[t] = from_best ? bs[i] : bs[K + j];
     }
     __syncwarp();
 #pragma unroll
-    for (int t = 0; t < EPL; ++t)
-        if (pos[t] < K) {
-            bd[pos[t]] = vd[t];
-            bs[pos[t]] = vs[t];
+    for (int t = 0; t < OPL; ++t) {
+        const int o = lane + 32 * t;
+        if (o < n) {
+            bd[o] = ov[t];
+            bs[o] = os[t];
         }
+    }
     __syncwarp();
 }
 
@@ -126,14 +188,15 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
     const TcSmem L = tc_smem(KC, M);
     unsigned char *A = smem + L.a;
     unsigned char *B = smem + L.b;
-    float *Dm = reinterpret_cast<float *>(smem + L.dm);
     float *BD = reinterpret_cast<float *>(smem + L.bd);
     int32_t *BS = reinterpret_cast<int32_t *>(smem + L.bs);
-    int32_t *Gs = reinterpret_cast<int32_t *>(smem + L.gs);
+    int32_t *Msl = reinterpret_cast<int32_t *>(smem + L.msl);     // slab ids
+    uint32_t *Mbits = reinterpret_cast<uint32_t *>(smem + L.mbits);  // their bitmaps
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.misc);
-    uint64_t *full = bars, *empty = bars + 2, *tfull = bars + 4, *tempty = bars + 6;
-    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(bars + 8);
-    int *s_item = reinterpret_cast<int *>(bars + 9);
+    uint64_t *full = bars, *empty = bars + TC_NST, *tfull = bars + 2 * TC_NST,
+             *tempty = bars + 2 * TC_NST + 2;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(bars + 2 * TC_NST + 4);
+    int *s_item = reinterpret_cast<int *>(bars + 2 * TC_NST + 5);
     int *s_abort = s_item + 1;
     __shared__ int32_t s_qpair[TC_N], s_cc[TC_N], s_nb[TC_N], s_ks[TC_N];
     __shared__ float s_kd[TC_N], s_qn[TC_N], s_qsc[TC_N];
@@ -145,9 +208,11 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
     const uint32_t idesc = DT == 0 ? mma_idesc(1, 1, TC_M, TC_N) : mma_idesc(0, 0, TC_M, TC_N);
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < TC_NST; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], 128);
         }
@@ -167,16 +232,10 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         const int item = *s_item;
         if (item >= a.ctl->nitems || *s_abort) break;
 
-        int lo = 0, hi = a.L;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.ibase[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int l = lo;
+        const int2 it = a.items[item];
+        const int l = it.x;
         const int nc_l = a.nch[l];
-        const int rel = item - a.ibase[l];
-        const int tile = rel / nc_l, chunk = rel % nc_l;
+        const int tile = it.y >> 8, chunk = it.y & 255;
         const int r0 = tile * TC_N;
         const int m = min(TC_N, a.lcnt[l] - r0);
         int ns_total = a.nslabs[l];
@@ -194,57 +253,40 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         const int qb = a.loff[l] + r0;
         for (int r = tid; r < TC_N; r += TC_NT) {
             const int pr = r < m ? a.qlist[qb + r] : -1;
+            const int qi = pr >= 0 ? pr / a.P : 0;
             s_qpair[r] = pr;
             s_cc[r] = 0;
             s_nb[r] = 0;
-            s_kd[r] = pr >= 0 ? __ldcg(a.thr + pr / a.P) : INFINITY;
+            s_kd[r] = pr >= 0 ? __ldcg(a.thr + qi) : INFINITY;
             s_ks[r] = 0x7fffffff;
-        }
-        __syncthreads();
-        // one warp per row: FP32 norm and (FP8) the query's inverse scale
-        for (int r = warp; r < TC_N; r += TC_NT / 32) {
-            const int pr = s_qpair[r];
-            float ss = 0.f, mx = 0.f;
-            if (pr >= 0) {
-                const float *qr = a.q + (size_t)(pr / a.P) * d;
-                for (int j = lane; j < d; j += 32) {
-                    const float v = qr[j];
-                    ss = fmaf(v, v, ss);
-                    mx = fmaxf(mx, fabsf(v));
-                }
-            }
-            ss = warp_sum(ss);
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) {
-                s_qn[r] = ss;
-                s_qsc[r] = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
-            }
+            s_qn[r] = pr >= 0 ? a.qn[qi] : 0.f;
+            s_qsc[r] = pr >= 0 ? a.qsc[qi] : 1.f;
         }
         __syncthreads();
         for (int e = tid; e < TC_N * KC * 8; e += TC_NT) {
             const int r = e / (KC * 8), kc = (e / 8) % KC, c = e % 8;
             const int pr = s_qpair[r];
-            const int k0 = kc * EPC + c * (16 / ESZ);
+            const int k0 = kc * EPC + c * (16 / ESZ);  // first element of the 16-byte chunk
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (pr >= 0) {
-                const float *qr = a.q + (size_t)(pr / a.P) * d;
+            if (pr >= 0 && k0 < d) {                  // d % 16 == 0: chunks are all in or out
+                const float4 *qr = reinterpret_cast<const float4 *>(a.q + (size_t)(pr / a.P) * d + k0);
                 if (DT == 0) {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int k = k0 + 2 * t;
-                        const float x0 = k < d ? qr[k] : 0.f, x1 = k + 1 < d ? qr[k + 1] : 0.f;
-                        __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-                        w[t] = *reinterpret_cast<uint32_t *>(&h);
-                    }
+                    const float4 f0 = qr[0], f1 = qr[1];
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(f0.x, f0.y);
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(f0.z, f0.w);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(f1.x, f1.y);
+                    __nv_bfloat162 h3 = __floats2bfloat162_rn(f1.z, f1.w);
+                    w[0] = *reinterpret_cast<uint32_t *>(&h0);
+                    w[1] = *reinterpret_cast<uint32_t *>(&h1);
+                    w[2] = *reinterpret_cast<uint32_t *>(&h2);
+                    w[3] = *reinterpret_cast<uint32_t *>(&h3);
                 } else {
                     const float sc = s_qsc[r];
+                    float4 f[4] = {qr[0], qr[1], qr[2], qr[3]};
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int k = k0 + 4 * t;
-                        float2 p0 = make_float2(k < d ? __fmul_rn(qr[k], sc) : 0.f,
-                                                k + 1 < d ? __fmul_rn(qr[k + 1], sc) : 0.f);
-                        float2 p1 = make_float2(k + 2 < d ? __fmul_rn(qr[k + 2], sc) : 0.f,
-                                                k + 3 < d ? __fmul_rn(qr[k + 3], sc) : 0.f);
+                        const float2 p0 = make_float2(__fmul_rn(f[t].x, sc), __fmul_rn(f[t].y, sc));
+                        const float2 p1 = make_float2(__fmul_rn(f[t].z, sc), __fmul_rn(f[t].w, sc));
                         const uint32_t lo8 = __nv_cvt_float2_to_fp8x2(p0, __NV_SATFINITE, __NV_E4M3);
                         const uint32_t hi8 = __nv_cvt_float2_to_fp8x2(p1, __NV_SATFINITE, __NV_E4M3);
                         w[t] = lo8 | (hi8 << 16);
@@ -262,7 +304,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         if (warp == 0) {
             if (lane == 0)
             for (int b = 0; b < nblk && !*s_abort; ++b) {
-                const uint32_t g = gblk + b, st = g & 1, u = g >> 1;
+                const uint32_t g = gblk + b, st = g % TC_NST, u = g / TC_NST;
                 if (u >= 1 && !mbar_wait_bounded(&empty[st], (u - 1) & 1, a.err)) {
                     *s_abort = 1;
                     break;
@@ -292,12 +334,13 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         } else if (warp == 1) {
             if (lane == 0)
             for (int b = 0; b < nblk && !*s_abort; ++b) {
-                const uint32_t g = gblk + b, st = g & 1, buf = g & 1, u = g >> 1;
+                const uint32_t g = gblk + b, st = g % TC_NST, u = g / TC_NST;
+                const uint32_t buf = g & 1, ub = g >> 1;
                 if (!mbar_wait_bounded(&full[st], u & 1, a.err)) {
                     *s_abort = 1;
                     break;
                 }
-                if (u >= 1 && !mbar_wait_bounded(&tempty[buf], (u - 1) & 1, a.err)) {
+                if (ub >= 1 && !mbar_wait_bounded(&tempty[buf], (ub - 1) & 1, a.err)) {
                     *s_abort = 1;
                     break;
                 }
@@ -320,9 +363,44 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         } else if (warp >= 4) {
             const int ew = warp - 4;          // epilogue warp = TMEM lane quarter
             const int v = ew * 32 + lane;     // A row = vector of the tile
+            const int CB = M - K;
+            const int BPS = TC_META / SPB;    // tiles whose slab metadata is staged
+            float xn_next = 0.f;
             for (int b = 0; b < nblk; ++b) {
-                const uint32_t g = gblk + b, buf = g & 1, u = g >> 1;
-                bool ok = !*s_abort && mbar_wait_bounded(&tfull[buf], u & 1, a.err);
+                const uint32_t g = gblk + b, buf = g & 1, ub = g >> 1;
+                if (b % BPS == 0) {
+                    // stage ids + bitmaps of the next TC_META slabs of the chunk
+                    named_bar_sync(1, 128);
+                    const int sb0 = b * SPB, sn = min(TC_META, ns - sb0);
+                    for (int i = v; i < sn; i += 128) {
+                        const int sl = dirl[sb0 + i];
+                        const bool okk = sl >= 0 && sl < a.n_slabs;
+                        Msl[i] = okk ? sl : -1;
+                        for (int w = 0; w < C / 32; ++w)
+                            Mbits[i * 4 + w] = okk ? __ldg(a.bits + (size_t)sl * (C / 32) + w) : 0u;
+                    }
+                    named_bar_sync(1, 128);
+                    const int j0 = v / C;
+                    const int s_first = j0 < min(SPB, ns - b * SPB) ? Msl[(b * SPB - sb0) + j0] : -1;
+                    xn_next = s_first >= 0 ? __ldg(a.xnorm + (size_t)s_first * C + v % C) : 0.f;
+                }
+                // row of this thread in the tile
+                const int nsl = min(SPB, ns - b * SPB);
+                const int j = v / C, slot = v % C;
+                const int mi = (b % BPS) * SPB + j;
+                const int sl = j < nsl ? Msl[mi] : -1;
+                const bool live = sl >= 0 && ((Mbits[mi * 4 + (slot >> 5)] >> (slot & 31)) & 1u);
+                const int32_t gslot = live ? sl * C + slot : -1;
+                const float xn = xn_next;
+                // prefetch ||x||^2 of the row of the next tile
+                if (b + 1 < nblk && (b + 1) % BPS != 0) {
+                    const int nsl2 = min(SPB, ns - (b + 1) * SPB);
+                    const int mi2 = ((b + 1) % BPS) * SPB + j;
+                    const int sl2 = j < nsl2 ? Msl[mi2] : -1;
+                    xn_next = sl2 >= 0 ? __ldg(a.xnorm + (size_t)sl2 * C + slot) : 0.f;
+                }
+
+                bool ok = !*s_abort && mbar_wait_bounded(&tfull[buf], ub & 1, a.err);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-aligned
                 if (!ok) *s_abort = 1;
                 tc_fence_after();
@@ -339,79 +417,54 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[buf]);
-                // row metadata
-                const int nsl = min(SPB, ns - b * SPB);
-                const int j = v / C, slot = v % C;
-                int s = -1;
-                bool live = false;
-                if (ok && j < nsl) {
-                    s = dirl[b * SPB + j];
-                    if (s >= 0 && s < a.n_slabs)
-                        live = (__ldg(a.bits + (size_t)s * (C / 32) + (slot >> 5)) >> (slot & 31)) & 1u;
-                }
-                const float xn = live ? __ldg(a.xnorm + (size_t)s * C + slot) : 0.f;
-                Gs[v] = live ? s * C + slot : -1;
+
+                // candidates straight from registers: per query a ballot over
+                // this warp's 32 rows (dist <= the row's bound, so ties stay)
+                // and one shared atomic for their buffer slots
 #pragma unroll
-                for (int n = 0; n < TC_N; ++n) {
-                    float dist = INFINITY;
-                    if (live) {
+                for (int n0 = 0; n0 < TC_N; n0 += 16) {
+                    if (n0 >= m) break;
+                    uint32_t mk[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int n = n0 + i;
                         const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
-                        dist = fmaf(-sc, dv[n], s_qn[n] + xn);
+                        const float dist = fmaf(-sc, dv[n], s_qn[n] + xn);
+                        mk[i] = __ballot_sync(0xffffffffu, ok && live && n < m && dist <= s_kd[n]);
                     }
-                    Dm[n * TC_DMP + v] = dist;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (!mk[i]) continue;
+                        const int n = n0 + i;
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_cc[n], __popc(mk[i]));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if ((mk[i] >> lane) & 1u) {
+                            const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
+                            const int p = K + base + __popc(mk[i] & lanemask_lt());
+                            BD[(size_t)n * M + p] = fmaf(-sc, dv[n], s_qn[n] + xn);
+                            BS[(size_t)n * M + p] = gslot;
+                        }
+                    }
                 }
                 named_bar_sync(1, 128);
-                // selection: warp ew takes rows n = ew, ew + 4, ...
+                // merges: warp ew takes rows n = ew, ew + 4, ...
                 const bool last = b + 1 == nblk;
-                const int CB = M - K;
                 for (int n = ew; n < m; n += 4) {
-                    const float kd = s_kd[n];
-                    const int32_t ks = s_ks[n];
+                    const int cc = s_cc[n];
+                    if (cc == 0 || !(last || cc > CB - TC_M)) continue;
                     float *bd = BD + (size_t)n * M;
                     int32_t *bs = BS + (size_t)n * M;
-                    int cc = s_cc[n];
-#pragma unroll
-                    for (int t = 0; t < TC_M / 32; ++t) {
-                        const int row = lane + 32 * t;
-                        const float dd = Dm[n * TC_DMP + row];
-                        const int32_t gs = Gs[row];
-                        const bool take = gs >= 0 && (dd < kd || (dd == kd && gs < ks));
-                        const uint32_t mk = __ballot_sync(0xffffffffu, take);
-                        if (take) {
-                            const int p = cc + __popc(mk & lanemask_lt());
-                            bd[K + p] = dd;
-                            bs[K + p] = gs;
-                        }
-                        cc += __popc(mk);
+                    const int nb = s_nb[n];
+                    if (cc <= 32) warp_sort_merge32<1>(bd, bs, K, nb, cc, lane);
+                    else if (cc <= 64) warp_sort_merge32<2>(bd, bs, K, nb, cc, lane);
+                    else warp_sort_merge32<4>(bd, bs, K, nb, cc, lane);
+                    const int nb2 = min(K, nb + cc);
+                    if (lane == 0) {
+                        s_nb[n] = nb2;
+                        s_cc[n] = 0;
+                        if (nb2 == K && bd[K - 1] < s_kd[n]) s_kd[n] = bd[K - 1];
                     }
-                    __syncwarp();
-                    if (cc > 0 && (last || cc > CB - TC_M)) {
-                        const int nb = s_nb[n];
-                        if (nb + cc <= 128) rank_merge32<4>(bd, bs, K, nb, cc, lane);
-                        else rank_merge32<8>(bd, bs, K, nb, cc, lane);
-                        const int nb2 = min(K, nb + cc);
-                        cc = 0;
-                        if (lane == 0) {
-                            s_nb[n] = nb2;
-                            float nkd = kd;
-                            int32_t nks = ks;
-                            const int q = s_qpair[n] / a.P;
-                            if (nb2 == K && (bd[K - 1] < nkd || (bd[K - 1] == nkd && bs[K - 1] < nks))) {
-                                nkd = bd[K - 1];
-                                nks = bs[K - 1];
-                                if (nkd >= 0.f)
-                                    atomicMin(reinterpret_cast<int *>(a.thr) + q, __float_as_int(nkd));
-                            }
-                            const float gthr = __ldcg(a.thr + q);
-                            if (gthr < nkd) {
-                                nkd = gthr;
-                                nks = 0x7fffffff;
-                            }
-                            s_kd[n] = nkd;
-                            s_ks[n] = nks;
-                        }
-                    }
-                    if (lane == 0) s_cc[n] = cc;
                     __syncwarp();
                 }
                 named_bar_sync(1, 128);
@@ -420,6 +473,11 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         gblk += nblk;
         __syncthreads();
 
+        // ---- publish each row's K'-th distance as its query's shared bound
+        for (int r = tid; r < m; r += TC_NT)
+            if (s_nb[r] == K && BD[(size_t)r * M + K - 1] >= 0.f)
+                atomicMin(reinterpret_cast<int *>(a.thr) + s_qpair[r] / a.P,
+                          __float_as_int(BD[(size_t)r * M + K - 1]));
         // ---- the best K' of each row (padded with (+inf, -1))
         for (int e = tid; e < m * K; e += TC_NT) {
             const int r = e / K, jj = e % K;
@@ -489,6 +547,35 @@ __global__ __launch_bounds__(128) void k_rerank(const float *__restrict__ q, int
     }
 }
 
+// per query: FP32 ||q||^2 and the FP8 inverse scale 448 / (2 max_j |q_j|)
+__global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
+                             float *__restrict__ qn, float *__restrict__ qsc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= nq) return;
+    const float *qr = q + (size_t)i * d;
+    float ss = 0.f, mx = 0.f;
+    for (int j = lane; j < d; j += 32) {
+        const float v = qr[j];
+        ss = fmaf(v, v, ss);
+        mx = fmaxf(mx, fabsf(v));
+    }
+    ss = warp_sum(ss);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        qn[i] = ss;
+        qsc[i] = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
+    }
+}
+
+void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
+                cudaStream_t st)
+{
+    ix->launches += 1;
+    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, qn, qsc);
+}
+
 // global slots -> labels (padding stays -1)
 __global__ void k_slots_to_ids(int64_t *v, int64_t n, const int64_t *__restrict__ ids)
 {
@@ -550,7 +637,7 @@ bool tc_make_maps(sivf_index *ix)
 
 // best K' entries + room for one more tile of candidates, at most 256 (the
 // rank merge's capacity) for K' <= 128
-int tc_buf_len(int K) { return (K + TC_M + 63) / 64 * 64; }
+int tc_buf_len(int K) { return (K + TC_M + 7) / 8 * 8; }
 
 bool tc_fits(const sivf_index *ix, int Kc)
 {
@@ -577,6 +664,9 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.part_d = s.part_d;
     a.part_i = s.part_i;
     a.thr = s.thr;
+    a.items = s.items;
+    a.qn = s.qn;
+    a.qsc = s.qsc;
     a.xnorm = ix->xnorm;
     a.bits = ix->bits;
     a.nslabs = ix->nslabs;

@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sivf.h"
+#include "sivf.h"
 
 namespace sivf {
 

@@ -132,7 +132,11 @@ def test_probe_sets_bit_exact(torch, P):
     o.set_centroids(cent)
     got = g.probe(cuda(torch, q), P).cpu().numpy()
     want = np.sort(o.probe(q, P), axis=1)
-    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(np.sort(got, axis=1), want)
+    # listed nearest first: the FP64 distance never decreases along a row
+    for r in range(len(q)):
+        d = [float(((q[r].astype(np.float64) - cent[c]) ** 2).sum()) for c in got[r]]
+        assert all(d[i] <= d[i + 1] + 1e-9 for i in range(len(d) - 1))
 
 
 # --------------------------------------------------- tiny sliding window
@@ -312,7 +316,7 @@ def test_sift_window_full_size_sampled(torch, P):
     gd, gi = gd.cpu().numpy(), gi.cpu().numpy()
     probes = g.probe(cuda(torch, Q[:200]), P).cpu().numpy()
     sample = rng.choice(w.n_queries, 25, replace=False)
-    np.testing.assert_array_equal(probes[:25], np.sort(o.probe(Q[:25], P), axis=1))
+    np.testing.assert_array_equal(np.sort(probes[:25], axis=1), np.sort(o.probe(Q[:25], P), axis=1))
     Xl = X[live]
     for r in sample:
         pr = set(o.probe(Q[r:r + 1], P)[0].tolist())
