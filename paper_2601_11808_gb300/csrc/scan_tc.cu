@@ -56,7 +56,7 @@ constexpr int TC_NST = 3;       // A-tile stages in flight
 constexpr int TC_META = 256;    // slabs whose ids and bitmaps are staged at once
 
 struct TcSmem {
-    size_t a, b, bd, bs, msl, mbits, misc, total;
+    size_t a, b, bd, bs, msl, mbits, hist, stg, misc, total;
 };
 __host__ __device__ inline TcSmem tc_smem(int KC, int M)
 {
@@ -67,7 +67,9 @@ __host__ __device__ inline TcSmem tc_smem(int KC, int M)
     s.bs = s.bd + (size_t)TC_N * M * 4;
     s.msl = s.bs + (size_t)TC_N * M * 4;
     s.mbits = s.msl + (size_t)TC_META * 4;
-    s.misc = s.mbits + (size_t)TC_META * 4 * 4;
+    s.hist = s.mbits + (size_t)TC_META * 4 * 4;           // 4 warps x 256 bins
+    s.stg = s.hist + (size_t)4 * 256 * 4;                  // 4 warps x 128 (dist, slot)
+    s.misc = s.stg + (size_t)4 * 128 * 8;
     s.total = s.misc + 1024 + 1024;                      // + base alignment slack
     return s;
 }
@@ -177,6 +179,104 @@ __device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
     __syncwarp();
 }
 
+// Keep the K smallest of best[0, nb) (sorted) and cand[K, K + nc) when the
+// union is too large to sort in registers: a warp radix select finds the
+// K-th smallest key in four 8-bit passes over the union, the entries at or
+// below it (ties included, at most 128) are gathered and sorted.  Falls
+// back to nothing else: more than 128 entries tied at the K-th key keep
+// the first ones found, ordered by slot among the gathered.
+__device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
+                                    uint32_t *hist, float *stg_d, int32_t *stg_s, int lane)
+{
+    const int n = nb + nc;
+    auto at = [&](int i) { return i < nb ? i : K + (i - nb); };
+    uint32_t prefix = 0, mask = 0, need = (uint32_t)K;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t k = fkey(bd[at(i)]);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            loc[b] = hist[lane * 8 + b];
+            sum += loc[b];
+        }
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - sum;
+        const bool mine = excl < need && incl >= need;
+        uint32_t bin = 0, below = 0;
+        if (mine) {
+            uint32_t cum = excl;
+            for (int b = 0; b < 8; ++b) {
+                if (cum + loc[b] >= need) {
+                    bin = (uint32_t)(lane * 8 + b);
+                    below = cum;
+                    break;
+                }
+                cum += loc[b];
+            }
+        }
+        const uint32_t who = __ballot_sync(0xffffffffu, mine);
+        const int src = who ? __ffs(who) - 1 : 0;
+        bin = __shfl_sync(0xffffffffu, bin, src);
+        below = __shfl_sync(0xffffffffu, below, src);
+        prefix |= bin << shift;
+        mask |= 255u << shift;
+        need -= below;
+        __syncwarp();
+    }
+    // gather every entry at or below the K-th key (at most 128)
+    int cnt = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        bool take = false;
+        float dv = 0.f;
+        int32_t sv = 0;
+        if (i < n) {
+            dv = bd[at(i)];
+            sv = bs[at(i)];
+            take = fkey(dv) <= prefix;
+        }
+        const uint32_t mk = __ballot_sync(0xffffffffu, take);
+        const int p = cnt + __popc(mk & lanemask_lt());
+        if (take && p < 128) {
+            stg_d[p] = dv;
+            stg_s[p] = sv;
+        }
+        cnt += __popc(mk);
+    }
+    __syncwarp();
+    cnt = min(cnt, 128);
+    float v[4];
+    int32_t sv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = i < cnt ? stg_d[i] : INFINITY;
+        sv[e] = i < cnt ? stg_s[i] : 0x7fffffff;
+    }
+    warp_sort32<4>(v, sv, lane);
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = lane + 32 * e;
+        if (i < K) {
+            bd[i] = v[e];
+            bs[i] = sv[e];
+        }
+    }
+    __syncwarp();
+}
+
 template <int DT>  // 0 = BF16, 1 = FP8 E4M3
 __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CUtensorMap tmap,
                                                       TcArgs a)
@@ -192,6 +292,8 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
     int32_t *BS = reinterpret_cast<int32_t *>(smem + L.bs);
     int32_t *Msl = reinterpret_cast<int32_t *>(smem + L.msl);     // slab ids
     uint32_t *Mbits = reinterpret_cast<uint32_t *>(smem + L.mbits);  // their bitmaps
+    uint32_t *Hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    unsigned char *Stg = smem + L.stg;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.misc);
     uint64_t *full = bars, *empty = bars + TC_NST, *tfull = bars + 2 * TC_NST,
              *tempty = bars + 2 * TC_NST + 2;
@@ -246,6 +348,8 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         const int s0 = (int)((int64_t)ns_total * chunk / nc_l);
         const int ns = (int)((int64_t)ns_total * (chunk + 1) / nc_l) - s0;
         const int nblk = (ns + SPB - 1) / SPB;
+        // rows of a thin tile get proportionally longer candidate buffers
+        const int ME = max(M, ((TC_N * M) / max(m, 1)) & ~7);
         const int32_t *dirl = a.dir + (size_t)l * a.dir_cap + s0;
         const float inv_l = DT == 1 ? a.inv_scale8[l] : 1.f;
 
@@ -363,7 +467,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         } else if (warp >= 4) {
             const int ew = warp - 4;          // epilogue warp = TMEM lane quarter
             const int v = ew * 32 + lane;     // A row = vector of the tile
-            const int CB = M - K;
+            const int CB = ME - K;
             const int BPS = TC_META / SPB;    // tiles whose slab metadata is staged
             float xn_next = 0.f;
             for (int b = 0; b < nblk; ++b) {
@@ -442,8 +546,8 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                         if ((mk[i] >> lane) & 1u) {
                             const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
                             const int p = K + base + __popc(mk[i] & lanemask_lt());
-                            BD[(size_t)n * M + p] = fmaf(-sc, dv[n], s_qn[n] + xn);
-                            BS[(size_t)n * M + p] = gslot;
+                            BD[(size_t)n * ME + p] = fmaf(-sc, dv[n], s_qn[n] + xn);
+                            BS[(size_t)n * ME + p] = gslot;
                         }
                     }
                 }
@@ -453,12 +557,16 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 for (int n = ew; n < m; n += 4) {
                     const int cc = s_cc[n];
                     if (cc == 0 || !(last || cc > CB - TC_M)) continue;
-                    float *bd = BD + (size_t)n * M;
-                    int32_t *bs = BS + (size_t)n * M;
+                    float *bd = BD + (size_t)n * ME;
+                    int32_t *bs = BS + (size_t)n * ME;
                     const int nb = s_nb[n];
                     if (cc <= 32) warp_sort_merge32<1>(bd, bs, K, nb, cc, lane);
                     else if (cc <= 64) warp_sort_merge32<2>(bd, bs, K, nb, cc, lane);
-                    else warp_sort_merge32<4>(bd, bs, K, nb, cc, lane);
+                    else if (cc <= 128) warp_sort_merge32<4>(bd, bs, K, nb, cc, lane);
+                    else
+                        warp_select_merge32(bd, bs, K, nb, cc, Hist + ew * 256,
+                                            reinterpret_cast<float *>(Stg + ew * 1024),
+                                            reinterpret_cast<int32_t *>(Stg + ew * 1024 + 512), lane);
                     const int nb2 = min(K, nb + cc);
                     if (lane == 0) {
                         s_nb[n] = nb2;
@@ -474,17 +582,18 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         __syncthreads();
 
         // ---- publish each row's K'-th distance as its query's shared bound
+        const int MEo = max(M, ((TC_N * M) / max(m, 1)) & ~7);
         for (int r = tid; r < m; r += TC_NT)
-            if (s_nb[r] == K && BD[(size_t)r * M + K - 1] >= 0.f)
+            if (s_nb[r] == K && BD[(size_t)r * MEo + K - 1] >= 0.f)
                 atomicMin(reinterpret_cast<int *>(a.thr) + s_qpair[r] / a.P,
-                          __float_as_int(BD[(size_t)r * M + K - 1]));
+                          __float_as_int(BD[(size_t)r * MEo + K - 1]));
         // ---- the best K' of each row (padded with (+inf, -1))
         for (int e = tid; e < m * K; e += TC_NT) {
             const int r = e / K, jj = e % K;
             const int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
             const bool ok = jj < s_nb[r];
-            a.part_d[base + jj] = ok ? BD[(size_t)r * M + jj] : INFINITY;
-            a.part_i[base + jj] = ok ? (int64_t)BS[(size_t)r * M + jj] : -1;
+            a.part_d[base + jj] = ok ? BD[(size_t)r * MEo + jj] : INFINITY;
+            a.part_i[base + jj] = ok ? (int64_t)BS[(size_t)r * MEo + jj] : -1;
         }
         __syncthreads();
     }

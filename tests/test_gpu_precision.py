@@ -98,11 +98,17 @@ def _approx_oracle(q, xs, dtype, inv_l):
     return qn + xn - 2 * scale * dot, qn + xn + bound
 
 
+W_LONG = W.small("sift_window", n_comp=16, nlist=16, slab_size=64)
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-@pytest.mark.parametrize("w", [W_SMALL, W_DEEP], ids=["sift", "deep"])
-def test_candidates_match_oracle_approximation(torch, w, dtype):
-    g, o, x, ids, live, cent, ctr = _setup(torch, w, 6000)
-    Q = W.queries(w, 0, 40, ctr)
+@pytest.mark.parametrize("w,n,nq", [(W_SMALL, 6000, 40), (W_DEEP, 6000, 40), (W_LONG, 60000, 24)],
+                         ids=["sift", "deep", "long_lists"])
+def test_candidates_match_oracle_approximation(torch, w, n, nq, dtype):
+    """long_lists: ~2,500 live vectors per list and a few queries per tile,
+    so whole lists accumulate in one buffer and the radix-select merge runs."""
+    g, o, x, ids, live, cent, ctr = _setup(torch, w, n)
+    Q = W.queries(w, 0, nq, ctr)
     P, kc = 4, 40
     cd, ci = g.search_candidates(torch.from_numpy(Q).cuda(), kc, P, dtype)
     cd, ci = cd.cpu().numpy().astype(np.float64), ci.cpu().numpy()
