@@ -190,14 +190,32 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
 {
     const int n = nb + nc;
     auto at = [&](int i) { return i < nb ? i : K + (i - nb); };
-    uint32_t prefix = 0, mask = 0, need = (uint32_t)K;
-    for (int shift = 24; shift >= 0; shift -= 8) {
+    // the keys share their leading bits (distances of one list are of one
+    // magnitude): start the 8-bit passes at the highest bit where they differ
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    for (int i = lane; i < n; i += 32) {
+        const uint32_t k = fkey(bd[at(i)]);
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    const uint32_t diff = kmin ^ kmax;
+    const int top = diff ? 31 - __clz(diff) : 0;  // highest differing bit
+    uint32_t mask = top >= 31 ? 0u : ~((2u << top) - 1u);
+    uint32_t prefix = kmin & mask, need = (uint32_t)K;
+    for (int hi = top; hi >= 0; hi -= 8) {
+        const int shift = max(hi - 7, 0);
+        const uint32_t width = (uint32_t)(hi - shift + 1);
+        const uint32_t bmask = (width >= 32 ? 0xffffffffu : ((1u << width) - 1u));
 #pragma unroll
         for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
             const uint32_t k = fkey(bd[at(i)]);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & bmask], 1u);
         }
         __syncwarp();
         uint32_t loc[8], sum = 0;
@@ -230,7 +248,7 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
         bin = __shfl_sync(0xffffffffu, bin, src);
         below = __shfl_sync(0xffffffffu, below, src);
         prefix |= bin << shift;
-        mask |= 255u << shift;
+        mask |= bmask << shift;
         need -= below;
         __syncwarp();
     }
@@ -302,6 +320,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
     int *s_abort = s_item + 1;
     __shared__ int32_t s_qpair[TC_N], s_cc[TC_N], s_nb[TC_N], s_ks[TC_N];
     __shared__ float s_kd[TC_N], s_qn[TC_N], s_qsc[TC_N];
+    __shared__ __align__(16) float s_t[TC_N];   // kd - ||q||^2 of each row, per tile
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int ESZ = DT == 0 ? 2 : 1;
@@ -365,6 +384,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
             s_ks[r] = 0x7fffffff;
             s_qn[r] = pr >= 0 ? a.qn[qi] : 0.f;
             s_qsc[r] = pr >= 0 ? a.qsc[qi] : 1.f;
+            s_t[r] = pr >= 0 ? s_kd[r] - s_qn[r] : -INFINITY;
         }
         __syncthreads();
         for (int e = tid; e < TC_N * KC * 8; e += TC_NT) {
@@ -522,19 +542,26 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 tc_fence_before();
                 mbar_arrive(&tempty[buf]);
 
-                // candidates straight from registers: per query a ballot over
-                // this warp's 32 rows (dist <= the row's bound, so ties stay)
-                // and one shared atomic for their buffer slots
+                // candidates straight from registers: a row passes for query n
+                // when -s q.x + ||x||^2 <= kd_n - ||q_n||^2 (= s_t[n], set per
+                // tile); per query one ballot over this warp's 32 rows and one
+                // shared atomic for their buffer slots
+                const float4 *t4 = reinterpret_cast<const float4 *>(s_t);
 #pragma unroll
                 for (int n0 = 0; n0 < TC_N; n0 += 16) {
                     if (n0 >= m) break;
                     uint32_t mk[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int n = n0 + i;
-                        const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
-                        const float dist = fmaf(-sc, dv[n], s_qn[n] + xn);
-                        mk[i] = __ballot_sync(0xffffffffu, ok && live && n < m && dist <= s_kd[n]);
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const float4 tv = t4[(n0 >> 2) + i4];
+                        const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int n = n0 + 4 * i4 + c;
+                            const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
+                            const float part = fmaf(-sc, dv[n], xn);
+                            mk[4 * i4 + c] = __ballot_sync(0xffffffffu, ok && live && part <= tt[c]);
+                        }
                     }
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
@@ -571,7 +598,10 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                     if (lane == 0) {
                         s_nb[n] = nb2;
                         s_cc[n] = 0;
-                        if (nb2 == K && bd[K - 1] < s_kd[n]) s_kd[n] = bd[K - 1];
+                        if (nb2 == K && bd[K - 1] < s_kd[n]) {
+                            s_kd[n] = bd[K - 1];
+                            s_t[n] = s_kd[n] - s_qn[n];
+                        }
                     }
                     __syncwarp();
                 }
