@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--nprobe", type=int, default=0, help="0 = calibrate for recall 0.95")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="skip the mixed-batch executor workload")
+    p.add_argument("--mixed-replays", type=int, default=5)
+    p.add_argument("--mixed-form", default="bf16")
     p.add_argument("--forms", default="fp32,bf16,fp8",
                    help="scan forms to measure; the fastest that reaches recall 0.95 "
                         "is the headline")
@@ -219,6 +223,165 @@ def config_of(w, nprobe, form="fp32"):
             "l2": "inputs larger than L2: 512 MB index, fresh insert/query batches "
                   "every step",
             "parallelism": "replicas"}
+
+
+# ---------------------------------------------------- mixed-batch queue
+def run_mixed(torch, sivf, dev, stream, replays, warmup, form="bf16"):
+    """The mixed-batch workload: a 5,000,000-vector index (d=128, nlist=2048,
+    slab 64) and a queue of 64 insert, 64 delete and 64 query batches of
+    log-uniform sizes (inserts 1..50,000, deletes 1..100,000 random live ids,
+    queries 1..4,096 with nprobe drawn from {8,...,128}, k=10), interleaved
+    1:1:1.  The queue is recorded once into a CUDA graph (scan tiles tuned per
+    batch bucket first) and replayed with fresh data written in place; one
+    replay of the same queue as single calls is timed beside it."""
+    from paper_2601_11808_gb300 import autotune
+    w = W.CONFIGS["mixed_batches"]
+    sched = W.mixed_schedule(64, 4096, 100_000, 50_000, w.nprobes, seed=w.seed)
+    n_ins = sum(n for k, n, _ in sched if k == "add")
+    n_rep = warmup + replays + 3
+    n_max = w.window + n_ins * (n_rep + 1) + 1
+    S = w.window // w.slab_size + 2 * w.nlist + n_rep * (n_ins // w.slab_size + w.nlist)
+    ctr = W.centers(w)
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S,
+                   scan_dtypes=(form,) if form != "fp32" else ())
+    g.set_centroids(torch.from_numpy(W.index_centroids(w, ctr)).to(dev))
+    alive = np.zeros(n_max, bool)
+    t_fill = time.time()
+    for b in range(0, w.window, 250_000):
+        n = min(250_000, w.window - b)
+        g.add(torch.from_numpy(W.stream_ids(b, n, n_max)).to(dev),
+              torch.from_numpy(W.vectors(w, b, n, ctr)).to(dev))
+    alive[:w.window] = True
+    g.sync()
+    t_fill = time.time() - t_fill
+    state = {"pos": w.window, "qpos": 0, "rnd": 0}
+
+    def fresh(kind, n):
+        if kind == "add":
+            ids = W.stream_ids(state["pos"], n, n_max)
+            x = W.vectors(w, state["pos"], n, ctr)
+            state["pos"] += n
+            alive[ids] = True
+            return ids, x
+        if kind == "remove":
+            state["rnd"] += 1
+            ids = W.sample_ids(w.seed, 8, state["rnd"], np.flatnonzero(alive), n)
+            alive[ids] = False
+            return (ids,)
+        q = W.queries(w, state["qpos"] % 1_000_000, n, ctr)
+        state["qpos"] += n
+        return (q,)
+
+    ops = []
+    for kind, n, P in sched:
+        if kind == "add":
+            ops.append({"kind": "add", "ids": torch.empty(n, dtype=torch.int64, device=dev),
+                        "x": torch.empty((n, w.d), dtype=torch.float32, device=dev)})
+        elif kind == "remove":
+            ops.append({"kind": "remove", "ids": torch.empty(n, dtype=torch.int64, device=dev)})
+        else:
+            ops.append({"kind": "search", "q": torch.empty((n, w.d), dtype=torch.float32,
+                                                           device=dev),
+                        "k": w.k, "nprobe": P, "dtype": form,
+                        "dist": torch.empty((n, w.k), dtype=torch.float32, device=dev),
+                        "labels": torch.empty((n, w.k), dtype=torch.int64, device=dev)})
+
+    def refill():
+        for op, (kind, n, _) in zip(ops, sched):
+            data = fresh(kind, n)
+            if kind == "add":
+                op["ids"].copy_(torch.from_numpy(data[0]))
+                op["x"].copy_(torch.from_numpy(data[1]))
+            elif kind == "remove":
+                op["ids"].copy_(torch.from_numpy(data[0]))
+            else:
+                op["q"].copy_(torch.from_numpy(data[0]))
+        torch.cuda.synchronize()
+
+    # tiles: one autotune per bucket the queue's query batches fall in
+    t_tune = time.time()
+    qs = torch.from_numpy(W.queries(w, 2_000_000, 4096, ctr)).to(dev)
+    tuned = autotune.tune(g, qs, [(n, w.k, P, form) for k, n, P in sched if k == "search"],
+                          reps=3)
+    t_tune = time.time() - t_tune
+    refill()
+    t_rec = time.time()
+    ex = g.executor(ops)
+    t_rec = time.time() - t_rec
+
+    def check(res):
+        for (kind, n, _), r in zip(sched, res):
+            want = n
+            if r[0] != 0 or r[1] != want:
+                raise RuntimeError(f"mixed batch {kind} n={n}: status/count {r}")
+
+    for _ in range(warmup):
+        ex.launch(stream)
+        torch.cuda.synchronize()
+        check(ex.results(stream))
+        refill()
+    graph_ms, per = [], {"add": [], "remove": [], "search": []}
+    for _ in range(replays):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ex.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms.append(e0.elapsed_time(e1))
+        res = ex.results(stream)
+        check(res)
+        for (kind, n, _), r in zip(sched, res):
+            per[kind].append(r[2])
+        refill()
+    # the same queue as single calls (scratch reserved, one untimed pass first)
+    g.reserve(max(n for k, n, _ in sched if k == "add"),
+              max(n for k, n, _ in sched if k == "remove"),
+              max(n for k, n, _ in sched if k == "search"), w.k, max(w.nprobes), stream)
+
+    def eager():
+        for op in ops:
+            if op["kind"] == "add":
+                g.add(op["ids"], op["x"])
+            elif op["kind"] == "remove":
+                g.remove(op["ids"])
+            else:
+                g.search(op["q"], op["k"], op["nprobe"], op["dtype"], dist=op["dist"],
+                         labels=op["labels"])
+
+    eager()
+    refill()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    eager()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+    g.sync()
+    kernels = ex.kernels
+    ex.close()
+    live = g.stats()["ntotal"]
+    g.close()
+    nq = sum(n for k, n, _ in sched if k == "search")
+    nd = sum(n for k, n, _ in sched if k == "remove")
+    gm = float(np.mean(graph_ms))
+    pct = {k: {"p50_ms": round(float(np.percentile(v, 50)), 4),
+               "p99_ms": round(float(np.percentile(v, 99)), 4)} for k, v in per.items()}
+    return {
+        "workload": "mixed_batches: 5,000,000 vectors d=128 (64-component mixture, "
+                    "centers U[-1,1], sigma 0.1), nlist=2048, slab 64; 64 insert + 64 delete "
+                    "+ 64 query batches, log-uniform sizes, nprobe per query batch from "
+                    "{8,16,32,64,128}, k=10, " + form + " scan + fp32 re-rank",
+        "batches": len(sched), "queries": nq, "inserted": n_ins, "deleted": nd,
+        "graph_launches_per_queue": 1, "kernels_per_queue": int(kernels),
+        "graph_ms_per_queue": round(gm, 3), "eager_ms_per_queue": round(eager_ms, 3),
+        "graph_speedup": round(eager_ms / gm, 3),
+        "queries_per_s": round(nq / (gm / 1e3), 1),
+        "ops_per_s": round((nq + n_ins + nd) / (gm / 1e3), 1),
+        "per_batch_device_ms": pct, "replays": replays,
+        "tuned_buckets": len(tuned), "tune_s": round(t_tune, 2), "record_s": round(t_rec, 3),
+        "prefill_s": round(t_fill, 1), "live_after": int(live),
+    }
 
 
 # ------------------------------------------------------------ our arm
@@ -445,9 +608,15 @@ def main():
                        "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g.close()
+    g.close()
+    torch.cuda.empty_cache()
+    if not args.no_mixed:
+        line["components"]["mixed_batches"] = run_mixed(
+            torch, sivf, dev, stream, max(1, min(args.mixed_replays, K)), max(1, min(Wm, 2)),
+            args.mixed_form)
         torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_ins, n_del, n_q = 1000, 1000, 200
         rr = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2)
         line["cpu_baseline"] = {

@@ -310,6 +310,130 @@ sivf_status sivf_profile(sivf_index *index, int enable);
 sivf_status sivf_profile_read(sivf_index *index, const char *kernel,
                               int64_t *launches, double *total_ms);
 
+/* ------------------------------------------------------------------------
+ * Scan tiles and the autotuner.  The list scan's work split is chosen per
+ * batch from a small table held by the index; a bucket of the table covers
+ * one scan dtype, one power-of-two range of (query, list) pairs per list
+ * (nq * nprobe / nlist, from 2^-8 to 2^15) and one range of kept
+ * candidates per (query, list) (k for SIVF_FP32, 4k for the reduced
+ * dtypes: <= 16, <= 64, <= 256, larger).  Buckets nobody set use built-in
+ * defaults.  The paper has no counterpart: its scan has one fixed shape.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t queries_per_tile; /* SIVF_FP32: 8, 16, 32 or 64 queries share
+                                 each slab load; the reduced dtypes use 64
+                                 (the tensor-core tile's N) and ignore it  */
+    int32_t slabs_per_chunk;  /* 1..16: a list is split into slab chunks
+                                 of at least this many slabs when the
+                                 batch has too few query tiles             */
+    int32_t items_per_sm;     /* 1..16: work items wanted per SM before
+                                 lists are split into chunks              */
+    int32_t select_slabs;     /* SIVF_FP32, 0..8: the k-select buffer of
+                                 each query row holds its best k plus room
+                                 for this many slabs of candidates (0: the
+                                 built-in width, two slabs while that stays
+                                 within 256 entries)                       */
+    int32_t nearest_first;    /* reduced dtypes: 1 scans each query's
+                                 nearest list in a launch of its own first,
+                                 so the other lists meet a tight bound     */
+} sivf_tile;
+
+/*
+ * sivf_set_tile -- install `tile` [host] for the bucket that a search of
+ * nq queries, k results and nprobe lists with `dtype` falls in; NULL
+ * clears the bucket (back to the defaults).  A tile whose buffers would not
+ * fit in shared memory for that batch is rejected with SIVF_E_ARG.
+ * sivf_get_tile stores in *out the tile a search of that shape would use
+ * now (the installed one or the default).
+ */
+sivf_status sivf_set_tile(sivf_index *index, sivf_scan_dtype dtype, int64_t nq,
+                          int k, int nprobe, const sivf_tile *tile);
+sivf_status sivf_get_tile(sivf_index *index, sivf_scan_dtype dtype, int64_t nq,
+                          int k, int nprobe, sivf_tile *out);
+
+/*
+ * sivf_autotune -- time sivf_search on the queries q [device] float32[nq, d]
+ * for a set of tiles (coordinate descent over the fields of sivf_tile,
+ * starting from the current tile), `reps` timed searches per tile after one
+ * warm-up, CUDA events on `stream`; install the fastest for the batch's
+ * bucket.  *best [host] receives it and *best_ms (optional) its mean time
+ * per search.  Forces syncs; allocates and frees its own output buffers.
+ * Results of the searches it runs are discarded; the index is not changed.
+ */
+sivf_status sivf_autotune(sivf_index *index, const float *q, int64_t nq, int k,
+                          int nprobe, sivf_scan_dtype dtype, int reps,
+                          void *stream, sivf_tile *best, double *best_ms);
+
+/* ------------------------------------------------------------------------
+ * Mixed-batch executor.  A queue of uneven add, remove and search batches
+ * (each search with its own k, nprobe and dtype) is recorded once into a
+ * CUDA graph and then replayed with one graph launch per queue.  Every
+ * batch reads its inputs from, and writes its outputs to, the device
+ * addresses given when the queue was recorded, so a caller refills those
+ * buffers in place between launches.  The batches run in queue order with
+ * the semantics of the single calls (sivf_add, sivf_remove, sivf_search),
+ * and the executor records, per batch, its status, its count and a device
+ * timestamp.  The paper runs each batch as separate launches; this has no
+ * counterpart there.
+ * ---------------------------------------------------------------------- */
+typedef enum { SIVF_OP_ADD = 0, SIVF_OP_REMOVE = 1, SIVF_OP_SEARCH = 2 } sivf_op_kind;
+
+typedef struct {
+    int32_t kind;        /* sivf_op_kind                                     */
+    int32_t dtype;       /* search: sivf_scan_dtype                          */
+    int32_t k;           /* search: results per query                        */
+    int32_t nprobe;      /* search: lists probed per query                   */
+    int64_t n;           /* ids (add, remove) or queries (search), >= 1      */
+    const int64_t *ids;  /* add, remove [device] int64[n]                    */
+    const float *x;      /* add: vectors, search: queries [device] [n, d]    */
+    float *dist;         /* search [device] float32[n, k]                    */
+    int64_t *labels;     /* search [device] int64[n, k]                      */
+} sivf_op;
+
+typedef struct {
+    int32_t status;      /* sivf_status of the batch (add: admission and id
+                            checks; remove: id checks; search: SIVF_OK)     */
+    int32_t pad;
+    int64_t count;       /* ids added / removed; queries answered           */
+    double device_ms;    /* device time from the end of the previous batch
+                            (or the start of the queue) to its end         */
+} sivf_op_result;
+
+typedef struct sivf_exec sivf_exec;
+
+/*
+ * sivf_exec_create -- check the `nops` batches of `ops` [host] (every
+ * argument rule of the single calls), reserve all the scratch they need
+ * (owned by the executor: it never shares scratch with the index's own
+ * calls), and record them into a CUDA graph.  The ops are copied; the
+ * device buffers they point to must stay valid while the executor lives.
+ * Recording enqueues nothing: the queue runs only at sivf_exec_launch.
+ * Errors: SIVF_E_ARG with the index's last error naming the bad batch.
+ */
+sivf_status sivf_exec_create(sivf_index *index, const sivf_op *ops, int nops,
+                             sivf_exec **out);
+
+/*
+ * sivf_exec_launch -- run the whole queue with one graph launch on
+ * `stream`.  Launches of one executor must not overlap each other or other
+ * work on the same index (order them on one stream).
+ */
+sivf_status sivf_exec_launch(sivf_exec *exec, void *stream);
+
+/*
+ * sivf_exec_results -- per-batch results of the last launch (forces a
+ * sync): results [host] sivf_op_result[nops].  Returns SIVF_E_CORRUPT or
+ * SIVF_E_TIMEOUT when the device error word is set, else SIVF_OK (the
+ * batches' own statuses are in the array).
+ */
+sivf_status sivf_exec_results(sivf_exec *exec, void *stream, sivf_op_result *results);
+
+/* sivf_exec_kernels -- kernel launches one sivf_exec_launch performs. */
+int64_t sivf_exec_kernels(const sivf_exec *exec);
+
+/* sivf_exec_destroy -- synchronize and free the graph and its scratch. */
+sivf_status sivf_exec_destroy(sivf_exec *exec);
+
 /* sivf_last_error -- text of the last error on this index (never NULL). */
 const char *sivf_last_error(const sivf_index *index);
 

@@ -177,7 +177,7 @@ namespace sivf {
 int prof_begin(sivf_index *ix, int k, int n, cudaStream_t st)
 {
     ix->launches += n;
-    if (!ix->prof_on) return -1;
+    if (!ix->prof_on || ix->capturing) return -1;
     ProfEvent e;
     e.kind = k;
     e.launches = n;
@@ -381,6 +381,43 @@ static int64_t query_chunk(const sivf_index *ix, int P, int k)
     return std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)512 << 20) / per));
 }
 
+// plan of the reduced-precision scan: tiles of 64 queries, K' candidates
+static SearchPlan plan_tc(const sivf_index *ix, int dtype, int64_t nq, int P, int Kc)
+{
+    return plan_from_tile(ix, dtype, nq, P, Kc, current_tile(ix, dtype, nq, P, Kc));
+}
+
+// scratch of one query chunk of m queries, and its scan plan
+static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dtype,
+                         SearchPlan *plo)
+{
+    if (dtype == SIVF_FP32) return search_bytes(ix, m, Kc, P, plo);
+    const int L = ix->nlist;
+    SearchPlan pl = plan_tc(ix, dtype, m, P, Kc);
+    *plo = pl;
+    return coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
+           (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * pl.K * 12 +
+           ((size_t)m * P + L) * pl.ch * 8 + 18 * 256;
+}
+
+// reduced-precision candidates: the re-rank depth K' = 4k
+static int rerank_depth(int k) { return 4 * k; }
+
+// scratch a search of exactly nq queries asks its stream for (the largest
+// of its query chunks)
+static size_t search_need(const sivf_index *ix, int64_t nq, int k, int P, int dtype)
+{
+    if (nq <= 0) return 0;
+    const int Kc = dtype == SIVF_FP32 ? k : rerank_depth(k);
+    const int64_t qc = query_chunk(ix, P, std::max(k, Kc));
+    SearchPlan pl;
+    size_t need = chunk_need(ix, std::min(qc, nq), P, Kc, dtype, &pl);
+    if (nq > qc && nq % qc) need = std::max(need, chunk_need(ix, nq % qc, P, Kc, dtype, &pl));
+    return need;
+}
+
+static size_t remove_need(const sivf_index *ix) { return (size_t)ix->nlist * 4 + 512; }
+
 sivf_status sivf_reserve(sivf_index *ix, int64_t max_add, int64_t max_remove,
                          int64_t max_queries, int max_k, int max_nprobe, void *stream)
 {
@@ -388,12 +425,15 @@ sivf_status sivf_reserve(sivf_index *ix, int64_t max_add, int64_t max_remove,
         max_nprobe < 0)
         return fail(ix, SIVF_E_ARG, "negative reserve");
     size_t need = add_bytes(ix, std::max<int64_t>(max_add, 1));
-    need = std::max(need, (size_t)std::max<int64_t>(max_remove, 1) * 4 +
-                              (size_t)ix->nlist * 4 + 512);
+    need = std::max(need, remove_need(ix));
     if (max_queries && max_k && max_nprobe) {
-        int P = std::min(max_nprobe, ix->nlist);
-        int64_t qc = std::min<int64_t>(max_queries, query_chunk(ix, P, max_k));
-        need = std::max(need, search_bytes(ix, qc, max_k, P, nullptr));
+        const int P = std::min(max_nprobe, ix->nlist);
+        // every batch size up to max_queries: the chunk plans differ by size
+        for (int dt = 0; dt < 3; ++dt) {
+            if ((dt == SIVF_BF16 && !ix->xb16) || (dt == SIVF_FP8E4M3 && !ix->x8)) continue;
+            for (int64_t m = max_queries; m >= 1; m = m > 64 ? m * 3 / 4 : m - 1)
+                need = std::max(need, search_need(ix, m, max_k, P, dt));
+        }
     }
     sivf_status st = grow_rank_rows(ix, max_add, stream);
     if (st) return st;
@@ -456,24 +496,51 @@ sivf_status sivf_remove(sivf_index *ix, const int64_t *ids, int64_t n, void *str
     return SIVF_OK;
 }
 
-// plan of the reduced-precision scan: tiles of 64 queries, K' candidates
-static SearchPlan plan_tc(const sivf_index *ix, int64_t nq, int P, int Kc)
+}  // extern "C"
+
+namespace sivf {
+size_t op_need(const sivf_index *ix, const sivf_op &op)
 {
-    SearchPlan pl;
-    pl.tq = 64;
-    pl.K = Kc;
-    const double touched = std::min<double>(ix->nlist, (double)nq * P);
-    const double tiles = std::max(touched, (double)nq * P / 64);
-    const double want = 4.0 * 152;
-    int ch = tiles >= want ? 1 : (int)std::min<double>(kMaxChunks, std::ceil(want / tiles));
-    ch = std::min(ch, std::max(1, 2048 / P));
-    pl.ch = std::max(1, ch);
-    pl.slabs_per_chunk = 4;
-    return pl;
+    switch (op.kind) {
+    case SIVF_OP_ADD: return add_bytes(ix, std::max<int64_t>(op.n, 1));
+    case SIVF_OP_REMOVE: return remove_need(ix);
+    default: return search_need(ix, op.n, op.k, op.nprobe, op.dtype);
+    }
 }
 
-// reduced-precision candidates: the re-rank depth K' = 4k, at most 128
-static int rerank_depth(int k) { return std::min(128, 4 * k); }
+sivf_status reserve_stream(sivf_index *ix, void *stream, size_t need, int64_t max_add)
+{
+    sivf_status st = grow_rank_rows(ix, max_add, stream);
+    if (st) return st;
+    Ctx *c;
+    return get_ctx(ix, stream, need, &c);
+}
+
+Ctl *stream_ctl(sivf_index *ix, void *stream)
+{
+    auto it = ex(ix).ctx.find(stream);
+    return it == ex(ix).ctx.end() ? nullptr : it->second.ctl;
+}
+
+void release_stream(sivf_index *ix, void *stream)
+{
+    auto it = ex(ix).ctx.find(stream);
+    if (it == ex(ix).ctx.end()) return;
+    if (it->second.ctl) cudaFree(it->second.ctl);
+    if (it->second.scratch) cudaFree(it->second.scratch);
+    if (it->second.host) cudaFreeHost(it->second.host);
+    ex(ix).ctx.erase(it);
+}
+
+sivf_status set_error(sivf_index *ix, sivf_status st, const char *what)
+{
+    return fail(ix, st, what);
+}
+
+void mark_corrupt(sivf_index *ix) { ex(ix).corrupt = true; }
+}  // namespace sivf
+
+extern "C" {
 
 static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k, int nprobe,
                                const int32_t *probes_in, sivf_scan_dtype dtype, float *dist,
@@ -504,15 +571,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
     for (int64_t q0 = 0; q0 < nq; q0 += qc) {
         const int64_t m = std::min(qc, nq - q0);
         SearchPlan pl;
-        size_t need = search_bytes(ix, m, Kc, P, &pl);
-        if (tc) {
-            pl = plan_tc(ix, m, P, Kc);
-            need = std::max(need, coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 +
-                                      (size_t)(L + 1) * 4 * 4 +
-                                      (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 +
-                                      (size_t)m * pl.K * 12 +
-                                      ((size_t)m * P + L) * pl.ch * 8 + 18 * 256);
-        }
+        const size_t need = chunk_need(ix, m, P, Kc, dtype, &pl);
         Ctx *c;
         if ((st = get_ctx(ix, stream, need, &c))) return st;
         Bump b{c->scratch};
@@ -552,7 +611,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             const int64_t sb = (int64_t)ix->C * ix->d * esz;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
             query_prep(ix, qq, m, sc.qn, sc.qsc, s);
-            const int split = P > 1 ? 1 : P;
+            const int split = P > 1 && pl.split ? 1 : P;
             group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
             scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
             if (split < P) {

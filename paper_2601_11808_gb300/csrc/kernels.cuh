@@ -51,7 +51,18 @@ struct SearchPlan {
     int ch;              // most slab chunks per list
     int slabs_per_chunk; // slabs per chunk before splitting stops
     int K;               // candidates kept per (query, item)
+    int M;               // FP32 scan: entries of each row's k-select buffer
+    int split;           // reduced precision: nearest list in a launch of its own
 };
+// tile choice for a batch: the installed one of its bucket, else the default
+int tune_bucket(const sivf_index *ix, int64_t nq, int P);
+int tune_kbucket(int K);
+sivf_tile default_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K);
+sivf_tile current_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K);
+bool tile_valid(const sivf_index *ix, int dtype, const sivf_tile &t, int K);
+SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K,
+                          const sivf_tile &t);
+// FP32 plan (dtype 0) with the batch's current tile
 SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K);
 bool scan_fits(const sivf_index *ix, int K);   // shared memory for k = K
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
@@ -73,5 +84,13 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
+
+// ---- C-ABI internals shared with the executor (abi.cu)
+size_t op_need(const sivf_index *ix, const sivf_op &op);   // scratch of one batch
+sivf_status reserve_stream(sivf_index *ix, void *stream, size_t need, int64_t max_add);
+Ctl *stream_ctl(sivf_index *ix, void *stream);
+void release_stream(sivf_index *ix, void *stream);        // free a stream's scratch
+sivf_status set_error(sivf_index *ix, sivf_status st, const char *what);
+void mark_corrupt(sivf_index *ix);
 
 }  // namespace sivf

@@ -13,6 +13,8 @@
 // probed lists, ties to the lower id, padded with (+inf, -1).
 #include <math.h>
 
+#include <cmath>
+
 #include "device_utils.cuh"
 #include "kernels.cuh"
 
@@ -690,26 +692,95 @@ static void launch_scan(sivf_index *ix, const ScanArgs &a, size_t smem, int grid
     prof_end(ix, tok, st);
 }
 
-SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
+int tune_bucket(const sivf_index *ix, int64_t nq, int P)
+{
+    const double r = std::max((double)nq * P / ix->nlist, 1.0 / 256);
+    const int b = (int)std::floor(std::log2(r)) + 8;
+    return std::min(std::max(b, 0), kTuneB - 1);
+}
+
+int tune_kbucket(int K) { return K <= 16 ? 0 : K <= 64 ? 1 : K <= 256 ? 2 : 3; }
+
+// k-select buffer of the FP32 scan: the best K plus `slabs` slabs of
+// candidates, beyond 256 entries a power of two (bitonic fallback);
+// slabs = 0 is the built-in width
+static int fp32_width(int K, int C, int slabs)
+{
+    if (slabs == 0) return scan_buf_len(K, C);
+    const int v = K + slabs * C;
+    return v <= 256 ? ((v + 15) & ~15) : scan_next_pow2(v);
+}
+
+sivf_tile default_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K)
+{
+    sivf_tile t;
+    if (dtype == SIVF_FP32) {
+        const double ppl = (double)nq * P / ix->nlist;
+        t.queries_per_tile = ppl >= 48 ? 64 : ppl >= 24 ? 32 : ppl >= 12 ? 16 : 8;
+        while (t.queries_per_tile > 8 &&
+               scan_smem(t.queries_per_tile, ix->C, ix->d, scan_buf_len(K, ix->C)).total >
+                   220 * 1024)
+            t.queries_per_tile >>= 1;
+        t.slabs_per_chunk = 2;
+        t.items_per_sm = 4;
+        t.select_slabs = 0;
+        t.nearest_first = 0;
+    } else {
+        t.queries_per_tile = 64;
+        t.slabs_per_chunk = 4;
+        t.items_per_sm = 4;
+        t.select_slabs = 0;
+        t.nearest_first = 1;
+    }
+    return t;
+}
+
+bool tile_valid(const sivf_index *ix, int dtype, const sivf_tile &t, int K)
+{
+    if (t.slabs_per_chunk < 1 || t.slabs_per_chunk > 16 || t.items_per_sm < 1 ||
+        t.items_per_sm > 16)
+        return false;
+    if (dtype == SIVF_FP32) {
+        const int tq = t.queries_per_tile;
+        if (!(tq == 8 || tq == 16 || tq == 32 || tq == 64)) return false;
+        if (t.select_slabs < 0 || t.select_slabs > 8) return false;
+        return scan_smem(tq, ix->C, ix->d, fp32_width(K, ix->C, t.select_slabs)).total <=
+               220 * 1024;
+    }
+    return t.nearest_first == 0 || t.nearest_first == 1;
+}
+
+sivf_tile current_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K)
+{
+    const TileChoice &c = ix->tune[dtype][tune_bucket(ix, nq, P)][tune_kbucket(K)];
+    if (c.set && tile_valid(ix, dtype, c.t, K)) return c.t;
+    return default_tile(ix, dtype, nq, P, K);
+}
+
+SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K,
+                          const sivf_tile &t)
 {
     SearchPlan pl;
-    const int C = ix->C, d = ix->d;
-    const double pairs_per_list = (double)nq * P / ix->nlist;
-    int tq = pairs_per_list >= 48 ? 64 : pairs_per_list >= 24 ? 32 : pairs_per_list >= 12 ? 16 : 8;
-    const int M = scan_buf_len(K, C);
-    while (tq > 8 && scan_smem(tq, C, d, M).total > 220 * 1024) tq >>= 1;
-    pl.tq = tq;
+    const bool fp32 = dtype == SIVF_FP32;
+    pl.tq = fp32 ? t.queries_per_tile : 64;
     pl.K = K;
+    pl.M = fp32 ? fp32_width(K, ix->C, t.select_slabs) : 0;
+    pl.split = fp32 ? 0 : t.nearest_first;
     // enough work items for every SM: split lists into slab chunks when the
     // query tiles alone are too few
     const double touched = std::min<double>(ix->nlist, (double)nq * P);
-    const double tiles = std::max(touched, (double)nq * P / tq);
-    const double want = 4.0 * 152;
+    const double tiles = std::max(touched, (double)nq * P / pl.tq);
+    const double want = (double)t.items_per_sm * 152;
     int ch = tiles >= want ? 1 : (int)std::min<double>(kMaxChunks, std::ceil(want / tiles));
     ch = std::min(ch, std::max(1, 2048 / P));  // runs per query the merge can hold
     pl.ch = std::max(1, ch);
-    pl.slabs_per_chunk = 2;
+    pl.slabs_per_chunk = t.slabs_per_chunk;
     return pl;
+}
+
+SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
+{
+    return plan_from_tile(ix, SIVF_FP32, nq, P, K, current_tile(ix, SIVF_FP32, nq, P, K));
 }
 
 bool scan_fits(const sivf_index *ix, int K)
@@ -747,7 +818,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
     a.nq = nq;
     a.P = P;
     a.K = pl.K;
-    a.M = scan_buf_len(pl.K, ix->C);
+    a.M = pl.M;
     a.CH = pl.ch;
     a.qlist = s.qlist;
     a.loff = s.loff;

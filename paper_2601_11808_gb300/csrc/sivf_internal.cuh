@@ -77,6 +77,15 @@ struct ProfEvent {
     cudaEvent_t start, stop;
 };
 
+// Installed scan tiles (sivf_set_tile / sivf_autotune): one per scan dtype,
+// log2 bucket of (query, list) pairs per list and bucket of kept candidates.
+constexpr int kTuneB = 24;           // pairs per list 2^-8 .. 2^15
+constexpr int kTuneK = 4;            // kept candidates <= 16, 64, 256, more
+struct TileChoice {
+    int set;
+    sivf_tile t;
+};
+
 }  // namespace sivf
 
 // The index handle.  Every array is device memory unless noted.
@@ -137,6 +146,10 @@ struct sivf_index {
     // scratch arena (grown on demand, reset per call)
     char *scratch;
     size_t scratch_bytes;
+
+    // scan tiles chosen per batch bucket (zero = defaults)
+    sivf::TileChoice tune[3][sivf::kTuneB][sivf::kTuneK];
+    bool capturing;                // a sivf_exec is recording: no profiler events
 
     // tracing: CUDA events around kernel groups, launch counts
     bool prof_on;

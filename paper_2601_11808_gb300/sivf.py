@@ -32,7 +32,12 @@ EXPORTS = [
     "sivf_assign", "sivf_probe", "sivf_sync",
     "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
     "sivf_profile", "sivf_profile_read", "sivf_last_error", "sivf_version",
+    "sivf_set_tile", "sivf_get_tile", "sivf_autotune",
+    "sivf_exec_create", "sivf_exec_launch", "sivf_exec_results", "sivf_exec_kernels",
+    "sivf_exec_destroy",
 ]
+
+OP_ADD, OP_REMOVE, OP_SEARCH = 0, 1, 2
 
 
 class sivf_config(C.Structure):
@@ -47,6 +52,26 @@ class sivf_stats_t(C.Structure):
                 ("last_status", C.c_int32), ("last_count", C.c_int64),
                 ("bytes_device", C.c_int64), ("pairs_scanned", C.c_int64),
                 ("slab_bytes_scanned", C.c_int64)]
+
+
+class sivf_tile(C.Structure):
+    _fields_ = [("queries_per_tile", C.c_int32), ("slabs_per_chunk", C.c_int32),
+                ("items_per_sm", C.c_int32), ("select_slabs", C.c_int32),
+                ("nearest_first", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sivf_op(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("k", C.c_int32),
+                ("nprobe", C.c_int32), ("n", C.c_int64), ("ids", C.c_void_p),
+                ("x", C.c_void_p), ("dist", C.c_void_p), ("labels", C.c_void_p)]
+
+
+class sivf_op_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("count", C.c_int64),
+                ("device_ms", C.c_double)]
 
 
 class SivfError(RuntimeError):
@@ -94,6 +119,15 @@ def load(path: str | None = None):
             "sivf_profile": (i32, [vp, i32]),
             "sivf_profile_read": (i32, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)]),
             "sivf_last_error": (C.c_char_p, [vp]),
+            "sivf_set_tile": (i32, [vp, i32, i64, i32, i32, C.POINTER(sivf_tile)]),
+            "sivf_get_tile": (i32, [vp, i32, i64, i32, i32, C.POINTER(sivf_tile)]),
+            "sivf_autotune": (i32, [vp, vp, i64, i32, i32, i32, i32, vp,
+                                    C.POINTER(sivf_tile), C.POINTER(C.c_double)]),
+            "sivf_exec_create": (i32, [vp, C.POINTER(sivf_op), i32, C.POINTER(vp)]),
+            "sivf_exec_launch": (i32, [vp, vp]),
+            "sivf_exec_results": (i32, [vp, vp, C.POINTER(sivf_op_result)]),
+            "sivf_exec_kernels": (i64, [vp]),
+            "sivf_exec_destroy": (i32, [vp]),
             "sivf_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -357,6 +391,104 @@ def sivf_profile_read(h, kernel: str):
     return n.value, ms.value
 
 
+def sivf_set_tile(h, dtype, nq, k, nprobe, tile: dict | None) -> None:
+    """Install (or with None clear) the scan tile of a batch shape's bucket."""
+    lib = load()
+    t = None
+    if tile is not None:
+        t = sivf_tile(**{f: int(tile[f]) for f, _ in sivf_tile._fields_})
+    _check(lib, h, lib.sivf_set_tile(h, int(dtype), int(nq), int(k), int(nprobe),
+                                     C.byref(t) if t is not None else None))
+
+
+def sivf_get_tile(h, dtype, nq, k, nprobe) -> dict:
+    lib = load()
+    t = sivf_tile()
+    _check(lib, h, lib.sivf_get_tile(h, int(dtype), int(nq), int(k), int(nprobe), C.byref(t)))
+    return t.as_dict()
+
+
+def sivf_autotune(h, q, k, nprobe, dtype=FP32, reps=5, stream=None):
+    """Time searches of q over scan tiles and install the fastest for the
+    batch's bucket; returns (tile dict, ms per search)."""
+    import torch
+    lib = load()
+    _dev(q, torch.float32)
+    t = sivf_tile()
+    ms = C.c_double(0.0)
+    _check(lib, h, lib.sivf_autotune(h, _ptr(q), q.shape[0], int(k), int(nprobe), int(dtype),
+                                     int(reps), _stream(stream), C.byref(t), C.byref(ms)))
+    return t.as_dict(), ms.value
+
+
+class Exec:
+    """A recorded queue of add / remove / search batches (sivf_exec).
+
+    ``ops`` is a list of dicts: {"kind": "add", "ids": t, "x": t},
+    {"kind": "remove", "ids": t}, {"kind": "search", "q": t, "k": k,
+    "nprobe": p, "dtype": "bf16", "dist": t, "labels": t}.  The tensors are
+    device buffers that stay bound to the queue: refill them in place
+    between launches.  The wrapper keeps references to them."""
+
+    KINDS = {"add": OP_ADD, "remove": OP_REMOVE, "search": OP_SEARCH}
+
+    def __init__(self, h, ops: list):
+        import torch
+        lib = load()
+        self.h = h
+        self._keep = []
+        arr = (sivf_op * len(ops))()
+        for i, o in enumerate(ops):
+            kind = self.KINDS[o["kind"]]
+            e = arr[i]
+            e.kind = kind
+            if kind == OP_SEARCH:
+                q = _dev(o["q"], torch.float32)
+                e.n = q.shape[0]
+                e.x = _ptr(q)
+                e.k, e.nprobe = int(o["k"]), int(o["nprobe"])
+                e.dtype = DTYPES[o.get("dtype", "fp32")]
+                e.dist = _ptr(_dev(o["dist"], torch.float32))
+                e.labels = _ptr(_dev(o["labels"], torch.int64))
+                self._keep += [q, o["dist"], o["labels"]]
+            else:
+                ids = _dev(o["ids"], torch.int64)
+                e.n = ids.numel()
+                e.ids = _ptr(ids)
+                self._keep.append(ids)
+                if kind == OP_ADD:
+                    x = _dev(o["x"], torch.float32)
+                    e.x = _ptr(x)
+                    self._keep.append(x)
+        self.nops = len(ops)
+        out = C.c_void_p()
+        _check(lib, h, lib.sivf_exec_create(h, arr, len(ops), C.byref(out)))
+        self.e = out.value
+        self.kernels = lib.sivf_exec_kernels(self.e)
+
+    def launch(self, stream=None) -> None:
+        lib = load()
+        _check(lib, self.h, lib.sivf_exec_launch(self.e, _stream(stream)))
+
+    def results(self, stream=None) -> list:
+        """Per batch: (status, count, device_ms) of the last launch."""
+        lib = load()
+        res = (sivf_op_result * self.nops)()
+        _check(lib, self.h, lib.sivf_exec_results(self.e, _stream(stream), res))
+        return [(r.status, r.count, r.device_ms) for r in res]
+
+    def close(self) -> None:
+        if getattr(self, "e", None):
+            load().sivf_exec_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------- convenience
 class Index:
     """Owning wrapper: one device index, calls on the torch current stream."""
@@ -436,6 +568,18 @@ class Index:
 
     def profile_read(self, kernel):
         return sivf_profile_read(self.h, kernel)
+
+    def set_tile(self, dtype, nq, k, nprobe, tile):
+        sivf_set_tile(self.h, DTYPES[dtype], nq, k, nprobe, tile)
+
+    def get_tile(self, dtype, nq, k, nprobe):
+        return sivf_get_tile(self.h, DTYPES[dtype], nq, k, nprobe)
+
+    def autotune(self, q, k, nprobe, dtype="fp32", reps=5, stream=None):
+        return sivf_autotune(self.h, q, k, nprobe, DTYPES[dtype], reps, stream)
+
+    def executor(self, ops):
+        return Exec(self.h, ops)
 
     def dump_payload(self, bf16=False, fp8=False, stream=None):
         return sivf_dump_payload(self.h, self.n_slabs, self.slab_size, self.d, self.nlist,

@@ -141,3 +141,37 @@ def small(name: str = "tiny_window", **over) -> Workload:
     fields = dict(base.__dict__)
     fields.update(over)
     return Workload(**fields)
+
+
+def log_uniform_sizes(seed: int, stream: int, n: int, hi: int) -> np.ndarray:
+    """n batch sizes floor(exp(U[0, ln hi])), clipped to [1, hi]."""
+    g = _rng(seed, stream, 0)
+    return np.clip(np.floor(np.exp(g.uniform(0.0, np.log(hi), size=n))), 1, hi).astype(np.int64)
+
+
+def mixed_schedule(n_batches: int = 64, max_query: int = 4096, max_delete: int = 100_000,
+                   max_insert: int = 50_000, nprobes=(8, 16, 32, 64, 128), seed: int = 0
+                   ) -> list:
+    """The uneven batch queue of the mixed-batch workload: n_batches each of
+    insert, delete and query batches with log-uniform sizes, interleaved
+    1:1:1 (insert, delete, query, insert, ...); every query batch draws its
+    own nprobe uniformly from `nprobes`.  Entries are (kind, size, nprobe)."""
+    qs = log_uniform_sizes(seed, 4, n_batches, max_query)
+    ds = log_uniform_sizes(seed, 5, n_batches, max_delete)
+    ins = log_uniform_sizes(seed, 6, n_batches, max_insert)
+    ps = _rng(seed, 7, 0).choice(np.asarray(nprobes), size=n_batches)
+    out = []
+    for i in range(n_batches):
+        out.append(("add", int(ins[i]), 0))
+        out.append(("remove", int(ds[i]), 0))
+        out.append(("search", int(qs[i]), int(ps[i])))
+    return out
+
+
+def sample_ids(seed: int, stream: int, block: int, pool: np.ndarray, n: int) -> np.ndarray:
+    """n distinct ids drawn without replacement from `pool` (all of it when
+    n >= len(pool))."""
+    g = _rng(seed, stream, block)
+    if n >= len(pool):
+        return g.permutation(pool)
+    return g.choice(pool, size=n, replace=False)
