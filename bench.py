@@ -58,6 +58,11 @@ def parse():
                    help="skip the mixed-batch executor workload")
     p.add_argument("--mixed-replays", type=int, default=5)
     p.add_argument("--mixed-form", default="bf16")
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving-loop workload")
+    p.add_argument("--serving-window", type=int, default=0,
+                   help="live vectors of the serving window (0 = 100,000,000)")
+    p.add_argument("--serving-seconds", type=float, default=2.0)
     p.add_argument("--forms", default="fp32,bf16,fp8",
                    help="scan forms to measure; the fastest that reaches recall 0.95 "
                         "is the headline")
@@ -384,6 +389,127 @@ def run_mixed(torch, sivf, dev, stream, replays, warmup, form="bf16"):
     }
 
 
+# ----------------------------------------------------------- serving loop
+def run_serving(torch, sivf, dev, window=0, seconds=2.0, loads=(0.5, 0.8, 0.95)):
+    """The serving workload: a sliding window of 100,000,000 vectors (d=128,
+    16,384-component mixture, nlist=16384, slab 128, FP32 payload + BF16
+    copy) served by the library's serving loop.  Requests arrive as a Poisson
+    stream: 70% inserts of 1..10,000 fresh vectors (each evicting the oldest
+    ids beyond the window), 10% deletes of the 1..10,000 oldest ids, 20%
+    queries of 1..256 vectors (k=10, nprobe=32, BF16 scan + FP32 re-rank),
+    sizes log-uniform.  The saturation rate is measured first (a burst served
+    as fast as possible), then each offered load runs for `seconds`;
+    latency is measured from each request's scheduled arrival."""
+    w = W.CONFIGS["serving"]
+    Wn = window or w.window
+    n_max = Wn + (1 << 22)
+    S = int(1.02 * Wn / w.slab_size) + 3 * w.nlist + (1 << 14)
+    ctr = W.centers(w)
+    pool = W.noise_pool(w, 1 << 20)
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S, scan_dtypes=("bf16",))
+    g.set_centroids(torch.from_numpy(W.index_centroids(w, ctr)).to(dev))
+    ctr_d, pool_d = torch.from_numpy(ctr).to(dev), torch.from_numpy(pool).to(dev)
+    sig = float(np.float32(w.sigma))
+    t_fill = time.time()
+    ch = 2_000_000
+    for b in range(0, Wn, ch):
+        n = min(ch, Wn - b)
+        c, r = W.pooled_parts(w, b, n, len(pool))
+        x = ctr_d[torch.from_numpy(c).to(dev)] + pool_d[torch.from_numpy(r).to(dev)] * sig
+        g.add(torch.from_numpy(W.stream_ids(b, n, n_max)).to(dev), x)
+        del x
+    g.sync()
+    t_fill = time.time() - t_fill
+    del ctr_d, pool_d
+    torch.cuda.empty_cache()
+    # page-locked payload pools: inserts reuse pool vectors under fresh ids
+    xpool = torch.from_numpy(W.pooled_vectors(w, 0, 1 << 20, ctr, pool)).pin_memory().numpy()
+    qpool = torch.from_numpy(W.queries(w, 0, 1 << 16, ctr)).pin_memory().numpy()
+    k, P = w.k, w.nprobes[0]
+    sv = sivf.Server(g, k=k, nprobe=P, dtype="bf16", depth=4, max_query_batch=2048,
+                     max_insert_batch=40_000, max_delete_batch=40_000)
+    win = {"lo": 0, "hi": Wn, "xo": 0, "qo": 0}
+
+    def submit(kind, n, t_arr):
+        if kind == 0:
+            ids = np.arange(win["hi"], win["hi"] + n, dtype=np.int64) % n_max
+            win["hi"] += n
+            over = max(0, win["hi"] - win["lo"] - Wn)
+            ev = np.arange(win["lo"], win["lo"] + over, dtype=np.int64) % n_max
+            win["lo"] += over
+            if win["xo"] + n > len(xpool):
+                win["xo"] = 0
+            x = xpool[win["xo"]:win["xo"] + n]
+            win["xo"] += n
+            return sv.add(ids, x, evict=ev, arrival_ns=t_arr)
+        if kind == 1:
+            n = min(n, win["hi"] - win["lo"])
+            ids = np.arange(win["lo"], win["lo"] + n, dtype=np.int64) % n_max
+            win["lo"] += n
+            return sv.remove(ids, arrival_ns=t_arr)
+        if win["qo"] + n > len(qpool):
+            win["qo"] = 0
+        q = qpool[win["qo"]:win["qo"] + n]
+        win["qo"] += n
+        return sv.search(q, arrival_ns=t_arr)
+
+    def run(n_req, rate, stream):
+        t_off, kinds, sizes = W.request_stream(n_req, rate, seed=w.seed, stream=stream)
+        st0 = sv.stats()
+        t0 = sivf.Server.now_ns() + 2_000_000
+        reqs = []
+        for off, kd, sz in zip(t_off.tolist(), kinds.tolist(), sizes.tolist()):
+            t_arr = t0 + off
+            while True:
+                now = sivf.Server.now_ns()
+                if now >= t_arr:
+                    break
+                if t_arr - now > 300_000:
+                    time.sleep((t_arr - now - 200_000) / 1e9)
+            reqs.append((kd, submit(kd, sz, t_arr)))
+        sv.drain()
+        infos = [(kd, sv.wait(r)) for kd, r in reqs]
+        st1 = sv.stats()
+        done = [t0 + off + 1e6 * i["latency_ms"] for off, (_, i) in zip(t_off.tolist(), infos)]
+        span = (max(done) - t0) / 1e9
+        out = {"offered_req_s": round(rate, 1), "requests": n_req,
+               "achieved_req_s": round(n_req / span, 1)}
+        for kd, name in enumerate(("insert", "delete", "query")):
+            lat = np.asarray([i["latency_ms"] for k2, i in infos if k2 == kd])
+            if len(lat):
+                out[name] = {"n": int(len(lat)), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                             "items_per_s": round((st1["items"][kd] - st0["items"][kd]) / span, 1),
+                             "batches": st1["batches"][kd] - st0["batches"][kd]}
+        out["rejected"] = st1["rejected"] - st0["rejected"]
+        out["deferred"] = st1["deferred"] - st0["deferred"]
+        out["max_in_flight"] = st1["max_in_flight"]
+        bad = [i for _, i in infos if i["status"] != 0]
+        out["failed"] = len(bad)
+        return out
+
+    # saturation: a burst with every arrival at once
+    burst = run(3000, 1e12, 30)
+    sat = burst["achieved_req_s"]
+    res = {"saturation": burst}
+    for i, ld in enumerate(loads):
+        n_req = max(200, int(sat * ld * seconds))
+        res[f"load_{ld}"] = run(n_req, sat * ld, 31 + i)
+    sv.close()
+    live = g.stats()["ntotal"]
+    g.close()
+    torch.cuda.empty_cache()
+    res.update({
+        "workload": f"serving: {Wn:,}-vector window d=128 (16,384-component mixture, centers "
+                    "U[-1,1], sigma 0.1, noise rows from a 2^20-vector pool), nlist=16384, slab "
+                    "128, FP32 + BF16 copy; Poisson 70% insert (1..10k, evicting beyond the "
+                    "window) / 10% delete-oldest (1..10k) / 20% query (1..256, k=10, nprobe=32, "
+                    "bf16 scan + fp32 re-rank), sizes log-uniform",
+        "prefill_s": round(t_fill, 1), "live_after": int(live), "seconds_per_load": seconds,
+        "latency": "from each request's scheduled arrival to its completion on the host"})
+    return res
+
+
 # ------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -615,6 +741,9 @@ def main():
             torch, sivf, dev, stream, max(1, min(args.mixed_replays, K)), max(1, min(Wm, 2)),
             args.mixed_form)
         torch.cuda.empty_cache()
+    if not args.no_serving:
+        line["components"]["serving"] = run_serving(
+            torch, sivf, dev, args.serving_window, args.serving_seconds)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_ins, n_del, n_q = 1000, 1000, 200

@@ -434,6 +434,106 @@ int64_t sivf_exec_kernels(const sivf_exec *exec);
 /* sivf_exec_destroy -- synchronize and free the graph and its scratch. */
 sivf_status sivf_exec_destroy(sivf_exec *exec);
 
+/* ------------------------------------------------------------------------
+ * Serving loop.  A server owns the index while it lives and drives it from
+ * one worker thread; callers on any thread submit requests (inserts,
+ * deletes, queries) from host memory and wait for them.  The worker serves
+ * the request queue in arrival order, coalescing each run of same-kind
+ * requests at the head into one batch (continuous batching: whatever
+ * arrived while earlier batches were on the GPU joins the next batch), and
+ * keeps up to `depth` batches in flight, each in its own slot (stream,
+ * pinned staging, device buffers, scratch).  Host-to-device copies, kernels
+ * and result copies of different slots overlap; query batches run
+ * concurrently with each other, and a mutation batch waits, on the device,
+ * for every batch launched before it (and every batch after it waits for
+ * it), so each request sees exactly the mutations served before it.
+ * Admission by free slabs: inserts are coalesced only while the batch's
+ * worst-case slab demand (ceil(n / C) plus one slab per touched list) fits
+ * the free slabs known on the host net of in-flight inserts; otherwise the
+ * worker waits for in-flight mutations, then serves the request alone and
+ * the device's exact all-or-nothing admission decides (SIVF_E_NOMEM).
+ * The paper has no serving loop; this follows the mixed
+ * insert/search/delete stream of its evaluation.
+ * ---------------------------------------------------------------------- */
+typedef struct sivf_server sivf_server;
+
+typedef struct {
+    int32_t k;                /* results per query                           */
+    int32_t nprobe;           /* lists probed per query                      */
+    int32_t dtype;            /* sivf_scan_dtype of every search             */
+    int32_t depth;            /* batches in flight, 1..8                     */
+    int32_t max_query_batch;  /* queries per search launch, >= 1             */
+    int32_t max_insert_batch; /* vectors per add launch, >= 1                */
+    int32_t max_delete_batch; /* ids per remove launch (evictions included)  */
+    int32_t pad;
+} sivf_server_config;
+
+typedef struct {
+    int32_t kind;             /* SIVF_OP_ADD / SIVF_OP_REMOVE / SIVF_OP_SEARCH */
+    int32_t status;           /* status of the batch that served it          */
+    int64_t count;            /* vectors / ids / queries it carried (0 when
+                                 its batch was rejected)                     */
+    int64_t batch;            /* serving order: sequence number of its batch */
+    double latency_ms;        /* arrival -> completion seen by the worker    */
+    double queue_ms;          /* arrival -> launch of its batch              */
+} sivf_request_info;
+
+typedef struct {
+    int64_t requests[3];      /* completed requests per kind (SIVF_OP_*)     */
+    int64_t batches[3];       /* batches per kind                            */
+    int64_t items[3];         /* vectors / ids / queries per kind            */
+    int64_t deferred;         /* times an insert waited for free slabs       */
+    int64_t rejected;         /* requests whose batch was rejected           */
+    int64_t max_in_flight;    /* most batches seen in flight at once         */
+} sivf_server_stats_t;
+
+/*
+ * sivf_server_create -- start a server on `index` (which must have its
+ * centroids).  Reserves every slot's buffers and scratch, then starts the
+ * worker.  While the server lives, no other call may use the index.
+ */
+sivf_status sivf_server_create(sivf_index *index, const sivf_server_config *cfg,
+                               sivf_server **out);
+
+/* sivf_server_now_ns -- the steady clock (ns) that arrival times use. */
+int64_t sivf_server_now_ns(void);
+
+/*
+ * sivf_server_submit -- queue one request; *req receives its id (ids count
+ * up from 0).  kind SIVF_OP_ADD: ids [host] int64[n], x [host] float32[n,d],
+ * and optionally evict [host] int64[n_evict] removed just before the insert
+ * (a sliding window's overflow), within the same batch; SIVF_OP_REMOVE:
+ * ids [host] int64[n]; SIVF_OP_SEARCH: x [host] float32[n, d] queries,
+ * dist [host] float32[n, k] and labels [host] int64[n, k] receive the
+ * results.  The host arrays must stay valid until the request completes.
+ * n must fit the kind's batch limit.  arrival_ns: when the request arrived,
+ * on sivf_server_now_ns's clock (0 = now); latency is measured from it.
+ */
+sivf_status sivf_server_submit(sivf_server *server, int kind, int64_t n, const int64_t *ids,
+                               const float *x, int64_t n_evict, const int64_t *evict,
+                               float *dist, int64_t *labels, int64_t arrival_ns,
+                               int64_t *req);
+
+/*
+ * sivf_server_wait -- wait up to timeout_us (< 0: forever) for request
+ * `req`; on completion fills *info (optional) and returns SIVF_OK, else
+ * SIVF_E_TIMEOUT.  A sticky device error is returned as SIVF_E_CORRUPT /
+ * SIVF_E_TIMEOUT once the worker has seen it.
+ */
+sivf_status sivf_server_wait(sivf_server *server, int64_t req, int64_t timeout_us,
+                             sivf_request_info *info);
+
+/* sivf_server_drain -- wait (up to timeout_us, < 0 forever) until every
+ * request submitted so far has completed. */
+sivf_status sivf_server_drain(sivf_server *server, int64_t timeout_us);
+
+/* sivf_server_stats -- counters since the server started. */
+sivf_status sivf_server_stats(sivf_server *server, sivf_server_stats_t *out);
+
+/* sivf_server_destroy -- serve what is queued, stop the worker, free the
+ * slots.  The index is usable by other calls again afterwards. */
+sivf_status sivf_server_destroy(sivf_server *server);
+
 /* sivf_last_error -- text of the last error on this index (never NULL). */
 const char *sivf_last_error(const sivf_index *index);
 

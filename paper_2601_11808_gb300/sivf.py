@@ -35,6 +35,8 @@ EXPORTS = [
     "sivf_set_tile", "sivf_get_tile", "sivf_autotune",
     "sivf_exec_create", "sivf_exec_launch", "sivf_exec_results", "sivf_exec_kernels",
     "sivf_exec_destroy",
+    "sivf_server_create", "sivf_server_now_ns", "sivf_server_submit", "sivf_server_wait",
+    "sivf_server_drain", "sivf_server_stats", "sivf_server_destroy",
 ]
 
 OP_ADD, OP_REMOVE, OP_SEARCH = 0, 1, 2
@@ -72,6 +74,24 @@ class sivf_op(C.Structure):
 class sivf_op_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("count", C.c_int64),
                 ("device_ms", C.c_double)]
+
+
+class sivf_server_config(C.Structure):
+    _fields_ = [("k", C.c_int32), ("nprobe", C.c_int32), ("dtype", C.c_int32),
+                ("depth", C.c_int32), ("max_query_batch", C.c_int32),
+                ("max_insert_batch", C.c_int32), ("max_delete_batch", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class sivf_request_info(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("status", C.c_int32), ("count", C.c_int64),
+                ("batch", C.c_int64), ("latency_ms", C.c_double), ("queue_ms", C.c_double)]
+
+
+class sivf_server_stats_t(C.Structure):
+    _fields_ = [("requests", C.c_int64 * 3), ("batches", C.c_int64 * 3),
+                ("items", C.c_int64 * 3), ("deferred", C.c_int64), ("rejected", C.c_int64),
+                ("max_in_flight", C.c_int64)]
 
 
 class SivfError(RuntimeError):
@@ -128,6 +148,14 @@ def load(path: str | None = None):
             "sivf_exec_results": (i32, [vp, vp, C.POINTER(sivf_op_result)]),
             "sivf_exec_kernels": (i64, [vp]),
             "sivf_exec_destroy": (i32, [vp]),
+            "sivf_server_create": (i32, [vp, C.POINTER(sivf_server_config), C.POINTER(vp)]),
+            "sivf_server_now_ns": (i64, []),
+            "sivf_server_submit": (i32, [vp, i32, i64, vp, vp, i64, vp, vp, vp, i64,
+                                         C.POINTER(i64)]),
+            "sivf_server_wait": (i32, [vp, i64, i64, C.POINTER(sivf_request_info)]),
+            "sivf_server_drain": (i32, [vp, i64]),
+            "sivf_server_stats": (i32, [vp, C.POINTER(sivf_server_stats_t)]),
+            "sivf_server_destroy": (i32, [vp]),
             "sivf_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -481,6 +509,98 @@ class Exec:
         if getattr(self, "e", None):
             load().sivf_exec_destroy(self.e)
             self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A serving loop over an index (sivf_server): submit requests from host
+    numpy arrays, wait for them.  The wrapper keeps each request's arrays
+    alive until it has been waited for."""
+
+    KINDS = {"add": OP_ADD, "remove": OP_REMOVE, "search": OP_SEARCH}
+
+    def __init__(self, index, k=10, nprobe=32, dtype="fp32", depth=3, max_query_batch=1024,
+                 max_insert_batch=16384, max_delete_batch=16384):
+        lib = load()
+        self.index = index
+        self.h = index.h
+        self.k, self.d = int(k), index.d
+        cfg = sivf_server_config(self.k, int(nprobe), DTYPES[dtype], int(depth),
+                                 int(max_query_batch), int(max_insert_batch),
+                                 int(max_delete_batch), 0)
+        out = C.c_void_p()
+        _check(lib, self.h, lib.sivf_server_create(self.h, C.byref(cfg), C.byref(out)))
+        self.s = out.value
+        self._keep = {}
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(load().sivf_server_now_ns())
+
+    def _submit(self, kind, n, ids=None, x=None, evict=None, dist=None, labels=None,
+                arrival_ns=0):
+        lib = load()
+        req = C.c_int64(0)
+        ne = 0 if evict is None else len(evict)
+        st = lib.sivf_server_submit(self.s, kind, int(n), _ptr(ids), _ptr(x), ne, _ptr(evict),
+                                    _ptr(dist), _ptr(labels), int(arrival_ns), C.byref(req))
+        _check(lib, self.h, st)
+        self._keep[req.value] = (ids, x, evict, dist, labels)
+        return req.value
+
+    def add(self, ids, x, evict=None, arrival_ns=0) -> int:
+        ids = np.ascontiguousarray(ids, np.int64)
+        x = np.ascontiguousarray(x, np.float32).reshape(len(ids), self.d)
+        ev = None if evict is None or len(evict) == 0 else np.ascontiguousarray(evict, np.int64)
+        return self._submit(OP_ADD, len(ids), ids=ids, x=x, evict=ev, arrival_ns=arrival_ns)
+
+    def remove(self, ids, arrival_ns=0) -> int:
+        ids = np.ascontiguousarray(ids, np.int64)
+        return self._submit(OP_REMOVE, len(ids), ids=ids, arrival_ns=arrival_ns)
+
+    def search(self, q, arrival_ns=0) -> int:
+        q = np.ascontiguousarray(q, np.float32).reshape(-1, self.d)
+        dist = np.empty((len(q), self.k), np.float32)
+        labels = np.empty((len(q), self.k), np.int64)
+        return self._submit(OP_SEARCH, len(q), x=q, dist=dist, labels=labels,
+                            arrival_ns=arrival_ns)
+
+    def wait(self, req, timeout_us=-1) -> dict:
+        """{kind, status, count, batch, latency_ms, queue_ms[, dist, labels]}."""
+        lib = load()
+        info = sivf_request_info()
+        _check(lib, self.h, lib.sivf_server_wait(self.s, int(req), int(timeout_us),
+                                                 C.byref(info)))
+        out = {f: getattr(info, f) for f, _ in sivf_request_info._fields_}
+        keep = self._keep.pop(req, None)
+        if keep is not None and info.kind == OP_SEARCH:
+            out["dist"], out["labels"] = keep[3], keep[4]
+        return out
+
+    def drain(self, timeout_us=-1) -> None:
+        lib = load()
+        _check(lib, self.h, lib.sivf_server_drain(self.s, int(timeout_us)))
+
+    def stats(self) -> dict:
+        lib = load()
+        st = sivf_server_stats_t()
+        _check(lib, self.h, lib.sivf_server_stats(self.s, C.byref(st)))
+        return {"requests": list(st.requests), "batches": list(st.batches),
+                "items": list(st.items), "deferred": st.deferred, "rejected": st.rejected,
+                "max_in_flight": st.max_in_flight}
+
+    def close(self) -> None:
+        if getattr(self, "s", None):
+            lib = load()
+            st = lib.sivf_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
+            _check(lib, self.h, st)
 
     def __del__(self):
         try:

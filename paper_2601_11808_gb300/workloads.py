@@ -175,3 +175,57 @@ def sample_ids(seed: int, stream: int, block: int, pool: np.ndarray, n: int) -> 
     if n >= len(pool):
         return g.permutation(pool)
     return g.choice(pool, size=n, replace=False)
+
+
+# ------------------------------------------------- pooled-noise windows
+# A window of 10^8 vectors is too large to draw on the host in a benchmark.
+# For it, position i gets a mixture component c_i and a row r_i of a fixed
+# pool of standard-normal noise vectors, both drawn per block from stream
+# 11, and the vector is fl32(center[c_i] + fl32(sigma * pool[r_i])): two
+# IEEE single-precision operations, so any device that composes it the same
+# way produces the same bits as `pooled_vectors` here.
+
+def noise_pool(w: Workload, size: int) -> np.ndarray:
+    """`size` standard-normal noise vectors, float32 [size, d] (stream 10)."""
+    return _rng(w.seed, 10, 0).standard_normal(size=(size, w.d), dtype=np.float32)
+
+
+def pooled_parts(w: Workload, start: int, n: int, pool_size: int):
+    """(component, pool row) of stream positions [start, start + n), int64."""
+    comp = np.empty(n, np.int64)
+    row = np.empty(n, np.int64)
+    pos = 0
+    for b in range(start // BLOCK, (start + n + BLOCK - 1) // BLOCK):
+        g = _rng(w.seed, 11, b)
+        c = g.integers(0, w.n_comp, size=BLOCK)
+        r = g.integers(0, pool_size, size=BLOCK)
+        lo = max(start, b * BLOCK) - b * BLOCK
+        hi = min(start + n, (b + 1) * BLOCK) - b * BLOCK
+        comp[pos:pos + hi - lo] = c[lo:hi]
+        row[pos:pos + hi - lo] = r[lo:hi]
+        pos += hi - lo
+    return comp, row
+
+
+def pooled_vectors(w: Workload, start: int, n: int, ctr: np.ndarray,
+                   pool: np.ndarray) -> np.ndarray:
+    """Window vectors [start, start + n) of a pooled-noise window, float32."""
+    if w.kind != "uniform_box":
+        raise ValueError("pooled windows are defined for the uniform-box mixture")
+    comp, row = pooled_parts(w, start, n, len(pool))
+    return ctr[comp] + pool[row] * np.float32(w.sigma)
+
+
+def request_stream(n: int, rate_per_s: float, mix=(0.7, 0.1, 0.2), sizes=(10_000, 10_000, 256),
+                   seed: int = 0, stream: int = 20):
+    """A Poisson request stream of n requests at `rate_per_s`: arrival
+    offsets (ns, ascending), kinds (0 insert, 1 delete-oldest, 2 query) drawn
+    with probabilities `mix`, and log-uniform sizes up to `sizes[kind]`."""
+    g = _rng(seed, stream, 0)
+    gaps = g.exponential(1e9 / rate_per_s, size=n)
+    t = np.cumsum(gaps).astype(np.int64)
+    kind = g.choice(3, size=n, p=np.asarray(mix, np.float64))
+    u = g.uniform(0.0, 1.0, size=n)
+    hi = np.asarray(sizes, np.float64)[kind]
+    size = np.clip(np.floor(np.exp(u * np.log(hi))), 1, hi).astype(np.int64)
+    return t, kind, size
