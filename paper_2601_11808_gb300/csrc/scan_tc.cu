@@ -30,7 +30,10 @@ namespace sivf {
 
 constexpr int TC_N = 64;        // queries per tile (MMA N)
 constexpr int TC_M = 128;       // rows per A tile (MMA M)
-constexpr int TC_NT = 256;
+constexpr int TC_EW = 16;                // epilogue warps: four per TMEM lane quarter
+constexpr int TC_EPI = TC_EW * 32;       // epilogue threads
+constexpr int TC_NT = 128 + TC_EPI;      // + TMA, MMA, TMEM-owner and one idle warp
+constexpr int TC_NCOL = TC_N / (TC_EW / 4);  // query columns per epilogue warp
 
 struct TcArgs {
     const float *q;
@@ -52,7 +55,7 @@ struct TcArgs {
     uint32_t *err;
 };
 
-constexpr int TC_NST = 3;       // A-tile stages in flight
+constexpr int TC_NST = TC_EW >= 16 ? 2 : 3;  // A-tile stages in flight
 constexpr int TC_META = 256;    // slabs whose ids and bitmaps are staged at once
 
 struct TcSmem {
@@ -67,9 +70,9 @@ __host__ __device__ inline TcSmem tc_smem(int KC, int M)
     s.bs = s.bd + (size_t)TC_N * M * 4;
     s.msl = s.bs + (size_t)TC_N * M * 4;
     s.mbits = s.msl + (size_t)TC_META * 4;
-    s.hist = s.mbits + (size_t)TC_META * 4 * 4;           // 4 warps x 256 bins
-    s.stg = s.hist + (size_t)4 * 256 * 4;                  // 4 warps x 128 (dist, slot)
-    s.misc = s.stg + (size_t)4 * 128 * 8;
+    s.hist = s.mbits + (size_t)TC_META * 4 * 4;           // per warp 256 bins
+    s.stg = s.hist + (size_t)TC_EW * 256 * 4;              // per warp 128 (dist, slot)
+    s.misc = s.stg + (size_t)TC_EW * 128 * 8;
     s.total = s.misc + 1024 + 1024;                      // + base alignment slack
     return s;
 }
@@ -335,7 +338,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 128);
+            mbar_init(&tempty[i], TC_EPI);
         }
         fence_mbar_init();
         *s_abort = 0;
@@ -485,8 +488,11 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
             }
             __syncwarp();
         } else if (warp >= 4) {
-            const int ew = warp - 4;          // epilogue warp = TMEM lane quarter
-            const int v = ew * 32 + lane;     // A row = vector of the tile
+            const int ew = warp - 4;          // epilogue warp
+            const int qt = ew & 3;            // its TMEM lane quarter (warp % 4)
+            const int c0 = (ew >> 2) * TC_NCOL;  // its first query column
+            const int et = ew * 32 + lane;    // epilogue thread
+            const int v = qt * 32 + lane;     // A row = vector of the tile
             const int CB = ME - K;
             const int BPS = TC_META / SPB;    // tiles whose slab metadata is staged
             float xn_next = 0.f;
@@ -494,16 +500,16 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 const uint32_t g = gblk + b, buf = g & 1, ub = g >> 1;
                 if (b % BPS == 0) {
                     // stage ids + bitmaps of the next TC_META slabs of the chunk
-                    named_bar_sync(1, 128);
+                    named_bar_sync(1, TC_EPI);
                     const int sb0 = b * SPB, sn = min(TC_META, ns - sb0);
-                    for (int i = v; i < sn; i += 128) {
+                    for (int i = et; i < sn; i += TC_EPI) {
                         const int sl = dirl[sb0 + i];
                         const bool okk = sl >= 0 && sl < a.n_slabs;
                         Msl[i] = okk ? sl : -1;
                         for (int w = 0; w < C / 32; ++w)
                             Mbits[i * 4 + w] = okk ? __ldg(a.bits + (size_t)sl * (C / 32) + w) : 0u;
                     }
-                    named_bar_sync(1, 128);
+                    named_bar_sync(1, TC_EPI);
                     const int j0 = v / C;
                     const int s_first = j0 < min(SPB, ns - b * SPB) ? Msl[(b * SPB - sb0) + j0] : -1;
                     xn_next = s_first >= 0 ? __ldg(a.xnorm + (size_t)s_first * C + v % C) : 0.f;
@@ -528,12 +534,12 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-aligned
                 if (!ok) *s_abort = 1;
                 tc_fence_after();
-                float dv[TC_N];
+                float dv[TC_NCOL];
                 if (ok) {
 #pragma unroll
-                    for (int c16 = 0; c16 < TC_N / 16; ++c16) {
+                    for (int c16 = 0; c16 < TC_NCOL / 16; ++c16) {
                         float t[16];
-                        tmem_ld16(tbase + buf * TC_N + c16 * 16 + ((uint32_t)(ew * 32) << 16), t);
+                        tmem_ld16(tbase + buf * TC_N + c0 + c16 * 16 + ((uint32_t)(qt * 32) << 16), t);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) dv[c16 * 16 + i] = t[i];
                     }
@@ -548,7 +554,8 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                 // shared atomic for their buffer slots
                 const float4 *t4 = reinterpret_cast<const float4 *>(s_t);
 #pragma unroll
-                for (int n0 = 0; n0 < TC_N; n0 += 16) {
+                for (int j0 = 0; j0 < TC_NCOL; j0 += 16) {
+                    const int n0 = c0 + j0;
                     if (n0 >= m) break;
                     uint32_t mk[16];
 #pragma unroll
@@ -559,7 +566,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                         for (int c = 0; c < 4; ++c) {
                             const int n = n0 + 4 * i4 + c;
                             const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
-                            const float part = fmaf(-sc, dv[n], xn);
+                            const float part = fmaf(-sc, dv[j0 + 4 * i4 + c], xn);
                             mk[4 * i4 + c] = __ballot_sync(0xffffffffu, ok && live && part <= tt[c]);
                         }
                     }
@@ -573,15 +580,15 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                         if ((mk[i] >> lane) & 1u) {
                             const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
                             const int p = K + base + __popc(mk[i] & lanemask_lt());
-                            BD[(size_t)n * ME + p] = fmaf(-sc, dv[n], s_qn[n] + xn);
+                            BD[(size_t)n * ME + p] = fmaf(-sc, dv[j0 + i], s_qn[n] + xn);
                             BS[(size_t)n * ME + p] = gslot;
                         }
                     }
                 }
-                named_bar_sync(1, 128);
-                // merges: warp ew takes rows n = ew, ew + 4, ...
+                named_bar_sync(1, TC_EPI);
+                // merges: warp ew takes rows n = ew, ew + TC_EW, ...
                 const bool last = b + 1 == nblk;
-                for (int n = ew; n < m; n += 4) {
+                for (int n = ew; n < m; n += TC_EW) {
                     const int cc = s_cc[n];
                     if (cc == 0 || !(last || cc > CB - TC_M)) continue;
                     float *bd = BD + (size_t)n * ME;
@@ -605,7 +612,7 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                     }
                     __syncwarp();
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(1, TC_EPI);
             }
         }
         gblk += nblk;
