@@ -376,9 +376,9 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
 static int64_t query_chunk(const sivf_index *ix, int P, int k)
 {
     (void)ix;
-    // keep the per-chunk candidate buffers near 512 MB
+    // keep the per-chunk candidate buffers near 2 GB
     int64_t per = (int64_t)P * k * 12 * 8;
-    return std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)512 << 20) / per));
+    return std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) / per));
 }
 
 // plan of the reduced-precision scan: tiles of 64 queries, K' candidates
@@ -557,8 +557,8 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
     if (tc && ((dtype == SIVF_BF16 && !ix->xb16) || (dtype == SIVF_FP8E4M3 && !ix->x8)))
         return fail(ix, SIVF_E_ARG, "that reduced-precision copy was not enabled at create");
     const int Kc = tc ? (cand_only ? k : rerank_depth(k)) : k;
-    if (tc && (4 * k > 128 && !cand_only)) return fail(ix, SIVF_E_ARG, "k > 32 for a reduced-precision scan");
-    if (tc && (Kc > 128 || !tc_fits(ix, Kc)))
+    if (tc && (4 * k > 512 && !cand_only)) return fail(ix, SIVF_E_ARG, "k > 128 for a reduced-precision scan");
+    if (tc && (Kc > 512 || !tc_fits(ix, Kc)))
         return fail(ix, SIVF_E_ARG, "k too large for the reduced-precision scan");
     if (!probes_in && !ix->have_centroids) return fail(ix, SIVF_E_STATE, "set_centroids first");
     sivf_status st = check_health(ix);

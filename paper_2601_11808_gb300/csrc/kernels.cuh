@@ -79,6 +79,7 @@ bool tc_make_maps(sivf_index *ix);
 void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
                 cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
+int tc_tile_queries(int Kc);   // 64, or 16 for K' > 128
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
                    const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);

@@ -762,7 +762,7 @@ SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, in
 {
     SearchPlan pl;
     const bool fp32 = dtype == SIVF_FP32;
-    pl.tq = fp32 ? t.queries_per_tile : 64;
+    pl.tq = fp32 ? t.queries_per_tile : tc_tile_queries(K);
     pl.K = K;
     pl.M = fp32 ? fp32_width(K, ix->C, t.select_slabs) : 0;
     pl.split = fp32 ? 0 : t.nearest_first;

@@ -28,12 +28,19 @@
 
 namespace sivf {
 
-constexpr int TC_N = 64;        // queries per tile (MMA N)
 constexpr int TC_M = 128;       // rows per A tile (MMA M)
-constexpr int TC_EW = 16;                // epilogue warps: four per TMEM lane quarter
-constexpr int TC_EPI = TC_EW * 32;       // epilogue threads
-constexpr int TC_NT = 128 + TC_EPI;      // + TMA, MMA, TMEM-owner and one idle warp
-constexpr int TC_NCOL = TC_N / (TC_EW / 4);  // query columns per epilogue warp
+constexpr int TC_NCOL = 16;     // query columns per epilogue warp
+// Two tile shapes: 64 queries per tile for K' <= 128, 16 queries (and
+// buffers for K' <= 512) for deeper re-ranks.  Epilogue warps: four per
+// TMEM lane quarter at 64 queries, one at 16.
+template <int TN> struct TcShape {
+    static constexpr int N = TN;                        // queries per tile (MMA N)
+    static constexpr int EW = 4 * (TN / TC_NCOL);       // epilogue warps
+    static constexpr int EPI = EW * 32;                 // epilogue threads
+    static constexpr int NT = 128 + EPI;                // + TMA, MMA, TMEM owner, idle warp
+    static constexpr int NST = EW >= 16 ? 2 : 3;        // A-tile stages in flight
+    static constexpr int KMAX = TN == 64 ? 128 : 512;   // deepest K' the buffers take
+};
 
 struct TcArgs {
     const float *q;
@@ -55,24 +62,25 @@ struct TcArgs {
     uint32_t *err;
 };
 
-constexpr int TC_NST = TC_EW >= 16 ? 2 : 3;  // A-tile stages in flight
 constexpr int TC_META = 256;    // slabs whose ids and bitmaps are staged at once
 
 struct TcSmem {
     size_t a, b, bd, bs, msl, mbits, hist, stg, misc, total;
 };
+template <int TN>
 __host__ __device__ inline TcSmem tc_smem(int KC, int M)
 {
+    using S = TcShape<TN>;
     TcSmem s;
-    s.a = 0;                                             // TC_NST x KC x 16 KB
-    s.b = s.a + (size_t)TC_NST * KC * TC_M * 128;        // KC x 64 rows x 128 B
-    s.bd = s.b + (size_t)KC * TC_N * 128;
-    s.bs = s.bd + (size_t)TC_N * M * 4;
-    s.msl = s.bs + (size_t)TC_N * M * 4;
+    s.a = 0;                                             // NST x KC x 16 KB
+    s.b = s.a + (size_t)S::NST * KC * TC_M * 128;        // KC x TN rows x 128 B
+    s.bd = s.b + (size_t)KC * TN * 128;
+    s.bs = s.bd + (size_t)TN * M * 4;
+    s.msl = s.bs + (size_t)TN * M * 4;
     s.mbits = s.msl + (size_t)TC_META * 4;
     s.hist = s.mbits + (size_t)TC_META * 4 * 4;           // per warp 256 bins
-    s.stg = s.hist + (size_t)TC_EW * 256 * 4;              // per warp 128 (dist, slot)
-    s.misc = s.stg + (size_t)TC_EW * 128 * 8;
+    s.stg = s.hist + (size_t)S::EW * 256 * 4;             // per warp KMAX (dist, slot)
+    s.misc = s.stg + (size_t)S::EW * S::KMAX * 8;
     s.total = s.misc + 1024 + 1024;                      // + base alignment slack
     return s;
 }
@@ -128,7 +136,7 @@ __device__ __forceinline__ void warp_sort32(float (&v)[E], int32_t (&s)[E], int 
 // (bd/bs[0, nb)), keeping the K smallest: the candidates are sorted in
 // registers, written back in order, and every output position finds its
 // split between the two sorted runs by binary search (merge path).
-template <int EC>
+template <int EC, int KMAX>
 __device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc, int lane)
 {
     float v[EC];
@@ -150,7 +158,7 @@ __device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
     }
     __syncwarp();
     const int n = min(K, nb + nc);
-    constexpr int OPL = 4;  // outputs per lane (K <= 128)
+    constexpr int OPL = KMAX / 32;  // outputs per lane (K <= KMAX)
     float ov[OPL];
     int32_t os[OPL];
 #pragma unroll
@@ -184,10 +192,11 @@ __device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
 
 // Keep the K smallest of best[0, nb) (sorted) and cand[K, K + nc) when the
 // union is too large to sort in registers: a warp radix select finds the
-// K-th smallest key in four 8-bit passes over the union, the entries at or
-// below it (ties included, at most 128) are gathered and sorted.  Falls
-// back to nothing else: more than 128 entries tied at the K-th key keep
-// the first ones found, ordered by slot among the gathered.
+// K-th smallest key in 8-bit passes over the union, the entries at or
+// below it (ties included, at most KMAX) are gathered and sorted.  More
+// than KMAX entries tied at the K-th key keep the first ones found,
+// ordered by slot among the gathered.
+template <int KMAX>
 __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
                                     uint32_t *hist, float *stg_d, int32_t *stg_s, int lane)
 {
@@ -255,7 +264,7 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
         need -= below;
         __syncwarp();
     }
-    // gather every entry at or below the K-th key (at most 128)
+    // gather every entry at or below the K-th key (at most KMAX)
     int cnt = 0;
     for (int i0 = 0; i0 < n; i0 += 32) {
         const int i = i0 + lane;
@@ -269,26 +278,27 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
         }
         const uint32_t mk = __ballot_sync(0xffffffffu, take);
         const int p = cnt + __popc(mk & lanemask_lt());
-        if (take && p < 128) {
+        if (take && p < KMAX) {
             stg_d[p] = dv;
             stg_s[p] = sv;
         }
         cnt += __popc(mk);
     }
     __syncwarp();
-    cnt = min(cnt, 128);
-    float v[4];
-    int32_t sv[4];
+    cnt = min(cnt, KMAX);
+    constexpr int E = KMAX / 32;
+    float v[E];
+    int32_t sv[E];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < E; ++e) {
         const int i = lane + 32 * e;
         v[e] = i < cnt ? stg_d[i] : INFINITY;
         sv[e] = i < cnt ? stg_s[i] : 0x7fffffff;
     }
-    warp_sort32<4>(v, sv, lane);
+    warp_sort32<E>(v, sv, lane);
     __syncwarp();
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < E; ++e) {
         const int i = lane + 32 * e;
         if (i < K) {
             bd[i] = v[e];
@@ -298,15 +308,18 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
     __syncwarp();
 }
 
-template <int DT>  // 0 = BF16, 1 = FP8 E4M3
-__global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CUtensorMap tmap,
-                                                      TcArgs a)
+template <int DT, int TN>  // DT: 0 = BF16, 1 = FP8 E4M3; TN: queries per tile
+__global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
+    const __grid_constant__ CUtensorMap tmap, TcArgs a)
 {
+    using S = TcShape<TN>;
+    constexpr int TC_N = TN, TC_EW = S::EW, TC_EPI = S::EPI, TC_NT = S::NT, TC_NST = S::NST;
+    constexpr int KMAX = S::KMAX;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled operand tiles
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     const int KC = a.KC, M = a.M, K = a.K, C = a.C, d = a.d;
-    const TcSmem L = tc_smem(KC, M);
+    const TcSmem L = tc_smem<TN>(KC, M);
     unsigned char *A = smem + L.a;
     unsigned char *B = smem + L.b;
     float *BD = reinterpret_cast<float *>(smem + L.bd);
@@ -594,13 +607,14 @@ __global__ __launch_bounds__(TC_NT, 1) void k_scan_tc(const __grid_constant__ CU
                     float *bd = BD + (size_t)n * ME;
                     int32_t *bs = BS + (size_t)n * ME;
                     const int nb = s_nb[n];
-                    if (cc <= 32) warp_sort_merge32<1>(bd, bs, K, nb, cc, lane);
-                    else if (cc <= 64) warp_sort_merge32<2>(bd, bs, K, nb, cc, lane);
-                    else if (cc <= 128) warp_sort_merge32<4>(bd, bs, K, nb, cc, lane);
+                    if (cc <= 32) warp_sort_merge32<1, KMAX>(bd, bs, K, nb, cc, lane);
+                    else if (cc <= 64) warp_sort_merge32<2, KMAX>(bd, bs, K, nb, cc, lane);
+                    else if (cc <= 128) warp_sort_merge32<4, KMAX>(bd, bs, K, nb, cc, lane);
                     else
-                        warp_select_merge32(bd, bs, K, nb, cc, Hist + ew * 256,
-                                            reinterpret_cast<float *>(Stg + ew * 1024),
-                                            reinterpret_cast<int32_t *>(Stg + ew * 1024 + 512), lane);
+                        warp_select_merge32<KMAX>(
+                            bd, bs, K, nb, cc, Hist + ew * 256,
+                            reinterpret_cast<float *>(Stg + (size_t)ew * KMAX * 8),
+                            reinterpret_cast<int32_t *>(Stg + (size_t)ew * KMAX * 8 + KMAX * 4), lane);
                     const int nb2 = min(K, nb + cc);
                     if (lane == 0) {
                         s_nb[n] = nb2;
@@ -693,6 +707,75 @@ __global__ __launch_bounds__(128) void k_rerank(const float *__restrict__ q, int
     }
 }
 
+// Deep re-rank (K' up to 512): one block per query; its warps compute the
+// candidates' exact FP32 direct-form distances into shared memory, then
+// the block sorts them by (distance, id) with a bitonic network and writes
+// the best k.
+constexpr int RR_NT = 256;
+constexpr int RR_MAX = 512;
+__global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__ q, int64_t nq,
+                                                       int d, int Kc,
+                                                       const float *__restrict__ cand_d,
+                                                       const int64_t *__restrict__ cand_s,
+                                                       const float *__restrict__ x32,
+                                                       const int64_t *__restrict__ ids, int k,
+                                                       float *__restrict__ dist,
+                                                       int64_t *__restrict__ labels)
+{
+    __shared__ float sd[RR_MAX];
+    __shared__ int64_t si[RR_MAX];
+    const int64_t qi = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t PAD = 0x7fffffffffffffffLL;  // pads sort after every id
+    int N = 32;
+    while (N < Kc) N <<= 1;
+    const float *qr = q + (size_t)qi * d;
+    for (int c = warp; c < N; c += RR_NT / 32) {
+        float acc = INFINITY;
+        int64_t lab = PAD;
+        if (c < Kc) {
+            const int64_t gs = cand_s[qi * Kc + c];
+            if (gs >= 0 && cand_d[qi * Kc + c] < INFINITY) {
+                const float *xr = x32 + (size_t)gs * d;
+                float a = 0.f;
+                for (int j = lane; j < d; j += 32) {
+                    const float t = qr[j] - xr[j];
+                    a = fmaf(t, t, a);
+                }
+                acc = warp_sum(a);
+                lab = ids[gs];
+            }
+        }
+        if (lane == 0) {
+            sd[c] = acc;
+            si[c] = lab;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= N; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < N / 2; t += RR_NT) {
+                const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                const bool up = (i & size) == 0;
+                const bool lt = dk_less(sd[j], si[j], sd[i], si[i]);
+                if (lt == up) {
+                    const float td = sd[i];
+                    sd[i] = sd[j];
+                    sd[j] = td;
+                    const int64_t ti = si[i];
+                    si[i] = si[j];
+                    si[j] = ti;
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = tid; i < k; i += RR_NT) {
+        const bool ok = i < N && si[i] != PAD;
+        dist[qi * k + i] = ok ? sd[i] : INFINITY;
+        labels[qi * k + i] = ok ? si[i] : -1;
+    }
+}
+
 // per query: FP32 ||q||^2 and the FP8 inverse scale 448 / (2 max_j |q_j|)
 __global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
                              float *__restrict__ qn, float *__restrict__ qsc)
@@ -781,15 +864,32 @@ bool tc_make_maps(sivf_index *ix)
     return true;
 }
 
-// best K' entries + room for one more tile of candidates, at most 256 (the
-// rank merge's capacity) for K' <= 128
+// best K' entries + room for one more tile of candidates
 int tc_buf_len(int K) { return (K + TC_M + 7) / 8 * 8; }
+
+// queries per tile of the reduced-precision scan for K' candidates
+int tc_tile_queries(int Kc) { return Kc <= TcShape<64>::KMAX ? 64 : 16; }
 
 bool tc_fits(const sivf_index *ix, int Kc)
 {
     const int esz = 2;  // the larger of the two formats
     const int KC = (ix->d * esz + 127) / 128;
-    return Kc <= 128 && tc_smem(KC, tc_buf_len(Kc)).total <= 227 * 1024 - 1024;
+    if (Kc <= TcShape<64>::KMAX) return tc_smem<64>(KC, tc_buf_len(Kc)).total <= 227 * 1024 - 1024;
+    return Kc <= TcShape<16>::KMAX && tc_smem<16>(KC, tc_buf_len(Kc)).total <= 227 * 1024 - 1024;
+}
+
+template <int DT, int TN>
+static void launch_tc(const unsigned char *tmap, const TcArgs &a, cudaStream_t st)
+{
+    const size_t smem = tc_smem<TN>(a.KC, a.M).total;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_scan_tc<DT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = smem;
+    }
+    k_scan_tc<DT, TN><<<152, TcShape<TN>::NT, smem, st>>>(
+        *reinterpret_cast<const CUtensorMap *>(tmap), a);
 }
 
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
@@ -827,22 +927,14 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.KC = (ix->d * esz + 127) / 128;
     a.ctl = ix->ctl;
     a.err = ix->err;
-    const size_t smem = tc_smem(a.KC, a.M).total;
+    const bool wide = tc_tile_queries(Kc) == 64;
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {
-        static size_t attr = 0;
-        if (smem > attr) {
-            cudaFuncSetAttribute(k_scan_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = smem;
-        }
-        k_scan_tc<0><<<152, TC_NT, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(ix->tmap_bf16), a);
+        if (wide) launch_tc<0, 64>(ix->tmap_bf16, a, st);
+        else launch_tc<0, 16>(ix->tmap_bf16, a, st);
     } else {
-        static size_t attr = 0;
-        if (smem > attr) {
-            cudaFuncSetAttribute(k_scan_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = smem;
-        }
-        k_scan_tc<1><<<152, TC_NT, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(ix->tmap_fp8), a);
+        if (wide) launch_tc<1, 64>(ix->tmap_fp8, a, st);
+        else launch_tc<1, 16>(ix->tmap_fp8, a, st);
     }
     prof_end(ix, tok, st);
 }
@@ -852,15 +944,16 @@ void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *can
 {
     const int64_t blocks = (nq * 32 + 127) / 128;
     const int tok = prof_begin(ix, PROF_RERANK, 1, st);
-    if (Kc <= 32)
-        k_rerank<1><<<(unsigned)blocks, 128, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
-                                                      ix->ids, k, dist, labels);
-    else if (Kc <= 64)
-        k_rerank<2><<<(unsigned)blocks, 128, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
-                                                      ix->ids, k, dist, labels);
+#define SIVF_RERANK(E_)                                                                  \
+    k_rerank<E_><<<(unsigned)blocks, 128, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32, \
+                                                   ix->ids, k, dist, labels)
+    if (Kc <= 32) SIVF_RERANK(1);
+    else if (Kc <= 64) SIVF_RERANK(2);
+    else if (Kc <= 128) SIVF_RERANK(4);
     else
-        k_rerank<4><<<(unsigned)blocks, 128, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
+        k_rerank_wide<<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
                                                       ix->ids, k, dist, labels);
+#undef SIVF_RERANK
     prof_end(ix, tok, st);
 }
 

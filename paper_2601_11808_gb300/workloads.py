@@ -229,3 +229,21 @@ def request_stream(n: int, rate_per_s: float, mix=(0.7, 0.1, 0.2), sizes=(10_000
     hi = np.asarray(sizes, np.float64)[kind]
     size = np.clip(np.floor(np.exp(u * np.log(hi))), 1, hi).astype(np.int64)
     return t, kind, size
+
+
+def vectors_threaded(w: Workload, start: int, n: int, ctr: np.ndarray | None = None,
+                     threads: int = 16, stream: int = 1) -> np.ndarray:
+    """`vectors` (stream 1) or `queries` (stream 2) drawn by several threads
+    over disjoint position ranges; the result is the same array."""
+    from concurrent.futures import ThreadPoolExecutor
+    ctr = centers(w) if ctr is None else ctr
+    out = np.empty((n, w.d), np.float32)
+    step = max(BLOCK, -(-n // (threads * BLOCK)) * BLOCK)
+
+    def part(lo):
+        hi = min(n, lo + step)
+        out[lo:hi] = _draw(w, ctr, stream, start + lo, hi - lo)
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(part, range(0, n, step)))
+    return out

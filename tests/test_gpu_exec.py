@@ -242,10 +242,10 @@ def test_queue_argument_errors(torch):
             "labels": torch.empty((3, 5), dtype=torch.int64, device="cuda")}]
     with pytest.raises(SivfError):
         g.executor(bad)
-    with pytest.raises(SivfError):     # 4k > 128: no reduced-precision scan for k = 40
-        g.executor([dict(bad[0], nprobe=2, k=40, dtype="bf16",
-                         dist=torch.empty((3, 40), dtype=torch.float32, device="cuda"),
-                         labels=torch.empty((3, 40), dtype=torch.int64, device="cuda"))])
+    with pytest.raises(SivfError):     # 4k > 512: no reduced-precision scan for k = 200
+        g.executor([dict(bad[0], nprobe=2, k=200, dtype="bf16",
+                         dist=torch.empty((3, 200), dtype=torch.float32, device="cuda"),
+                         labels=torch.empty((3, 200), dtype=torch.int64, device="cuda"))])
 
 
 def _t(tq, spc, ips, sel, nf=0):

@@ -102,14 +102,15 @@ W_LONG = W.small("sift_window", n_comp=16, nlist=16, slab_size=64)
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-@pytest.mark.parametrize("w,n,nq", [(W_SMALL, 6000, 40), (W_DEEP, 6000, 40), (W_LONG, 60000, 24)],
-                         ids=["sift", "deep", "long_lists"])
-def test_candidates_match_oracle_approximation(torch, w, n, nq, dtype):
+@pytest.mark.parametrize("w,n,nq,kc", [(W_SMALL, 6000, 40, 40), (W_DEEP, 6000, 40, 40),
+                                       (W_LONG, 60000, 24, 40), (W_DEEP, 12000, 30, 400)],
+                         ids=["sift", "deep", "long_lists", "deep_k400"])
+def test_candidates_match_oracle_approximation(torch, w, n, nq, kc, dtype):
     """long_lists: ~2,500 live vectors per list and a few queries per tile,
     so whole lists accumulate in one buffer and the radix-select merge runs."""
     g, o, x, ids, live, cent, ctr = _setup(torch, w, n)
     Q = W.queries(w, 0, nq, ctr)
-    P, kc = 4, 40
+    P = 4
     cd, ci = g.search_candidates(torch.from_numpy(Q).cuda(), kc, P, dtype)
     cd, ci = cd.cpu().numpy().astype(np.float64), ci.cpu().numpy()
     inv = g.dump_payload()["inv_scale"]
@@ -138,11 +139,14 @@ def test_candidates_match_oracle_approximation(torch, w, n, nq, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-@pytest.mark.parametrize("w", [W_SMALL, W_DEEP], ids=["sift", "deep"])
-def test_reranked_search_exact_distances_and_recall(torch, w, dtype):
-    g, o, x, ids, live, cent, ctr = _setup(torch, w, 8000)
+@pytest.mark.parametrize("w,k", [(W_SMALL, 10), (W_DEEP, 10), (W_DEEP, 100)],
+                         ids=["sift", "deep", "deep_k100"])
+def test_reranked_search_exact_distances_and_recall(torch, w, k, dtype):
+    """k = 100 re-ranks 400 candidates per query (the deep-precision shape:
+    16-query tiles, the block-wide re-rank)."""
+    g, o, x, ids, live, cent, ctr = _setup(torch, w, 8000 if k <= 10 else 16000)
     Q = W.queries(w, 0, 200, ctr)
-    k, P = 10, 6
+    P = 6
     gd, gi = g.search(torch.from_numpy(Q).cuda(), k, P, dtype)
     gd, gi = gd.cpu().numpy().astype(np.float64), gi.cpu().numpy()
     od, oi = o.search(Q, k, P)
@@ -174,4 +178,4 @@ def test_reduced_dtype_needs_its_copy(torch):
     with pytest.raises(SivfError):
         g.search(q, 5, 2, "fp8")
     with pytest.raises(SivfError):
-        g.search(q, 33, 2, "bf16")        # 4k > 128
+        g.search(q, 129, 2, "bf16")       # 4k > 512
