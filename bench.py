@@ -42,6 +42,11 @@ NPROBES = (8, 16, 32, 64, 128)
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# ncu capture of the BF16 list scan on this workload (nprobe 8): mean
+# dram__bytes_read.sum + dram__bytes_write.sum over its two launches, and the
+# scan kernel source it was taken of
+TC_PROFILED_SHA = "914051e0047bb9a0"
+TC_PROFILED_TRAFFIC = round((279.867648 + 6.304 + 280.654592 + 27.030272) / 2 * 1e6)
 
 
 def parse():
@@ -729,6 +734,7 @@ def main():
             "scan": prof["scan"], "launches": launches, "clocks": clk,
             "pairs": st1["pairs_scanned"] - st0["pairs_scanned"],
             "sbytes": st1["slab_bytes_scanned"] - st0["slab_bytes_scanned"],
+            "ubytes": st1["list_bytes_scanned"] - st0["list_bytes_scanned"],
         }
 
     ok = [f for f in forms if calib[f]["meets_target"]] or forms
@@ -747,16 +753,29 @@ def main():
                                  "form issues 2 instructions per 3 flops, so its ceiling is 0.75",
                     "kernel": "k_scan (FP32 direct form)"}
     else:
-        gbs = r["sbytes"] / (scan_ms / 1e3) / 1e9 if scan_ms > 0 else 0.0
+        # algorithmic bytes: the unique bytes of the lists each launch probes
+        # (payload copy, norms, bitmaps), the list-centric lower bound
+        gbs = r["ubytes"] / (scan_ms / 1e3) / 1e9 if scan_ms > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.get("hbm_gbs"),
                     "unit": "GB/s", "frac": round(gbs / pk.get("hbm_gbs", 6695.5), 4),
-                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), "
+                                 "of measured",
                     "kernel": f"k_scan_tc<{head}> (tcgen05 scan of the {head} copy)",
                     "tensor_view": {"tflops": round(2.0 * w.d * r["pairs"] / (scan_ms / 1e3) / 1e12, 2),
-                                    "peak_bf16_tflops": pk.get("bf16_tflops")}}
-    roofline.update({"traffic": None, "launches": scan_n,
+                                    "peak_bf16_tflops": pk.get("bf16_tflops")},
+                    "tile_read_bytes_per_launch": r["sbytes"] / max(scan_n, 1)}
+    traffic = None
+    if head != "fp32":
+        # DRAM bytes per launch of this kernel from one ncu capture on this
+        # workload, valid while the kernel source is the one it was taken of
+        import hashlib
+        src = os.path.join(ROOT, "paper_2601_11808_gb300", "csrc", "scan_tc.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TC_PROFILED_SHA:
+            traffic = TC_PROFILED_TRAFFIC
+    roofline.update({"traffic": traffic, "launches": scan_n,
                      "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
-                     "algorithmic_bytes_per_launch": r["sbytes"] / max(scan_n, 1),
+                     "algorithmic_bytes_per_launch": (r["ubytes"] if head != "fp32" else r["sbytes"])
+                     / max(scan_n, 1),
                      "flops_per_launch": (3.0 if head == "fp32" else 2.0) * w.d * r["pairs"]
                      / max(scan_n, 1)})
 

@@ -81,9 +81,12 @@ typedef struct {
     int64_t bytes_device;/* device memory held by the index                  */
     int64_t pairs_scanned;      /* (query, live vector) pairs the list scans
                                    have scored since creation (FP32 path)    */
-    int64_t slab_bytes_scanned; /* slab payload + id bytes the list scans
-                                   streamed since creation, one read per
-                                   (list, query tile)                        */
+    int64_t slab_bytes_scanned; /* slab bytes the list scans streamed since
+                                   creation (payload, ids or norms, bitmap),
+                                   one read per (list, query tile)           */
+    int64_t list_bytes_scanned; /* the same counted once per list a scan
+                                   launch probes: the unique bytes of the
+                                   probed lists, the list-centric bound     */
 } sivf_stats_t;
 
 /*

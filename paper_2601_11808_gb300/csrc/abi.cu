@@ -608,7 +608,8 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             // phase 1: every query's nearest list alone sets a tight bound on
             // its K'-th distance; phase 2 scans the other lists under it
             const int esz = dtype == SIVF_BF16 ? 2 : 1;
-            const int64_t sb = (int64_t)ix->C * ix->d * esz;
+            // per slab: payload copy, ||x||^2 and the validity bitmap
+            const int64_t sb = (int64_t)ix->C * (ix->d * esz + 4) + ix->C / 8;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
             query_prep(ix, qq, m, sc.qn, sc.qsc, s);
             const int split = P > 1 && pl.split ? 1 : P;
@@ -703,6 +704,7 @@ sivf_status sivf_stats(sivf_index *ix, void *stream, sivf_stats_t *out)
     const int64_t live = stat[0];
     out->pairs_scanned = stat[1];
     out->slab_bytes_scanned = stat[2];
+    out->list_bytes_scanned = stat[3];
     CUDA_TRY(ix, cudaMemcpy(&top, ix->free_top, 4, cudaMemcpyDeviceToHost));
     CUDA_TRY(ix, cudaMemcpy(&err, ix->err, 4, cudaMemcpyDeviceToHost));
     out->ntotal = live;

@@ -63,7 +63,7 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
     const int per = (L + 1023) / 1024;
     const int b0 = tid * per, b1 = min(L, b0 + per);
     int32_t ca = 0, cb = 0;
-    unsigned long long pairs = 0, bytes = 0;
+    unsigned long long pairs = 0, bytes = 0, ubytes = 0;
     for (int l = b0; l < b1; ++l) {
         int m = lcnt[l], ns = nslabs[l];
         int nt = (m + tq - 1) / tq;
@@ -75,10 +75,12 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
         if (c) {
             pairs += (unsigned long long)m * (unsigned long long)max(list_live[l], 0);
             bytes += (unsigned long long)nt * ns * slab_bytes;
+            ubytes += (unsigned long long)ns * slab_bytes;
         }
     }
     if (pairs) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 1), pairs);
     if (bytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 2), bytes);
+    if (ubytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 3), ubytes);
     sa[tid] = ca;
     sb[tid] = cb;
     __syncthreads();
@@ -811,7 +813,8 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
 {
     const int L = ix->nlist;
     cudaMemsetAsync(s.thr, 0x7f, sizeof(float) * nq, st);  // 3.4e38: no bound yet
-    group_pairs(ix, nq, P, 0, P, probes, dedupe, pl, s, (int64_t)ix->C * (ix->d * 4 + 8), st);
+    group_pairs(ix, nq, P, 0, P, probes, dedupe, pl, s,
+                (int64_t)ix->C * (ix->d * 4 + 8) + ix->C / 8, st);
 
     ScanArgs a;
     a.q = q;

@@ -53,7 +53,7 @@ class sivf_stats_t(C.Structure):
                 ("used_slabs", C.c_int64), ("error_bits", C.c_uint32),
                 ("last_status", C.c_int32), ("last_count", C.c_int64),
                 ("bytes_device", C.c_int64), ("pairs_scanned", C.c_int64),
-                ("slab_bytes_scanned", C.c_int64)]
+                ("slab_bytes_scanned", C.c_int64), ("list_bytes_scanned", C.c_int64)]
 
 
 class sivf_tile(C.Structure):
