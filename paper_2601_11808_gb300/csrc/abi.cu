@@ -397,7 +397,7 @@ static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dty
     *plo = pl;
     return coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
            (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * pl.K * 12 +
-           ((size_t)m * P + L) * pl.ch * 8 + 18 * 256;
+           ((size_t)m * P + L) * pl.ch * 8 + (size_t)m * ix->d * 2 + 19 * 256;
 }
 
 // reduced-precision candidates: the re-rank depth K' = 4k
@@ -590,6 +590,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.items = b.take<int2>(((size_t)m * P + L) * pl.ch);
         sc.qn = b.take<float>((size_t)m);
         sc.qsc = b.take<float>((size_t)m);
+        sc.qcast = tc ? b.take<unsigned char>((size_t)m * ix->d * 2) : nullptr;
         float *cand_d = b.take<float>((size_t)m * pl.K);
         int64_t *cand_s = b.take<int64_t>((size_t)m * pl.K);
         const int64_t rows = coarse_rows(ix, m);
@@ -611,7 +612,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             // per slab: payload copy, ||x||^2 and the validity bitmap
             const int64_t sb = (int64_t)ix->C * (ix->d * esz + 4) + ix->C / 8;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
-            query_prep(ix, qq, m, sc.qn, sc.qsc, s);
+            query_prep(ix, dtype, qq, m, sc.qn, sc.qsc, sc.qcast, s);
             const int split = P > 1 && pl.split ? 1 : P;
             group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
             scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
@@ -620,11 +621,10 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
                 scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
             }
             if (cand_only) {
-                merge_topk(ix, m, P, probes, pl, sc, Kc, dist + q0 * k,
-                           reinterpret_cast<int64_t *>(labels + q0 * k), s);
+                merge_tc(ix, m, P, pl, sc, Kc, dist + q0 * k, labels + q0 * k, s);
                 slots_to_ids(ix, labels + q0 * k, m * k, s);
             } else {
-                merge_topk(ix, m, P, probes, pl, sc, Kc, cand_d, cand_s, s);
+                merge_tc(ix, m, P, pl, sc, Kc, cand_d, cand_s, s);
                 rerank(ix, qq, m, Kc, cand_d, cand_s, k, dist + q0 * k, labels + q0 * k, s);
             }
         }

@@ -375,6 +375,199 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
     }
 }
 
+// ----------------------------------------------- warp-per-row selection
+// The same selection for P <= CW_PMAX with one warp per row and no block
+// barriers: each lane keeps the CW_PMAX smallest upper bounds of its lists
+// (sorted, in registers), the warp extracts the P-th smallest of their
+// union as T, then gathers S, tests the sure members and re-decides the
+// rest in FP64 exactly as above.  Rows whose S exceeds CW_SCAP take the
+// serial FP64 path.
+constexpr int CW_ROWS = 4;     // rows (warps) per block
+constexpr int CW_PMAX = 8;
+constexpr int CW_SCAP = 128;
+
+__global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
+{
+    __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP];
+    __shared__ int sIdx[CW_ROWS][CW_SCAP];
+    __shared__ double sDx[CW_ROWS][CW_SCAP];
+    __shared__ unsigned char sSure[CW_ROWS][CW_SCAP];
+    __shared__ int sSel[CW_ROWS][CW_PMAX];
+    __shared__ double sHd[CW_ROWS][CW_PMAX];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * CW_ROWS + w;
+    if (row >= a.m) return;  // whole warps
+    const int L = a.L, P = a.P;
+    const float *Dr = a.D + (size_t)row * L;
+    const float *xr = a.x + (size_t)row * a.d;
+
+    // ||x|| upper bound from an FP64 sum
+    double part = 0.0;
+    for (int j = lane; j < a.d; j += 32) part += (double)xr[j] * (double)xr[j];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const float xn = __double2float_ru(sqrt(part) * (1.0 + 1e-12));
+
+    // T = P-th smallest upper bound
+    float top[CW_PMAX];
+#pragma unroll
+    for (int k = 0; k < CW_PMAX; ++k) top[k] = INFINITY;
+    for (int c = lane; c < L; c += 32) {
+        const float Dt = Dr[c];
+        float v = upper_of(Dt, bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2));
+#pragma unroll
+        for (int k = 0; k < CW_PMAX; ++k) {  // insert into the sorted list
+            const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
+            top[k] = lo;
+            v = hi;
+        }
+    }
+    float T = INFINITY;
+    for (int t = 0; t < P; ++t) {
+        float v = top[0];
+        int who = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int ow = __shfl_xor_sync(0xffffffffu, who, o);
+            if (ov < v || (ov == v && ow < who)) {
+                v = ov;
+                who = ow;
+            }
+        }
+        T = v;
+        if (lane == who) {
+#pragma unroll
+            for (int k = 0; k + 1 < CW_PMAX; ++k) top[k] = top[k + 1];
+            top[CW_PMAX - 1] = INFINITY;
+        }
+    }
+
+    // candidate set S
+    int ns = 0;
+    for (int c0 = 0; c0 < L; c0 += 32) {
+        const int c = c0 + lane;
+        float lb = 0.f, ub = 0.f;
+        bool in = false;
+        if (c < L) {
+            const float Dt = Dr[c];
+            const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
+            lb = lower_of(Dt, E);
+            ub = upper_of(Dt, E);
+            in = lb <= T;
+        }
+        const uint32_t mk = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int p = ns + __popc(mk & lanemask_lt());
+            if (p < CW_SCAP) {
+                sLB[w][p] = lb;
+                sUB[w][p] = ub;
+                sIdx[w][p] = c;
+            }
+        }
+        ns += __popc(mk);
+    }
+    __syncwarp();
+    int32_t *outr = a.out + (size_t)row * P;
+    int nsel = 0;
+    if (ns <= CW_SCAP) {
+        // sure members
+        for (int p0 = 0; p0 < ns; p0 += 32) {
+            const int p = p0 + lane;
+            bool sure = false;
+            if (p < ns) {
+                const float ub = sUB[w][p];
+                int cnt = 0;
+                for (int q = 0; q < ns; ++q) cnt += (q != p && sLB[w][q] <= ub);
+                sure = ub <= T && cnt < P;
+                sSure[w][p] = sure;
+            }
+            const uint32_t mk = __ballot_sync(0xffffffffu, sure);
+            if (sure) {
+                const int s = nsel + __popc(mk & lanemask_lt());
+                if (s < CW_PMAX) sSel[w][s] = sIdx[w][p];
+            }
+            nsel += __popc(mk);
+        }
+        __syncwarp();
+        const int r = P - nsel, nb = ns - nsel;
+        if (r > 0) {
+            // boundary members: exact FP64 distances, rank among them
+            if (nb > r) {
+                for (int p = lane; p < ns; p += 32)
+                    if (!sSure[w][p]) sDx[w][p] = exact_dist(xr, a.cent + (size_t)sIdx[w][p] * a.d, a.d);
+                __syncwarp();
+            }
+            for (int p0 = 0; p0 < ns; p0 += 32) {
+                const int p = p0 + lane;
+                bool take = false;
+                if (p < ns && !sSure[w][p]) {
+                    take = true;
+                    if (nb > r) {
+                        const double Dc = sDx[w][p];
+                        const int c = sIdx[w][p];
+                        int rank = 0;
+                        for (int q = 0; q < ns; ++q) {
+                            if (q == p || sSure[w][q]) continue;
+                            rank += (sDx[w][q] < Dc || (sDx[w][q] == Dc && sIdx[w][q] < c));
+                        }
+                        take = rank < r;
+                    }
+                }
+                const uint32_t mk = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const int s = nsel + __popc(mk & lanemask_lt());
+                    if (s < CW_PMAX) sSel[w][s] = sIdx[w][p];
+                }
+                nsel += __popc(mk);
+            }
+        }
+    } else {
+        // pathological (more than CW_SCAP candidates, e.g. many identical
+        // centroids): exact FP64 insertion into a sorted array of P, lists
+        // in index order (keeps the lowest index among ties)
+        if (lane == 0) {
+            int n = 0;
+            for (int c = 0; c < L; ++c) {
+                const float Dt = Dr[c];
+                const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
+                if (lower_of(Dt, E) > T) continue;
+                const double Dc = exact_dist(xr, a.cent + (size_t)c * a.d, a.d);
+                if (n == P && !(Dc < sHd[w][n - 1])) continue;
+                int pos = n < P ? n : P - 1;
+                while (pos > 0 && Dc < sHd[w][pos - 1]) {
+                    sHd[w][pos] = sHd[w][pos - 1];
+                    sSel[w][pos] = sSel[w][pos - 1];
+                    --pos;
+                }
+                sHd[w][pos] = Dc;
+                sSel[w][pos] = c;
+                if (n < P) ++n;
+            }
+            nsel = n;
+        }
+        nsel = __shfl_sync(0xffffffffu, nsel, 0);
+    }
+    __syncwarp();
+    // the selected set nearest first: ascending approximate distance, ties
+    // to the lower list index (the set itself is the exact one)
+    if (nsel != P && lane == 0) atomicOr(a.err, ERR_SELECT);
+    nsel = min(nsel, P);
+    if (lane < P) {
+        if (lane >= nsel) {
+            outr[lane] = -1;
+        } else {
+            const int c = sSel[w][lane];
+            const float dc = Dr[c];
+            int pos = 0;
+            for (int q = 0; q < nsel; ++q) {
+                const int c2 = sSel[w][q];
+                const float d2 = Dr[c2];
+                pos += d2 < dc || (d2 == dc && c2 < c);
+            }
+            outr[pos] = c;
+        }
+    }
+}
+
 // ------------------------------------------------------------ host drivers
 void centroid_prep(sivf_index *ix, cudaStream_t st)
 {
@@ -409,7 +602,10 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.gamma2 = (float)(2.0 * gd * (1.0 + 1e-6));
         a.out = out + r0 * P;
         a.err = ix->err;
-        k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
+        if (P <= CW_PMAX)
+            k_coarse_select_w<<<(unsigned)((mc + CW_ROWS - 1) / CW_ROWS), CW_ROWS * 32, 0, st>>>(a);
+        else
+            k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
         prof_end(ix, tok, st);
     }
 }

@@ -45,6 +45,7 @@ struct SearchScratch {
     int2 *items;         // [(nq * P + nlist) * CH] work items (list, tile << 8 | chunk)
     float *qn;           // [nq] ||q||^2 (reduced-precision scans)
     float *qsc;          // [nq] FP8 inverse scale of each query
+    unsigned char *qcast; // [nq, d] queries rounded to the scan format
 };
 struct SearchPlan {
     int tq;              // queries per work item
@@ -76,13 +77,18 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
 
 // ---- reduced-precision scan + re-rank (scan_tc.cu)
 bool tc_make_maps(sivf_index *ix);
-void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
-                cudaStream_t st);
+// ||q||^2, FP8 inverse scale and the row rounded to the scan format `dtype`
+void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn, float *qsc,
+                unsigned char *qcast, cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
-int tc_tile_queries(int Kc);   // 64, or 16 for K' > 128
+int tc_tile_queries(int Kc);   // 64 (K' <= 64), 32 (<= 128) or 16 (<= 512)
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
                    const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);
+// per query: the best Kc (distance, slot) of its reduced-precision item
+// outputs, sorted ascending
+void merge_tc(sivf_index *ix, int64_t nq, int P, const SearchPlan &pl, const SearchScratch &s,
+              int Kc, float *out_d, int64_t *out_s, cudaStream_t st);
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
 

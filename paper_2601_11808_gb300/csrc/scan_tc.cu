@@ -3,22 +3,37 @@
 // only).
 //
 // Lists keep a BF16 or an FP8 E4M3 copy of every payload row (per-list
-// scale for FP8).  One CTA takes one (list, tile of up to 64 queries, slab
-// chunk) item.  The list's slabs stream through shared memory as 128-row
-// A tiles (TMA 2-D loads, 128-byte swizzle); the query tile, rounded to the
-// same format, is the B operand; tcgen05.mma accumulates the 128 x 64 dot
-// products in FP32 in tensor memory (double-buffered, so the next tile's
-// MMAs overlap the epilogue of this one).  The epilogue forms the expanded
-// distance ||q||^2 + ||x||^2 - 2 s q.x (FP32 norms of the unrounded
-// vectors, s the dequantisation scale), and every query keeps its best K'
-// (= 4k) (distance, slot) candidates.  A per-query shared bound (the K'-th
+// scale for FP8).  One persistent CTA per SM takes (list, tile of up to TN
+// queries, slab chunk) items from a work counter.  The list's slabs stream
+// through shared memory as 128-row A tiles (TMA 2-D loads, 128-byte
+// swizzle); the query tile, rounded to the same format, is the B operand;
+// tcgen05.mma accumulates the 128 x TN dot products in FP32 in tensor
+// memory (two accumulators, so the next tile's MMAs overlap the epilogue of
+// this one).  The epilogue forms the expanded distance
+// ||q||^2 + ||x||^2 - 2 s q.x (FP32 norms of the unrounded vectors, s the
+// dequantisation scale), and every query keeps its best K' (= 4k)
+// (distance, slot) candidates.  A per-query shared bound (the K'-th
 // distance any item has found) prunes the rest.  A final pass recomputes
 // the K' survivors' distances exactly in FP32 from the FP32 payload and
 // keeps the best k by (distance, id).
 //
-// Roles inside the CTA (8 warps): thread 0 drives TMA, warp 1 lane 0 issues
-// the MMAs, warp 2 owns the tensor-memory allocation, warps 4-7 read tensor
-// memory and select candidates.  Every wait is bounded.
+// Roles inside the CTA, all running one item ahead of the epilogue:
+//   warp 2  item contexts: takes the next item, stages its queries' norms,
+//           scales and bounds, its slab ids and validity bitmaps, and
+//           prefetches the first slabs into L2 (two contexts in flight);
+//   warp 3  builds the rounded, swizzled query tile (two B buffers);
+//   warp 0  (one lane) TMA loads of the A tiles and bulk copies of the
+//           rows' ||x||^2, plus L2 prefetches further ahead in the list;
+//   warp 1  (one lane) issues the MMAs; warp 2 also owns the TMEM;
+//   warps 4.. the epilogue: TN / 16 warps per TMEM lane quarter, 16
+//           query columns each.
+// A tile's passing rows are appended to their query's buffer at positions
+// reserved by one shared atomic per (warp, query); a buffer is reduced to
+// its best K' (radix select, left unsorted) only after a tile that leaves
+// it too full for the next one, so most tiles end on a single barrier.
+// Each item writes its rows' best K' unsorted; a per-query merge selects
+// and sorts the best K' of all its items.  Every wait is bounded, and a
+// wait that gives up stops every role.
 #include <cudaTypedefs.h>
 #include <math.h>
 
@@ -30,16 +45,25 @@ namespace sivf {
 
 constexpr int TC_M = 128;       // rows per A tile (MMA M)
 constexpr int TC_NCOL = 16;     // query columns per epilogue warp
-// Two tile shapes: 64 queries per tile for K' <= 128, 16 queries (and
-// buffers for K' <= 512) for deeper re-ranks.  Epilogue warps: four per
-// TMEM lane quarter at 64 queries, one at 16.
+constexpr int TC_META = 256;    // slabs of one sub-item (ids and bitmaps staged together)
+constexpr int TC_CTX = 2;       // item contexts in flight
+constexpr int TC_XR = 8;        // entries of the ||x||^2 ring (one per A tile)
+constexpr int TC_MAXST = 4;     // most A-tile stages
+constexpr int TC_HIST = 256;    // radix-select bins per epilogue warp
+constexpr int TC_PF_BYTES = 192 * 1024;  // L2 prefetch distance per CTA
+
+// Query tiles: 48 queries for K' <= 64 (small enough candidate buffers for
+// three A stages), 32 for K' <= 128, 16 (and candidate buffers up to
+// K' = 512) for deeper re-ranks.  TN / 16 epilogue warps per TMEM lane
+// quarter, 16 query columns each.
 template <int TN> struct TcShape {
     static constexpr int N = TN;                        // queries per tile (MMA N)
     static constexpr int EW = 4 * (TN / TC_NCOL);       // epilogue warps
     static constexpr int EPI = EW * 32;                 // epilogue threads
-    static constexpr int NT = 128 + EPI;                // + TMA, MMA, TMEM owner, idle warp
-    static constexpr int NST = EW >= 16 ? 2 : 3;        // A-tile stages in flight
-    static constexpr int KMAX = TN == 64 ? 128 : 512;   // deepest K' the buffers take
+    static constexpr int NT = 128 + EPI;                // + TMA, MMA, context, B warps
+    static constexpr int KMAX = TN == 48 ? 64 : TN == 32 ? 128 : 512;  // deepest K'
+    // TMEM columns per accumulator buffer (power of two, >= 32)
+    static constexpr int TB = TN <= 32 ? 32 : 64;
 };
 
 struct TcArgs {
@@ -49,6 +73,7 @@ struct TcArgs {
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
     const int2 *items;
     const float *qn, *qsc;
+    const unsigned char *qcast;  // [nq, d] queries in the scan format (BF16 or E4M3)
     float *part_d;
     int64_t *part_i;  // global slot (slab * C + slot) of each candidate
     float *thr;
@@ -56,32 +81,43 @@ struct TcArgs {
     const uint32_t *bits;
     const int32_t *nslabs, *dir;
     const float *inv_scale8;
+    const unsigned char *pay;  // the scanned copy (BF16 or E4M3 rows)
     int64_t n_slabs, dir_cap;
     int L, d, C, KC;  // KC = 128-byte K chunks per row
+    int nst;          // A-tile stages
+    int pf_tiles;     // A tiles prefetched into L2 ahead of the loads
     Ctl *ctl;
     uint32_t *err;
 };
 
-constexpr int TC_META = 256;    // slabs whose ids and bitmaps are staged at once
+// One item context: a header, the tile's queries, the sub-item's slabs.
+//   int32 hdr[16]: list, m, first slab, slabs, A tiles, row stride ME,
+//                  -, chunk, flags (1 first, 2 last, 4 stop), inv scale
+//   int32 qpair[TN]; float qn[TN], qsc[TN], kd0[TN]; int32 qi[TN];
+//   int32 sl[TC_META]; uint32 bits[TC_META][4]
+enum : int { CF_FIRST = 1, CF_LAST = 2, CF_STOP = 4 };
+__host__ __device__ constexpr size_t tc_ctx_bytes(int TN)
+{
+    return 64 + (size_t)20 * TN + (size_t)4 * TC_META + (size_t)16 * TC_META;
+}
 
 struct TcSmem {
-    size_t a, b, bd, bs, msl, mbits, hist, stg, misc, total;
+    size_t a, b, xn, bd, bs, ctx, hist, bars, total;
 };
 template <int TN>
-__host__ __device__ inline TcSmem tc_smem(int KC, int M)
+__host__ __device__ inline TcSmem tc_smem(int KC, int M, int nst)
 {
     using S = TcShape<TN>;
     TcSmem s;
-    s.a = 0;                                             // NST x KC x 16 KB
-    s.b = s.a + (size_t)S::NST * KC * TC_M * 128;        // KC x TN rows x 128 B
-    s.bd = s.b + (size_t)KC * TN * 128;
+    s.a = 0;                                             // nst x KC x 16 KB
+    s.b = s.a + (size_t)nst * KC * TC_M * 128;           // 2 x KC x TN rows x 128 B
+    s.xn = s.b + (size_t)2 * KC * TN * 128;              // TC_XR x 128 floats
+    s.bd = s.xn + (size_t)TC_XR * TC_M * 4;
     s.bs = s.bd + (size_t)TN * M * 4;
-    s.msl = s.bs + (size_t)TN * M * 4;
-    s.mbits = s.msl + (size_t)TC_META * 4;
-    s.hist = s.mbits + (size_t)TC_META * 4 * 4;           // per warp 256 bins
-    s.stg = s.hist + (size_t)S::EW * 256 * 4;             // per warp KMAX (dist, slot)
-    s.misc = s.stg + (size_t)S::EW * S::KMAX * 8;
-    s.total = s.misc + 1024 + 1024;                      // + base alignment slack
+    s.ctx = s.bs + (size_t)TN * M * 4;
+    s.hist = s.ctx + (size_t)TC_CTX * tc_ctx_bytes(TN);
+    s.bars = s.hist + (size_t)S::EW * TC_HIST * 4;
+    s.total = s.bars + 48 * 8 + 1024;                    // + base alignment slack
     return s;
 }
 
@@ -89,6 +125,12 @@ __host__ __device__ inline TcSmem tc_smem(int KC, int M)
 __device__ __forceinline__ bool ds_less(float a, int32_t sa, float b, int32_t sb)
 {
     return a < b || (a == b && sa < sb);
+}
+
+// 64-bit key with the (distance, slot) order
+__device__ __forceinline__ uint64_t ds_key(float d, int32_t s)
+{
+    return ((uint64_t)fkey(d) << 32) | (uint32_t)s;
 }
 
 // Ascending bitonic sort of 32*E (distance, slot) pairs held E per lane.
@@ -132,102 +174,43 @@ __device__ __forceinline__ void warp_sort32(float (&v)[E], int32_t (&s)[E], int 
             }
 }
 
-// Merge nc unsorted candidates (bd/bs[K, K+nc)) into the sorted best list
-// (bd/bs[0, nb)), keeping the K smallest: the candidates are sorted in
-// registers, written back in order, and every output position finds its
-// split between the two sorted runs by binary search (merge path).
-template <int EC, int KMAX>
-__device__ void warp_sort_merge32(float *bd, int32_t *bs, int K, int nb, int nc, int lane)
+// Radix select over n distinct 64-bit keys key(i), i < n: returns the
+// (prefix, mask) for which exactly the K smallest keys satisfy
+// (key & mask) <= prefix.  Keys equal to ~0 are padding: they never count
+// among the K smallest, and at least K keys are not padding.  8 bits per
+// pass, starting at the highest bit where the keys differ and stopping at
+// the first pass whose chosen bin is taken whole.
+template <class KeyF>
+__device__ __forceinline__ void warp_radix_kth(KeyF key, int n, int K, uint32_t *hist, int lane,
+                                               uint64_t &prefix_out, uint64_t &mask_out)
 {
-    float v[EC];
-    int32_t sv[EC];
-#pragma unroll
-    for (int e = 0; e < EC; ++e) {
-        const int i = lane + 32 * e;
-        v[e] = i < nc ? bd[K + i] : INFINITY;
-        sv[e] = i < nc ? bs[K + i] : 0x7fffffff;
-    }
-    warp_sort32<EC>(v, sv, lane);
-#pragma unroll
-    for (int e = 0; e < EC; ++e) {
-        const int i = lane + 32 * e;
-        if (i < nc) {
-            bd[K + i] = v[e];
-            bs[K + i] = sv[e];
-        }
-    }
-    __syncwarp();
-    const int n = min(K, nb + nc);
-    constexpr int OPL = KMAX / 32;  // outputs per lane (K <= KMAX)
-    float ov[OPL];
-    int32_t os[OPL];
-#pragma unroll
-    for (int t = 0; t < OPL; ++t) {
-        const int o = lane + 32 * t;
-        if (o >= n) continue;
-        // smallest i in [lo, hi] with: taking i best and o - i candidates
-        int lo = max(0, o - nc), hi = min(o, nb);
-        while (lo < hi) {
-            const int i = (lo + hi) >> 1;          // i best, o - i candidates before o
-            const int j = o - i - 1;               // last candidate taken
-            if (ds_less(bd[K + j], bs[K + j], bd[i], bs[i])) hi = i;
-            else lo = i + 1;
-        }
-        const int i = lo, j = o - lo;
-        const bool from_best = i < nb && (j >= nc || !ds_less(bd[K + j], bs[K + j], bd[i], bs[i]));
-        ov[t] = from_best ? bd[i] : bd[K + j];
-        os[t] = from_best ? bs[i] : bs[K + j];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < OPL; ++t) {
-        const int o = lane + 32 * t;
-        if (o < n) {
-            bd[o] = ov[t];
-            bs[o] = os[t];
-        }
-    }
-    __syncwarp();
-}
-
-// Keep the K smallest of best[0, nb) (sorted) and cand[K, K + nc) when the
-// union is too large to sort in registers: a warp radix select finds the
-// K-th smallest key in 8-bit passes over the union, the entries at or
-// below it (ties included, at most KMAX) are gathered and sorted.  More
-// than KMAX entries tied at the K-th key keep the first ones found,
-// ordered by slot among the gathered.
-template <int KMAX>
-__device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int nc,
-                                    uint32_t *hist, float *stg_d, int32_t *stg_s, int lane)
-{
-    const int n = nb + nc;
-    auto at = [&](int i) { return i < nb ? i : K + (i - nb); };
-    // the keys share their leading bits (distances of one list are of one
-    // magnitude): start the 8-bit passes at the highest bit where they differ
-    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    uint64_t kmin = ~0ull, kmax = 0ull;
     for (int i = lane; i < n; i += 32) {
-        const uint32_t k = fkey(bd[at(i)]);
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
+        const uint64_t k = key(i);
+        if (k != ~0ull) {
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmin, o));
+        kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmax, o));
     }
-    const uint32_t diff = kmin ^ kmax;
-    const int top = diff ? 31 - __clz(diff) : 0;  // highest differing bit
-    uint32_t mask = top >= 31 ? 0u : ~((2u << top) - 1u);
-    uint32_t prefix = kmin & mask, need = (uint32_t)K;
+    const uint64_t diff = kmin ^ kmax;
+    const int top = diff ? 63 - __clzll((long long)diff) : 0;
+    uint64_t mask = top >= 63 ? 0ull : ~((2ull << top) - 1ull);
+    uint64_t prefix = kmin & mask;
+    uint32_t need = (uint32_t)K;
     for (int hi = top; hi >= 0; hi -= 8) {
         const int shift = max(hi - 7, 0);
-        const uint32_t width = (uint32_t)(hi - shift + 1);
-        const uint32_t bmask = (width >= 32 ? 0xffffffffu : ((1u << width) - 1u));
+        const uint32_t bmask = (1u << (hi - shift + 1)) - 1u;
 #pragma unroll
         for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
-            const uint32_t k = fkey(bd[at(i)]);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & bmask], 1u);
+            const uint64_t k = key(i);
+            if (k != ~0ull && (k & mask) == prefix)
+                atomicAdd(&hist[(uint32_t)(k >> shift) & bmask], 1u);
         }
         __syncwarp();
         uint32_t loc[8], sum = 0;
@@ -243,13 +226,14 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
         }
         const uint32_t excl = incl - sum;
         const bool mine = excl < need && incl >= need;
-        uint32_t bin = 0, below = 0;
+        uint32_t bin = 0, below = 0, cnt = 0;
         if (mine) {
             uint32_t cum = excl;
             for (int b = 0; b < 8; ++b) {
                 if (cum + loc[b] >= need) {
                     bin = (uint32_t)(lane * 8 + b);
                     below = cum;
+                    cnt = loc[b];
                     break;
                 }
                 cum += loc[b];
@@ -259,53 +243,267 @@ __device__ void warp_select_merge32(float *bd, int32_t *bs, int K, int nb, int n
         const int src = who ? __ffs(who) - 1 : 0;
         bin = __shfl_sync(0xffffffffu, bin, src);
         below = __shfl_sync(0xffffffffu, below, src);
-        prefix |= bin << shift;
-        mask |= bmask << shift;
+        cnt = __shfl_sync(0xffffffffu, cnt, src);
+        prefix |= (uint64_t)bin << shift;
+        mask |= (uint64_t)bmask << shift;
         need -= below;
         __syncwarp();
+        if (cnt == need) break;
     }
-    // gather every entry at or below the K-th key (at most KMAX)
-    int cnt = 0;
-    for (int i0 = 0; i0 < n; i0 += 32) {
+    prefix_out = prefix;
+    mask_out = mask;
+}
+
+// Keep in bd/bs[0, K) the K smallest (distance, slot) entries of the two
+// unsorted runs [0, nb) and [K, K + nc), with nb + nc > K; the kept
+// entries stay unsorted (a slot appears once per buffer, so the keys are
+// distinct).  Returns the largest kept distance.
+__device__ float warp_select_keep(float *bd, int32_t *bs, int K, int nb, int nc,
+                                  uint32_t *hist, int lane)
+{
+    auto at = [&](int i) { return i < nb ? i : K + (i - nb); };
+    uint64_t prefix, mask;
+    warp_radix_kth([&](int i) { return ds_key(bd[at(i)], bs[at(i)]); }, nb + nc, K, hist, lane,
+                   prefix, mask);
+    // stable compaction in place (every write index <= its read index)
+    int w = 0;
+    float dmax = -INFINITY;
+    for (int i0 = 0; i0 < nb; i0 += 32) {
         const int i = i0 + lane;
-        bool take = false;
         float dv = 0.f;
         int32_t sv = 0;
-        if (i < n) {
-            dv = bd[at(i)];
-            sv = bs[at(i)];
-            take = fkey(dv) <= prefix;
+        bool take = false;
+        if (i < nb) {
+            dv = bd[i];
+            sv = bs[i];
+            take = (ds_key(dv, sv) & mask) <= prefix;
         }
         const uint32_t mk = __ballot_sync(0xffffffffu, take);
-        const int p = cnt + __popc(mk & lanemask_lt());
-        if (take && p < KMAX) {
-            stg_d[p] = dv;
-            stg_s[p] = sv;
+        __syncwarp();
+        if (take) {
+            const int p = w + __popc(mk & lanemask_lt());
+            bd[p] = dv;
+            bs[p] = sv;
+            dmax = fmaxf(dmax, dv);
         }
-        cnt += __popc(mk);
+        w += __popc(mk);
+        __syncwarp();
     }
-    __syncwarp();
-    cnt = min(cnt, KMAX);
-    constexpr int E = KMAX / 32;
-    float v[E];
-    int32_t sv[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        v[e] = i < cnt ? stg_d[i] : INFINITY;
-        sv[e] = i < cnt ? stg_s[i] : 0x7fffffff;
-    }
-    warp_sort32<E>(v, sv, lane);
-    __syncwarp();
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        if (i < K) {
-            bd[i] = v[e];
-            bs[i] = sv[e];
+    for (int i0 = 0; i0 < nc; i0 += 32) {
+        const int i = K + i0 + lane;
+        float dv = 0.f;
+        int32_t sv = 0;
+        bool take = false;
+        if (i0 + lane < nc) {
+            dv = bd[i];
+            sv = bs[i];
+            take = (ds_key(dv, sv) & mask) <= prefix;
         }
+        const uint32_t mk = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int p = w + __popc(mk & lanemask_lt());
+            if (p < K) {
+                bd[p] = dv;
+                bs[p] = sv;
+            }
+            dmax = fmaxf(dmax, dv);
+        }
+        w += __popc(mk);
     }
     __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    return dmax;
+}
+
+// Register form of warp_select_keep for nb + nc <= 32 * EK: every key is
+// read once into registers, the radix passes count from registers, and the
+// kept entries are written back from the keys (distance and slot both live
+// in the key), so no entry is re-read from shared memory.
+template <int EK>
+__device__ float warp_select_keep_reg(float *bd, int32_t *bs, int K, int nb, int nc,
+                                      uint32_t *hist, int lane)
+{
+    const int n = nb + nc;
+    uint64_t key[EK];
+#pragma unroll
+    for (int e = 0; e < EK; ++e) {
+        const int i = lane + 32 * e;
+        const int ai = i < nb ? i : K + (i - nb);
+        key[e] = i < n ? ds_key(bd[ai], bs[ai]) : ~0ull;
+    }
+    uint64_t kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+    for (int e = 0; e < EK; ++e)
+        if (key[e] != ~0ull) {
+            kmin = min(kmin, key[e]);
+            kmax = max(kmax, key[e]);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmin, o));
+        kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmax, o));
+    }
+    const uint64_t diff = kmin ^ kmax;
+    const int top = diff ? 63 - __clzll((long long)diff) : 0;
+    uint64_t mask = top >= 63 ? 0ull : ~((2ull << top) - 1ull);
+    uint64_t prefix = kmin & mask;
+    uint32_t need = (uint32_t)K;
+    for (int hi = top; hi >= 0; hi -= 8) {
+        const int shift = max(hi - 7, 0);
+        const uint32_t bmask = (1u << (hi - shift + 1)) - 1u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < EK; ++e)
+            if (key[e] != ~0ull && (key[e] & mask) == prefix)
+                atomicAdd(&hist[(uint32_t)(key[e] >> shift) & bmask], 1u);
+        __syncwarp();
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            loc[b] = hist[lane * 8 + b];
+            sum += loc[b];
+        }
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - sum;
+        const bool mine = excl < need && incl >= need;
+        uint32_t bin = 0, below = 0, cnt = 0;
+        if (mine) {
+            uint32_t cum = excl;
+            for (int b = 0; b < 8; ++b) {
+                if (cum + loc[b] >= need) {
+                    bin = (uint32_t)(lane * 8 + b);
+                    below = cum;
+                    cnt = loc[b];
+                    break;
+                }
+                cum += loc[b];
+            }
+        }
+        const uint32_t who = __ballot_sync(0xffffffffu, mine);
+        const int src = who ? __ffs(who) - 1 : 0;
+        bin = __shfl_sync(0xffffffffu, bin, src);
+        below = __shfl_sync(0xffffffffu, below, src);
+        cnt = __shfl_sync(0xffffffffu, cnt, src);
+        prefix |= (uint64_t)bin << shift;
+        mask |= (uint64_t)bmask << shift;
+        need -= below;
+        __syncwarp();
+        if (cnt == need) break;
+    }
+    // every key is in registers: write the K kept entries to [0, K)
+    int w = 0;
+    float dmax = -INFINITY;
+#pragma unroll
+    for (int e = 0; e < EK; ++e) {
+        const bool take = key[e] != ~0ull && (key[e] & mask) <= prefix;
+        const uint32_t mk = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int p = w + __popc(mk & lanemask_lt());
+            const float dv = fkey_inv((uint32_t)(key[e] >> 32));
+            bd[p] = dv;
+            bs[p] = (int32_t)(uint32_t)key[e];
+            dmax = fmaxf(dmax, dv);
+        }
+        w += __popc(mk);
+    }
+    __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    return dmax;
+}
+
+// Fold the nc pending candidates of one row into its best set: keep the
+// best K' of the union (unsorted); move them down when they fit whole.
+// Returns the new K'-th distance (+inf while fewer than K' are held).
+__device__ __forceinline__ float fold_row(float *bd, int32_t *bs, int K, int &nb, int nc,
+                                          uint32_t *hist, int lane)
+{
+    if (nb + nc > K) {
+        const int n = nb + nc;
+        const float kd = n <= 64    ? warp_select_keep_reg<2>(bd, bs, K, nb, nc, hist, lane)
+                         : n <= 128 ? warp_select_keep_reg<4>(bd, bs, K, nb, nc, hist, lane)
+                         : n <= 192 ? warp_select_keep_reg<6>(bd, bs, K, nb, nc, hist, lane)
+                         : n <= 320 ? warp_select_keep_reg<10>(bd, bs, K, nb, nc, hist, lane)
+                                    : warp_select_keep(bd, bs, K, nb, nc, hist, lane);
+        nb = K;
+        return kd;
+    }
+    for (int i = lane; i < nc; i += 32) {  // write index < K <= read index
+        const float dv = bd[K + i];
+        const int32_t sv = bs[K + i];
+        bd[nb + i] = dv;
+        bs[nb + i] = sv;
+    }
+    nb += nc;
+    __syncwarp();
+    if (nb < K) return INFINITY;
+    float dmax = -INFINITY;
+    for (int i = lane; i < nb; i += 32) dmax = fmaxf(dmax, bd[i]);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    return dmax;
+}
+
+// mbarrier wait bounded by an iteration limit that also gives up as soon
+// as another role of the CTA has stopped (abort flag in shared memory).
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, uint32_t *err,
+                                             volatile int *abort_flag)
+{
+    for (uint32_t it = 0; it < 4000000u; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 127u) == 127u && *abort_flag) return false;
+    }
+    atomicOr(err, ERR_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+}
+
+// named barrier over `n` threads that also returns the AND of `pred`
+__device__ __forceinline__ bool named_bar_and(int id, int n, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// named barrier over `n` threads that also returns the OR of `pred`
+__device__ __forceinline__ bool named_bar_or(int id, int n, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// 16-byte asynchronous copy global -> shared; bytes past `src_bytes` (0 or
+// 16) are zero-filled
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <int DT, int TN>  // DT: 0 = BF16, 1 = FP8 E4M3; TN: queries per tile
@@ -313,345 +511,563 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
     const __grid_constant__ CUtensorMap tmap, TcArgs a)
 {
     using S = TcShape<TN>;
-    constexpr int TC_N = TN, TC_EW = S::EW, TC_EPI = S::EPI, TC_NT = S::NT, TC_NST = S::NST;
-    constexpr int KMAX = S::KMAX;
+    constexpr int EW = S::EW, EPI = S::EPI, TB = S::TB;
+    constexpr int ESZ = DT == 0 ? 2 : 1;
+    constexpr int EPC = 128 / ESZ;  // elements per 128-byte chunk
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled operand tiles
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    const int KC = a.KC, M = a.M, K = a.K, C = a.C, d = a.d;
-    const TcSmem L = tc_smem<TN>(KC, M);
+    const int KC = a.KC, M = a.M, K = a.K, C = a.C, d = a.d, NST = a.nst;
+    const TcSmem L = tc_smem<TN>(KC, M, NST);
     unsigned char *A = smem + L.a;
     unsigned char *B = smem + L.b;
+    float *XN = reinterpret_cast<float *>(smem + L.xn);
     float *BD = reinterpret_cast<float *>(smem + L.bd);
     int32_t *BS = reinterpret_cast<int32_t *>(smem + L.bs);
-    int32_t *Msl = reinterpret_cast<int32_t *>(smem + L.msl);     // slab ids
-    uint32_t *Mbits = reinterpret_cast<uint32_t *>(smem + L.mbits);  // their bitmaps
+    unsigned char *CTX = smem + L.ctx;
     uint32_t *Hist = reinterpret_cast<uint32_t *>(smem + L.hist);
-    unsigned char *Stg = smem + L.stg;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.misc);
-    uint64_t *full = bars, *empty = bars + TC_NST, *tfull = bars + 2 * TC_NST,
-             *tempty = bars + 2 * TC_NST + 2;
-    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(bars + 2 * TC_NST + 4);
-    int *s_item = reinterpret_cast<int *>(bars + 2 * TC_NST + 5);
-    int *s_abort = s_item + 1;
-    __shared__ int32_t s_qpair[TC_N], s_cc[TC_N], s_nb[TC_N], s_ks[TC_N];
-    __shared__ float s_kd[TC_N], s_qn[TC_N], s_qsc[TC_N];
-    __shared__ __align__(16) float s_t[TC_N];   // kd - ||q||^2 of each row, per tile
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *full = bars, *empty = bars + 4, *tfull = bars + 8, *tempty = bars + 10,
+             *xfull = bars + 12, *xempty = bars + 20, *cfull = bars + 28, *cempty = bars + 30,
+             *bfull = bars + 32, *bfree = bars + 34;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(bars + 40);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(bars + 41);
+    __shared__ int32_t s_cnt[TN], s_nb[TN];  // pending candidates, held best
+    __shared__ float s_kd[TN];
+    __shared__ __align__(16) float s_t[TN];   // kd - ||q||^2 of each row
+    __shared__ __align__(16) float s_sc[TN];  // 2 x dequantisation scale of each row
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int ESZ = DT == 0 ? 2 : 1;
-    constexpr int EPC = 128 / ESZ;  // elements per 128-byte chunk
-    const int SPB = TC_M / C;       // slabs per A tile
-    const uint32_t idesc = DT == 0 ? mma_idesc(1, 1, TC_M, TC_N) : mma_idesc(0, 0, TC_M, TC_N);
+    const int SPB = TC_M / C;  // slabs per A tile
+    const uint32_t idesc = DT == 0 ? mma_idesc(1, 1, TC_M, TN) : mma_idesc(0, 0, TC_M, TN);
+    constexpr size_t CTXB = tc_ctx_bytes(TN);
+    auto hdr = [&](int j) { return reinterpret_cast<int32_t *>(CTX + j * CTXB); };
+    auto c_qpair = [&](int j) { return reinterpret_cast<int32_t *>(CTX + j * CTXB + 64); };
+    auto c_qn = [&](int j) { return reinterpret_cast<float *>(CTX + j * CTXB + 64 + 4 * TN); };
+    auto c_qsc = [&](int j) { return reinterpret_cast<float *>(CTX + j * CTXB + 64 + 8 * TN); };
+    auto c_kd0 = [&](int j) { return reinterpret_cast<float *>(CTX + j * CTXB + 64 + 12 * TN); };
+    auto c_qi = [&](int j) { return reinterpret_cast<int32_t *>(CTX + j * CTXB + 64 + 16 * TN); };
+    auto c_sl = [&](int j) { return reinterpret_cast<int32_t *>(CTX + j * CTXB + 64 + 20 * TN); };
+    auto c_bits = [&](int j) {
+        return reinterpret_cast<uint32_t *>(CTX + j * CTXB + 64 + 20 * TN + 4 * TC_META);
+    };
 
     if (tid == 0) {
-        for (int i = 0; i < TC_NST; ++i) {
+        for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], TC_EPI);
+            mbar_init(&tempty[i], EW);
+            mbar_init(&bfull[i], 32);
+            mbar_init(&bfree[i], 1);
+        }
+        for (int i = 0; i < TC_XR; ++i) {
+            mbar_init(&xfull[i], 1);
+            mbar_init(&xempty[i], EW);
+        }
+        for (int i = 0; i < TC_CTX; ++i) {
+            mbar_init(&cfull[i], 32);
+            mbar_init(&cempty[i], EW);
         }
         fence_mbar_init();
         *s_abort = 0;
     }
-    if (warp == 2) tmem_alloc(tmem_base, 2 * TC_N);
+    if (warp == 2) tmem_alloc(tmem_base, 2 * TB);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_base;
 
-    uint32_t gblk = 0;  // A tiles processed by this CTA (all roles agree)
-    for (;;) {
-        if (tid == 0) *s_item = atomicAdd(&a.ctl->next_item, 1);
-        __syncthreads();
-        const int item = *s_item;
-        if (item >= a.ctl->nitems || *s_abort) break;
-
-        const int2 it = a.items[item];
-        const int l = it.x;
-        const int nc_l = a.nch[l];
-        const int tile = it.y >> 8, chunk = it.y & 255;
-        const int r0 = tile * TC_N;
-        const int m = min(TC_N, a.lcnt[l] - r0);
-        int ns_total = a.nslabs[l];
-        if (ns_total > a.dir_cap) {
-            if (tid == 0) atomicOr(a.err, ERR_DIR_BOUND);
-            ns_total = (int)a.dir_cap;
-        }
-        const int s0 = (int)((int64_t)ns_total * chunk / nc_l);
-        const int ns = (int)((int64_t)ns_total * (chunk + 1) / nc_l) - s0;
-        const int nblk = (ns + SPB - 1) / SPB;
-        // rows of a thin tile get proportionally longer candidate buffers
-        const int ME = max(M, ((TC_N * M) / max(m, 1)) & ~7);
-        const int32_t *dirl = a.dir + (size_t)l * a.dir_cap + s0;
-        const float inv_l = DT == 1 ? a.inv_scale8[l] : 1.f;
-
-        // ---- query tile: norms, thresholds, B operand (rounded, swizzled)
-        const int qb = a.loff[l] + r0;
-        for (int r = tid; r < TC_N; r += TC_NT) {
-            const int pr = r < m ? a.qlist[qb + r] : -1;
-            const int qi = pr >= 0 ? pr / a.P : 0;
-            s_qpair[r] = pr;
-            s_cc[r] = 0;
-            s_nb[r] = 0;
-            s_kd[r] = pr >= 0 ? __ldcg(a.thr + qi) : INFINITY;
-            s_ks[r] = 0x7fffffff;
-            s_qn[r] = pr >= 0 ? a.qn[qi] : 0.f;
-            s_qsc[r] = pr >= 0 ? a.qsc[qi] : 1.f;
-            s_t[r] = pr >= 0 ? s_kd[r] - s_qn[r] : -INFINITY;
-        }
-        __syncthreads();
-        for (int e = tid; e < TC_N * KC * 8; e += TC_NT) {
-            const int r = e / (KC * 8), kc = (e / 8) % KC, c = e % 8;
-            const int pr = s_qpair[r];
-            const int k0 = kc * EPC + c * (16 / ESZ);  // first element of the 16-byte chunk
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (pr >= 0 && k0 < d) {                  // d % 16 == 0: chunks are all in or out
-                const float4 *qr = reinterpret_cast<const float4 *>(a.q + (size_t)(pr / a.P) * d + k0);
-                if (DT == 0) {
-                    const float4 f0 = qr[0], f1 = qr[1];
-                    __nv_bfloat162 h0 = __floats2bfloat162_rn(f0.x, f0.y);
-                    __nv_bfloat162 h1 = __floats2bfloat162_rn(f0.z, f0.w);
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(f1.x, f1.y);
-                    __nv_bfloat162 h3 = __floats2bfloat162_rn(f1.z, f1.w);
-                    w[0] = *reinterpret_cast<uint32_t *>(&h0);
-                    w[1] = *reinterpret_cast<uint32_t *>(&h1);
-                    w[2] = *reinterpret_cast<uint32_t *>(&h2);
-                    w[3] = *reinterpret_cast<uint32_t *>(&h3);
+    if (warp == 2) {
+        // ---- item contexts
+        int sub = 0, nsub = 0, l = 0, m = 0, s0 = 0, ns = 0, chunk = 0, qb = 0;
+        float inv_l = 1.f;
+        for (int it = 0;; ++it) {
+            const int j = it % TC_CTX;
+            const uint32_t cu = (uint32_t)(it / TC_CTX);
+            bool ok = cu == 0 || mbar_wait_ab(&cempty[j], (cu - 1) & 1, a.err, s_abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            int32_t *h = hdr(j);
+            bool stop = false;
+            if (sub == nsub) {
+                int nx = 0, go = 0;
+                if (lane == 0) {
+                    nx = atomicAdd(&a.ctl->next_item, 1);
+                    go = nx < a.ctl->nitems && !*s_abort;
+                }
+                nx = __shfl_sync(0xffffffffu, nx, 0);
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    stop = true;
                 } else {
-                    const float sc = s_qsc[r];
-                    float4 f[4] = {qr[0], qr[1], qr[2], qr[3]};
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const float2 p0 = make_float2(__fmul_rn(f[t].x, sc), __fmul_rn(f[t].y, sc));
-                        const float2 p1 = make_float2(__fmul_rn(f[t].z, sc), __fmul_rn(f[t].w, sc));
-                        const uint32_t lo8 = __nv_cvt_float2_to_fp8x2(p0, __NV_SATFINITE, __NV_E4M3);
-                        const uint32_t hi8 = __nv_cvt_float2_to_fp8x2(p1, __NV_SATFINITE, __NV_E4M3);
-                        w[t] = lo8 | (hi8 << 16);
+                    const int2 itv = a.items[nx];
+                    l = itv.x;
+                    const int nc_l = a.nch[l];
+                    const int tile = itv.y >> 8;
+                    chunk = itv.y & 255;
+                    const int r0 = tile * TN;
+                    m = min(TN, a.lcnt[l] - r0);
+                    int ns_total = a.nslabs[l];
+                    if (ns_total > a.dir_cap) {
+                        if (lane == 0) atomicOr(a.err, ERR_DIR_BOUND);
+                        ns_total = (int)a.dir_cap;
                     }
+                    s0 = (int)((int64_t)ns_total * chunk / nc_l);
+                    ns = (int)((int64_t)ns_total * (chunk + 1) / nc_l) - s0;
+                    nsub = max(1, (ns + TC_META - 1) / TC_META);
+                    sub = 0;
+                    qb = a.loff[l] + r0;
+                    inv_l = DT == 1 ? a.inv_scale8[l] : 1.f;
                 }
             }
-            unsigned char *dst = B + (size_t)kc * TC_N * 128 + (size_t)(r >> 3) * 1024 +
-                                 (r & 7) * 128 + ((c ^ (r & 7)) << 4);
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            __syncwarp();
+            if (stop) {
+                if (lane == 0) h[8] = CF_STOP;
+                __syncwarp();
+                mbar_arrive(&cfull[j]);
+                break;
+            }
+            const int ss0 = s0 + sub * TC_META;
+            const int sns = max(0, min(TC_META, ns - sub * TC_META));
+            const int nblk = (sns + SPB - 1) / SPB;
+            if (lane == 0) {
+                h[0] = l;
+                h[1] = m;
+                h[2] = ss0;
+                h[3] = sns;
+                h[4] = nblk;
+                h[5] = max(M, ((TN * M) / max(m, 1)) & ~7);  // rows of a thin tile get longer buffers
+                h[7] = chunk;
+                h[8] = (sub == 0 ? CF_FIRST : 0) | (sub + 1 == nsub ? CF_LAST : 0);
+                h[9] = __float_as_int(inv_l);
+            }
+            int32_t *qp = c_qpair(j), *cqi = c_qi(j);
+            float *cqn = c_qn(j), *cqsc = c_qsc(j), *ckd = c_kd0(j);
+            for (int r = lane; r < TN; r += 32) {
+                const int pr = r < m ? a.qlist[qb + r] : -1;
+                const int qi = pr >= 0 ? pr / a.P : 0;
+                qp[r] = pr;
+                cqi[r] = qi;
+                cqn[r] = pr >= 0 ? a.qn[qi] : 0.f;
+                cqsc[r] = pr >= 0 ? a.qsc[qi] : 1.f;
+                ckd[r] = pr >= 0 ? __ldcg(a.thr + qi) : INFINITY;
+            }
+            int32_t *sl = c_sl(j);
+            uint32_t *bt = c_bits(j);
+            const int32_t *dirl = a.dir + (size_t)l * a.dir_cap + ss0;
+            const int W = C / 32;
+            const uint32_t pay_bytes = (uint32_t)(C * d * ESZ);
+            for (int i = lane; i < sns; i += 32) {
+                const int s = dirl[i];
+                const bool okk = s >= 0 && s < a.n_slabs;
+                if (!okk) atomicOr(a.err, ERR_BAD_SLAB);
+                sl[i] = okk ? s : -1;
+                for (int w = 0; w < W; ++w) bt[i * 4 + w] = okk ? __ldg(a.bits + (size_t)s * W + w) : 0u;
+                if (okk && i < a.pf_tiles * SPB) {
+                    prefetch_l2(a.pay + (size_t)s * pay_bytes, pay_bytes);
+                    prefetch_l2(a.xnorm + (size_t)s * C, (uint32_t)(C * 4));
+                }
+            }
+            __syncwarp();
+            mbar_arrive(&cfull[j]);
+            ++sub;
         }
-        fence_proxy_async_smem();  // B is read by the tensor cores (async proxy)
-        __syncthreads();
-
-        // ---- block loop: TMA -> MMA -> epilogue -> selection
-        if (warp == 0) {
-            if (lane == 0)
-            for (int b = 0; b < nblk && !*s_abort; ++b) {
-                const uint32_t g = gblk + b, st = g % TC_NST, u = g / TC_NST;
-                if (u >= 1 && !mbar_wait_bounded(&empty[st], (u - 1) & 1, a.err)) {
-                    *s_abort = 1;
-                    break;
-                }
-                const int nsl = min(SPB, ns - b * SPB);
-                int okc = 0;
-                int sl[4];
-                for (int j = 0; j < nsl; ++j) {
-                    sl[j] = dirl[b * SPB + j];
-                    if (sl[j] < 0 || sl[j] >= a.n_slabs) {
-                        atomicOr(a.err, ERR_BAD_SLAB);
-                        sl[j] = -1;
-                    } else {
-                        ++okc;
+    } else if (warp == 3) {
+        // ---- query tiles (B operand), rounded and swizzled
+        for (int it = 0;; ++it) {
+            const int j = it % TC_CTX, bb = it & 1;
+            bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            if (hdr(j)[8] & CF_STOP) break;
+            ok = it < 2 || mbar_wait_ab(&bfree[bb], (uint32_t)((it >> 1) - 1) & 1, a.err, s_abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int32_t *cqi = c_qi(j);
+            const int m = hdr(j)[1];
+            unsigned char *Bb = B + (size_t)bb * KC * TN * 128;
+            // 16-byte asynchronous copies of the rounded query rows straight
+            // into the swizzled tile (no registers, every copy in flight at
+            // once); chunks past the row (d * ESZ < KC * 128) are zero-filled
+            const int rowc = d * ESZ / 16, CPR = KC * 8;
+            for (int e = lane; e < m * CPR; e += 32) {
+                const int r = (CPR & (CPR - 1)) == 0 ? e >> (__ffs(CPR) - 1) : e / CPR;
+                const int c = e - r * CPR, kc = c >> 3, cc = c & 7;
+                const bool in = c < rowc;
+                const unsigned char *src = a.qcast + (in ? ((size_t)cqi[r] * d * ESZ + (size_t)c * 16) : 0);
+                cp_async16(Bb + (size_t)kc * TN * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                               ((cc ^ (r & 7)) << 4),
+                           src, in ? 16u : 0u);
+            }
+            cp_async_wait_all();
+            fence_proxy_async_smem();  // B is read by the tensor cores (async proxy)
+            mbar_arrive(&bfull[bb]);
+        }
+    } else if (warp == 0) {
+        // ---- TMA producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            const uint32_t pay_bytes = (uint32_t)(C * d * ESZ);
+            for (int it = 0;; ++it) {
+                const int j = it % TC_CTX;
+                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort)) break;
+                const int32_t *h = hdr(j);
+                if (h[8] & CF_STOP) break;
+                const int sns = h[3], nblk = h[4];
+                const int32_t *sl = c_sl(j);
+                bool ab = false;
+                for (int b = 0; b < nblk; ++b, ++g) {
+                    const uint32_t st = g % NST, u = g / NST, xs = g % TC_XR, xu = g / TC_XR;
+                    if (u >= 1 && !mbar_wait_ab(&empty[st], (u - 1) & 1, a.err, s_abort)) {
+                        ab = true;
+                        break;
                     }
+                    if (xu >= 1 && !mbar_wait_ab(&xempty[xs], (xu - 1) & 1, a.err, s_abort)) {
+                        ab = true;
+                        break;
+                    }
+                    const int nsl = min(SPB, sns - b * SPB);
+                    int okc = 0;
+                    for (int jj = 0; jj < nsl; ++jj) okc += sl[b * SPB + jj] >= 0;
+                    mbar_arrive_expect_tx(&full[st], (uint32_t)(okc * KC * C * 128));
+                    mbar_arrive_expect_tx(&xfull[xs], (uint32_t)(okc * C * 4));
+                    for (int jj = 0; jj < nsl; ++jj) {
+                        const int s = sl[b * SPB + jj];
+                        if (s < 0) continue;
+                        for (int kc = 0; kc < KC; ++kc)
+                            tma_load_2d(A + (size_t)st * KC * TC_M * 128 + (size_t)kc * TC_M * 128 +
+                                            (size_t)jj * C * 128,
+                                        &tmap, kc * EPC, s * C, &full[st]);
+                        bulk_g2s(XN + (size_t)xs * TC_M + jj * C, a.xnorm + (size_t)s * C,
+                                 (uint32_t)(C * 4), &xfull[xs]);
+                    }
+                    const int bp = b + a.pf_tiles;  // keep the L2 prefetch ahead
+                    if (bp < nblk)
+                        for (int jj = 0; jj < min(SPB, sns - bp * SPB); ++jj) {
+                            const int s = sl[bp * SPB + jj];
+                            if (s < 0) continue;
+                            prefetch_l2(a.pay + (size_t)s * pay_bytes, pay_bytes);
+                            prefetch_l2(a.xnorm + (size_t)s * C, (uint32_t)(C * 4));
+                        }
                 }
-                mbar_arrive_expect_tx(&full[st], (uint32_t)(okc * KC * C * 128));
-                for (int j = 0; j < nsl; ++j) {
-                    if (sl[j] < 0) continue;
+                if (ab) break;
+            }
+            // the copies of the last tiles issued have landed before exit
+            for (uint32_t t = g > (uint32_t)NST ? g - NST : 0; t < g; ++t)
+                mbar_wait_bounded(&full[t % NST], (t / NST) & 1, a.err);
+            for (uint32_t t = g > (uint32_t)TC_XR ? g - TC_XR : 0; t < g; ++t)
+                mbar_wait_bounded(&xfull[t % TC_XR], (t / TC_XR) & 1, a.err);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int it = 0;; ++it) {
+                const int j = it % TC_CTX, bb = it & 1;
+                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort)) break;
+                if (hdr(j)[8] & CF_STOP) break;
+                const int nblk = hdr(j)[4];
+                if (!mbar_wait_ab(&bfull[bb], (uint32_t)(it >> 1) & 1, a.err, s_abort)) break;
+                const uint32_t bbase = smem_u32(B + (size_t)bb * KC * TN * 128);
+                bool ab = false;
+                for (int b = 0; b < nblk; ++b, ++g) {
+                    const uint32_t st = g % NST, u = g / NST, buf = g & 1, ub = g >> 1;
+                    if (!mbar_wait_ab(&full[st], u & 1, a.err, s_abort)) {
+                        ab = true;
+                        break;
+                    }
+                    if (ub >= 1 && !mbar_wait_ab(&tempty[buf], (ub - 1) & 1, a.err, s_abort)) {
+                        ab = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t abase = smem_u32(A + (size_t)st * KC * TC_M * 128);
                     for (int kc = 0; kc < KC; ++kc)
-                        tma_load_2d(A + (size_t)st * KC * TC_M * 128 + (size_t)kc * TC_M * 128 +
-                                        (size_t)j * C * 128,
-                                    &tmap, kc * EPC, sl[j] * C, &full[st]);
-                }
-            }
-            __syncwarp();
-        } else if (warp == 1) {
-            if (lane == 0)
-            for (int b = 0; b < nblk && !*s_abort; ++b) {
-                const uint32_t g = gblk + b, st = g % TC_NST, u = g / TC_NST;
-                const uint32_t buf = g & 1, ub = g >> 1;
-                if (!mbar_wait_bounded(&full[st], u & 1, a.err)) {
-                    *s_abort = 1;
-                    break;
-                }
-                if (ub >= 1 && !mbar_wait_bounded(&tempty[buf], (ub - 1) & 1, a.err)) {
-                    *s_abort = 1;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t abase = smem_u32(A + (size_t)st * KC * TC_M * 128);
-                const uint32_t bbase = smem_u32(B);
-                for (int kc = 0; kc < KC; ++kc)
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = smem_desc_sw128(abase + kc * TC_M * 128 + ks * 32, 1024);
-                        const uint64_t bd = smem_desc_sw128(bbase + kc * TC_N * 128 + ks * 32, 1024);
-                        const uint32_t acc = (kc | ks) != 0;
-                        if (DT == 0) mma_bf16(tbase + buf * TC_N, ad, bd, idesc, acc);
-                        else mma_fp8(tbase + buf * TC_N, ad, bd, idesc, acc);
-                    }
-                mma_commit(&tfull[buf]);
-                mma_commit(&empty[st]);
-            }
-            __syncwarp();
-        } else if (warp >= 4) {
-            const int ew = warp - 4;          // epilogue warp
-            const int qt = ew & 3;            // its TMEM lane quarter (warp % 4)
-            const int c0 = (ew >> 2) * TC_NCOL;  // its first query column
-            const int et = ew * 32 + lane;    // epilogue thread
-            const int v = qt * 32 + lane;     // A row = vector of the tile
-            const int CB = ME - K;
-            const int BPS = TC_META / SPB;    // tiles whose slab metadata is staged
-            float xn_next = 0.f;
-            for (int b = 0; b < nblk; ++b) {
-                const uint32_t g = gblk + b, buf = g & 1, ub = g >> 1;
-                if (b % BPS == 0) {
-                    // stage ids + bitmaps of the next TC_META slabs of the chunk
-                    named_bar_sync(1, TC_EPI);
-                    const int sb0 = b * SPB, sn = min(TC_META, ns - sb0);
-                    for (int i = et; i < sn; i += TC_EPI) {
-                        const int sl = dirl[sb0 + i];
-                        const bool okk = sl >= 0 && sl < a.n_slabs;
-                        Msl[i] = okk ? sl : -1;
-                        for (int w = 0; w < C / 32; ++w)
-                            Mbits[i * 4 + w] = okk ? __ldg(a.bits + (size_t)sl * (C / 32) + w) : 0u;
-                    }
-                    named_bar_sync(1, TC_EPI);
-                    const int j0 = v / C;
-                    const int s_first = j0 < min(SPB, ns - b * SPB) ? Msl[(b * SPB - sb0) + j0] : -1;
-                    xn_next = s_first >= 0 ? __ldg(a.xnorm + (size_t)s_first * C + v % C) : 0.f;
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = smem_desc_sw128(abase + kc * TC_M * 128 + ks * 32, 1024);
+                            const uint64_t bd = smem_desc_sw128(bbase + kc * TN * 128 + ks * 32, 1024);
+                            const uint32_t acc = (kc | ks) != 0;
+                            if (DT == 0) mma_bf16(tbase + buf * TB, ad, bd, idesc, acc);
+                            else mma_fp8(tbase + buf * TB, ad, bd, idesc, acc);
+                        }
+                    mma_commit(&tfull[buf]);
+                    mma_commit(&empty[st]);
                 }
+                if (ab) break;
+                mma_commit(&bfree[bb]);
+            }
+            // the last accumulator is written before TMEM is released
+            if (g > 0) mbar_wait_bounded(&tfull[(g - 1) & 1], ((g - 1) >> 1) & 1, a.err);
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---- epilogue
+        const int ew = warp - 4;             // epilogue warp
+        const int qt = ew & 3;               // its TMEM lane quarter (warp % 4)
+        const int c0 = (ew >> 2) * TC_NCOL;  // its first query column
+        const int et = ew * 32 + lane;       // epilogue thread
+        const int v = qt * 32 + lane;        // A row = vector of the tile
+        uint32_t *hist = Hist + ew * TC_HIST;
+        uint32_t g = 0;
+        for (int it = 0;; ++it) {
+            const int j = it % TC_CTX;
+            const bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort);
+            if (!named_bar_and(1, EPI, ok && !*s_abort)) break;
+            const int32_t *h = hdr(j);
+            const int flags = h[8];
+            if (flags & CF_STOP) break;
+            const int m = h[1], sns = h[3], nblk = h[4], ME = h[5], chunk = h[7];
+            const float inv_l = __int_as_float(h[9]);
+            // a row's pending candidates are folded into its best K' once a
+            // tile leaves more than FT of them: FT plus one tile always fits
+            const int FT = min(ME - K, 256) - TC_M;
+            const int32_t *qp = c_qpair(j);
+            const float *cqn = c_qn(j), *cqsc = c_qsc(j), *ckd = c_kd0(j);
+            const int32_t *sl = c_sl(j);
+            const uint32_t *bt = c_bits(j);
+            if (flags & CF_FIRST) {
+                for (int r = et; r < TN; r += EPI) {
+                    const bool on = r < m;
+                    s_cnt[r] = 0;
+                    s_nb[r] = 0;
+                    s_kd[r] = on ? ckd[r] : INFINITY;
+                    s_t[r] = on ? ckd[r] - cqn[r] : -INFINITY;
+                    s_sc[r] = DT == 0 ? 2.f : 2.f / (inv_l * cqsc[r]);
+                }
+            }
+            named_bar_sync(1, EPI);
+            bool run = true;
+            for (int b = 0; b < nblk; ++b, ++g) {
+                const uint32_t buf = g & 1, ub = g >> 1, xs = g % TC_XR, xu = g / TC_XR;
                 // row of this thread in the tile
-                const int nsl = min(SPB, ns - b * SPB);
-                const int j = v / C, slot = v % C;
-                const int mi = (b % BPS) * SPB + j;
-                const int sl = j < nsl ? Msl[mi] : -1;
-                const bool live = sl >= 0 && ((Mbits[mi * 4 + (slot >> 5)] >> (slot & 31)) & 1u);
-                const int32_t gslot = live ? sl * C + slot : -1;
-                const float xn = xn_next;
-                // prefetch ||x||^2 of the row of the next tile
-                if (b + 1 < nblk && (b + 1) % BPS != 0) {
-                    const int nsl2 = min(SPB, ns - (b + 1) * SPB);
-                    const int mi2 = ((b + 1) % BPS) * SPB + j;
-                    const int sl2 = j < nsl2 ? Msl[mi2] : -1;
-                    xn_next = sl2 >= 0 ? __ldg(a.xnorm + (size_t)sl2 * C + slot) : 0.f;
-                }
-
-                bool ok = !*s_abort && mbar_wait_bounded(&tfull[buf], ub & 1, a.err);
-                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-aligned
-                if (!ok) *s_abort = 1;
+                const int nsl = min(SPB, sns - b * SPB);
+                const int jr = v / C, slot = v % C, mi = b * SPB + jr;
+                const int s = jr < nsl ? sl[mi] : -1;
+                const bool live = s >= 0 && ((bt[mi * 4 + (slot >> 5)] >> (slot & 31)) & 1u);
+                const int32_t gslot = s * C + slot;
+                bool wok = mbar_wait_ab(&xfull[xs], xu & 1, a.err, s_abort);
+                const float xn = XN[xs * TC_M + v];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xempty[xs]);
+                wok = wok && mbar_wait_ab(&tfull[buf], ub & 1, a.err, s_abort);
+                wok = __all_sync(0xffffffffu, wok);  // tcgen05.ld is warp-aligned
                 tc_fence_after();
+                const bool cols = c0 < m;           // warp-uniform
                 float dv[TC_NCOL];
-                if (ok) {
-#pragma unroll
-                    for (int c16 = 0; c16 < TC_NCOL / 16; ++c16) {
-                        float t[16];
-                        tmem_ld16(tbase + buf * TC_N + c0 + c16 * 16 + ((uint32_t)(qt * 32) << 16), t);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) dv[c16 * 16 + i] = t[i];
-                    }
+                if (wok && cols) {
+                    tmem_ld16(tbase + buf * TB + c0 + ((uint32_t)(qt * 32) << 16), dv);
                     tmem_ld_wait();
                 }
                 tc_fence_before();
-                mbar_arrive(&tempty[buf]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
 
-                // candidates straight from registers: a row passes for query n
-                // when -s q.x + ||x||^2 <= kd_n - ||q_n||^2 (= s_t[n], set per
-                // tile); per query one ballot over this warp's 32 rows and one
-                // shared atomic for their buffer slots
-                const float4 *t4 = reinterpret_cast<const float4 *>(s_t);
+                // a row passes for query n when -s q.x + ||x||^2 <= kd_n - ||q_n||^2:
+                // the 16 ballots first (independent), then, only if a row
+                // passed, lane i reserves column i's buffer positions with one
+                // shared atomic and the passing rows are written
+                bool need = false;
+                if (wok && cols) {
+                    uint32_t mk[TC_NCOL];
+                    const float4 *t4 = reinterpret_cast<const float4 *>(s_t + c0);
+                    const float4 *sc4 = reinterpret_cast<const float4 *>(s_sc + c0);
 #pragma unroll
-                for (int j0 = 0; j0 < TC_NCOL; j0 += 16) {
-                    const int n0 = c0 + j0;
-                    if (n0 >= m) break;
-                    uint32_t mk[16];
-#pragma unroll
-                    for (int i4 = 0; i4 < 4; ++i4) {
-                        const float4 tv = t4[(n0 >> 2) + i4];
+                    for (int i4 = 0; i4 < TC_NCOL / 4; ++i4) {
+                        const float4 tv = t4[i4];
                         const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+                        float sc[4] = {2.f, 2.f, 2.f, 2.f};
+                        if (DT == 1) {
+                            const float4 sv = sc4[i4];
+                            sc[0] = sv.x;
+                            sc[1] = sv.y;
+                            sc[2] = sv.z;
+                            sc[3] = sv.w;
+                        }
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const int n = n0 + 4 * i4 + c;
-                            const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
-                            const float part = fmaf(-sc, dv[j0 + 4 * i4 + c], xn);
-                            mk[4 * i4 + c] = __ballot_sync(0xffffffffu, ok && live && part <= tt[c]);
+                            const int i = 4 * i4 + c;
+                            const float part = fmaf(-sc[c], dv[i], xn);
+                            mk[i] = __ballot_sync(0xffffffffu, live && c0 + i < m && part <= tt[c]);
                         }
                     }
+                    uint32_t any = 0u;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        if (!mk[i]) continue;
-                        const int n = n0 + i;
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&s_cc[n], __popc(mk[i]));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if ((mk[i] >> lane) & 1u) {
-                            const float sc = DT == 0 ? 2.f : 2.f / (inv_l * s_qsc[n]);
-                            const int p = K + base + __popc(mk[i] & lanemask_lt());
-                            BD[(size_t)n * ME + p] = fmaf(-sc, dv[j0 + i], s_qn[n] + xn);
-                            BS[(size_t)n * ME + p] = gslot;
+                    for (int i = 0; i < TC_NCOL; ++i) any |= mk[i];
+                    if (any) {
+                        uint32_t my = 0u;
+#pragma unroll
+                        for (int i = 0; i < TC_NCOL; ++i)
+                            if (lane == i) my = mk[i];
+                        int mybase = 0;
+                        if (my) {
+                            mybase = atomicAdd(&s_cnt[c0 + lane], __popc(my));
+                            need = mybase + __popc(my) > FT;
+                        }
+#pragma unroll
+                        for (int i = 0; i < TC_NCOL; ++i) {
+                            if (!mk[i]) continue;
+                            const int n = c0 + i;
+                            const int base = __shfl_sync(0xffffffffu, mybase, i);
+                            if ((mk[i] >> lane) & 1u) {
+                                const int p = K + base + __popc(mk[i] & lanemask_lt());
+                                BD[(size_t)n * ME + p] = fmaf(-s_sc[n], dv[i], cqn[n] + xn);
+                                BS[(size_t)n * ME + p] = gslot;
+                            }
                         }
                     }
                 }
-                named_bar_sync(1, TC_EPI);
-                // merges: warp ew takes rows n = ew, ew + TC_EW, ...
-                const bool last = b + 1 == nblk;
-                for (int n = ew; n < m; n += TC_EW) {
-                    const int cc = s_cc[n];
-                    if (cc == 0 || !(last || cc > CB - TC_M)) continue;
+                if (named_bar_or(1, EPI, need || !wok || *s_abort)) {
+                    run = named_bar_and(1, EPI, wok && !*s_abort);
+                    if (!run) break;
+                    // fold the rows whose pending candidates passed FT
+                    for (int n = ew; n < m; n += EW) {
+                        const int cc = s_cnt[n];
+                        if (cc <= FT) continue;
+                        int nb = s_nb[n];
+                        const float kd = fold_row(BD + (size_t)n * ME, BS + (size_t)n * ME, K, nb,
+                                                  cc, hist, lane);
+                        if (lane == 0) {
+                            s_nb[n] = nb;
+                            s_cnt[n] = 0;
+                            if (kd < s_kd[n]) {
+                                s_kd[n] = kd;
+                                s_t[n] = kd - cqn[n];
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    named_bar_sync(1, EPI);
+                }
+            }
+            if (!run) {
+                if (et == 0) *s_abort = 1;
+                break;
+            }
+            if (flags & CF_LAST) {
+                // each row's best K' (unsorted; the per-query merge sorts),
+                // padded with (+inf, -1); its K'-th distance becomes a bound
+                // of the query for the items that follow
+                named_bar_sync(1, EPI);
+                for (int n = ew; n < m; n += EW) {
+                    const int cc = s_cnt[n];
+                    int nb = s_nb[n];
                     float *bd = BD + (size_t)n * ME;
                     int32_t *bs = BS + (size_t)n * ME;
-                    const int nb = s_nb[n];
-                    if (cc <= 32) warp_sort_merge32<1, KMAX>(bd, bs, K, nb, cc, lane);
-                    else if (cc <= 64) warp_sort_merge32<2, KMAX>(bd, bs, K, nb, cc, lane);
-                    else if (cc <= 128) warp_sort_merge32<4, KMAX>(bd, bs, K, nb, cc, lane);
-                    else
-                        warp_select_merge32<KMAX>(
-                            bd, bs, K, nb, cc, Hist + ew * 256,
-                            reinterpret_cast<float *>(Stg + (size_t)ew * KMAX * 8),
-                            reinterpret_cast<int32_t *>(Stg + (size_t)ew * KMAX * 8 + KMAX * 4), lane);
-                    const int nb2 = min(K, nb + cc);
-                    if (lane == 0) {
-                        s_nb[n] = nb2;
-                        s_cc[n] = 0;
-                        if (nb2 == K && bd[K - 1] < s_kd[n]) {
-                            s_kd[n] = bd[K - 1];
-                            s_t[n] = s_kd[n] - s_qn[n];
-                        }
+                    float kd = s_kd[n];
+                    if (cc > 0) kd = fminf(kd, fold_row(bd, bs, K, nb, cc, hist, lane));
+                    const int64_t base = ((int64_t)qp[n] * a.CH + chunk) * K;
+                    for (int i = lane; i < K; i += 32) {
+                        a.part_d[base + i] = i < nb ? bd[i] : INFINITY;
+                        a.part_i[base + i] = i < nb ? (int64_t)bs[i] : -1;
                     }
+                    if (lane == 0 && kd >= 0.f && kd < INFINITY)
+                        atomicMin(reinterpret_cast<int *>(a.thr) + qp[n] / a.P, __float_as_int(kd));
                     __syncwarp();
                 }
-                named_bar_sync(1, TC_EPI);
             }
+            named_bar_sync(1, EPI);
+            if (lane == 0) mbar_arrive(&cempty[j]);
         }
-        gblk += nblk;
-        __syncthreads();
-
-        // ---- publish each row's K'-th distance as its query's shared bound
-        const int MEo = max(M, ((TC_N * M) / max(m, 1)) & ~7);
-        for (int r = tid; r < m; r += TC_NT)
-            if (s_nb[r] == K && BD[(size_t)r * MEo + K - 1] >= 0.f)
-                atomicMin(reinterpret_cast<int *>(a.thr) + s_qpair[r] / a.P,
-                          __float_as_int(BD[(size_t)r * MEo + K - 1]));
-        // ---- the best K' of each row (padded with (+inf, -1))
-        for (int e = tid; e < m * K; e += TC_NT) {
-            const int r = e / K, jj = e % K;
-            const int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
-            const bool ok = jj < s_nb[r];
-            a.part_d[base + jj] = ok ? BD[(size_t)r * MEo + jj] : INFINITY;
-            a.part_i[base + jj] = ok ? (int64_t)BS[(size_t)r * MEo + jj] : -1;
-        }
-        __syncthreads();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 2) tmem_dealloc(tbase, 2 * TC_N);
+    if (warp == 2) tmem_dealloc(tbase, 2 * TB);
+}
+
+// ------------------------------------------------------- per-query merge
+// One warp per query: the best K' (distance, slot) of the query's item
+// outputs (P x CH runs of K' unsorted entries, valid ones first, padded
+// with (+inf, -1); runs with chunk >= pnch were not scanned) by a radix
+// select over the 64-bit (distance, slot) keys, then sorted ascending,
+// padded with (+inf, -1).
+constexpr int MT_NT = 128;
+template <int E>
+__global__ __launch_bounds__(MT_NT) void k_merge_tc(const int32_t *__restrict__ pnch,
+                                                    int64_t nq, int P, int CH, int K,
+                                                    const float *__restrict__ part_d,
+                                                    const int64_t *__restrict__ part_i,
+                                                    float *__restrict__ out_d,
+                                                    int64_t *__restrict__ out_s)
+{
+    constexpr int NW = MT_NT / 32;
+    __shared__ uint32_t hist[NW][TC_HIST];
+    __shared__ uint32_t vrun[NW][2048 / 32];  // scanned runs (R <= 2048)
+    __shared__ float sd[NW][32 * E];
+    __shared__ int32_t ss[NW][32 * E];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
+    if (q >= nq) return;  // whole warps
+    const int R = P * CH, N = R * K;
+    const int64_t base = q * (int64_t)N;
+    for (int w = lane; w < (R + 31) / 32; w += 32) vrun[warp][w] = 0u;
+    __syncwarp();
+    for (int r = lane; r < R; r += 32)
+        if (r % CH < pnch[q * P + r / CH]) atomicOr(&vrun[warp][r >> 5], 1u << (r & 31));
+    __syncwarp();
+    auto key = [&](int i) -> uint64_t {
+        const int r = i / K;
+        if (!((vrun[warp][r >> 5] >> (r & 31)) & 1u)) return ~0ull;
+        const int64_t sl = part_i[base + i];
+        return sl < 0 ? ~0ull : ds_key(part_d[base + i], (int32_t)sl);
+    };
+    int nv = 0;
+    for (int i = lane; i < N; i += 32) nv += key(i) != ~0ull;
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    uint64_t prefix = ~0ull, mask = 0ull;  // keep every valid entry
+    if (nv > K) warp_radix_kth(key, N, K, hist[warp], lane, prefix, mask);
+    int w = 0;
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + lane;
+        const uint64_t k = i < N ? key(i) : ~0ull;
+        const bool take = k != ~0ull && (k & mask) <= prefix;
+        const uint32_t mk = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int p = w + __popc(mk & lanemask_lt());
+            if (p < 32 * E) {
+                sd[warp][p] = part_d[base + i];
+                ss[warp][p] = (int32_t)part_i[base + i];
+            }
+        }
+        w += __popc(mk);
+    }
+    __syncwarp();
+    const int nk = min(w, K);
+    float v[E];
+    int32_t sv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = i < nk ? sd[warp][i] : INFINITY;
+        sv[e] = i < nk ? ss[warp][i] : 0x7fffffff;
+    }
+    warp_sort32<E>(v, sv, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < K) {
+            out_d[q * K + i] = i < nk ? v[e] : INFINITY;
+            out_s[q * K + i] = i < nk ? (int64_t)sv[e] : -1;
+        }
+    }
+}
+
+void merge_tc(sivf_index *ix, int64_t nq, int P, const SearchPlan &pl, const SearchScratch &s,
+              int Kc, float *out_d, int64_t *out_s, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
+    const int tok = prof_begin(ix, PROF_MERGE, 1, st);
+#define SIVF_MTC(E_)                                                                    \
+    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.pnch, nq, P, pl.ch, Kc, s.part_d, s.part_i, \
+                                             out_d, out_s)
+    if (Kc <= 32) SIVF_MTC(1);
+    else if (Kc <= 64) SIVF_MTC(2);
+    else if (Kc <= 128) SIVF_MTC(4);
+    else if (Kc <= 256) SIVF_MTC(8);
+    else SIVF_MTC(16);
+#undef SIVF_MTC
+    prof_end(ix, tok, st);
 }
 
 // ---------------------------------------------------------------- re-rank
@@ -776,9 +1192,12 @@ __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__
     }
 }
 
-// per query: FP32 ||q||^2 and the FP8 inverse scale 448 / (2 max_j |q_j|)
-__global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
-                             float *__restrict__ qn, float *__restrict__ qsc)
+// per query: FP32 ||q||^2, the FP8 inverse scale 448 / (2 max_j |q_j|) and
+// the row in the scan format (dtype 1: BF16, round to nearest even; 2: E4M3
+// of fl32(q_j * scale), round to nearest even, saturated)
+__global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d, int dtype,
+                             float *__restrict__ qn, float *__restrict__ qsc,
+                             unsigned char *__restrict__ qcast)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -792,17 +1211,31 @@ __global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
     }
     ss = warp_sum(ss);
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float sc = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
     if (lane == 0) {
         qn[i] = ss;
-        qsc[i] = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
+        qsc[i] = sc;
+    }
+    if (dtype == SIVF_BF16) {
+        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(qcast) + (size_t)i * d;
+        for (int j = lane; j < d; j += 32) o[j] = __float2bfloat16_rn(qr[j]);
+    } else if (dtype == SIVF_FP8E4M3) {
+        unsigned char *o = qcast + (size_t)i * d;
+        for (int j = 2 * lane; j < d; j += 64) {
+            const float2 p = make_float2(__fmul_rn(qr[j], sc), __fmul_rn(qr[j + 1], sc));
+            const uint32_t two = __nv_cvt_float2_to_fp8x2(p, __NV_SATFINITE, __NV_E4M3);
+            o[j] = (unsigned char)(two & 0xffu);
+            o[j + 1] = (unsigned char)(two >> 8);
+        }
     }
 }
 
-void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
-                cudaStream_t st)
+void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn, float *qsc,
+                unsigned char *qcast, cudaStream_t st)
 {
     ix->launches += 1;
-    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, qn, qsc);
+    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, dtype, qn, qsc,
+                                                                    qcast);
 }
 
 // global slots -> labels (padding stays -1)
@@ -868,20 +1301,39 @@ bool tc_make_maps(sivf_index *ix)
 int tc_buf_len(int K) { return (K + TC_M + 7) / 8 * 8; }
 
 // queries per tile of the reduced-precision scan for K' candidates
-int tc_tile_queries(int Kc) { return Kc <= TcShape<64>::KMAX ? 64 : 16; }
+int tc_tile_queries(int Kc)
+{
+    return Kc <= TcShape<48>::KMAX ? 48 : Kc <= TcShape<32>::KMAX ? 32 : 16;
+}
+
+// dynamic shared memory one CTA may take (the kernel's static arrays aside)
+constexpr size_t kTcSmemMax = 227 * 1024 - 4096;
+
+template <int TN>
+static int tc_stages(int KC, int M)
+{
+    int nst = TC_MAXST;
+    while (nst > 2 && tc_smem<TN>(KC, M, nst).total > kTcSmemMax) --nst;
+    return nst;
+}
 
 bool tc_fits(const sivf_index *ix, int Kc)
 {
     const int esz = 2;  // the larger of the two formats
     const int KC = (ix->d * esz + 127) / 128;
-    if (Kc <= TcShape<64>::KMAX) return tc_smem<64>(KC, tc_buf_len(Kc)).total <= 227 * 1024 - 1024;
-    return Kc <= TcShape<16>::KMAX && tc_smem<16>(KC, tc_buf_len(Kc)).total <= 227 * 1024 - 1024;
+    const int M = tc_buf_len(Kc);
+    switch (tc_tile_queries(Kc)) {
+    case 48: return tc_smem<48>(KC, M, 2).total <= kTcSmemMax;
+    case 32: return tc_smem<32>(KC, M, 2).total <= kTcSmemMax;
+    default: return Kc <= TcShape<16>::KMAX && tc_smem<16>(KC, M, 2).total <= kTcSmemMax;
+    }
 }
 
 template <int DT, int TN>
-static void launch_tc(const unsigned char *tmap, const TcArgs &a, cudaStream_t st)
+static void launch_tc(const unsigned char *tmap, TcArgs a, cudaStream_t st)
 {
-    const size_t smem = tc_smem<TN>(a.KC, a.M).total;
+    a.nst = tc_stages<TN>(a.KC, a.M);
+    const size_t smem = tc_smem<TN>(a.KC, a.M, a.nst).total;
     static size_t attr = 0;
     if (smem > attr) {
         cudaFuncSetAttribute(k_scan_tc<DT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -913,6 +1365,7 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.items = s.items;
     a.qn = s.qn;
     a.qsc = s.qsc;
+    a.qcast = s.qcast;
     a.xnorm = ix->xnorm;
     a.bits = ix->bits;
     a.nslabs = ix->nslabs;
@@ -924,16 +1377,21 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.d = ix->d;
     a.C = ix->C;
     const int esz = dtype == SIVF_BF16 ? 2 : 1;
+    a.pay = dtype == SIVF_BF16 ? reinterpret_cast<const unsigned char *>(ix->xb16) : ix->x8;
     a.KC = (ix->d * esz + 127) / 128;
+    a.nst = 2;
+    a.pf_tiles = std::max(2, TC_PF_BYTES / (TC_M * ix->d * esz));
     a.ctl = ix->ctl;
     a.err = ix->err;
-    const bool wide = tc_tile_queries(Kc) == 64;
+    const int tn = tc_tile_queries(Kc);
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {
-        if (wide) launch_tc<0, 64>(ix->tmap_bf16, a, st);
+        if (tn == 48) launch_tc<0, 48>(ix->tmap_bf16, a, st);
+        else if (tn == 32) launch_tc<0, 32>(ix->tmap_bf16, a, st);
         else launch_tc<0, 16>(ix->tmap_bf16, a, st);
     } else {
-        if (wide) launch_tc<1, 64>(ix->tmap_fp8, a, st);
+        if (tn == 48) launch_tc<1, 48>(ix->tmap_fp8, a, st);
+        else if (tn == 32) launch_tc<1, 32>(ix->tmap_fp8, a, st);
         else launch_tc<1, 16>(ix->tmap_fp8, a, st);
     }
     prof_end(ix, tok, st);
