@@ -45,8 +45,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu capture of the BF16 list scan on this workload (nprobe 8): mean
 # dram__bytes_read.sum + dram__bytes_write.sum over its two launches, and the
 # scan kernel source it was taken of
-TC_PROFILED_SHA = "914051e0047bb9a0"
-TC_PROFILED_TRAFFIC = round((279.867648 + 6.304 + 280.654592 + 27.030272) / 2 * 1e6)
+TC_PROFILED_SHA = "39e5ef2ca9d3ff7b"
+TC_PROFILED_TRAFFIC = round((279.312384 + 6.300928 + 275.782656 + 27.657984) / 2 * 1e6)
 
 
 def parse():
