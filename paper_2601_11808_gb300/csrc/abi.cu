@@ -250,6 +250,9 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
     ALLOC(ix->cent, (size_t)L * d);
     ALLOC(ix->cnorm, (size_t)L);
     ALLOC(ix->cnrm_up, (size_t)L);
+    // BF16 copy of the centroids for the tensor-core first stage of the
+    // coarse selection (d % 16 == 0)
+    if (d % 16 == 0 && d <= kMaxD) ALLOC(ix->cent_bf16, (size_t)L * d);
     ALLOC(ix->x32, rows * d);
     if (ix->dtypes & (1u << SIVF_BF16)) ALLOC(ix->xb16, rows * d);
     if (ix->dtypes & (1u << SIVF_FP8E4M3)) ALLOC(ix->x8, rows * d);

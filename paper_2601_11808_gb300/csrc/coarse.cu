@@ -19,18 +19,28 @@
 //   of S by their FP64 distance, computed in the same order and with the
 //   same roundings as the definition (no fused multiply-add).
 // Only near-ties ever reach the FP64 step.
+//
+// For assignment (P = 1) with d % 16 == 0 the distances of the first stage
+// come from a BF16 tensor-core GEMM instead (tcgen05.mma, FP32
+// accumulation): the same
+// selection then runs twice.  With the bound of the BF16 stage (rounding of
+// x and c to BF16 plus the accumulation) it keeps the lists S_b that can
+// still be among the top P; their distances are recomputed in FP32 and the
+// selection above runs on S_b with the FP32 bound.  Lists outside S_b have
+// exact distances above the P-th smallest, so the result is the same set.
 #include <float.h>
 #include <math.h>
 
 #include "device_utils.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace sivf {
 
 // ------------------------------------------------------------ centroid prep
 __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
                                  float *__restrict__ cn, float *__restrict__ cnrm_up,
-                                 float *__restrict__ inv_scale8)
+                                 float *__restrict__ inv_scale8, uint16_t *__restrict__ cb)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L) return;
@@ -43,6 +53,11 @@ __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
     }
     cn[c] = __double2float_rn(s);
     cnrm_up[c] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+    if (cb)
+        for (int j = 0; j < d; ++j) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+            cb[(size_t)c * d + j] = *reinterpret_cast<const uint16_t *>(&h);
+        }
     if (inv_scale8) inv_scale8[c] = mx > 0.0 ? (float)(448.0 / (2.0 * mx)) : 1.0f;
 }
 
@@ -125,6 +140,8 @@ struct SelArgs {
     const float *cn;       // [L]
     const float *cnrm_up;  // [L]
     float gamma2;          // 2 * gamma_d
+    float gamma2_first;    // the same factor for the first-stage distances D
+    int two_level;         // D is the BF16 tensor-core stage: recheck S in FP32
     int32_t *out;          // [m, P]
     uint32_t *err;
 };
@@ -375,6 +392,130 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
     }
 }
 
+// ------------------------------------------ BF16 tensor-core first stage
+// out[i][c] = fl(cn[c] - 2 * acc[i][c]), acc = sum_j bf16(x[i][j]) *
+// bf16(cent[c][j]) accumulated in FP32 by tcgen05.mma.  One CTA: 128 rows
+// of x (rounded and swizzled by its threads) against 256 centroids (BF16
+// rows copied with cp.async), K = d (d % 16 == 0, <= 256), accumulator in
+// 256 TMEM columns; four warps read their TMEM lane quarter back.
+constexpr int CT_M = 128, CT_N = 256;
+
+__host__ __device__ inline size_t coarse_tc_smem(int d)
+{
+    const int KC = (d * 2 + 127) / 128;
+    return (size_t)KC * (CT_M + CT_N) * 128 + 1024;
+}
+
+__device__ __forceinline__ void cp_async16_c(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ x, int m, int d,
+                                                      const uint16_t *__restrict__ cb,
+                                                      const float *__restrict__ cn, int L,
+                                                      float *__restrict__ out, uint32_t *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int KC = (d * 2 + 127) / 128;
+    unsigned char *A = smem;                          // KC x 128 rows x 128 B
+    unsigned char *B = smem + (size_t)KC * CT_M * 128;  // KC x 256 rows x 128 B
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = blockIdx.x * CT_M, col0 = blockIdx.y * CT_N;
+    const int ncol = min(CT_N, L - col0);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, CT_N);
+    // B: BF16 centroid rows; chunks past L or d are zero
+    for (int e = tid; e < CT_N * KC * 8; e += 128) {
+        const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
+        const int k0 = kc * 64 + c * 8;  // first element of the 16-byte chunk
+        const bool in = col0 + r < L && k0 < d;
+        cp_async16_c(B + (size_t)kc * CT_N * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                         ((c ^ (r & 7)) << 4),
+                     in ? (const void *)(cb + (size_t)(col0 + r) * d + k0) : (const void *)cb,
+                     in ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // A: rows of x rounded to BF16 (round to nearest even); zero past m or d
+    for (int e = tid; e < CT_M * KC * 8; e += 128) {
+        const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
+        const int k0 = kc * 64 + c * 8;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (row0 + r < m && k0 < d) {
+            const float4 *xr = reinterpret_cast<const float4 *>(x + (size_t)(row0 + r) * d + k0);
+            const float4 f0 = __ldg(xr), f1 = __ldg(xr + 1);
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(f0.x, f0.y);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(f0.z, f0.w);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(f1.x, f1.y);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(f1.z, f1.w);
+            w[0] = *reinterpret_cast<uint32_t *>(&h0);
+            w[1] = *reinterpret_cast<uint32_t *>(&h1);
+            w[2] = *reinterpret_cast<uint32_t *>(&h2);
+            w[3] = *reinterpret_cast<uint32_t *>(&h3);
+        }
+        *reinterpret_cast<uint4 *>(A + (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 +
+                                   (r & 7) * 128 + ((c ^ (r & 7)) << 4)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+    if (tid == 0) {
+        const uint32_t idesc = mma_idesc(1, 1, CT_M, CT_N);
+        const uint32_t abase = smem_u32(A), bbase = smem_u32(B);
+        for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_bf16(tbase, smem_desc_sw128(abase + kc * CT_M * 128 + ks * 32, 1024),
+                         smem_desc_sw128(bbase + kc * CT_N * 128 + ks * 32, 1024), idesc,
+                         (kc | ks) != 0);
+        mma_commit(&bar);
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0, err));
+    tc_fence_after();
+    const int r = row0 + warp * 32 + lane;
+    const bool vec = (L & 3) == 0;
+    for (int c16 = 0; c16 * 16 < ncol; ++c16) {  // warp-uniform
+        float v[16];
+        if (ok) {
+            tmem_ld16(tbase + c16 * 16 + ((uint32_t)(warp * 32) << 16), v);
+            tmem_ld_wait();
+        }
+        if (!ok || r >= m) continue;
+        const int cb0 = col0 + c16 * 16;
+        float *o = out + (size_t)r * L + cb0;
+        if (vec && c16 * 16 + 16 <= ncol) {
+#pragma unroll
+            for (int i4 = 0; i4 < 4; ++i4) {
+                const float4 cv = __ldg(reinterpret_cast<const float4 *>(cn + cb0) + i4);
+                reinterpret_cast<float4 *>(o)[i4] =
+                    make_float4(fmaf(-2.f, v[4 * i4], cv.x), fmaf(-2.f, v[4 * i4 + 1], cv.y),
+                                fmaf(-2.f, v[4 * i4 + 2], cv.z), fmaf(-2.f, v[4 * i4 + 3], cv.w));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (c16 * 16 + i < ncol) o[i] = fmaf(-2.f, v[i], __ldg(cn + cb0 + i));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tbase, CT_N);
+}
+
 // ----------------------------------------------- warp-per-row selection
 // The same selection for P <= CW_PMAX with one warp per row and no block
 // barriers: each lane keeps the CW_PMAX smallest upper bounds of its lists
@@ -388,18 +529,21 @@ constexpr int CW_SCAP = 128;
 
 __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 {
-    __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP];
+    __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP], sDt[CW_ROWS][CW_SCAP];
     __shared__ int sIdx[CW_ROWS][CW_SCAP];
     __shared__ double sDx[CW_ROWS][CW_SCAP];
     __shared__ unsigned char sSure[CW_ROWS][CW_SCAP];
     __shared__ int sSel[CW_ROWS][CW_PMAX];
+    __shared__ float sSelDt[CW_ROWS][CW_PMAX];
     __shared__ double sHd[CW_ROWS][CW_PMAX];
+    __shared__ __align__(16) float sX[CW_ROWS][kMaxD];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * CW_ROWS + w;
     if (row >= a.m) return;  // whole warps
     const int L = a.L, P = a.P;
     const float *Dr = a.D + (size_t)row * L;
     const float *xr = a.x + (size_t)row * a.d;
+    const float g1 = a.two_level ? a.gamma2_first : a.gamma2;
 
     // ||x|| upper bound from an FP64 sum
     double part = 0.0;
@@ -407,65 +551,146 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     const float xn = __double2float_ru(sqrt(part) * (1.0 + 1e-12));
 
-    // T = P-th smallest upper bound
-    float top[CW_PMAX];
+    // P-th smallest of the values v(i), i < n, each lane keeping its
+    // CW_PMAX smallest in a sorted register list
+    auto pth_smallest = [&](auto val, int n) {
+        float top[CW_PMAX];
 #pragma unroll
-    for (int k = 0; k < CW_PMAX; ++k) top[k] = INFINITY;
-    for (int c = lane; c < L; c += 32) {
-        const float Dt = Dr[c];
-        float v = upper_of(Dt, bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2));
+        for (int k = 0; k < CW_PMAX; ++k) top[k] = INFINITY;
+        constexpr int CU = 8;  // values per lane loaded ahead
+        for (int i0 = lane; i0 < n; i0 += 32 * CU) {
+            float vv[CU];
 #pragma unroll
-        for (int k = 0; k < CW_PMAX; ++k) {  // insert into the sorted list
-            const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
-            top[k] = lo;
-            v = hi;
-        }
-    }
-    float T = INFINITY;
-    for (int t = 0; t < P; ++t) {
-        float v = top[0];
-        int who = lane;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int ow = __shfl_xor_sync(0xffffffffu, who, o);
-            if (ov < v || (ov == v && ow < who)) {
-                v = ov;
-                who = ow;
+            for (int u = 0; u < CU; ++u) vv[u] = i0 + 32 * u < n ? val(i0 + 32 * u) : INFINITY;
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                float v = vv[u];
+#pragma unroll
+                for (int k = 0; k < CW_PMAX; ++k) {  // insert into the sorted list
+                    const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
+                    top[k] = lo;
+                    v = hi;
+                }
             }
         }
-        T = v;
-        if (lane == who) {
+        float T = INFINITY;
+        for (int t = 0; t < P; ++t) {
+            float v = top[0];
+            int who = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int ow = __shfl_xor_sync(0xffffffffu, who, o);
+                if (ov < v || (ov == v && ow < who)) {
+                    v = ov;
+                    who = ow;
+                }
+            }
+            T = v;
+            if (lane == who) {
 #pragma unroll
-            for (int k = 0; k + 1 < CW_PMAX; ++k) top[k] = top[k + 1];
-            top[CW_PMAX - 1] = INFINITY;
+                for (int k = 0; k + 1 < CW_PMAX; ++k) top[k] = top[k + 1];
+                top[CW_PMAX - 1] = INFINITY;
+            }
         }
-    }
+        return T;
+    };
 
-    // candidate set S
+    // T = P-th smallest upper bound over all lists
+    float T = pth_smallest([&](int c) {
+        const float Dt = __ldg(Dr + c);
+        return upper_of(Dt, bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1));
+    }, L);
+
+    // candidate set S = {c : lower bound <= T}
     int ns = 0;
-    for (int c0 = 0; c0 < L; c0 += 32) {
-        const int c = c0 + lane;
-        float lb = 0.f, ub = 0.f;
-        bool in = false;
-        if (c < L) {
-            const float Dt = Dr[c];
-            const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
-            lb = lower_of(Dt, E);
-            ub = upper_of(Dt, E);
-            in = lb <= T;
-        }
-        const uint32_t mk = __ballot_sync(0xffffffffu, in);
-        if (in) {
-            const int p = ns + __popc(mk & lanemask_lt());
-            if (p < CW_SCAP) {
-                sLB[w][p] = lb;
-                sUB[w][p] = ub;
-                sIdx[w][p] = c;
+    constexpr int CU = 8;
+    for (int c00 = 0; c00 < L; c00 += 32 * CU) {
+        float lbv[CU], ubv[CU], dtv[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int c = c00 + 32 * u + lane;
+            lbv[u] = INFINITY;
+            ubv[u] = INFINITY;
+            dtv[u] = 0.f;
+            if (c < L) {
+                const float Dt = __ldg(Dr + c);
+                const float E = bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1);
+                lbv[u] = lower_of(Dt, E);
+                ubv[u] = upper_of(Dt, E);
+                dtv[u] = Dt;
             }
         }
-        ns += __popc(mk);
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int c = c00 + 32 * u + lane;
+            const bool in = c < L && lbv[u] <= T;
+            const uint32_t mk = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int p = ns + __popc(mk & lanemask_lt());
+                if (p < CW_SCAP) {
+                    sLB[w][p] = lbv[u];
+                    sUB[w][p] = ubv[u];
+                    sDt[w][p] = dtv[u];
+                    sIdx[w][p] = c;
+                }
+            }
+            ns += __popc(mk);
+        }
     }
     __syncwarp();
+    if (a.two_level && ns <= CW_SCAP) {
+        // S holds every list that can be among the top P (BF16-stage
+        // bound); recompute their distances in FP32, one list per lane,
+        // rebuild T and S with the FP32 bound inside S
+        for (int j = lane; j < a.d; j += 32) sX[w][j] = xr[j];
+        __syncwarp();
+        const float4 *x4 = reinterpret_cast<const float4 *>(sX[w]);
+        for (int p = lane; p < ns; p += 32) {
+            const int c = sIdx[w][p];
+            const float4 *c4 = reinterpret_cast<const float4 *>(a.cent + (size_t)c * a.d);
+            float acc = 0.f;
+            for (int j4 = 0; j4 < a.d / 4; ++j4) {
+                const float4 xv = x4[j4], cv = __ldg(c4 + j4);
+                acc = fmaf(xv.x, cv.x, acc);
+                acc = fmaf(xv.y, cv.y, acc);
+                acc = fmaf(xv.z, cv.z, acc);
+                acc = fmaf(xv.w, cv.w, acc);
+            }
+            const float cnc = __ldg(a.cn + c);
+            const float Dt = fmaf(-2.f, acc, cnc);
+            const float E = bound_of(Dt, cnc, __ldg(a.cnrm_up + c), xn, a.gamma2);
+            sLB[w][p] = lower_of(Dt, E);
+            sUB[w][p] = upper_of(Dt, E);
+            sDt[w][p] = Dt;
+        }
+        __syncwarp();
+        T = pth_smallest([&](int p) { return sUB[w][p]; }, ns);
+        int n2 = 0;
+        for (int p0 = 0; p0 < ns; p0 += 32) {
+            const int p = p0 + lane;
+            const bool keep = p < ns && sLB[w][p] <= T;
+            float lb = 0.f, ub = 0.f, dt = 0.f;
+            int c = 0;
+            if (keep) {
+                lb = sLB[w][p];
+                ub = sUB[w][p];
+                dt = sDt[w][p];
+                c = sIdx[w][p];
+            }
+            const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) {  // write index <= read index
+                const int q = n2 + __popc(mk & lanemask_lt());
+                sLB[w][q] = lb;
+                sUB[w][q] = ub;
+                sDt[w][q] = dt;
+                sIdx[w][q] = c;
+            }
+            n2 += __popc(mk);
+            __syncwarp();
+        }
+        ns = n2;
+    }
     int32_t *outr = a.out + (size_t)row * P;
     int nsel = 0;
     if (ns <= CW_SCAP) {
@@ -483,7 +708,10 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
             const uint32_t mk = __ballot_sync(0xffffffffu, sure);
             if (sure) {
                 const int s = nsel + __popc(mk & lanemask_lt());
-                if (s < CW_PMAX) sSel[w][s] = sIdx[w][p];
+                if (s < CW_PMAX) {
+                    sSel[w][s] = sIdx[w][p];
+                    sSelDt[w][s] = sDt[w][p];
+                }
             }
             nsel += __popc(mk);
         }
@@ -515,7 +743,10 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
                 const uint32_t mk = __ballot_sync(0xffffffffu, take);
                 if (take) {
                     const int s = nsel + __popc(mk & lanemask_lt());
-                    if (s < CW_PMAX) sSel[w][s] = sIdx[w][p];
+                    if (s < CW_PMAX) {
+                        sSel[w][s] = sIdx[w][p];
+                        sSelDt[w][s] = sDt[w][p];
+                    }
                 }
                 nsel += __popc(mk);
             }
@@ -528,7 +759,7 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
             int n = 0;
             for (int c = 0; c < L; ++c) {
                 const float Dt = Dr[c];
-                const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, a.gamma2);
+                const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, g1);
                 if (lower_of(Dt, E) > T) continue;
                 const double Dc = exact_dist(xr, a.cent + (size_t)c * a.d, a.d);
                 if (n == P && !(Dc < sHd[w][n - 1])) continue;
@@ -542,6 +773,7 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
                 sSel[w][pos] = c;
                 if (n < P) ++n;
             }
+            for (int i = 0; i < n; ++i) sSelDt[w][i] = (float)sHd[w][i];
             nsel = n;
         }
         nsel = __shfl_sync(0xffffffffu, nsel, 0);
@@ -556,11 +788,11 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
             outr[lane] = -1;
         } else {
             const int c = sSel[w][lane];
-            const float dc = Dr[c];
+            const float dc = sSelDt[w][lane];
             int pos = 0;
             for (int q = 0; q < nsel; ++q) {
                 const int c2 = sSel[w][q];
-                const float d2 = Dr[c2];
+                const float d2 = sSelDt[w][q];
                 pos += d2 < dc || (d2 == dc && c2 < c);
             }
             outr[pos] = c;
@@ -573,7 +805,7 @@ void centroid_prep(sivf_index *ix, cudaStream_t st)
 {
     ix->launches += 1;
     k_centroid_norms<<<(ix->nlist + 127) / 128, 128, 0, st>>>(
-        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8);
+        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16);
 }
 
 // rows [0, m) of x -> out[m, P]; `Dbuf` holds at least rows_per_chunk * L
@@ -584,11 +816,33 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
     const int L = ix->nlist, d = ix->d;
     const double u = 5.9604644775390625e-08;
     const double gd = d * u / (1.0 - d * u);
+    // BF16 first stage: rounding of x and c (2 ub + ub^2 relative, ub =
+    // 2^-8) and the FP32 accumulation of the exact BF16 products (taken as
+    // d * 2^-20 relative, several ulps per addition)
+    const double ub = 1.0 / 256.0, gacc = d * std::ldexp(1.0, -20);
+    // The BF16 bound is a few percent of ||x|| ||c||: tight enough to isolate
+    // the nearest centroid (assignment, P = 1) but not to separate the P-th
+    // from the (P+1)-th of a dense shell of far centroids, so probe selection
+    // keeps the FP32 first stage
+    const bool two = ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD;
     for (int64_t r0 = 0; r0 < m; r0 += rows_per_chunk) {
         int mc = (int)std::min<int64_t>(rows_per_chunk, m - r0);
-        dim3 g((L + GBN - 1) / GBN, (mc + GBM - 1) / GBM);
         const int tok = prof_begin(ix, PROF_COARSE, 2, st);
-        k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
+        if (two) {
+            const size_t smem = coarse_tc_smem(d);
+            static size_t attr = 0;
+            if (smem > attr) {
+                cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+                attr = smem;
+            }
+            dim3 g((mc + CT_M - 1) / CT_M, (L + CT_N - 1) / CT_N);
+            k_coarse_tc<<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cnorm, L,
+                                               Dbuf, ix->err);
+        } else {
+            dim3 g((L + GBN - 1) / GBN, (mc + GBM - 1) / GBM);
+            k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
+        }
         SelArgs a;
         a.D = Dbuf;
         a.m = mc;
@@ -600,6 +854,8 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.cn = ix->cnorm;
         a.cnrm_up = ix->cnrm_up;
         a.gamma2 = (float)(2.0 * gd * (1.0 + 1e-6));
+        a.gamma2_first = (float)(2.0 * ((2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub)) * (1.0 + 1e-6));
+        a.two_level = two;
         a.out = out + r0 * P;
         a.err = ix->err;
         if (P <= CW_PMAX)

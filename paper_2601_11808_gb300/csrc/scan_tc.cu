@@ -1073,44 +1073,57 @@ void merge_tc(sivf_index *ix, int64_t nq, int P, const SearchPlan &pl, const Sea
 // ---------------------------------------------------------------- re-rank
 // One warp per query: exact FP32 direct-form distances of the K' merged
 // candidates (global slots) from the FP32 payload, then the best k by
-// (distance, id).
+// (distance, id).  Candidate c belongs to lane c % 32 (register c / 32),
+// which reads its whole payload row with 16-byte loads, so the warp has 32
+// rows in flight; the query row is staged in shared memory.
+constexpr int RK_NT = 128;
 template <int E>
-__global__ __launch_bounds__(128) void k_rerank(const float *__restrict__ q, int64_t nq, int d,
+__global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, int64_t nq, int d,
                                                 int Kc, const float *__restrict__ cand_d,
                                                 const int64_t *__restrict__ cand_s,
                                                 const float *__restrict__ x32,
                                                 const int64_t *__restrict__ ids, int k,
                                                 float *__restrict__ dist, int64_t *__restrict__ labels)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ __align__(16) float sq[RK_NT / 32][kMaxD];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t qi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (qi >= nq) return;
+    if (qi >= nq) return;  // whole warps
     const float *qr = q + (size_t)qi * d;
+    for (int j = lane; j < d; j += 32) sq[w][j] = qr[j];
+    __syncwarp();
+    const float4 *q4 = reinterpret_cast<const float4 *>(sq[w]);
     float v[E];
     int64_t id[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
+        const int c = lane + 32 * e;
         v[e] = INFINITY;
         id[e] = -1;
-    }
-    for (int c = 0; c < Kc; ++c) {
+        if (c >= Kc) continue;
         const int64_t gs = cand_s[qi * Kc + c];
         if (gs < 0 || !(cand_d[qi * Kc + c] < INFINITY)) continue;
-        const float *xr = x32 + (size_t)gs * d;
+        const float4 *x4 = reinterpret_cast<const float4 *>(x32 + (size_t)gs * d);
         float acc = 0.f;
-        for (int j = lane; j < d; j += 32) {
-            const float t = qr[j] - xr[j];
-            acc = fmaf(t, t, acc);
-        }
-        acc = warp_sum(acc);
-        const int64_t lab = ids[gs];
-        // candidate c lives in register e = c / 32 of lane c % 32
+        for (int j4 = 0; j4 < d / 4; j4 += 4) {  // d % 16 == 0
+            float4 xv[4];
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (c / 32 == e && lane == c % 32) {
-                v[e] = acc;
-                id[e] = lab;
+            for (int u = 0; u < 4; ++u) xv[u] = __ldg(x4 + j4 + u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 qv = q4[j4 + u];
+                float t = qv.x - xv[u].x;
+                acc = fmaf(t, t, acc);
+                t = qv.y - xv[u].y;
+                acc = fmaf(t, t, acc);
+                t = qv.z - xv[u].z;
+                acc = fmaf(t, t, acc);
+                t = qv.w - xv[u].w;
+                acc = fmaf(t, t, acc);
             }
+        }
+        v[e] = acc;
+        id[e] = __ldg(ids + gs);
     }
     warp_bitonic_sort<E>(v, id, lane);
 #pragma unroll
@@ -1400,10 +1413,10 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st)
 {
-    const int64_t blocks = (nq * 32 + 127) / 128;
+    const int64_t blocks = (nq * 32 + RK_NT - 1) / RK_NT;
     const int tok = prof_begin(ix, PROF_RERANK, 1, st);
 #define SIVF_RERANK(E_)                                                                  \
-    k_rerank<E_><<<(unsigned)blocks, 128, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32, \
+    k_rerank<E_><<<(unsigned)blocks, RK_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32, \
                                                    ix->ids, k, dist, labels)
     if (Kc <= 32) SIVF_RERANK(1);
     else if (Kc <= 64) SIVF_RERANK(2);

@@ -106,6 +106,14 @@ def _assign_cases():
     yield "midpoints", np.concatenate([a, b]), mid
     yield "one_list", rng.standard_normal((1, 12)).astype(np.float32), \
         rng.standard_normal((100, 12)).astype(np.float32)
+    # d % 16 == 0 takes the BF16 tensor-core first stage: duplicated
+    # centroids and integer grids with many exact ties (more candidates than
+    # the warp selection holds take its serial FP64 path)
+    c16 = rng.standard_normal((33, 16)).astype(np.float32)
+    yield "dup_centroids_d16", np.concatenate([c16] * 5), \
+        rng.standard_normal((2000, 16)).astype(np.float32)
+    yield "int_ties_d32", rng.integers(-2, 3, (300, 32)).astype(np.float32), \
+        rng.integers(-2, 3, (3000, 32)).astype(np.float32)
 
 
 @pytest.mark.parametrize("case", [c[0] for c in _assign_cases()])
@@ -118,6 +126,22 @@ def test_assign_bit_exact(torch, case):
     o.set_centroids(cent)
     got = g.assign(cuda(torch, x)).cpu().numpy()
     np.testing.assert_array_equal(got, o.assign(x))
+
+
+@pytest.mark.parametrize("P", [1, 5, 8])
+def test_probe_sets_bit_exact_d16(torch, P):
+    """d = 16 with heavy ties: P = 1 takes the BF16 tensor-core first stage
+    (FP32 recheck, FP64 near-ties), P > 1 the FP32 first stage."""
+    rng = np.random.default_rng(100 + P)
+    cent = rng.integers(-3, 4, (300, 16)).astype(np.float32)   # heavy ties
+    q = rng.integers(-3, 4, (700, 16)).astype(np.float32)
+    from paper_2601_11808_gb300.sivf import Index
+    g = Index(16, 300, 32, 100, 10)
+    g.set_centroids(cuda(torch, cent))
+    o = oracle.OracleIVF(16, 300, n_max=10, n_slabs=10)
+    o.set_centroids(cent)
+    got = g.probe(cuda(torch, q), P).cpu().numpy()
+    np.testing.assert_array_equal(np.sort(got, axis=1), np.sort(o.probe(q, P), axis=1))
 
 
 @pytest.mark.parametrize("P", [1, 7, 64, 200])
