@@ -253,6 +253,7 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
     // BF16 copy of the centroids for the tensor-core first stage of the
     // coarse selection (d % 16 == 0)
     if (d % 16 == 0 && d <= kMaxD) ALLOC(ix->cent_bf16, (size_t)L * d);
+    if (d % 16 == 0 && d <= 128) ALLOC(ix->cent_lo, (size_t)L * d);
     ALLOC(ix->x32, rows * d);
     if (ix->dtypes & (1u << SIVF_BF16)) ALLOC(ix->xb16, rows * d);
     if (ix->dtypes & (1u << SIVF_FP8E4M3)) ALLOC(ix->x8, rows * d);
@@ -302,7 +303,7 @@ sivf_status sivf_destroy(sivf_index *ix)
 {
     if (!ix) return SIVF_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {ix->cent, ix->cnorm, ix->cnrm_up, ix->cent_bf16, ix->x32, ix->xb16,
+    void *ptrs[] = {ix->cent, ix->cnorm, ix->cnrm_up, ix->cent_bf16, ix->cent_lo, ix->x32, ix->xb16,
                     ix->x8, ix->inv_scale8, ix->xnorm, ix->ids, ix->bits, ix->meta,
                     ix->free_list, ix->free_top, ix->head, ix->nslabs, ix->list_live, ix->dir, ix->att,
                     ix->claim, ix->list_flag, ix->aff_flag, ix->runcnt, ix->err};

@@ -40,7 +40,8 @@ namespace sivf {
 // ------------------------------------------------------------ centroid prep
 __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
                                  float *__restrict__ cn, float *__restrict__ cnrm_up,
-                                 float *__restrict__ inv_scale8, uint16_t *__restrict__ cb)
+                                 float *__restrict__ inv_scale8, uint16_t *__restrict__ cb,
+                                 uint16_t *__restrict__ clo)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L) return;
@@ -57,6 +58,10 @@ __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
         for (int j = 0; j < d; ++j) {
             const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
             cb[(size_t)c * d + j] = *reinterpret_cast<const uint16_t *>(&h);
+            if (clo) {
+                const __nv_bfloat16 l = __float2bfloat16_rn(v[j] - __bfloat162float(h));
+                clo[(size_t)c * d + j] = *reinterpret_cast<const uint16_t *>(&l);
+            }
         }
     if (inv_scale8) inv_scale8[c] = mx > 0.0 ? (float)(448.0 / (2.0 * mx)) : 1.0f;
 }
@@ -393,17 +398,22 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
 }
 
 // ------------------------------------------ BF16 tensor-core first stage
-// out[i][c] = fl(cn[c] - 2 * acc[i][c]), acc = sum_j bf16(x[i][j]) *
-// bf16(cent[c][j]) accumulated in FP32 by tcgen05.mma.  One CTA: 128 rows
-// of x (rounded and swizzled by its threads) against 256 centroids (BF16
-// rows copied with cp.async), K = d (d % 16 == 0, <= 256), accumulator in
-// 256 TMEM columns; four warps read their TMEM lane quarter back.
+// out[i][c] = fl(cn[c] - 2 * acc[i][c]) with, accumulated in FP32 by
+// tcgen05.mma,
+//   SPLIT = 1:  acc = sum_j bf16(x_ij) bf16(c_cj)
+//   SPLIT = 3:  acc = sum_j xh xh' ... the three leading products of
+//               x = xh + xl, c = ch + cl (xh = bf16(x), xl = bf16(x - xh),
+//               likewise c): xh ch + xh cl + xl ch.
+// One CTA: 128 rows of x (rounded, split and swizzled by its threads)
+// against 256 centroids (BF16 rows copied with cp.async), K = d (d % 16 ==
+// 0), accumulator in 256 TMEM columns; four warps read their TMEM lane
+// quarter back.
 constexpr int CT_M = 128, CT_N = 256;
 
-__host__ __device__ inline size_t coarse_tc_smem(int d)
+__host__ __device__ inline size_t coarse_tc_smem(int d, int split)
 {
     const int KC = (d * 2 + 127) / 128;
-    return (size_t)KC * (CT_M + CT_N) * 128 + 1024;
+    return (size_t)(split == 3 ? 2 : 1) * KC * (CT_M + CT_N) * 128 + 1024;
 }
 
 __device__ __forceinline__ void cp_async16_c(void *dst, const void *src, uint32_t src_bytes)
@@ -413,18 +423,21 @@ __device__ __forceinline__ void cp_async16_c(void *dst, const void *src, uint32_
                  : "memory");
 }
 
+template <int SPLIT>
 __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ x, int m, int d,
                                                       const uint16_t *__restrict__ cb,
+                                                      const uint16_t *__restrict__ clo,
                                                       const float *__restrict__ cn, int L,
                                                       float *__restrict__ out, uint32_t *err)
 {
+    constexpr int NP = SPLIT == 3 ? 2 : 1;  // hi (and lo) parts
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int KC = (d * 2 + 127) / 128;
-    unsigned char *A = smem;                          // KC x 128 rows x 128 B
-    unsigned char *B = smem + (size_t)KC * CT_M * 128;  // KC x 256 rows x 128 B
+    unsigned char *A = smem;                                // NP x KC x 128 rows x 128 B
+    unsigned char *B = smem + (size_t)NP * KC * CT_M * 128;  // NP x KC x 256 rows x 128 B
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * CT_M, col0 = blockIdx.y * CT_N;
     const int ncol = min(CT_N, L - col0);
@@ -434,36 +447,46 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
     }
     if (warp == 0) tmem_alloc(&tmem_base, CT_N);
     // B: BF16 centroid rows; chunks past L or d are zero
-    for (int e = tid; e < CT_N * KC * 8; e += 128) {
-        const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
-        const int k0 = kc * 64 + c * 8;  // first element of the 16-byte chunk
-        const bool in = col0 + r < L && k0 < d;
-        cp_async16_c(B + (size_t)kc * CT_N * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
-                         ((c ^ (r & 7)) << 4),
-                     in ? (const void *)(cb + (size_t)(col0 + r) * d + k0) : (const void *)cb,
-                     in ? 16u : 0u);
+    for (int pp = 0; pp < NP; ++pp) {
+        const uint16_t *src0 = pp ? clo : cb;
+        unsigned char *Bp = B + (size_t)pp * KC * CT_N * 128;
+        for (int e = tid; e < CT_N * KC * 8; e += 128) {
+            const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
+            const int k0 = kc * 64 + c * 8;  // first element of the 16-byte chunk
+            const bool in = col0 + r < L && k0 < d;
+            cp_async16_c(Bp + (size_t)kc * CT_N * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                             ((c ^ (r & 7)) << 4),
+                         in ? (const void *)(src0 + (size_t)(col0 + r) * d + k0) : (const void *)src0,
+                         in ? 16u : 0u);
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // A: rows of x rounded to BF16 (round to nearest even); zero past m or d
     for (int e = tid; e < CT_M * KC * 8; e += 128) {
         const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
         const int k0 = kc * 64 + c * 8;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        uint32_t w[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
         if (row0 + r < m && k0 < d) {
             const float4 *xr = reinterpret_cast<const float4 *>(x + (size_t)(row0 + r) * d + k0);
             const float4 f0 = __ldg(xr), f1 = __ldg(xr + 1);
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(f0.x, f0.y);
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(f0.z, f0.w);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(f1.x, f1.y);
-            __nv_bfloat162 h3 = __floats2bfloat162_rn(f1.z, f1.w);
-            w[0] = *reinterpret_cast<uint32_t *>(&h0);
-            w[1] = *reinterpret_cast<uint32_t *>(&h1);
-            w[2] = *reinterpret_cast<uint32_t *>(&h2);
-            w[3] = *reinterpret_cast<uint32_t *>(&h3);
+            const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * t], f[2 * t + 1]);
+                w[t] = *reinterpret_cast<uint32_t *>(&h);
+                if (NP == 2) {
+                    __nv_bfloat162 l = __floats2bfloat162_rn(f[2 * t] - __low2float(h),
+                                                             f[2 * t + 1] - __high2float(h));
+                    wl[t] = *reinterpret_cast<uint32_t *>(&l);
+                }
+            }
         }
-        *reinterpret_cast<uint4 *>(A + (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 +
-                                   (r & 7) * 128 + ((c ^ (r & 7)) << 4)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        const size_t off = (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                           ((c ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4 *>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (NP == 2)
+            *reinterpret_cast<uint4 *>(A + (size_t)KC * CT_M * 128 + off) =
+                make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     fence_proxy_async_smem();
@@ -473,13 +496,19 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
     const uint32_t tbase = tmem_base;
     if (tid == 0) {
         const uint32_t idesc = mma_idesc(1, 1, CT_M, CT_N);
-        const uint32_t abase = smem_u32(A), bbase = smem_u32(B);
-        for (int kc = 0; kc < KC; ++kc)
+        // products: (x hi, c hi), then for the split (x hi, c lo), (x lo, c hi)
+        constexpr int NPROD = SPLIT == 3 ? 3 : 1;
+        for (int pr = 0; pr < NPROD; ++pr) {
+            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+            const uint32_t abase = smem_u32(A + (size_t)pa * KC * CT_M * 128);
+            const uint32_t bbase = smem_u32(B + (size_t)pb * KC * CT_N * 128);
+            for (int kc = 0; kc < KC; ++kc)
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-                mma_bf16(tbase, smem_desc_sw128(abase + kc * CT_M * 128 + ks * 32, 1024),
-                         smem_desc_sw128(bbase + kc * CT_N * 128 + ks * 32, 1024), idesc,
-                         (kc | ks) != 0);
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_bf16(tbase, smem_desc_sw128(abase + kc * CT_M * 128 + ks * 32, 1024),
+                             smem_desc_sw128(bbase + kc * CT_N * 128 + ks * 32, 1024), idesc,
+                             (pr | kc | ks) != 0);
+        }
         mma_commit(&bar);
     }
     __syncwarp();
@@ -805,7 +834,8 @@ void centroid_prep(sivf_index *ix, cudaStream_t st)
 {
     ix->launches += 1;
     k_centroid_norms<<<(ix->nlist + 127) / 128, 128, 0, st>>>(
-        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16);
+        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16,
+        ix->cent_lo);
 }
 
 // rows [0, m) of x -> out[m, P]; `Dbuf` holds at least rows_per_chunk * L
@@ -816,29 +846,45 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
     const int L = ix->nlist, d = ix->d;
     const double u = 5.9604644775390625e-08;
     const double gd = d * u / (1.0 - d * u);
-    // BF16 first stage: rounding of x and c (2 ub + ub^2 relative, ub =
-    // 2^-8) and the FP32 accumulation of the exact BF16 products (taken as
-    // d * 2^-20 relative, several ulps per addition)
-    const double ub = 1.0 / 256.0, gacc = d * std::ldexp(1.0, -20);
-    // The BF16 bound is a few percent of ||x|| ||c||: tight enough to isolate
-    // the nearest centroid (assignment, P = 1) but not to separate the P-th
-    // from the (P+1)-th of a dense shell of far centroids, so probe selection
-    // keeps the FP32 first stage
-    const bool two = ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD;
+    // The single BF16 product is within a few percent of ||x|| ||c||: tight
+    // enough to isolate the nearest centroid (assignment, P = 1) but not to
+    // separate the P-th from the (P+1)-th of a dense shell of far centroids;
+    // probe selection takes the split form (three products, ~1e-4 of
+    // ||x|| ||c||), which needs twice the shared memory (d <= 128)
+    const int split = (ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD) ? 1
+                      : (ix->cent_lo && P > 1 && P <= CW_PMAX && d % 16 == 0 && d <= 128) ? 3
+                                                                                           : 0;
+    const bool two = split != 0;
+    // BF16 first stage: unit roundoff of BF16 ub = 2^-8; the FP32
+    // accumulation of the exact BF16 products is taken as up to two ulps per
+    // addition, over d (single) or 3 d (split) terms
+    const double ub = 1.0 / 256.0;
+    const double gacc = (split == 3 ? 3.0 * d : (double)d) * std::ldexp(1.0, -22);
     for (int64_t r0 = 0; r0 < m; r0 += rows_per_chunk) {
         int mc = (int)std::min<int64_t>(rows_per_chunk, m - r0);
         const int tok = prof_begin(ix, PROF_COARSE, 2, st);
         if (two) {
-            const size_t smem = coarse_tc_smem(d);
-            static size_t attr = 0;
-            if (smem > attr) {
-                cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-                attr = smem;
-            }
+            const size_t smem = coarse_tc_smem(d, split);
             dim3 g((mc + CT_M - 1) / CT_M, (L + CT_N - 1) / CT_N);
-            k_coarse_tc<<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cnorm, L,
-                                               Dbuf, ix->err);
+            if (split == 1) {
+                static size_t attr = 0;
+                if (smem > attr) {
+                    cudaFuncSetAttribute(k_coarse_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                    attr = smem;
+                }
+                k_coarse_tc<1><<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, nullptr,
+                                                      ix->cnorm, L, Dbuf, ix->err);
+            } else {
+                static size_t attr = 0;
+                if (smem > attr) {
+                    cudaFuncSetAttribute(k_coarse_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                    attr = smem;
+                }
+                k_coarse_tc<3><<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cent_lo,
+                                                      ix->cnorm, L, Dbuf, ix->err);
+            }
         } else {
             dim3 g((L + GBN - 1) / GBN, (mc + GBM - 1) / GBM);
             k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
@@ -854,7 +900,13 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.cn = ix->cnorm;
         a.cnrm_up = ix->cnrm_up;
         a.gamma2 = (float)(2.0 * gd * (1.0 + 1e-6));
-        a.gamma2_first = (float)(2.0 * ((2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub)) * (1.0 + 1e-6));
+        // |acc - x.c| / (||x|| ||c||): single: 2 ub + ub^2 (both roundings)
+        // plus the accumulation; split: the dropped products xl cl, and the
+        // roundings of xl and cl (each ub^2 relative), 3.1 ub^2 in all, plus
+        // the accumulation
+        const double rel = split == 3 ? 3.1 * ub * ub + gacc * (1 + 2 * ub)
+                                      : (2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub);
+        a.gamma2_first = (float)(2.0 * rel * (1.0 + 1e-6));
         a.two_level = two;
         a.out = out + r0 * P;
         a.err = ix->err;

@@ -102,7 +102,8 @@ struct sivf_index {
     float *cent;                   // [nlist, d]
     float *cnorm;                  // [nlist] fl32(||c||^2), from an FP64 sum
     float *cnrm_up;                // [nlist] upper bound of ||c||
-    uint16_t *cent_bf16;           // [nlist, d] bf16 copy (tensor-core path)
+    uint16_t *cent_bf16;           // [nlist, d] bf16(c) (tensor-core coarse stage)
+    uint16_t *cent_lo;             // [nlist, d] bf16(c - bf16(c)) (split stage)
 
     // slab pool (Sec. 3.1)
     float *x32;                    // [S, C, d] FP32 payload
