@@ -315,105 +315,82 @@ __device__ float warp_select_keep(float *bd, int32_t *bs, int K, int nb, int nc,
     return dmax;
 }
 
-// Register form of warp_select_keep for nb + nc <= 32 * EK: every key is
-// read once into registers, the radix passes count from registers, and the
-// kept entries are written back from the keys (distance and slot both live
-// in the key), so no entry is re-read from shared memory.
+// Binary-search form of warp_select_keep for nb + nc <= 32 * EK: the 32-bit
+// distance keys and the slots live in registers; the K-th smallest key is
+// found by bisection on the key value, each step one compare and one ballot
+// per register (no shared memory); distance ties at the K-th
+// place keep the lowest slots (a second bisection on the slot).  The kept
+// entries are written back from registers.
 template <int EK>
-__device__ float warp_select_keep_reg(float *bd, int32_t *bs, int K, int nb, int nc,
-                                      uint32_t *hist, int lane)
+__device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int nc, int lane)
 {
     const int n = nb + nc;
-    uint64_t key[EK];
+    uint32_t key[EK];
+    int32_t slt[EK];
 #pragma unroll
     for (int e = 0; e < EK; ++e) {
         const int i = lane + 32 * e;
         const int ai = i < nb ? i : K + (i - nb);
-        key[e] = i < n ? ds_key(bd[ai], bs[ai]) : ~0ull;
+        key[e] = i < n ? fkey(bd[ai]) : 0xffffffffu;
+        slt[e] = i < n ? bs[ai] : 0x7fffffff;
     }
-    uint64_t kmin = ~0ull, kmax = 0ull;
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
     for (int e = 0; e < EK; ++e)
-        if (key[e] != ~0ull) {
+        if (key[e] != 0xffffffffu) {
             kmin = min(kmin, key[e]);
             kmax = max(kmax, key[e]);
         }
-    for (int o = 16; o > 0; o >>= 1) {
-        kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmin, o));
-        kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmax, o));
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    uint32_t lo = kmin, hi = kmax;  // smallest v with #(key <= v) >= K
+    while (lo < hi) {  // counts by independent ballots (every lane gets them)
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        uint32_t c = 0;
+#pragma unroll
+        for (int e = 0; e < EK; ++e) c += __popc(__ballot_sync(0xffffffffu, key[e] <= mid));
+        if (c >= (uint32_t)K) hi = mid;
+        else lo = mid + 1;
     }
-    const uint64_t diff = kmin ^ kmax;
-    const int top = diff ? 63 - __clzll((long long)diff) : 0;
-    uint64_t mask = top >= 63 ? 0ull : ~((2ull << top) - 1ull);
-    uint64_t prefix = kmin & mask;
-    uint32_t need = (uint32_t)K;
-    for (int hi = top; hi >= 0; hi -= 8) {
-        const int shift = max(hi - 7, 0);
-        const uint32_t bmask = (1u << (hi - shift + 1)) - 1u;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
-        __syncwarp();
-#pragma unroll
-        for (int e = 0; e < EK; ++e)
-            if (key[e] != ~0ull && (key[e] & mask) == prefix)
-                atomicAdd(&hist[(uint32_t)(key[e] >> shift) & bmask], 1u);
-        __syncwarp();
-        uint32_t loc[8], sum = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            loc[b] = hist[lane * 8 + b];
-            sum += loc[b];
-        }
-        uint32_t incl = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint32_t excl = incl - sum;
-        const bool mine = excl < need && incl >= need;
-        uint32_t bin = 0, below = 0, cnt = 0;
-        if (mine) {
-            uint32_t cum = excl;
-            for (int b = 0; b < 8; ++b) {
-                if (cum + loc[b] >= need) {
-                    bin = (uint32_t)(lane * 8 + b);
-                    below = cum;
-                    cnt = loc[b];
-                    break;
-                }
-                cum += loc[b];
-            }
-        }
-        const uint32_t who = __ballot_sync(0xffffffffu, mine);
-        const int src = who ? __ffs(who) - 1 : 0;
-        bin = __shfl_sync(0xffffffffu, bin, src);
-        below = __shfl_sync(0xffffffffu, below, src);
-        cnt = __shfl_sync(0xffffffffu, cnt, src);
-        prefix |= (uint64_t)bin << shift;
-        mask |= (uint64_t)bmask << shift;
-        need -= below;
-        __syncwarp();
-        if (cnt == need) break;
-    }
-    // every key is in registers: write the K kept entries to [0, K)
-    int w = 0;
-    float dmax = -INFINITY;
+    const uint32_t kth = lo;
+    uint32_t clt = 0, ceq = 0;
 #pragma unroll
     for (int e = 0; e < EK; ++e) {
-        const bool take = key[e] != ~0ull && (key[e] & mask) <= prefix;
+        clt += key[e] < kth;
+        ceq += key[e] == kth;
+    }
+    clt = __reduce_add_sync(0xffffffffu, clt);
+    ceq = __reduce_add_sync(0xffffffffu, ceq);
+    const uint32_t need = (uint32_t)K - clt;  // 1 <= need <= ceq
+    int32_t cut = 0x7fffffff;                 // tied entries kept: slot <= cut
+    if (ceq > need) {
+        int32_t slo = 0, shi = 0x7fffffff;
+        while (slo < shi) {
+            const int32_t mid = slo + ((shi - slo) >> 1);
+            uint32_t c = 0;
+#pragma unroll
+            for (int e = 0; e < EK; ++e)
+                c += __popc(__ballot_sync(0xffffffffu, key[e] == kth && slt[e] <= mid));
+            if (c >= need) shi = mid;
+            else slo = mid + 1;
+        }
+        cut = slo;
+    }
+    __syncwarp();  // every lane has read its entries before any is written
+    int w = 0;
+#pragma unroll
+    for (int e = 0; e < EK; ++e) {
+        const bool take = key[e] < kth || (key[e] == kth && slt[e] <= cut);
         const uint32_t mk = __ballot_sync(0xffffffffu, take);
         if (take) {
             const int p = w + __popc(mk & lanemask_lt());
-            const float dv = fkey_inv((uint32_t)(key[e] >> 32));
-            bd[p] = dv;
-            bs[p] = (int32_t)(uint32_t)key[e];
-            dmax = fmaxf(dmax, dv);
+            bd[p] = fkey_inv(key[e]);
+            bs[p] = slt[e];
         }
         w += __popc(mk);
     }
     __syncwarp();
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    return dmax;
+    return fkey_inv(kth);
 }
 
 // Fold the nc pending candidates of one row into its best set: keep the
@@ -424,10 +401,10 @@ __device__ __forceinline__ float fold_row(float *bd, int32_t *bs, int K, int &nb
 {
     if (nb + nc > K) {
         const int n = nb + nc;
-        const float kd = n <= 64    ? warp_select_keep_reg<2>(bd, bs, K, nb, nc, hist, lane)
-                         : n <= 128 ? warp_select_keep_reg<4>(bd, bs, K, nb, nc, hist, lane)
-                         : n <= 192 ? warp_select_keep_reg<6>(bd, bs, K, nb, nc, hist, lane)
-                         : n <= 320 ? warp_select_keep_reg<10>(bd, bs, K, nb, nc, hist, lane)
+        const float kd = n <= 64    ? warp_select_keep_bs<2>(bd, bs, K, nb, nc, lane)
+                         : n <= 128 ? warp_select_keep_bs<4>(bd, bs, K, nb, nc, lane)
+                         : n <= 192 ? warp_select_keep_bs<6>(bd, bs, K, nb, nc, lane)
+                         : n <= 320 ? warp_select_keep_bs<10>(bd, bs, K, nb, nc, lane)
                                     : warp_select_keep(bd, bs, K, nb, nc, hist, lane);
         nb = K;
         return kd;
