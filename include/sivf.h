@@ -112,6 +112,34 @@ sivf_status sivf_destroy(sivf_index *index);
 sivf_status sivf_set_centroids(sivf_index *index, const float *c, void *stream);
 
 /*
+ * sivf_train -- train the coarse quantizer by Lloyd's k-means and install
+ * it as sivf_set_centroids does.  The paper uses a trained Faiss quantizer
+ * and does not describe training (Sec. 4.1); this is the plain reading.
+ *   x [device] float32[n, d] training rows, nlist <= n <= 2^31 - 1;
+ *   iters >= 0 Lloyd iterations; seed picks the initial centroids.
+ * Initial centroids: the training rows r_t = (t-th SplitMix64 output from
+ * state `seed`) mod n, in draw order, rows already taken skipped, until
+ * nlist rows are taken (SplitMix64: Steele, Lea and Flood, OOPSLA 2014).
+ * One iteration: every row goes to its nearest centroid (exactly as
+ * sivf_assign: FP64 definition, ties to the lowest index); every centroid
+ * with at least one row becomes the FP32 rounding of the FP64 mean of its
+ * rows; a centroid with no rows keeps its value.  The FP64 sums are
+ * accumulated with device atomics, so their last bits may depend on the
+ * order of the additions; the FP32 result is the same unless a mean lies
+ * within an FP64 rounding of an FP32 rounding boundary.
+ * The index must be empty (SIVF_E_STATE); synchronizes `stream` at entry.
+ */
+sivf_status sivf_train(sivf_index *index, const float *x, int64_t n, int iters,
+                       uint64_t seed, void *stream);
+
+/*
+ * sivf_get_centroids -- copy the current coarse quantizer (as loaded by
+ * sivf_set_centroids or produced by sivf_train) to `c` [device]
+ * float32[nlist, d].  SIVF_E_STATE before any centroids exist.
+ */
+sivf_status sivf_get_centroids(sivf_index *index, float *c, void *stream);
+
+/*
  * sivf_set_list_scales -- per-list FP8 E4M3 inverse scales: list l stores
  * code(fl32(x_j * inv_scale[l])) and decodes x_j ~ code / inv_scale[l].
  * `inv_scale` [device] is [nlist] float32, each finite and > 0.  Must be

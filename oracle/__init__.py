@@ -70,6 +70,9 @@ def load_lib(path: str):
         "oivf_from_e4m3": (None, [p, p, i64]),
         "oivf_num_threads": (i32, [i32]),
         "oivf_dists": (None, [p, p, i64, i32, p]),
+        "oivf_splitmix64": (None, [C.c_uint64, i64, p]),
+        "oivf_kmeans_init_rows": (i32, [i64, i32, C.c_uint64, p]),
+        "oivf_kmeans": (i32, [p, i64, i32, i32, i32, C.c_uint64, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -292,3 +295,31 @@ def from_e4m3(c) -> np.ndarray:
     out = np.zeros(c.shape, np.float64)
     _load().oivf_from_e4m3(_ptr(c), _ptr(out), c.size)
     return out
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """The first n outputs of SplitMix64 from state `seed` (uint64)."""
+    out = np.empty(n, np.uint64)
+    _load().oivf_splitmix64(C.c_uint64(seed), n, _ptr(out))
+    return out
+
+
+def kmeans_init_rows(n: int, nlist: int, seed: int) -> np.ndarray:
+    """The nlist distinct training rows the k-means starts from."""
+    rows = np.empty(nlist, np.int64)
+    if _load().oivf_kmeans_init_rows(n, nlist, C.c_uint64(seed), _ptr(rows)):
+        raise OracleError(E_ARG)
+    return rows
+
+
+def kmeans(x, nlist: int, iters: int, seed: int):
+    """Lloyd's k-means (the reading documented in sivf_oracle.c): returns
+    (centroids float32 [nlist, d], final assignment int32 [n])."""
+    x = _f32(x)
+    n, d = x.shape
+    cent = np.empty((nlist, d), np.float32)
+    lab = np.empty(n, np.int32)
+    st = _load().oivf_kmeans(_ptr(x), n, d, nlist, iters, C.c_uint64(seed), _ptr(cent), _ptr(lab))
+    if st:
+        raise OracleError(st)
+    return cent, lab

@@ -621,3 +621,116 @@ void oivf_to_e4m3(const float *in, float inv_scale, uint8_t *out, int64_t n)
         out[i] = (uint8_t)(sign | best);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* coarse quantizer training                                            */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper takes its coarse quantizer from Faiss and does not describe
+ * training (Sec. 4.1).  The reading used here is Lloyd's k-means:
+ *   - initial centroids: nlist distinct training rows.  Row r_t is the t-th
+ *     output of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+ *     pseudorandom number generators", OOPSLA 2014) from the state `seed`,
+ *     reduced mod n; a row already taken is skipped;
+ *   - one iteration: every row goes to its nearest centroid (the FP64
+ *     definition of the coarse quantizer above, ties to the lowest index);
+ *     every centroid with at least one row becomes the FP32 rounding of the
+ *     FP64 mean of its rows, summed in row order; a centroid with no rows
+ *     keeps its value.
+ */
+
+/* SplitMix64: the state advances by the golden-ratio increment; the output
+ * is the state passed through two xor-shift-multiply rounds and a final
+ * xor-shift. */
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void oivf_splitmix64(uint64_t seed, int64_t n, uint64_t *out)
+{
+    uint64_t s = seed;
+    for (int64_t i = 0; i < n; ++i) out[i] = splitmix64_next(&s);
+}
+
+/* nearest of `nlist` centroids `c` to x; ties to the lowest index */
+static int32_t nearest_of(const float *c, int nlist, int d, const float *x)
+{
+    int32_t best = 0;
+    double bd = sqdist(x, c, d);
+    for (int k = 1; k < nlist; ++k) {
+        double dk = sqdist(x, c + (size_t)k * d, d);
+        if (dk < bd) {
+            bd = dk;
+            best = k;
+        }
+    }
+    return best;
+}
+
+/* the initial rows; returns -1 when fewer than nlist distinct rows exist */
+int oivf_kmeans_init_rows(int64_t n, int nlist, uint64_t seed, int64_t *rows)
+{
+    if (n < nlist) return -1;
+    unsigned char *taken = calloc((size_t)n, 1);
+    if (!taken) return -1;
+    uint64_t s = seed;
+    int k = 0;
+    while (k < nlist) {
+        int64_t r = (int64_t)(splitmix64_next(&s) % (uint64_t)n);
+        if (taken[r]) continue;
+        taken[r] = 1;
+        rows[k++] = r;
+    }
+    free(taken);
+    return 0;
+}
+
+/* Lloyd's k-means as above; cent (nlist x d) receives the result; lab (n)
+ * the assignment to the final centroids (may be NULL).  Returns O_OK or
+ * O_E_ARG. */
+int oivf_kmeans(const float *x, int64_t n, int d, int nlist, int iters, uint64_t seed,
+                float *cent, int32_t *lab_out)
+{
+    if (n < nlist || nlist < 1 || d < 1 || iters < 0) return O_E_ARG;
+    int64_t *rows = malloc(sizeof(int64_t) * (size_t)nlist);
+    int32_t *lab = malloc(sizeof(int32_t) * (size_t)n);
+    double *sum = malloc(sizeof(double) * (size_t)nlist * d);
+    int64_t *cnt = malloc(sizeof(int64_t) * (size_t)nlist);
+    if (!rows || !lab || !sum || !cnt || oivf_kmeans_init_rows(n, nlist, seed, rows)) {
+        free(rows);
+        free(lab);
+        free(sum);
+        free(cnt);
+        return O_E_ARG;
+    }
+    for (int k = 0; k < nlist; ++k)
+        memcpy(cent + (size_t)k * d, x + (size_t)rows[k] * d, sizeof(float) * (size_t)d);
+    for (int it = 0; it < iters; ++it) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) lab[i] = nearest_of(cent, nlist, d, x + (size_t)i * d);
+        memset(sum, 0, sizeof(double) * (size_t)nlist * d);
+        memset(cnt, 0, sizeof(int64_t) * (size_t)nlist);
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t k = lab[i];
+            ++cnt[k];
+            for (int j = 0; j < d; ++j) sum[(size_t)k * d + j] += (double)x[(size_t)i * d + j];
+        }
+        for (int k = 0; k < nlist; ++k)
+            if (cnt[k] > 0)
+                for (int j = 0; j < d; ++j)
+                    cent[(size_t)k * d + j] = (float)(sum[(size_t)k * d + j] / (double)cnt[k]);
+    }
+    if (lab_out) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) lab_out[i] = nearest_of(cent, nlist, d, x + (size_t)i * d);
+    }
+    free(rows);
+    free(lab);
+    free(sum);
+    free(cnt);
+    return O_OK;
+}

@@ -347,6 +347,78 @@ sivf_status sivf_set_centroids(sivf_index *ix, const float *c, void *stream)
     return SIVF_OK;
 }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the state advances by the
+// golden-ratio increment; the output is that state through two
+// xor-shift-multiply rounds and a final xor-shift
+static uint64_t splitmix64_next(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+sivf_status sivf_train(sivf_index *ix, const float *x, int64_t n, int iters, uint64_t seed,
+                       void *stream)
+{
+    if (!ix) return SIVF_E_ARG;
+    if (!x || n < ix->nlist || n > INT32_MAX || iters < 0)
+        return fail(ix, SIVF_E_ARG, "bad train arguments (need nlist <= n, iters >= 0)");
+    sivf_status st = check_health(ix);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(ix, cudaStreamSynchronize(s));
+    int64_t live = 0;
+    if ((st = live_count(ix, &live))) return st;
+    if (live) return fail(ix, SIVF_E_STATE, "train on a non-empty index");
+    const int L = ix->nlist, d = ix->d;
+    // initial centroids: SplitMix64 outputs mod n in draw order, repeats skipped
+    std::vector<int64_t> rows;
+    rows.reserve(L);
+    {
+        std::vector<unsigned char> taken((size_t)n, 0);
+        uint64_t state = seed;
+        while ((int)rows.size() < L) {
+            const int64_t r = (int64_t)(splitmix64_next(state) % (uint64_t)n);
+            if (taken[(size_t)r]) continue;
+            taken[(size_t)r] = 1;
+            rows.push_back(r);
+        }
+    }
+    const int64_t crows = coarse_rows(ix, n);
+    const size_t need = coarse_bytes(ix, n) + (size_t)n * 4 + (size_t)L * d * 8 + (size_t)L * 4 +
+                        (size_t)L * 8 + 5 * 256;
+    Ctx *c;
+    if ((st = get_ctx(ix, stream, need, &c))) return st;
+    Bump b{c->scratch};
+    int32_t *lab = b.take<int32_t>((size_t)n);
+    float *Dbuf = b.take<float>((size_t)crows * L);
+    double *sum = b.take<double>((size_t)L * d);
+    int32_t *cnt = b.take<int32_t>((size_t)L);
+    int64_t *rows_dev = b.take<int64_t>((size_t)L);
+    CUDA_TRY(ix, cudaMemcpy(rows_dev, rows.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice));
+    CUDA_TRY(ix, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));
+    train_gather(ix, x, rows_dev, s);
+    centroid_prep(ix, s);
+    for (int it = 0; it < iters; ++it) {
+        coarse_topP(ix, x, n, 1, lab, Dbuf, crows, s);
+        train_step(ix, x, n, lab, sum, cnt, s);
+        centroid_prep(ix, s);
+    }
+    CUDA_TRY(ix, cudaGetLastError());
+    ix->have_centroids = true;
+    return SIVF_OK;
+}
+
+sivf_status sivf_get_centroids(sivf_index *ix, float *c, void *stream)
+{
+    if (!ix || !c) return fail(ix, SIVF_E_ARG, "null argument");
+    if (!ix->have_centroids) return fail(ix, SIVF_E_STATE, "no centroids yet");
+    CUDA_TRY(ix, cudaMemcpyAsync(c, ix->cent, sizeof(float) * ix->nlist * ix->d,
+                                 cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SIVF_OK;
+}
+
 sivf_status sivf_set_list_scales(sivf_index *ix, const float *inv_scale, void *stream)
 {
     if (!ix || !inv_scale) return fail(ix, SIVF_E_ARG, "null argument");

@@ -555,6 +555,7 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
 constexpr int CW_ROWS = 4;     // rows (warps) per block
 constexpr int CW_PMAX = 8;
 constexpr int CW_SCAP = 128;
+constexpr int CW_LMAX = 4096;  // most lists for one warp per row
 
 __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 {
@@ -851,9 +852,13 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
     // separate the P-th from the (P+1)-th of a dense shell of far centroids;
     // probe selection takes the split form (three products, ~1e-4 of
     // ||x|| ||c||), which needs twice the shared memory (d <= 128)
-    const int split = (ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD) ? 1
-                      : (ix->cent_lo && P > 1 && P <= CW_PMAX && d % 16 == 0 && d <= 128) ? 3
-                                                                                           : 0;
+    // one warp per row suits up to a few thousand lists; beyond, the block
+    // kernel (256 threads per row) selects, from the FP32 first stage
+    const bool warp_rows = P <= CW_PMAX && L <= CW_LMAX;
+    const int split = !warp_rows ? 0
+                      : (ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD) ? 1
+                      : (ix->cent_lo && P > 1 && d % 16 == 0 && d <= 128)      ? 3
+                                                                                : 0;
     const bool two = split != 0;
     // BF16 first stage: unit roundoff of BF16 ub = 2^-8; the FP32
     // accumulation of the exact BF16 products is taken as up to two ulps per
@@ -910,7 +915,7 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.two_level = two;
         a.out = out + r0 * P;
         a.err = ix->err;
-        if (P <= CW_PMAX)
+        if (warp_rows)
             k_coarse_select_w<<<(unsigned)((mc + CW_ROWS - 1) / CW_ROWS), CW_ROWS * 32, 0, st>>>(a);
         else
             k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);

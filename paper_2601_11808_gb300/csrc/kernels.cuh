@@ -16,6 +16,14 @@ void centroid_prep(sivf_index *ix, cudaStream_t st);
 void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                  float *Dbuf, int64_t rows_per_chunk, cudaStream_t st);
 
+// ---- quantizer training (train.cu)
+// centroids := the given training rows (device, nlist of them)
+void train_gather(sivf_index *ix, const float *x, const int64_t *rows, cudaStream_t st);
+// one Lloyd update from the labels of the n rows: FP64 sums and counts
+// (scratch), then centroids := FP32(mean); empty centroids keep their value
+void train_step(sivf_index *ix, const float *x, int64_t n, const int32_t *lab, double *sum,
+                int32_t *cnt, cudaStream_t st);
+
 // ---- insert / delete (mutate.cu)
 struct InsertScratch {
     int32_t *lab;        // [n] list of each vector

@@ -27,6 +27,7 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 # every symbol include/sivf.h declares
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
+    "sivf_train", "sivf_get_centroids",
     "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
     "sivf_search_with_probes", "sivf_search_noalloc", "sivf_search_candidates",
     "sivf_assign", "sivf_probe", "sivf_sync",
@@ -121,6 +122,8 @@ def load(path: str | None = None):
             "sivf_create": (i32, [C.POINTER(sivf_config), C.POINTER(vp)]),
             "sivf_destroy": (i32, [vp]),
             "sivf_set_centroids": (i32, [vp, vp, vp]),
+            "sivf_train": (i32, [vp, vp, i64, i32, C.c_uint64, vp]),
+            "sivf_get_centroids": (i32, [vp, vp, vp]),
             "sivf_set_list_scales": (i32, [vp, vp, vp]),
             "sivf_reserve": (i32, [vp, i64, i64, i64, i32, i32, vp]),
             "sivf_add": (i32, [vp, vp, vp, i64, vp, C.POINTER(i64)]),
@@ -222,6 +225,20 @@ def sivf_set_centroids(h, c, stream=None) -> None:
     import torch
     lib = load()
     _check(lib, h, lib.sivf_set_centroids(h, _ptr(_dev(c, torch.float32)), _stream(stream)))
+
+
+def sivf_train(h, x, iters: int, seed: int, stream=None) -> None:
+    import torch
+    lib = load()
+    xx = _dev(x, torch.float32)
+    _check(lib, h, lib.sivf_train(h, _ptr(xx), xx.shape[0], iters, C.c_uint64(seed),
+                                  _stream(stream)))
+
+
+def sivf_get_centroids(h, out, stream=None) -> None:
+    import torch
+    lib = load()
+    _check(lib, h, lib.sivf_get_centroids(h, _ptr(_dev(out, torch.float32)), _stream(stream)))
 
 
 def sivf_set_list_scales(h, inv_scale, stream=None) -> None:
@@ -643,6 +660,17 @@ class Index:
 
     def set_list_scales(self, inv_scale, stream=None):
         sivf_set_list_scales(self.h, inv_scale, stream)
+
+    def train(self, x, iters: int, seed: int = 0, stream=None):
+        """Lloyd's k-means on the device rows x; installs the centroids."""
+        sivf_train(self.h, x, iters, seed, stream)
+
+    def centroids(self, stream=None):
+        """The current centroids as a new [nlist, d] float32 CUDA tensor."""
+        import torch
+        out = torch.empty((self.nlist, self.d), dtype=torch.float32, device="cuda")
+        sivf_get_centroids(self.h, out, stream)
+        return out
 
     def reserve(self, max_add=0, max_remove=0, max_queries=0, max_k=0, max_nprobe=0,
                 stream=None):

@@ -9,10 +9,14 @@ them; ``test_oracle_mutants.py`` plants such mistakes to show it.
 """
 from fractions import Fraction
 
+import os
+
 import numpy as np
 import pytest
 
 import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 from oracle import OracleIVF, OracleError
 
 
@@ -426,3 +430,92 @@ def test_e4m3_decode_all_codes_matches_torch():
     want = torch.from_numpy(codes).view(torch.float8_e4m3fn).double().numpy()
     np.testing.assert_array_equal(got, want)
     assert got.max() == 448.0 and got[got > 0].min() == 2.0 ** -9
+
+
+# ------------------------------------------------------ quantizer training
+def _golden_splitmix():
+    out = {}
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        seed, vals = line.split(":")
+        out[int(seed)] = [int(v) for v in vals.split()]
+    return out
+
+
+def test_splitmix64_matches_published_outputs():
+    for seed, vals in _golden_splitmix().items():
+        np.testing.assert_array_equal(oracle.splitmix64(seed, len(vals)),
+                                      np.array(vals, dtype=np.uint64))
+
+
+def test_kmeans_init_rows_follow_the_generator():
+    """Initial rows = SplitMix64 outputs mod n in draw order, repeats
+    skipped (checked against the published outputs)."""
+    vals = _golden_splitmix()[1234567]
+    n = 7
+    want = []
+    for v in vals:
+        if v % n not in want:
+            want.append(v % n)
+    rows = oracle.kmeans_init_rows(n, len(want), 1234567)
+    np.testing.assert_array_equal(rows, want)
+    assert len(set(oracle.kmeans_init_rows(1000, 500, 9).tolist())) == 500
+
+
+def _two_blobs(rng):
+    a = rng.integers(-3, 4, (50, 6)) - 100
+    b = rng.integers(-3, 4, (70, 6)) + 100
+    return np.concatenate([a, b]).astype(np.float32)
+
+
+def test_kmeans_one_step_is_the_blob_means():
+    """Two well-separated integer blobs, initial rows in different blobs:
+    one Lloyd step gives the FP32 rounding of each blob's mean."""
+    x = _two_blobs(np.random.default_rng(3))
+    seed = next(s for s in range(100)
+                if len({int(r >= 50) for r in oracle.kmeans_init_rows(len(x), 2, s)}) == 2)
+    cent, lab = oracle.kmeans(x, 2, 1, seed)
+    first = int(oracle.kmeans_init_rows(len(x), 2, seed)[0] >= 50)
+    means = [x[:50].astype(np.float64).mean(0), x[50:].astype(np.float64).mean(0)]
+    np.testing.assert_array_equal(cent[0], means[first].astype(np.float32))
+    np.testing.assert_array_equal(cent[1], means[1 - first].astype(np.float32))
+    assert (lab == np.where(np.arange(len(x)) < 50, first, 1 - first)).all()
+
+
+def test_kmeans_empty_cell_keeps_its_centroid():
+    """98 copies of A and 2 of B; when both initial rows are copies of A the
+    two centroids tie, every row goes to the lower index, and the other
+    centroid keeps its value A."""
+    A = np.arange(4, dtype=np.float32)
+    B = A + 8
+    x = np.stack([A] * 98 + [B] * 2)
+    seed = next(s for s in range(1000) if (oracle.kmeans_init_rows(100, 2, s) < 98).all())
+    cent, lab = oracle.kmeans(x, 2, 1, seed)
+    np.testing.assert_array_equal(cent[1], A)
+    np.testing.assert_array_equal(cent[0], ((98 * A.astype(np.float64) + 2 * B) / 100).astype(np.float32))
+    # final assignment: A lies on centroid 1, B is nearer the shifted centroid 0
+    assert (lab[:98] == 1).all() and (lab[98:] == 0).all()
+
+
+def _objective(x, cent):
+    d = np.stack([oracle.dists(c, x) for c in cent])   # FP64 distances
+    return d.min(axis=0).sum()
+
+
+def test_kmeans_objective_never_increases_and_fixed_point():
+    rng = np.random.default_rng(11)
+    ctr = rng.uniform(-1, 1, (12, 8))
+    x = (ctr[rng.integers(0, 12, 3000)] + 0.2 * rng.standard_normal((3000, 8))).astype(np.float32)
+    js = [_objective(x, oracle.kmeans(x, 12, it, 5)[0]) for it in range(0, 8)]
+    assert all(js[i + 1] <= js[i] * (1 + 1e-12) for i in range(len(js) - 1)), js
+    # converged: another step changes nothing, and each centroid is the
+    # FP32 mean of its rows
+    c1, lab = oracle.kmeans(x, 12, 60, 5)
+    c2, _ = oracle.kmeans(x, 12, 61, 5)
+    np.testing.assert_array_equal(c1, c2)
+    for k in range(12):
+        sel = x[lab == k].astype(np.float64)
+        if len(sel):
+            np.testing.assert_allclose(c1[k], sel.mean(0), rtol=1e-6, atol=1e-6)
