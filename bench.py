@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--serving-seconds", type=float, default=2.0)
     p.add_argument("--no-deep", action="store_true",
                    help="skip the deep-precision (k=100) workload")
+    p.add_argument("--no-train", action="store_true",
+                   help="skip the quantizer-training measurement")
     p.add_argument("--forms", default="fp32,bf16,fp8",
                    help="scan forms to measure; the fastest that reaches recall 0.95 "
                         "is the headline")
@@ -518,6 +520,42 @@ def run_serving(torch, sivf, dev, window=0, seconds=2.0, loads=(0.5, 0.8, 0.95))
 
 
 # ------------------------------------------------------- deep precision
+def run_train(torch, sivf, dev, n=200_000, iters=10, reps=3):
+    """Lloyd's k-means of the coarse quantizer (sivf_train) on n rows of the
+    SIFT-shaped stream, nlist 1024, `iters` iterations: device time per run
+    (CUDA events on the stream; the call synchronises the stream at entry,
+    so a run's time includes that host round trip)."""
+    w = W.CONFIGS["sift_window"]
+    ctr = W.centers(w)
+    x = W.vectors(w, 0, n, ctr)
+    xd = torch.from_numpy(x).to(dev)
+    g = sivf.Index(w.d, w.nlist, w.slab_size, 1024, 4 * w.nlist)
+    g.train(xd, 1, 1)
+    torch.cuda.synchronize()
+    times = []
+    for r in range(reps):
+        t0 = time.time()
+        g.train(xd, iters, r)
+        torch.cuda.synchronize()
+        times.append(time.time() - t0)
+    g.close()
+    best = min(times)
+    return {"rows": n, "d": w.d, "nlist": w.nlist, "iters": iters,
+            "seconds": round(best, 4), "row_iters_per_s": round(n * iters / best, 1)}
+
+
+def oracle_train_sample(n=10_000, iters=2):
+    """The oracle's k-means on a bounded sample of the same rows (host cores)."""
+    import oracle
+    w = W.CONFIGS["sift_window"]
+    x = W.vectors(w, 0, n, W.centers(w))
+    t0 = time.time()
+    oracle.kmeans(x, w.nlist, iters, 0)
+    s = time.time() - t0
+    return {"rows": n, "iters": iters, "seconds": round(s, 3),
+            "row_iters_per_s": round(n * iters / s, 1)}
+
+
 def run_deep(torch, sivf, dev, steps=3, n_truth=100):
     """The precision workload: 10,000,000 unit-norm vectors d=96 from a
     4,096-component mixture, nlist=4096, slab 32, with FP32, BF16 and FP8
@@ -845,6 +883,8 @@ def main():
         torch.cuda.empty_cache()
     if not args.no_deep:
         line["components"]["deep_precision"] = run_deep(torch, sivf, dev)
+    if not args.no_train:
+        line["components"]["train"] = run_train(torch, sivf, dev)
     if not args.no_serving:
         line["components"]["serving"] = run_serving(
             torch, sivf, dev, args.serving_window, args.serving_seconds)
@@ -862,6 +902,8 @@ def main():
             "components": {k: round(rr[k], 3) for k in ("search_qps", "insert_vec_s",
                                                         "delete_vec_s", "p99_update_ms")},
         }
+        if not args.no_train:
+            line["cpu_baseline"]["components"]["train"] = oracle_train_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
