@@ -106,8 +106,10 @@ sivf_status sivf_destroy(sivf_index *index);
  * sivf_set_centroids -- load the coarse quantizer (Sec. 3.3: the lists are
  * the cells of nearest-centroid assignment).  `c` [device] is [nlist, d]
  * float32.  The index must be empty (SIVF_E_STATE otherwise).  Also sets
- * every list's FP8 inverse scale to 448 / (2 * max_j |c_lj|) (1.0 when the
- * centroid is zero); sivf_set_list_scales overrides it.
+ * every list's FP8 inverse scale to fl32(448 / R_l), R_l the distance from
+ * c_l to its nearest other centroid (FP64); with one list or R_l = 0,
+ * fl32(448 / (2 * max_j |c_lj|)) (1.0 when the centroid is zero);
+ * sivf_set_list_scales overrides it.
  */
 sivf_status sivf_set_centroids(sivf_index *index, const float *c, void *stream);
 
@@ -140,8 +142,9 @@ sivf_status sivf_train(sivf_index *index, const float *x, int64_t n, int iters,
 sivf_status sivf_get_centroids(sivf_index *index, float *c, void *stream);
 
 /*
- * sivf_set_list_scales -- per-list FP8 E4M3 inverse scales: list l stores
- * code(fl32(x_j * inv_scale[l])) and decodes x_j ~ code / inv_scale[l].
+ * sivf_set_list_scales -- per-list FP8 E4M3 inverse scales: list l stores the
+ * residual codes code(fl32(fl32(x_j - c_lj) * inv_scale[l])) and decodes
+ * x_j ~ c_lj + code / inv_scale[l].
  * `inv_scale` [device] is [nlist] float32, each finite and > 0.  Must be
  * called while the index is empty.
  */
@@ -207,8 +210,10 @@ sivf_status sivf_remove(sivf_index *index, const int64_t *ids, int64_t n,
  * dtype SIVF_FP32 scans the FP32 payload with direct-form distances.
  * SIVF_BF16 / SIVF_FP8E4M3 scan the reduced copy (which must have been
  * enabled at create; d % 16 == 0) on tensor cores, keep the best 4k
- * candidates per query (k <= 32) and re-rank them with exact FP32
- * direct-form distances from the FP32 payload.
+ * candidates per query (k <= 128) and re-rank them with exact FP32
+ * direct-form distances from the FP32 payload.  The FP8 copy holds the
+ * residuals x - c_l of each list; the query is coded per (query, list)
+ * pair as q - c_l with its own scale 448 / (2 max_j |q_j - c_lj|).
  */
 sivf_status sivf_search(sivf_index *index, const float *q, int64_t nq, int k,
                         int nprobe, sivf_scan_dtype dtype, float *dist,
@@ -218,7 +223,9 @@ sivf_status sivf_search(sivf_index *index, const float *q, int64_t nq, int k,
  * sivf_search_candidates -- the first stage of a reduced-precision search
  * alone: the `kc` best candidates of each query by the reduced-precision
  * distance ||q||^2 + ||x||^2 - 2 s q^.x^ over the nprobe nearest lists
- * (q^, x^ the BF16 / FP8 roundings; FP32 accumulation), ascending, ties to
+ * (q^, x^ the BF16 roundings of q and x, or for FP8 the E4M3 codes of the
+ * residuals q - c_l, x - c_l with ||q - c_l||^2, ||x - c_l||^2 as the norms;
+ * FP32 accumulation), ascending, ties to
  * the lower slot.  dist [device] float32[nq, kc] holds those approximate
  * distances, labels [device] int64[nq, kc] the ids; padding (+inf, -1).
  * 1 <= kc <= 128; dtype SIVF_BF16 or SIVF_FP8E4M3.

@@ -73,6 +73,7 @@ def load_lib(path: str):
         "oivf_splitmix64": (None, [C.c_uint64, i64, p]),
         "oivf_kmeans_init_rows": (i32, [i64, i32, C.c_uint64, p]),
         "oivf_kmeans": (i32, [p, i64, i32, i32, i32, C.c_uint64, p, p]),
+        "oivf_fp8_list_scales": (None, [p, i32, i32, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -323,3 +324,11 @@ def kmeans(x, nlist: int, iters: int, seed: int):
     if st:
         raise OracleError(st)
     return cent, lab
+
+
+def fp8_list_scales(cent) -> np.ndarray:
+    """Per-list FP8 inverse scales of the residual codes (see sivf_oracle.c)."""
+    cent = _f32(cent)
+    out = np.empty(cent.shape[0], np.float32)
+    _load().oivf_fp8_list_scales(_ptr(cent), cent.shape[0], cent.shape[1], _ptr(out))
+    return out

@@ -734,3 +734,30 @@ int oivf_kmeans(const float *x, int64_t n, int d, int nlist, int iters, uint64_t
     free(cnt);
     return O_OK;
 }
+
+/*
+ * FP8 residual codes (precision path; no passage, a reading): list l keeps
+ * E4M3(fl32(fl32(x_j - c_lj) * s_l)) with s_l = fl32(448 / R_l), R_l the
+ * distance from c_l to its nearest other centroid (FP64, squared distance
+ * summed in index order); with a single list or R_l = 0 the raw-magnitude
+ * rule fl32(448 / (2 max_j |c_lj|)) (1 for a zero centroid).
+ */
+void oivf_fp8_list_scales(const float *cent, int nlist, int d, float *out)
+{
+    for (int l = 0; l < nlist; ++l) {
+        const float *cl = cent + (size_t)l * d;
+        double best = INFINITY;
+        for (int o = 0; o < nlist; ++o) {
+            if (o == l) continue;
+            const double s = sqdist(cl, cent + (size_t)o * d, d);
+            if (s < best) best = s;
+        }
+        if (best > 0.0 && best < INFINITY) {
+            out[l] = (float)(448.0 / sqrt(best));
+        } else {
+            double mx = 0.0;
+            for (int j = 0; j < d; ++j) mx = fmax(mx, fabs((double)cl[j]));
+            out[l] = mx > 0.0 ? (float)(448.0 / (2.0 * mx)) : 1.0f;
+        }
+    }
+}

@@ -257,6 +257,7 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
     ALLOC(ix->x32, rows * d);
     if (ix->dtypes & (1u << SIVF_BF16)) ALLOC(ix->xb16, rows * d);
     if (ix->dtypes & (1u << SIVF_FP8E4M3)) ALLOC(ix->x8, rows * d);
+    if (ix->dtypes & (1u << SIVF_FP8E4M3)) ALLOC(ix->rnorm, rows);
     ALLOC(ix->inv_scale8, (size_t)L);
     ALLOC(ix->xnorm, rows);
     ALLOC(ix->ids, rows);
@@ -304,7 +305,7 @@ sivf_status sivf_destroy(sivf_index *ix)
     if (!ix) return SIVF_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {ix->cent, ix->cnorm, ix->cnrm_up, ix->cent_bf16, ix->cent_lo, ix->x32, ix->xb16,
-                    ix->x8, ix->inv_scale8, ix->xnorm, ix->ids, ix->bits, ix->meta,
+                    ix->x8, ix->rnorm, ix->inv_scale8, ix->xnorm, ix->ids, ix->bits, ix->meta,
                     ix->free_list, ix->free_top, ix->head, ix->nslabs, ix->list_live, ix->dir, ix->att,
                     ix->claim, ix->list_flag, ix->aff_flag, ix->runcnt, ix->err};
     for (void *p : ptrs)
@@ -473,7 +474,8 @@ static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dty
     *plo = pl;
     return coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
            (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * pl.K * 12 +
-           ((size_t)m * P + L) * pl.ch * 8 + (size_t)m * ix->d * 2 + 19 * 256;
+           ((size_t)m * P + L) * pl.ch * 8 + (size_t)m * ix->d * 2 +
+           (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 21 * 256;
 }
 
 // reduced-precision candidates: the re-rank depth K' = 4k
@@ -666,7 +668,11 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.items = b.take<int2>(((size_t)m * P + L) * pl.ch);
         sc.qn = b.take<float>((size_t)m);
         sc.qsc = b.take<float>((size_t)m);
-        sc.qcast = tc ? b.take<unsigned char>((size_t)m * ix->d * 2) : nullptr;
+        const bool fp8 = dtype == SIVF_FP8E4M3;
+        sc.qcast = tc ? b.take<unsigned char>(fp8 ? (size_t)m * P * ix->d : (size_t)m * ix->d * 2)
+                      : nullptr;
+        sc.pqn = fp8 ? b.take<float>((size_t)m * P) : nullptr;
+        sc.pqsc = fp8 ? b.take<float>((size_t)m * P) : nullptr;
         float *cand_d = b.take<float>((size_t)m * pl.K);
         int64_t *cand_s = b.take<int64_t>((size_t)m * pl.K);
         const int64_t rows = coarse_rows(ix, m);
@@ -688,7 +694,8 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             // per slab: payload copy, ||x||^2 and the validity bitmap
             const int64_t sb = (int64_t)ix->C * (ix->d * esz + 4) + ix->C / 8;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
-            query_prep(ix, dtype, qq, m, sc.qn, sc.qsc, sc.qcast, s);
+            if (fp8) pair_prep(ix, qq, m, P, probes, sc.pqn, sc.pqsc, sc.qcast, s);
+            else query_prep(ix, dtype, qq, m, sc.qn, sc.qsc, sc.qcast, s);
             const int split = P > 1 && pl.split ? 1 : P;
             group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
             scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);

@@ -63,7 +63,7 @@ __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
                 clo[(size_t)c * d + j] = *reinterpret_cast<const uint16_t *>(&l);
             }
         }
-    if (inv_scale8) inv_scale8[c] = mx > 0.0 ? (float)(448.0 / (2.0 * mx)) : 1.0f;
+    (void)mx;
 }
 
 // ----------------------------------------------------- FP32 tile GEMM (SIMT)
@@ -830,6 +830,44 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
     }
 }
 
+// FP8 inverse scale of each list for its residual codes x - c_l: 448 / R_l
+// with R_l the distance from c_l to its nearest other centroid (FP64, the
+// squared distance summed in index order, no fused multiply-add); with a
+// single list or a duplicated centroid (R_l = 0) the raw-magnitude rule
+// 448 / (2 max_j |c_lj|) (1 for a zero centroid).  One warp per list, its
+// lanes striding over the other centroids.
+__global__ void k_fp8_scales(const float *__restrict__ cent, int L, int d,
+                             float *__restrict__ inv_scale8)
+{
+    const int lane = threadIdx.x & 31;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= L) return;
+    const float *cl = cent + (size_t)l * d;
+    double best = INFINITY;
+    for (int o = lane; o < L; o += 32) {
+        if (o == l) continue;
+        const float *co = cent + (size_t)o * d;
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const double t = __dsub_rn((double)cl[j], (double)co[j]);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+        best = fmin(best, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) {
+        float inv;
+        if (best > 0.0 && best < INFINITY) {
+            inv = __double2float_rn(448.0 / sqrt(best));
+        } else {
+            double mx = 0.0;
+            for (int j = 0; j < d; ++j) mx = fmax(mx, fabs((double)cl[j]));
+            inv = mx > 0.0 ? __double2float_rn(448.0 / (2.0 * mx)) : 1.0f;
+        }
+        inv_scale8[l] = inv;
+    }
+}
+
 // ------------------------------------------------------------ host drivers
 void centroid_prep(sivf_index *ix, cudaStream_t st)
 {
@@ -837,6 +875,11 @@ void centroid_prep(sivf_index *ix, cudaStream_t st)
     k_centroid_norms<<<(ix->nlist + 127) / 128, 128, 0, st>>>(
         ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16,
         ix->cent_lo);
+    if (ix->x8) {
+        ix->launches += 1;
+        k_fp8_scales<<<(ix->nlist * 32 + 127) / 128, 128, 0, st>>>(ix->cent, ix->nlist, ix->d,
+                                                                    ix->inv_scale8);
+    }
 }
 
 // rows [0, m) of x -> out[m, P]; `Dbuf` holds at least rows_per_chunk * L

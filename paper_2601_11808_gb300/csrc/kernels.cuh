@@ -53,7 +53,10 @@ struct SearchScratch {
     int2 *items;         // [(nq * P + nlist) * CH] work items (list, tile << 8 | chunk)
     float *qn;           // [nq] ||q||^2 (reduced-precision scans)
     float *qsc;          // [nq] FP8 inverse scale of each query
-    unsigned char *qcast; // [nq, d] queries rounded to the scan format
+    unsigned char *qcast; // [nq, d] queries rounded to BF16, or [nq * P, d]
+                          // E4M3 residuals of each (query, probe) pair
+    float *pqn;          // [nq * P] ||q - c_l||^2 of each pair (FP8)
+    float *pqsc;         // [nq * P] FP8 inverse scale of each pair's residual
 };
 struct SearchPlan {
     int tq;              // queries per work item
@@ -88,6 +91,9 @@ bool tc_make_maps(sivf_index *ix);
 // ||q||^2, FP8 inverse scale and the row rounded to the scan format `dtype`
 void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn, float *qsc,
                 unsigned char *qcast, cudaStream_t st);
+// FP8 residual scan: per (query, probe) pair ||q - c_l||^2, scale, E4M3 row
+void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
+               float *qn, float *qsc, unsigned char *qcast, cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
 int tc_tile_queries(int Kc);   // 64 (K' <= 64), 32 (<= 128) or 16 (<= 512)
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,

@@ -46,6 +46,8 @@ struct IndexView {
     int32_t *free_list, *free_top;
     int32_t *head, *nslabs, *dir, *list_live;
     const float *inv_scale8;
+    const float *cent;  // [nlist, d] (FP8 residual codes)
+    float *rnorm;       // [S, C] ||x - c_l||^2 or null
     int64_t *att;
     int32_t *claim, *list_flag, *aff_flag, *runcnt;
     Ctl *ctl;
@@ -78,6 +80,8 @@ static IndexView view_of(sivf_index *ix)
     v.dir = ix->dir;
     v.list_live = ix->list_live;
     v.inv_scale8 = ix->inv_scale8;
+    v.cent = ix->cent;
+    v.rnorm = ix->rnorm;
     v.att = ix->att;
     v.claim = ix->claim;
     v.list_flag = ix->list_flag;
@@ -393,7 +397,8 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
         const size_t row = (size_t)s * C + slot;
         const float *xi = x + (size_t)i * d;
         const float inv = V.x8 ? V.inv_scale8[l] : 1.f;
-        float ss = 0.f;
+        const float *cl = V.cent + (size_t)l * d;
+        float ss = 0.f, rs = 0.f;
         for (int j = lane * 4; j < d; j += 128) {
             const float4 v = *reinterpret_cast<const float4 *>(xi + j);
             *reinterpret_cast<float4 *>(V.x32 + row * d + j) = v;
@@ -410,8 +415,16 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
                 *reinterpret_cast<uint2 *>(V.xb16 + row * d + j) = pk;
             }
             if (V.x8) {
-                float2 a = make_float2(__fmul_rn(v.x, inv), __fmul_rn(v.y, inv));
-                float2 b = make_float2(__fmul_rn(v.z, inv), __fmul_rn(v.w, inv));
+                // residual r = fl32(x - c_l), code = E4M3(fl32(r * inv))
+                const float4 c4 = *reinterpret_cast<const float4 *>(cl + j);
+                const float4 rv = make_float4(__fsub_rn(v.x, c4.x), __fsub_rn(v.y, c4.y),
+                                              __fsub_rn(v.z, c4.z), __fsub_rn(v.w, c4.w));
+                rs = fmaf(rv.x, rv.x, rs);
+                rs = fmaf(rv.y, rv.y, rs);
+                rs = fmaf(rv.z, rv.z, rs);
+                rs = fmaf(rv.w, rv.w, rs);
+                float2 a = make_float2(__fmul_rn(rv.x, inv), __fmul_rn(rv.y, inv));
+                float2 b = make_float2(__fmul_rn(rv.z, inv), __fmul_rn(rv.w, inv));
                 __nv_fp8x2_storage_t pa = __nv_cvt_float2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
                 __nv_fp8x2_storage_t pb = __nv_cvt_float2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
                 *reinterpret_cast<uint32_t *>(V.x8 + row * d + j) =
@@ -419,9 +432,11 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
             }
         }
         ss = warp_sum(ss);
+        if (V.x8) rs = warp_sum(rs);
         if (lane == 0) {
             const int64_t id = ids[i];
             V.xnorm[row] = ss;
+            if (V.rnorm) V.rnorm[row] = rs;
             V.ids[row] = id;
             V.att[id] = (s << 32) | (int64_t)slot;
         }

@@ -73,7 +73,9 @@ struct TcArgs {
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
     const int2 *items;
     const float *qn, *qsc;
-    const unsigned char *qcast;  // [nq, d] queries in the scan format (BF16 or E4M3)
+    const unsigned char *qcast;  // [nq, d] queries in the scan format (BF16), or
+                                 // [nq * P, d] residuals q - c_l of each pair (E4M3)
+    int per_pair;                // qn, qsc, qcast are per (query, probe) pair (FP8)
     float *part_d;
     int64_t *part_i;  // global slot (slab * C + slot) of each candidate
     float *thr;
@@ -624,10 +626,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             for (int r = lane; r < TN; r += 32) {
                 const int pr = r < m ? a.qlist[qb + r] : -1;
                 const int qi = pr >= 0 ? pr / a.P : 0;
+                const int qrow = a.per_pair ? (pr >= 0 ? pr : 0) : qi;  // row of qn, qsc, qcast
                 qp[r] = pr;
-                cqi[r] = qi;
-                cqn[r] = pr >= 0 ? a.qn[qi] : 0.f;
-                cqsc[r] = pr >= 0 ? a.qsc[qi] : 1.f;
+                cqi[r] = qrow;
+                cqn[r] = pr >= 0 ? a.qn[qrow] : 0.f;
+                cqsc[r] = pr >= 0 ? a.qsc[qrow] : 1.f;
                 ckd[r] = pr >= 0 ? __ldcg(a.thr + qi) : INFINITY;
             }
             int32_t *sl = c_sl(j);
@@ -1228,6 +1231,56 @@ void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn
                                                                     qcast);
 }
 
+// FP8 residual scan: per (query, probe) pair e = q * P + p with list l =
+// probes[e]: the residual r = fl32(q - c_l), ||r||^2 (FP32), its inverse
+// scale 448 / (2 max_j |r_j|) (1 when r = 0) and the row E4M3(fl32(r_j *
+// scale)) (round to nearest even, saturated).  One warp per pair; pairs with
+// no list are left untouched (they are never scanned).
+__global__ void k_pair_prep(const float *__restrict__ q, int64_t npairs, int P, int d, int L,
+                            const int32_t *__restrict__ probes, const float *__restrict__ cent,
+                            float *__restrict__ qn, float *__restrict__ qsc,
+                            unsigned char *__restrict__ qcast)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (e >= npairs) return;
+    const int l = probes[e];
+    if (l < 0 || l >= L) return;
+    const float *qr = q + (size_t)(e / P) * d;
+    const float *cl = cent + (size_t)l * d;
+    float ss = 0.f, mx = 0.f;
+    for (int j = lane; j < d; j += 32) {
+        const float r = __fsub_rn(qr[j], cl[j]);
+        ss = fmaf(r, r, ss);
+        mx = fmaxf(mx, fabsf(r));
+    }
+    ss = warp_sum(ss);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float sc = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
+    if (lane == 0) {
+        qn[e] = ss;
+        qsc[e] = sc;
+    }
+    unsigned char *o = qcast + (size_t)e * d;
+    for (int j = 2 * lane; j < d; j += 64) {
+        const float2 p = make_float2(__fmul_rn(__fsub_rn(qr[j], cl[j]), sc),
+                                     __fmul_rn(__fsub_rn(qr[j + 1], cl[j + 1]), sc));
+        const uint32_t two = __nv_cvt_float2_to_fp8x2(p, __NV_SATFINITE, __NV_E4M3);
+        o[j] = (unsigned char)(two & 0xffu);
+        o[j + 1] = (unsigned char)(two >> 8);
+    }
+}
+
+void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
+               float *qn, float *qsc, unsigned char *qcast, cudaStream_t st)
+{
+    ix->launches += 1;
+    const int64_t np = nq * P;
+    k_pair_prep<<<(unsigned)((np * 32 + 255) / 256), 256, 0, st>>>(q, np, P, ix->d, ix->nlist,
+                                                                  probes, ix->cent, qn, qsc,
+                                                                  qcast);
+}
+
 // global slots -> labels (padding stays -1)
 __global__ void k_slots_to_ids(int64_t *v, int64_t n, const int64_t *__restrict__ ids)
 {
@@ -1353,10 +1406,11 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.part_i = s.part_i;
     a.thr = s.thr;
     a.items = s.items;
-    a.qn = s.qn;
-    a.qsc = s.qsc;
+    a.per_pair = dtype == SIVF_FP8E4M3;
+    a.qn = a.per_pair ? s.pqn : s.qn;
+    a.qsc = a.per_pair ? s.pqsc : s.qsc;
     a.qcast = s.qcast;
-    a.xnorm = ix->xnorm;
+    a.xnorm = a.per_pair ? ix->rnorm : ix->xnorm;
     a.bits = ix->bits;
     a.nslabs = ix->nslabs;
     a.dir = ix->dir;

@@ -110,6 +110,7 @@ struct sivf_index {
     __nv_bfloat16 *xb16;           // [S, C, d] BF16 copy or null
     uint8_t *x8;                   // [S, C, d] FP8 E4M3 copy or null
     float *xnorm;                  // [S, C] fl32(||x||^2)
+    float *rnorm;                  // [S, C] fl32(||x - c_l||^2) (FP8 residual copy) or null
     int64_t *ids;                  // [S, C] label of each slot
     uint32_t *bits;                // [S, W] validity bitmaps
     sivf::SlabMeta *meta;          // [S]

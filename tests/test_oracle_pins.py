@@ -519,3 +519,17 @@ def test_kmeans_objective_never_increases_and_fixed_point():
         sel = x[lab == k].astype(np.float64)
         if len(sel):
             np.testing.assert_allclose(c1[k], sel.mean(0), rtol=1e-6, atol=1e-6)
+
+
+def test_fp8_list_scales_closed_form():
+    """s_l = 448 / R_l with R_l the distance to the nearest other centroid;
+    one list alone falls back to 448 / (2 max_j |c_j|)."""
+    c = np.zeros((3, 4), np.float32)
+    c[1, 0] = 3.0
+    c[2, 1] = 4.0
+    np.testing.assert_array_equal(oracle.fp8_list_scales(c),
+                                  np.float32([448 / 3, 448 / 3, 448 / 4]))
+    one = np.array([[1.0, -2.5, 0.5, 2.0]], np.float32)
+    np.testing.assert_array_equal(oracle.fp8_list_scales(one), np.float32([448 / 5]))
+    np.testing.assert_array_equal(oracle.fp8_list_scales(np.zeros((1, 4), np.float32)),
+                                  np.float32([1.0]))
