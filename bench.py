@@ -42,11 +42,10 @@ NPROBES = (8, 16, 32, 64, 128)
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# ncu capture of the BF16 list scan on this workload (nprobe 8): mean
-# dram__bytes_read.sum + dram__bytes_write.sum over its two launches, and the
-# scan kernel source it was taken of
-TC_PROFILED_SHA = "39e5ef2ca9d3ff7b"
-TC_PROFILED_TRAFFIC = round((279.312384 + 6.300928 + 275.782656 + 27.657984) / 2 * 1e6)
+# ncu captures of the reduced-precision list scan on this workload (nprobe
+# 8), per scan form: the scan kernel source they were taken of and the mean
+# dram__bytes_read.sum + dram__bytes_write.sum over the search's two launches
+TC_PROFILED = {}
 
 
 def parse():
@@ -808,8 +807,9 @@ def main():
         # workload, valid while the kernel source is the one it was taken of
         import hashlib
         src = os.path.join(ROOT, "paper_2601_11808_gb300", "csrc", "scan_tc.cu")
-        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TC_PROFILED_SHA:
-            traffic = TC_PROFILED_TRAFFIC
+        sha, nbytes = TC_PROFILED.get(head, (None, None))
+        if sha and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == sha:
+            traffic = nbytes
     roofline.update({"traffic": traffic, "launches": scan_n,
                      "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
                      "algorithmic_bytes_per_launch": (r["ubytes"] if head != "fp32" else r["sbytes"])
