@@ -103,6 +103,26 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out);
 sivf_status sivf_destroy(sivf_index *index);
 
 /*
+ * sivf_save -- checkpoint: write the index's configuration and every array
+ * that carries its state (centroids, FP8 scales, the slab pool with its
+ * payload copies, norms, ids, bitmaps and slab metadata, the free stack,
+ * list heads, directories and live counts, the address table, the live
+ * and scan counters) to the file `path` [host string].  Synchronizes
+ * `stream`.  The paper has no counterpart (its index lives as long as its
+ * process).  Errors: SIVF_E_ARG (file cannot be written), SIVF_E_CORRUPT
+ * (the index has a sticky device error), SIVF_E_CUDA.
+ *
+ * sivf_load -- create an index on the current device from a file written by
+ * sivf_save; every saved array is restored bit for bit (derived arrays are
+ * recomputed), so searches and later updates give the same results as on
+ * the saved index.  Scan tiles installed with sivf_set_tile are not saved.
+ * Errors: SIVF_E_ARG (missing, foreign or truncated file), SIVF_E_NOMEM,
+ * SIVF_E_CUDA.
+ */
+sivf_status sivf_save(sivf_index *index, const char *path, void *stream);
+sivf_status sivf_load(const char *path, sivf_index **out);
+
+/*
  * sivf_set_centroids -- load the coarse quantizer (Sec. 3.3: the lists are
  * the cells of nearest-centroid assignment).  `c` [device] is [nlist, d]
  * float32.  The index must be empty (SIVF_E_STATE otherwise).  Also sets

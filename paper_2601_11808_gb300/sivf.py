@@ -27,7 +27,7 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 # every symbol include/sivf.h declares
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
-    "sivf_train", "sivf_get_centroids",
+    "sivf_train", "sivf_get_centroids", "sivf_save", "sivf_load",
     "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
     "sivf_search_with_probes", "sivf_search_noalloc", "sivf_search_candidates",
     "sivf_assign", "sivf_probe", "sivf_sync",
@@ -124,6 +124,8 @@ def load(path: str | None = None):
             "sivf_set_centroids": (i32, [vp, vp, vp]),
             "sivf_train": (i32, [vp, vp, i64, i32, C.c_uint64, vp]),
             "sivf_get_centroids": (i32, [vp, vp, vp]),
+            "sivf_save": (i32, [vp, C.c_char_p, vp]),
+            "sivf_load": (i32, [C.c_char_p, C.POINTER(vp)]),
             "sivf_set_list_scales": (i32, [vp, vp, vp]),
             "sivf_reserve": (i32, [vp, i64, i64, i64, i32, i32, vp]),
             "sivf_add": (i32, [vp, vp, vp, i64, vp, C.POINTER(i64)]),
@@ -219,6 +221,18 @@ def sivf_create(d, nlist, slab_size, n_max, n_slabs, dir_cap=0, scan_dtypes=0) -
 
 def sivf_destroy(h) -> None:
     load().sivf_destroy(h)
+
+
+def sivf_save(h, path: str, stream=None) -> None:
+    lib = load()
+    _check(lib, h, lib.sivf_save(h, os.fsencode(path), _stream(stream)))
+
+
+def sivf_load(path: str) -> int:
+    lib = load()
+    h = C.c_void_p()
+    _check(lib, None, lib.sivf_load(os.fsencode(path), C.byref(h)))
+    return h.value
 
 
 def sivf_set_centroids(h, c, stream=None) -> None:
@@ -648,6 +662,25 @@ class Index:
         if getattr(self, "h", None):
             sivf_destroy(self.h)
             self.h = None
+
+    def save(self, path: str, stream=None):
+        """Checkpoint the whole index state to a file."""
+        sivf_save(self.h, path, stream)
+
+    @classmethod
+    def load(cls, path: str):
+        """A new index restored from a file written by save()."""
+        import struct
+        h = sivf_load(path)
+        with open(path, "rb") as f:  # the checkpoint header (configuration)
+            hdr = f.read(struct.calcsize("<8sIiiiqqqII"))
+        _, _, d, nlist, slab, n_max, n_slabs, dir_cap, dtypes, _ = struct.unpack("<8sIiiiqqqII", hdr)
+        self = cls.__new__(cls)
+        self.h = h
+        self.d, self.nlist, self.slab_size = d, nlist, slab
+        self.n_max, self.n_slabs, self.dir_cap = n_max, n_slabs, dir_cap
+        self.scan_dtypes = tuple(t for t, v in (("bf16", BF16), ("fp8", FP8E4M3)) if dtypes & (1 << v))
+        return self
 
     def __del__(self):
         try:
