@@ -71,6 +71,8 @@ def parse():
                    help="skip the deep-precision (k=100) workload")
     p.add_argument("--no-train", action="store_true",
                    help="skip the quantizer-training measurement")
+    p.add_argument("--no-zipf", action="store_true",
+                   help="skip the Zipf-skewed ingestion workload")
     p.add_argument("--forms", default="fp32,bf16,fp8",
                    help="scan forms to measure; the fastest that reaches recall 0.95 "
                         "is the headline")
@@ -635,6 +637,115 @@ def run_deep(torch, sivf, dev, steps=3, n_truth=100):
     return out
 
 
+def run_zipf(torch, sivf, dev, reps=3, n_truth=100, batch=10_000):
+    """Skewed ingestion: 1,000,000 SIFT-shaped vectors whose 1,024 mixture
+    components are drawn with P(rank r) ~ 1/r (the heaviest list takes 13 %
+    of the rows, about 2,100 slabs of 64), nlist=1024.  Ingestion time of
+    the whole set in one call and in batches of 10,000 (device-resident
+    input, CUDA events; best of `reps` fresh indexes), beside the same
+    ingestion with components drawn uniformly; then 10,000 queries from the
+    same skewed law, k=10, nprobe=8, per scan form: QPS and recall@10
+    against exact FP64 brute force on a sample of queries."""
+    w = W.CONFIGS["zipf_ingest"]
+    n, k, P = w.window, w.k, w.nprobes[0]
+    ctr = W.centers(w)
+    cent = W.index_centroids(w, ctr)
+    S = int(1.25 * (n // w.slab_size + 2 * w.nlist))
+    stream = torch.cuda.current_stream()
+    ids = torch.from_numpy(W.stream_ids(0, n, n)).to(dev)
+    cent_d = torch.from_numpy(cent).to(dev)
+
+    def ingest(xd, step):
+        best = None
+        for _ in range(reps):
+            g = sivf.Index(w.d, w.nlist, w.slab_size, n, S, scan_dtypes=("bf16", "fp8"))
+            g.set_centroids(cent_d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for b in range(0, n, step):
+                g.add(ids[b:b + step], xd[b:b + step])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g.sync()
+            assert g.stats()["ntotal"] == n
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                if best is not None:
+                    best[1].close()
+                best = (ms, g)
+            else:
+                g.close()
+        return best
+
+    Xu = torch.from_numpy(W.vectors_threaded(W.small("zipf_ingest", zipf=0.0), 0, n, ctr)).to(dev)
+    uni_ms, gu = ingest(Xu, n)
+    gu.close()
+    del Xu
+    X = W.vectors_threaded(w, 0, n, ctr)
+    Xd = torch.from_numpy(X).to(dev)
+    bat_ms, gb = ingest(Xd, batch)
+    gb.close()
+    one_ms, g = ingest(Xd, n)
+    sizes = np.asarray(g.list_sizes())
+    Q = W.queries(w, 0, w.n_queries, ctr)
+    Qd = torch.from_numpy(Q).to(dev)
+    # exact FP64 top-k of a query sample
+    qs = Q[:n_truth].astype(np.float64)
+    x64 = X.astype(np.float64)
+    dd = (qs ** 2).sum(1)[:, None] + (x64 ** 2).sum(1)[None, :] - 2.0 * (qs @ x64.T)
+    truth = np.argsort(dd, axis=1, kind="stable")[:, :k]
+    del dd, x64
+    out = {}
+    for form in ("fp32", "bf16", "fp8"):
+        dist = torch.empty((w.n_queries, k), dtype=torch.float32, device=dev)
+        lab = torch.empty((w.n_queries, k), dtype=torch.int64, device=dev)
+        for _ in range(2):
+            g.search(Qd, k, P, form, dist=dist, labels=lab)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            g.search(Qd, k, P, form, dist=dist, labels=lab)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        gi = lab[:n_truth].cpu().numpy()
+        rec = float(np.mean([len(set(a) & set(b)) / k for a, b in zip(gi.tolist(),
+                                                                     truth.tolist())]))
+        out[form] = {"qps": round(w.n_queries / (ms / 1e3), 1), "ms_per_search": round(ms, 3),
+                     "recall_at_10": round(rec, 4)}
+    g.close()
+    del Xd, Qd
+    torch.cuda.empty_cache()
+    return {
+        "workload": "zipf_ingest: 1,000,000 SIFT-shaped vectors d=128 from 1,024 components "
+                    "with P(rank r) ~ 1/r, nlist=1024, slab 64; 10,000 queries of the same law, "
+                    "k=10, nprobe=8",
+        "ingest_one_call_s": round(one_ms / 1e3, 4),
+        "ingest_one_call_vec_s": round(n / (one_ms / 1e3), 1),
+        f"ingest_batches_{batch}_s": round(bat_ms / 1e3, 4),
+        "uniform_ingest_one_call_s": round(uni_ms / 1e3, 4),
+        "largest_list": int(sizes.max()), "mean_list": round(float(sizes.mean()), 1),
+        "search": out,
+        "truth": f"exact FP64 brute force over all vectors for {n_truth} sampled queries",
+    }
+
+
+def oracle_zipf_sample(n=100_000):
+    """The oracle's ingestion of the first n rows of the skewed stream."""
+    import oracle
+    w = W.CONFIGS["zipf_ingest"]
+    ctr = W.centers(w)
+    x = W.vectors(w, 0, n, ctr)
+    o = oracle.OracleIVF(w.d, w.nlist, w.slab_size, n, 2 * (n // w.slab_size + w.nlist))
+    o.set_centroids(W.index_centroids(w, ctr))
+    t0 = time.time()
+    o.add(W.stream_ids(0, n, n), x)
+    s = time.time() - t0
+    return {"rows": n, "seconds": round(s, 3), "vec_s": round(n / s, 1)}
+
+
 # ------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -885,6 +996,8 @@ def main():
         line["components"]["deep_precision"] = run_deep(torch, sivf, dev)
     if not args.no_train:
         line["components"]["train"] = run_train(torch, sivf, dev)
+    if not args.no_zipf:
+        line["components"]["zipf_ingest"] = run_zipf(torch, sivf, dev)
     if not args.no_serving:
         line["components"]["serving"] = run_serving(
             torch, sivf, dev, args.serving_window, args.serving_seconds)
@@ -904,6 +1017,8 @@ def main():
         }
         if not args.no_train:
             line["cpu_baseline"]["components"]["train"] = oracle_train_sample()
+        if not args.no_zipf:
+            line["cpu_baseline"]["components"]["zipf_ingest"] = oracle_zipf_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -382,15 +382,21 @@ typedef struct {
                                  each slab load; the reduced dtypes use 64
                                  (the tensor-core tile's N) and ignore it  */
     int32_t slabs_per_chunk;  /* 1..16: a list is split into slab chunks
-                                 of at least this many slabs when the
-                                 batch has too few query tiles             */
-    int32_t items_per_sm;     /* 1..16: work items wanted per SM before
-                                 lists are split into chunks              */
+                                 of at least this many slabs              */
+    int32_t items_per_sm;     /* 1..16: a list is split into chunks so that
+                                 no work item exceeds 1 / (items_per_sm x
+                                 152) of the scan's work (query tiles x
+                                 slabs over the probed lists): a heavy list
+                                 of a skewed index spreads over many SMs  */
     int32_t select_slabs;     /* SIVF_FP32, 0..8: the k-select buffer of
                                  each query row holds its best k plus room
                                  for this many slabs of candidates (0: the
                                  built-in width, two slabs while that stays
-                                 within 256 entries)                       */
+                                 within 256 entries).  Reduced dtypes,
+                                 0..3: room for this many 128-row tiles of
+                                 candidates beside the best 4k (0: two
+                                 where shared memory keeps three load
+                                 stages, else one)                         */
     int32_t nearest_first;    /* reduced dtypes: 1 scans each query's
                                  nearest list in a launch of its own first,
                                  so the other lists meet a tight bound     */

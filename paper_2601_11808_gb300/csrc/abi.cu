@@ -444,10 +444,10 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
     const int L = ix->nlist;
     SearchPlan pl = plan_search(ix, nq, P, k);
     if (plo) *plo = pl;
-    size_t parts = (size_t)nq * P * pl.ch * pl.K;
+    size_t parts = (size_t)pl.run_cap * pl.K;
     return coarse_bytes(ix, nq) + (size_t)nq * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
-           parts * 12 + (size_t)nq * 4 * 3 + (size_t)nq * pl.K * 12 +
-           ((size_t)nq * P + L) * pl.ch * 8 + 18 * 256;
+           parts * 12 + (size_t)nq * 4 * 3 + (size_t)nq * 16 + (size_t)nq * pl.K * 12 +
+           (size_t)pl.item_cap * 8 + 19 * 256;
 }
 
 static int64_t query_chunk(const sivf_index *ix, int P, int k)
@@ -473,9 +473,9 @@ static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dty
     SearchPlan pl = plan_tc(ix, dtype, m, P, Kc);
     *plo = pl;
     return coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
-           (size_t)m * P * pl.ch * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * pl.K * 12 +
-           ((size_t)m * P + L) * pl.ch * 8 + (size_t)m * ix->d * 2 +
-           (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 21 * 256;
+           (size_t)pl.run_cap * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * 16 +
+           (size_t)m * pl.K * 12 + (size_t)pl.item_cap * 8 + (size_t)m * ix->d * 2 +
+           (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 22 * 256;
 }
 
 // reduced-precision candidates: the re-rank depth K' = 4k
@@ -661,11 +661,12 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.nch = b.take<int32_t>(L);
         sc.prank = b.take<int32_t>((size_t)m * P);
         sc.qlist = b.take<int32_t>((size_t)m * P);
-        sc.pnch = b.take<int32_t>((size_t)m * P);
-        sc.part_d = b.take<float>((size_t)m * P * pl.ch * pl.K);
-        sc.part_i = b.take<int64_t>((size_t)m * P * pl.ch * pl.K);
+        sc.prun = b.take<int32_t>((size_t)m * P);
+        sc.qrun = b.take<int2>((size_t)2 * m);
+        sc.part_d = b.take<float>((size_t)pl.run_cap * pl.K);
+        sc.part_i = b.take<int64_t>((size_t)pl.run_cap * pl.K);
         sc.thr = b.take<float>((size_t)m);
-        sc.items = b.take<int2>(((size_t)m * P + L) * pl.ch);
+        sc.items = b.take<int2>((size_t)pl.item_cap);
         sc.qn = b.take<float>((size_t)m);
         sc.qsc = b.take<float>((size_t)m);
         const bool fp8 = dtype == SIVF_FP8E4M3;
@@ -703,11 +704,12 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
                 group_pairs(ix, m, P, split, P, probes, probes_in != nullptr, pl, sc, sb, s);
                 scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
             }
+            const int nphase = split < P ? 2 : 1;
             if (cand_only) {
-                merge_tc(ix, m, P, pl, sc, Kc, dist + q0 * k, labels + q0 * k, s);
+                merge_tc(ix, m, nphase, sc, Kc, dist + q0 * k, labels + q0 * k, s);
                 slots_to_ids(ix, labels + q0 * k, m * k, s);
             } else {
-                merge_tc(ix, m, P, pl, sc, Kc, cand_d, cand_s, s);
+                merge_tc(ix, m, nphase, sc, Kc, cand_d, cand_s, s);
                 rerank(ix, qq, m, Kc, cand_d, cand_s, k, dist + q0 * k, labels + q0 * k, s);
             }
         }

@@ -355,6 +355,7 @@ sivf_status sivf_autotune(sivf_index *ix, const float *q, int64_t nq, int k, int
     static const int ips_v[] = {1, 2, 4, 8, 16};
     static const int sel_v[] = {0, 1, 2, 4};
     static const int nf_v[] = {0, 1};
+    static const int tsel_v[] = {0, 1, 2};
     struct Knob {
         int32_t sivf_tile::*field;
         const int *v;
@@ -366,6 +367,7 @@ sivf_status sivf_autotune(sivf_index *ix, const float *q, int64_t nq, int k, int
         knobs.push_back({&sivf_tile::select_slabs, sel_v, 4});
     } else {
         knobs.push_back({&sivf_tile::nearest_first, nf_v, 2});
+        knobs.push_back({&sivf_tile::select_slabs, tsel_v, 3});
     }
     knobs.push_back({&sivf_tile::slabs_per_chunk, spc_v, 4});
     knobs.push_back({&sivf_tile::items_per_sm, ips_v, 5});

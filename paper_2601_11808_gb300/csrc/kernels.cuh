@@ -46,11 +46,14 @@ struct SearchScratch {
     int32_t *nch;        // [nlist] slab chunks of each list
     int32_t *prank;      // [nq * P] rank of the pair inside its list group
     int32_t *qlist;      // [nq * P] pairs grouped by list (q * P + p)
-    float *part_d;       // [nq * P * CH * K]
-    int64_t *part_i;     // [nq * P * CH * K]
+    float *part_d;       // [run_cap * K] item outputs: one run of K per (pair, chunk)
+    int64_t *part_i;     // [run_cap * K]
     float *thr;          // [nq] shared bound of each query's k-th distance
-    int32_t *pnch;       // [nq * P] slab chunks scanned for each pair (0: none)
-    int2 *items;         // [(nq * P + nlist) * CH] work items (list, tile << 8 | chunk)
+    int32_t *prun;       // [nq * P] run of the pair's chunk 0 (chunk c writes run
+                         // prun + c); -1: the pair is not scanned
+    int2 *qrun;          // [2 * nq] (first run, runs) of each query in each scan
+                         // phase; a query's runs of one phase are contiguous
+    int2 *items;         // [item_cap] work items (list, tile << 8 | chunk)
     float *qn;           // [nq] ||q||^2 (reduced-precision scans)
     float *qsc;          // [nq] FP8 inverse scale of each query
     unsigned char *qcast; // [nq, d] queries rounded to BF16, or [nq * P, d]
@@ -60,10 +63,13 @@ struct SearchScratch {
 };
 struct SearchPlan {
     int tq;              // queries per work item
-    int ch;              // most slab chunks per list
+    int ch;              // most slab chunks per list (P * ch <= 2048 runs per query)
     int slabs_per_chunk; // slabs per chunk before splitting stops
+    int ips;             // work items per SM the chunking aims at
+    int64_t run_cap;     // output runs of one query chunk (both phases)
+    int64_t item_cap;    // work items of one scan launch
     int K;               // candidates kept per (query, item)
-    int M;               // FP32 scan: entries of each row's k-select buffer
+    int M;               // entries of each row's k-select / candidate buffer
     int split;           // reduced precision: nearest list in a launch of its own
 };
 // tile choice for a batch: the installed one of its bucket, else the default
@@ -76,6 +82,9 @@ SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, in
                           const sivf_tile &t);
 // FP32 plan (dtype 0) with the batch's current tile
 SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K);
+// output runs and work items one query chunk of nq queries may need
+int64_t plan_run_cap(int64_t nq, int P, int tq, int ips);
+int64_t plan_item_cap(int64_t nq, int P, int L, int ips);
 bool scan_fits(const sivf_index *ix, int K);   // shared memory for k = K
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
@@ -95,14 +104,18 @@ void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn
 void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                float *qn, float *qsc, unsigned char *qcast, cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
-int tc_tile_queries(int Kc);   // 64 (K' <= 64), 32 (<= 128) or 16 (<= 512)
+// entries of a row's candidate buffer (sel: tiles of room, 0 = default) and
+// whether a buffer of M entries fits in shared memory
+int tc_buf_entries(const sivf_index *ix, int dtype, int Kc, int sel);
+bool tc_buf_fits(const sivf_index *ix, int dtype, int Kc, int M);
+int tc_tile_queries(int Kc);   // 48 (K' <= 64), 32 (<= 128) or 16 (<= 512)
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
                    const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);
 // per query: the best Kc (distance, slot) of its reduced-precision item
-// outputs, sorted ascending
-void merge_tc(sivf_index *ix, int64_t nq, int P, const SearchPlan &pl, const SearchScratch &s,
-              int Kc, float *out_d, int64_t *out_s, cudaStream_t st);
+// outputs (the runs of `nphase` scan phases), sorted ascending
+void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc,
+              float *out_d, int64_t *out_s, cudaStream_t st);
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
 

@@ -65,11 +65,12 @@ size_t need_bytes(const sivf_index *ix, int64_t nq, int P, const sivf::SearchPla
     add(L * 4);                       // nch
     add((size_t)nq * P * 4);          // prank
     add((size_t)nq * P * 4);          // qlist
-    add((size_t)nq * P * pl.ch * pl.K * 4);   // part_d
-    add((size_t)nq * P * pl.ch * pl.K * 8);   // part_i
+    add((size_t)pl.run_cap * pl.K * 4);   // part_d
+    add((size_t)pl.run_cap * pl.K * 8);   // part_i
     add((size_t)nq * 4);              // thr
-    add((size_t)nq * P * 4);          // pnch
-    add(((size_t)nq * P + L) * pl.ch * 8);   // items
+    add((size_t)nq * P * 4);          // prun
+    add((size_t)nq * 2 * 8);          // qrun
+    add((size_t)pl.item_cap * 8);     // items
     add((size_t)rows * L * 4);        // coarse distances
     return b;
 }
@@ -97,7 +98,12 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
     const int P = nprobe, L = ix->nlist;
     SearchPlan pl = plan_search(ix, nq, P, k);
     int64_t rows = std::min<int64_t>(nq, std::max<int64_t>(1, ((int64_t)8 << 20) / (4 * L)));
-    while (need_bytes(ix, nq, P, pl, rows) > kNoallocBytes && pl.ch > 1) pl.ch >>= 1;
+    // fewer items per SM: fewer extra chunk runs
+    while (need_bytes(ix, nq, P, pl, rows) > kNoallocBytes && pl.ips > 1) {
+        pl.ips >>= 1;
+        pl.run_cap = plan_run_cap(nq, P, pl.tq, pl.ips);
+        pl.item_cap = plan_item_cap(nq, P, L, pl.ips);
+    }
     while (need_bytes(ix, nq, P, pl, rows) > kNoallocBytes && rows > 1) rows >>= 1;
     if (need_bytes(ix, nq, P, pl, rows) > kNoallocBytes) {
         char b[200];
@@ -136,11 +142,12 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
     sc.nch = c.take<int32_t>(L);
     sc.prank = c.take<int32_t>((size_t)nq * P);
     sc.qlist = c.take<int32_t>((size_t)nq * P);
-    sc.part_d = c.take<float>((size_t)nq * P * pl.ch * pl.K);
-    sc.part_i = c.take<int64_t>((size_t)nq * P * pl.ch * pl.K);
+    sc.part_d = c.take<float>((size_t)pl.run_cap * pl.K);
+    sc.part_i = c.take<int64_t>((size_t)pl.run_cap * pl.K);
     sc.thr = c.take<float>((size_t)nq);
-    sc.pnch = c.take<int32_t>((size_t)nq * P);
-    sc.items = c.take<int2>(((size_t)nq * P + L) * pl.ch);
+    sc.prun = c.take<int32_t>((size_t)nq * P);
+    sc.qrun = c.take<int2>((size_t)nq * 2);
+    sc.items = c.take<int2>((size_t)pl.item_cap);
     float *Dbuf = c.take<float>((size_t)rows * L);
     if (!c.ok()) return fail(SIVF_E_ARG, "scratch carve-up overflow");
 

@@ -45,29 +45,51 @@ __global__ void k_srch_hist(const int32_t *__restrict__ probes, int64_t nq, int 
     }
 }
 
-// One block: exclusive scans over the lists of the pair counts and of the
-// work items (query tiles x slab chunks).
+// One block.  Chunking: a list is cut into slab chunks so that no work item
+// is longer than 1 / (ips * 152) of the launch's whole work W (query tiles x
+// slabs summed over the probed lists) and no chunk is shorter than `spc`
+// slabs, at most `chmax` chunks per list; a heavy list (a skewed
+// distribution puts most vectors in a few lists) is spread over many SMs
+// instead of holding one SM for the length of the launch.  With
+// target = max(spc, ceil(W / (ips * 152))) the chunks beyond the first of
+// every list add at most ips * 152 items, and at most tq * ips * 152 output
+// runs, to one tile per pair: the scratch is sized from that bound.  Then
+// exclusive scans over the lists of the pair counts and of the work items.
 __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ lcnt,
                                                     const int32_t *__restrict__ nslabs,
                                                     const int32_t *__restrict__ list_live,
-                                                    int L, int tq, int ch, int spc,
-                                                    int64_t slab_bytes,
+                                                    int L, int tq, int chmax, int spc, int ips,
+                                                    int64_t item_cap, int64_t slab_bytes,
                                                     int32_t *__restrict__ loff,
                                                     int32_t *__restrict__ ibase,
                                                     int32_t *__restrict__ nch,
                                                     int2 *__restrict__ items, Ctl *ctl,
-                                                    int64_t *stat)
+                                                    int64_t *stat, uint32_t *err)
 {
     __shared__ int32_t sa[1024], sb[1024];
+    __shared__ unsigned long long sw[32];
     const int tid = threadIdx.x;
     const int per = (L + 1023) / 1024;
     const int b0 = tid * per, b1 = min(L, b0 + per);
+    unsigned long long wsum = 0;
+    for (int l = b0; l < b1; ++l) {
+        const int m = lcnt[l], ns = nslabs[l];
+        if (m > 0 && ns > 0) wsum += (unsigned long long)((m + tq - 1) / tq) * ns;
+    }
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if ((tid & 31) == 0) sw[tid >> 5] = wsum;
+    __syncthreads();
+    unsigned long long W = 0;
+    for (int i = 0; i < 32; ++i) W += sw[i];
+    const unsigned long long slots = (unsigned long long)ips * 152;
+    const unsigned long long share = (W + slots - 1) / slots;
+    const int target = (int)min(max((unsigned long long)spc, share), 1ull << 30);
     int32_t ca = 0, cb = 0;
     unsigned long long pairs = 0, bytes = 0, ubytes = 0;
     for (int l = b0; l < b1; ++l) {
         int m = lcnt[l], ns = nslabs[l];
         int nt = (m + tq - 1) / tq;
-        int c = (m > 0 && ns > 0) ? min(ch, max(1, (ns + spc - 1) / spc)) : 0;
+        int c = (m > 0 && ns > 0) ? min(chmax, max(1, (ns + target - 1) / target)) : 0;
         c = min(c, ns);
         nch[l] = c;
         ca += m;
@@ -97,38 +119,73 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
         loff[l] = ea;
         ibase[l] = eb;
         // work items of list l: (list, tile << 8 | chunk)
-        for (int t = 0; t < nt * c; ++t) items[eb + t] = make_int2(l, ((t / c) << 8) | (t % c));
+        for (int t = 0; t < nt * c; ++t) {
+            if (eb + t < item_cap) items[eb + t] = make_int2(l, ((t / c) << 8) | (t % c));
+        }
         ea += m;
         eb += nt * c;
     }
     if (tid == 1023) {
         loff[L] = sa[1023];
         ibase[L] = sb[1023];
-        ctl->nitems = sb[1023];
+        if (sb[1023] > item_cap) atomicOr(err, ERR_PLAN);
+        ctl->nitems = (int32_t)min((int64_t)sb[1023], item_cap);
         ctl->nscan = sa[1023];
         ctl->next_item = 0;
     }
 }
 
-// pairs grouped by list; pnch = slab chunks the pair's list is split into
-// (0: the pair is not scanned)
+// One thread per query, whole warps together: each pair goes to its list's
+// group (qlist), and the query's pairs of this phase reserve consecutive
+// output runs (one per slab chunk of the pair's list; one atomic per warp).
+// prun = the pair's first run (-1: not scanned); qrun[phase][q] = (first
+// run, runs) of the query.  A reservation past run_cap (the plan's bound
+// makes this impossible) sets ERR_PLAN and leaves the query's runs out.
 __global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, int P, int p0,
                                int p1, const int32_t *__restrict__ prank,
                                const int32_t *__restrict__ loff, const int32_t *__restrict__ nch,
-                               int32_t *__restrict__ qlist, int32_t *__restrict__ pnch)
+                               int32_t *__restrict__ qlist, int32_t *__restrict__ prun,
+                               int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap,
+                               uint32_t *err)
 {
-    const int np = p1 - p0;
-    const int64_t n = nq * np;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = (t / np) * P + p0 + t % np;
-        const int r = prank[e];
-        if (r >= 0) {
-            const int l = probes[e];
-            qlist[loff[l] + r] = (int32_t)e;
-            pnch[e] = nch[l];
-        } else {
-            pnch[e] = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); q0 < nq;
+         q0 += stride) {
+        const int64_t q = q0 + lane;
+        int cnt = 0;
+        if (q < nq)
+            for (int p = p0; p < p1; ++p) {
+                const int64_t e = q * P + p;
+                const int r = prank[e];
+                int c = 0;
+                if (r >= 0) {
+                    const int l = probes[e];
+                    qlist[loff[l] + r] = (int32_t)e;
+                    c = nch[l];
+                }
+                prun[e] = c;
+                cnt += c;
+            }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&ctl->nruns, incl);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+        if (q < nq) {
+            const bool fits = base >= 0 && (int64_t)base + cnt <= run_cap;
+            if (!fits) atomicOr(err, ERR_PLAN);
+            int run = base;
+            for (int p = p0; p < p1; ++p) {
+                const int64_t e = q * P + p;
+                const int c = prun[e];
+                prun[e] = (c > 0 && fits) ? run : -1;
+                run += c;
+            }
+            qrun[(p0 > 0 ? nq : 0) + q] = fits ? make_int2(base, cnt) : make_int2(0, 0);
         }
     }
 }
@@ -140,8 +197,9 @@ constexpr int NST = 2;  // slab stages in flight
 struct ScanArgs {
     const float *q;
     int64_t nq;
-    int P, K, M, CH;
+    int P, K, M;
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
+    const int32_t *prun;  // first output run of each pair
     const int2 *items;
     float *part_d;
     int64_t *part_i;
@@ -581,7 +639,9 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
         // the best K of each row of the tile (padded with (+inf, -1))
         for (int e = tid; e < m * K; e += SCAN_NT) {
             const int r = e / K, j = e % K;
-            const int64_t base = ((int64_t)s_qpair[r] * a.CH + chunk) * K;
+            const int run = a.prun[s_qpair[r]];
+            if (run < 0) continue;
+            const int64_t base = ((int64_t)run + chunk) * K;
             const bool ok = j < s_nb[r];
             a.part_d[base + j] = ok ? BD[(size_t)r * M + j] : INFINITY;
             a.part_i[base + j] = ok ? BI[(size_t)r * M + j] : -1;
@@ -601,8 +661,8 @@ __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
 constexpr int MERGE_NT = 128;
 constexpr int MERGE_RUNS_PER_LANE = 64;
 
-__global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ pnch, int64_t nq,
-                                                    int P, int CH, int K, int k,
+__global__ __launch_bounds__(MERGE_NT) void k_merge(const int2 *__restrict__ qrun, int64_t nq,
+                                                    int K, int k,
                                                     const float *__restrict__ part_d,
                                                     const int64_t *__restrict__ part_i,
                                                     float *__restrict__ dist,
@@ -611,16 +671,12 @@ __global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ 
     const int lane = threadIdx.x & 31;
     const int64_t q = (blockIdx.x * (int64_t)MERGE_NT + threadIdx.x) >> 5;
     if (q >= nq) return;
-    // runs owned by this lane: (p, chunk) pairs numbered r = p * CH + chunk,
-    // r = lane, lane + 32, ...; cursor per run kept in local memory
+    // the query's runs (sorted, padded with (+inf, -1)) are contiguous:
+    // r = lane, lane + 32, ... of them, cursor per run kept in local memory
+    const int2 qr = qrun[q];
     int cur[MERGE_RUNS_PER_LANE];
     int nrun = 0;
-    const int R = P * CH;
-    for (int r = lane; r < R && nrun < MERGE_RUNS_PER_LANE; r += 32) {
-        int p = r / CH, c = r % CH;
-        bool ok = c < pnch[q * P + p];
-        cur[nrun++] = ok ? 0 : K;
-    }
+    for (int r = lane; r < qr.y && nrun < MERGE_RUNS_PER_LANE; r += 32) cur[nrun++] = 0;
     auto head = [&](int j, float &hd, int64_t &hi) {
         int r = lane + 32 * j;
         if (cur[j] >= K) {
@@ -628,7 +684,7 @@ __global__ __launch_bounds__(MERGE_NT) void k_merge(const int32_t *__restrict__ 
             hi = -1;
             return;
         }
-        int64_t e = ((q * P + r / CH) * (int64_t)CH + r % CH) * K + cur[j];
+        int64_t e = ((int64_t)qr.x + r) * K + cur[j];
         hd = part_d[e];
         hi = part_i[e];
         if (hi < 0) hd = INFINITY;
@@ -749,6 +805,8 @@ bool tile_valid(const sivf_index *ix, int dtype, const sivf_tile &t, int K)
         return scan_smem(tq, ix->C, ix->d, fp32_width(K, ix->C, t.select_slabs)).total <=
                220 * 1024;
     }
+    if (t.select_slabs < 0 || t.select_slabs > 3) return false;
+    if (!tc_buf_fits(ix, dtype, K, tc_buf_entries(ix, dtype, K, t.select_slabs))) return false;
     return t.nearest_first == 0 || t.nearest_first == 1;
 }
 
@@ -766,18 +824,31 @@ SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, in
     const bool fp32 = dtype == SIVF_FP32;
     pl.tq = fp32 ? t.queries_per_tile : tc_tile_queries(K);
     pl.K = K;
-    pl.M = fp32 ? fp32_width(K, ix->C, t.select_slabs) : 0;
+    pl.M = fp32 ? fp32_width(K, ix->C, t.select_slabs)
+                : tc_buf_entries(ix, dtype, K, t.select_slabs);
     pl.split = fp32 ? 0 : t.nearest_first;
-    // enough work items for every SM: split lists into slab chunks when the
-    // query tiles alone are too few
-    const double touched = std::min<double>(ix->nlist, (double)nq * P);
-    const double tiles = std::max(touched, (double)nq * P / pl.tq);
-    const double want = (double)t.items_per_sm * 152;
-    int ch = tiles >= want ? 1 : (int)std::min<double>(kMaxChunks, std::ceil(want / tiles));
-    ch = std::min(ch, std::max(1, 2048 / P));  // runs per query the merge can hold
-    pl.ch = std::max(1, ch);
+    // slab chunks: a list is split when its items would be long against the
+    // launch's work per SM (decided on the device from the grouped pairs);
+    // at most 2048 runs per query reach the merge
+    pl.ch = std::max(1, std::min(kMaxChunks, 2048 / std::max(P, 1)));
     pl.slabs_per_chunk = t.slabs_per_chunk;
+    pl.ips = t.items_per_sm;
+    pl.run_cap = plan_run_cap(nq, P, pl.tq, pl.ips);
+    pl.item_cap = plan_item_cap(nq, P, ix->nlist, pl.ips);
     return pl;
+}
+
+int64_t plan_run_cap(int64_t nq, int P, int tq, int ips)
+{
+    // a run per scanned pair, plus per scan phase (at most two) the chunks
+    // past the first: at most tq * ips * 152
+    return nq * P + 2 * (int64_t)tq * ips * 152;
+}
+
+int64_t plan_item_cap(int64_t nq, int P, int L, int ips)
+{
+    // a tile per (list, up to tq pairs), plus at most ips * 152 extra chunks
+    return nq * P + L + (int64_t)ips * 152;
 }
 
 SearchPlan plan_search(const sivf_index *ix, int64_t nq, int P, int K)
@@ -798,13 +869,14 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
     cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
     const int64_t n = nq * (p1 - p0);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+    const int gq = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, 152 * 16));
     const int tg = prof_begin(ix, PROF_GROUP, 3, st);
     k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
     k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
-                                    pl.slabs_per_chunk, slab_bytes, s.loff, s.ibase, s.nch,
-                                    s.items, ix->ctl, ix->stat);
-    k_srch_scatter<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
-                                      s.pnch);
+                                    pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff,
+                                    s.ibase, s.nch, s.items, ix->ctl, ix->stat, ix->err);
+    k_srch_scatter<<<gq, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
+                                       s.prun, s.qrun, ix->ctl, pl.run_cap, ix->err);
     prof_end(ix, tg, st);
 }
 
@@ -822,7 +894,7 @@ void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t
     a.P = P;
     a.K = pl.K;
     a.M = pl.M;
-    a.CH = pl.ch;
+    a.prun = s.prun;
     a.qlist = s.qlist;
     a.loff = s.loff;
     a.lcnt = s.lcnt;
@@ -862,8 +934,8 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
     int64_t warps = nq;
     int64_t blocks = (warps * 32 + MERGE_NT - 1) / MERGE_NT;
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
-    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(s.pnch, nq, P, pl.ch, pl.K, k, s.part_d,
-                                                  s.part_i, dist, labels);
+    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(s.qrun, nq, pl.K, k, s.part_d, s.part_i,
+                                                  dist, labels);
     prof_end(ix, tok, st);
 }
 

@@ -69,8 +69,9 @@ template <int TN> struct TcShape {
 struct TcArgs {
     const float *q;
     int64_t nq;
-    int P, K, M, CH;
+    int P, K, M;
     const int32_t *qlist, *loff, *lcnt, *ibase, *nch;
+    const int32_t *prun;  // first output run of each pair (-1: not scanned)
     const int2 *items;
     const float *qn, *qsc;
     const unsigned char *qcast;  // [nq, d] queries in the scan format (BF16), or
@@ -936,8 +937,9 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                     int32_t *bs = BS + (size_t)n * ME;
                     float kd = s_kd[n];
                     if (cc > 0) kd = fminf(kd, fold_row(bd, bs, K, nb, cc, hist, lane));
-                    const int64_t base = ((int64_t)qp[n] * a.CH + chunk) * K;
-                    for (int i = lane; i < K; i += 32) {
+                    const int run = a.prun[qp[n]];
+                    const int64_t base = ((int64_t)run + chunk) * K;
+                    for (int i = lane; i < K && run >= 0; i += 32) {
                         a.part_d[base + i] = i < nb ? bd[i] : INFINITY;
                         a.part_i[base + i] = i < nb ? (int64_t)bs[i] : -1;
                     }
@@ -958,14 +960,14 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
 
 // ------------------------------------------------------- per-query merge
 // One warp per query: the best K' (distance, slot) of the query's item
-// outputs (P x CH runs of K' unsorted entries, valid ones first, padded
-// with (+inf, -1); runs with chunk >= pnch were not scanned) by a radix
-// select over the 64-bit (distance, slot) keys, then sorted ascending,
-// padded with (+inf, -1).
+// outputs (runs of K' unsorted entries, valid ones first, padded with
+// (+inf, -1); the runs of one scan phase are contiguous, qrun[phase][q] =
+// (first run, runs)) by a radix select over the 64-bit (distance, slot)
+// keys, then sorted ascending, padded with (+inf, -1).
 constexpr int MT_NT = 128;
 template <int E>
-__global__ __launch_bounds__(MT_NT) void k_merge_tc(const int32_t *__restrict__ pnch,
-                                                    int64_t nq, int P, int CH, int K,
+__global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qrun, int64_t nq,
+                                                    int nphase, int K,
                                                     const float *__restrict__ part_d,
                                                     const int64_t *__restrict__ part_i,
                                                     float *__restrict__ out_d,
@@ -973,24 +975,22 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int32_t *__restrict__ 
 {
     constexpr int NW = MT_NT / 32;
     __shared__ uint32_t hist[NW][TC_HIST];
-    __shared__ uint32_t vrun[NW][2048 / 32];  // scanned runs (R <= 2048)
     __shared__ float sd[NW][32 * E];
     __shared__ int32_t ss[NW][32 * E];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
     if (q >= nq) return;  // whole warps
-    const int R = P * CH, N = R * K;
-    const int64_t base = q * (int64_t)N;
-    for (int w = lane; w < (R + 31) / 32; w += 32) vrun[warp][w] = 0u;
-    __syncwarp();
-    for (int r = lane; r < R; r += 32)
-        if (r % CH < pnch[q * P + r / CH]) atomicOr(&vrun[warp][r >> 5], 1u << (r & 31));
-    __syncwarp();
+    const int2 r0 = qrun[q];
+    const int2 r1 = nphase > 1 ? qrun[nq + q] : make_int2(0, 0);
+    const int N0 = r0.y * K, N = N0 + r1.y * K;
+    // entry i of the query's runs -> its place in part_d / part_i
+    auto at = [&](int i) -> int64_t {
+        return i < N0 ? (int64_t)r0.x * K + i : (int64_t)r1.x * K + (i - N0);
+    };
     auto key = [&](int i) -> uint64_t {
-        const int r = i / K;
-        if (!((vrun[warp][r >> 5] >> (r & 31)) & 1u)) return ~0ull;
-        const int64_t sl = part_i[base + i];
-        return sl < 0 ? ~0ull : ds_key(part_d[base + i], (int32_t)sl);
+        const int64_t e = at(i);
+        const int64_t sl = part_i[e];
+        return sl < 0 ? ~0ull : ds_key(part_d[e], (int32_t)sl);
     };
     int nv = 0;
     for (int i = lane; i < N; i += 32) nv += key(i) != ~0ull;
@@ -1006,8 +1006,8 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int32_t *__restrict__ 
         if (take) {
             const int p = w + __popc(mk & lanemask_lt());
             if (p < 32 * E) {
-                sd[warp][p] = part_d[base + i];
-                ss[warp][p] = (int32_t)part_i[base + i];
+                sd[warp][p] = part_d[at(i)];
+                ss[warp][p] = (int32_t)part_i[at(i)];
             }
         }
         w += __popc(mk);
@@ -1033,13 +1033,13 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int32_t *__restrict__ 
     }
 }
 
-void merge_tc(sivf_index *ix, int64_t nq, int P, const SearchPlan &pl, const SearchScratch &s,
-              int Kc, float *out_d, int64_t *out_s, cudaStream_t st)
+void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc,
+              float *out_d, int64_t *out_s, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
 #define SIVF_MTC(E_)                                                                    \
-    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.pnch, nq, P, pl.ch, Kc, s.part_d, s.part_i, \
+    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, s.part_d, s.part_i, \
                                              out_d, out_s)
     if (Kc <= 32) SIVF_MTC(1);
     else if (Kc <= 64) SIVF_MTC(2);
@@ -1340,8 +1340,9 @@ bool tc_make_maps(sivf_index *ix)
     return true;
 }
 
-// best K' entries + room for one more tile of candidates
-int tc_buf_len(int K) { return (K + TC_M + 7) / 8 * 8; }
+// a row's candidate buffer: its best K' plus room for `tiles` tiles of
+// candidates (TC_M each)
+static int tc_buf_len(int K, int tiles) { return (K + tiles * TC_M + 7) / 8 * 8; }
 
 // queries per tile of the reduced-precision scan for K' candidates
 int tc_tile_queries(int Kc)
@@ -1360,11 +1361,44 @@ static int tc_stages(int KC, int M)
     return nst;
 }
 
+static size_t tc_total(int tn, int KC, int M, int nst)
+{
+    switch (tn) {
+    case 48: return tc_smem<48>(KC, M, nst).total;
+    case 32: return tc_smem<32>(KC, M, nst).total;
+    default: return tc_smem<16>(KC, M, nst).total;
+    }
+}
+
+// Entries of a row's candidate buffer.  A row folds its pending candidates
+// into its best K' once more than (room - 1) tiles of them wait, so with
+// room for one tile any candidate at all costs a fold per tile; the default
+// takes room for two tiles where three A stages still fit beside it (FP8
+// rows), else one.  sel > 0 asks for sel tiles of room.
+int tc_buf_entries(const sivf_index *ix, int dtype, int Kc, int sel)
+{
+    if (sel > 0) return tc_buf_len(Kc, sel);
+    const int esz = dtype == SIVF_BF16 ? 2 : 1;
+    const int KC = (ix->d * esz + 127) / 128;
+    const int tn = tc_tile_queries(Kc);
+    if (tc_total(tn, KC, tc_buf_len(Kc, 2), 3) <= kTcSmemMax) return tc_buf_len(Kc, 2);
+    return tc_buf_len(Kc, 1);
+}
+
+// a buffer of M entries fits beside two A stages
+bool tc_buf_fits(const sivf_index *ix, int dtype, int Kc, int M)
+{
+    const int esz = dtype == SIVF_BF16 ? 2 : 1;
+    const int KC = (ix->d * esz + 127) / 128;
+    const int tn = tc_tile_queries(Kc);
+    return (tn != 16 || Kc <= TcShape<16>::KMAX) && tc_total(tn, KC, M, 2) <= kTcSmemMax;
+}
+
 bool tc_fits(const sivf_index *ix, int Kc)
 {
     const int esz = 2;  // the larger of the two formats
     const int KC = (ix->d * esz + 127) / 128;
-    const int M = tc_buf_len(Kc);
+    const int M = tc_buf_len(Kc, 1);
     switch (tc_tile_queries(Kc)) {
     case 48: return tc_smem<48>(KC, M, 2).total <= kTcSmemMax;
     case 32: return tc_smem<32>(KC, M, 2).total <= kTcSmemMax;
@@ -1395,8 +1429,8 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.nq = nq;
     a.P = P;
     a.K = Kc;
-    a.M = tc_buf_len(Kc);
-    a.CH = pl.ch;
+    a.M = pl.M;
+    a.prun = s.prun;
     a.qlist = s.qlist;
     a.loff = s.loff;
     a.lcnt = s.lcnt;

@@ -30,6 +30,7 @@ enum : uint32_t {
     ERR_STACK = 4u,      // free stack under- or overflow
     ERR_TIMEOUT = 8u,    // an mbarrier wait ran out of iterations
     ERR_SELECT = 16u,    // coarse selection could not place a row
+    ERR_PLAN = 32u,      // a search plan outgrew the scratch sized for it
 };
 
 // batch flags (Ctl::flags)
@@ -50,7 +51,8 @@ struct Ctl {
     int32_t nitems;      // search work items
     int32_t next_item;   // search work-queue cursor
     int32_t nscan;       // (query, list) pairs in the search
-    int32_t pad[7];
+    int32_t nruns;       // search output runs reserved so far
+    int32_t pad[6];
 };
 
 struct SlabMeta {        // 16 bytes per slab

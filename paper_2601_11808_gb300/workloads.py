@@ -9,7 +9,9 @@ stream ``s`` is drawn from ``PCG64(SeedSequence([seed, s, b]))``; a vector's
 value therefore depends only on its position in the stream, never on how a
 caller batches it.  Streams: 0 = mixture centers, 1 = database vectors,
 2 = queries, 3 = extra centroids (sample points, used when there are more
-lists than mixture components).
+lists than mixture components), 12 = the rank permutation of a Zipf-skewed
+mixture (the skewed ingestion workload of the paper's Section 5.4 draws its
+components with probability falling as a power of their rank).
 
 The paper's datasets (SIFT1M, GIST1M, Deep1B, T2I-1B, DINO10B) are not
 available; these mixtures stand in for them with the same dimensions and
@@ -40,9 +42,10 @@ class Workload:
     k: int
     nprobes: tuple = field(default=(8,))
     seed: int = 0
+    zipf: float = 0.0    # > 0: components drawn with P(rank r) ~ r^-zipf
 
 
-# the five workload shapes (sizes, distributions and index parameters)
+# the workload shapes (sizes, distributions and index parameters)
 CONFIGS = {
     "tiny_window": Workload("tiny_window", d=32, n_comp=64, kind="uniform_box",
                             sigma=0.1, nlist=64, slab_size=32, window=20_000,
@@ -64,6 +67,10 @@ CONFIGS = {
                         sigma=0.1, nlist=16384, slab_size=128,
                         window=100_000_000, step=0, n_queries=256, k=10,
                         nprobes=(32,)),
+    "zipf_ingest": Workload("zipf_ingest", d=128, n_comp=1024, kind="sift",
+                            sigma=20.0, nlist=1024, slab_size=64,
+                            window=1_000_000, step=0, n_queries=10_000, k=10,
+                            nprobes=(8,), zipf=1.0),
 }
 
 
@@ -87,14 +94,34 @@ def centers(w: Workload) -> np.ndarray:
     return c.astype(np.float32)
 
 
+def zipf_law(w: Workload):
+    """(probabilities by rank, rank -> component) of a skewed mixture: the
+    component of rank r (1-based) is drawn with probability r^-s / H(n, s),
+    H the generalised harmonic number; which component holds which rank is
+    a seeded permutation (stream 12), so the heavy components are spread
+    over the space rather than being the first rows of `centers`."""
+    r = np.arange(1, w.n_comp + 1, dtype=np.float64)
+    p = r ** -float(w.zipf)
+    p /= p.sum()
+    return p, _rng(w.seed, 12, 0).permutation(w.n_comp)
+
+
+def _components(w: Workload, g: np.random.Generator, law) -> np.ndarray:
+    if law is None:
+        return g.integers(0, w.n_comp, size=BLOCK)
+    p, perm = law
+    return perm[g.choice(w.n_comp, size=BLOCK, p=p)]
+
+
 def _draw(w: Workload, ctr: np.ndarray, stream: int, start: int,
           n: int) -> np.ndarray:
     out = np.empty((n, w.d), np.float32)
     pos = 0
+    law = zipf_law(w) if w.zipf > 0 else None
     b0, b1 = start // BLOCK, (start + n + BLOCK - 1) // BLOCK
     for b in range(b0, b1):
         g = _rng(w.seed, stream, b)
-        comp = g.integers(0, w.n_comp, size=BLOCK)
+        comp = _components(w, g, law)
         noise = g.standard_normal(size=(BLOCK, w.d))
         blk = ctr[comp].astype(np.float64) + w.sigma * noise
         if w.kind == "sift":

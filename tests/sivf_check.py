@@ -8,6 +8,8 @@ import re
 
 import numpy as np
 
+import oracle
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -140,3 +142,111 @@ def compare_topk(gd, gi, od, oi, rtol: float = 1e-5, what: str = ""):
             if gd[r][j] == gd[r][j - 1]:
                 assert gi[r][j] > gi[r][j - 1]
     return ties
+
+
+# ------------------------------------------- reduced-precision candidates
+def approx_oracle(q, xs, dtype, inv_l, cent_l):
+    """FP64 value of the distance the reduced-precision scan approximates,
+    ||q||^2 + ||x||^2 - 2 s q^.x^, for one query q against rows xs, and a
+    magnitude bound for its FP32 accumulation error.  BF16: q^, x^ are the
+    rounded vectors, s = 1.  FP8: q^ and x^ are the E4M3 codes of the
+    residuals from each row's list centroid (cent_l, one row per member),
+    the row's with its list's inverse scale inv_l, the query's with
+    448 / (2 max|q - c_l|); s undoes both scales.  Rows of one list are
+    encoded together."""
+    if dtype == "bf16":
+        q64, x64 = q.astype(np.float64), xs.astype(np.float64)
+        qn = (q64 ** 2).sum()
+        xn = (x64 ** 2).sum(axis=1)
+        qh = oracle.from_bf16(oracle.to_bf16(q)).astype(np.float64)
+        xh = oracle.from_bf16(oracle.to_bf16(xs)).astype(np.float64)
+        prod = xh * qh[None, :]
+        scale = np.ones(len(xs))
+    else:
+        rq = (q[None, :] - cent_l).astype(np.float32)       # per member's list
+        rx = (xs - cent_l).astype(np.float32)
+        qn = (rq.astype(np.float64) ** 2).sum(axis=1)
+        xn = (rx.astype(np.float64) ** 2).sum(axis=1)
+        mx = np.abs(rq).max(axis=1)
+        invq = np.where(mx > 0, np.float32(448.0) / (np.float32(2.0) * mx),
+                        np.float32(1.0)).astype(np.float32)
+        qh = np.empty(rq.shape, np.float64)
+        xh = np.empty(rx.shape, np.float64)
+        crow = np.ascontiguousarray(cent_l, np.float32)
+        rowkey = crow.view(np.dtype((np.void, 4 * crow.shape[1]))).ravel()
+        _, grp = np.unique(rowkey, return_inverse=True)
+        grp = grp.ravel()
+        for gidx in np.unique(grp):
+            sel = np.nonzero(grp == gidx)[0]
+            j = sel[0]
+            assert (inv_l[sel] == inv_l[j]).all()
+            qh[sel] = oracle.from_e4m3(oracle.to_e4m3(rq[j], invq[j]))[None, :]
+            xh[sel] = oracle.from_e4m3(oracle.to_e4m3(rx[sel], inv_l[j]))
+        prod = xh * qh
+        scale = 1.0 / (inv_l.astype(np.float64) * invq.astype(np.float64))
+    dot = prod.sum(axis=1)
+    bound = 2 * np.abs(prod).sum(axis=1) * scale
+    return qn + xn - 2 * scale * dot, qn + xn + bound
+
+
+# ------------------------------------------------ device index beside oracle
+def cuda(t, a, dtype=None):
+    x = t.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        x = x.to(dtype)
+    return x.cuda()
+
+
+class Pair:
+    """A device index and an oracle driven with the same operations."""
+
+    def __init__(self, torch, d, nlist, C, n_max, n_slabs, cent, dir_cap=0, dtypes=()):
+        from paper_2601_11808_gb300.sivf import Index
+        self.t = torch
+        self.g = Index(d, nlist, C, n_max, n_slabs, dir_cap, dtypes)
+        self.o = oracle.OracleIVF(d, nlist, C, n_max, n_slabs, dir_cap or n_slabs)
+        self.C, self.S = C, n_slabs
+        self.g.set_centroids(cuda(torch, cent))
+        self.o.set_centroids(cent)
+
+    def add(self, ids, x):
+        from paper_2601_11808_gb300.sivf import SivfError
+        try:
+            og = self.o.add(ids, x)
+            ost = 0
+        except oracle.OracleError as e:
+            og, ost = 0, e.status
+        try:
+            gg = self.g.add(cuda(self.t, np.asarray(ids, np.int64)),
+                            cuda(self.t, np.asarray(x, np.float32).reshape(-1, self.g.d)),
+                            sync=True)
+            gst = 0
+        except SivfError as e:
+            gg, gst = 0, e.status
+        assert (gst, gg) == (ost, og), f"add status/count {gst, gg} != oracle {ost, og}"
+        return gst
+
+    def remove(self, ids):
+        from paper_2601_11808_gb300.sivf import SivfError
+        try:
+            og, ost = self.o.remove(ids), 0
+        except oracle.OracleError as e:
+            og, ost = 0, e.status
+        try:
+            gg = self.g.remove(cuda(self.t, np.asarray(ids, np.int64)), sync=True)
+            gst = 0
+        except SivfError as e:
+            gg, gst = 0, e.status
+        assert (gst, gg) == (ost, og), f"remove status/count {gst, gg} != oracle {ost, og}"
+        return gst
+
+    def check(self):
+        compare_state(self.g.dump(), self.o, self.C, self.S)
+        assert self.g.stats()["ntotal"] == self.o.ntotal
+        np.testing.assert_array_equal(
+            self.g.list_sizes(), [self.o.list_size(l) for l in range(self.g.nlist)])
+
+    def search(self, q, k, P):
+        gd, gi = self.g.search(cuda(self.t, q), k, P)
+        od, oi = self.o.search(q, k, P)
+        return gd.cpu().numpy(), gi.cpu().numpy(), od, oi

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from sivf_check import build_lib, check_invariants, compare_state, compare_topk
+from sivf_check import Pair, build_lib, check_invariants, compare_topk, cuda
 from paper_2601_11808_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -23,68 +23,6 @@ def torch():
     import torch as t
     build_lib()
     return t
-
-
-def cuda(t, a, dtype=None):
-    x = t.from_numpy(np.ascontiguousarray(a))
-    if dtype is not None:
-        x = x.to(dtype)
-    return x.cuda()
-
-
-class Pair:
-    """A device index and an oracle driven with the same operations."""
-
-    def __init__(self, torch, d, nlist, C, n_max, n_slabs, cent, dir_cap=0, dtypes=()):
-        from paper_2601_11808_gb300.sivf import Index
-        self.t = torch
-        self.g = Index(d, nlist, C, n_max, n_slabs, dir_cap, dtypes)
-        self.o = oracle.OracleIVF(d, nlist, C, n_max, n_slabs, dir_cap or n_slabs)
-        self.C, self.S = C, n_slabs
-        self.g.set_centroids(cuda(torch, cent))
-        self.o.set_centroids(cent)
-
-    def add(self, ids, x):
-        from paper_2601_11808_gb300.sivf import SivfError
-        try:
-            og = self.o.add(ids, x)
-            ost = 0
-        except oracle.OracleError as e:
-            og, ost = 0, e.status
-        try:
-            gg = self.g.add(cuda(self.t, np.asarray(ids, np.int64)),
-                            cuda(self.t, np.asarray(x, np.float32).reshape(-1, self.g.d)),
-                            sync=True)
-            gst = 0
-        except SivfError as e:
-            gg, gst = 0, e.status
-        assert (gst, gg) == (ost, og), f"add status/count {gst, gg} != oracle {ost, og}"
-        return gst
-
-    def remove(self, ids):
-        from paper_2601_11808_gb300.sivf import SivfError
-        try:
-            og, ost = self.o.remove(ids), 0
-        except oracle.OracleError as e:
-            og, ost = 0, e.status
-        try:
-            gg = self.g.remove(cuda(self.t, np.asarray(ids, np.int64)), sync=True)
-            gst = 0
-        except SivfError as e:
-            gg, gst = 0, e.status
-        assert (gst, gg) == (ost, og), f"remove status/count {gst, gg} != oracle {ost, og}"
-        return gst
-
-    def check(self):
-        compare_state(self.g.dump(), self.o, self.C, self.S)
-        assert self.g.stats()["ntotal"] == self.o.ntotal
-        np.testing.assert_array_equal(
-            self.g.list_sizes(), [self.o.list_size(l) for l in range(self.g.nlist)])
-
-    def search(self, q, k, P):
-        gd, gi = self.g.search(cuda(self.t, q), k, P)
-        od, oi = self.o.search(q, k, P)
-        return gd.cpu().numpy(), gi.cpu().numpy(), od, oi
 
 
 # ------------------------------------------------------------ coarse steps

@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
-from sivf_check import build_lib
+from sivf_check import approx_oracle as _approx_oracle, build_lib
 from paper_2601_11808_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -77,34 +77,6 @@ def test_encodings_bit_exact(torch, w):
         resid = (xl[sel] - cent[l]).astype(np.float32)
         np.testing.assert_array_equal(pay["x8"][rows[sel]], oracle.to_e4m3(resid, inv[l]))
     np.testing.assert_array_equal(pay["x32"][rows], xl)
-
-
-def _approx_oracle(q, xs, dtype, inv_l, cent_l):
-    """FP64 ||q||^2 + ||x||^2 - 2 s q^.x^ with the oracle's encoders (FP8:
-    residuals from each member's list centroid cent_l)."""
-    if dtype == "bf16":
-        q64, x64 = q.astype(np.float64), xs.astype(np.float64)
-        qn = (q64 ** 2).sum()
-        xn = (x64 ** 2).sum(axis=1)
-        qh = oracle.from_bf16(oracle.to_bf16(q)).astype(np.float64)
-        xh = oracle.from_bf16(oracle.to_bf16(xs)).astype(np.float64)
-        prod = xh * qh[None, :]
-        scale = np.ones(len(xs))
-    else:
-        rq = (q[None, :] - cent_l).astype(np.float32)       # per member's list
-        rx = (xs - cent_l).astype(np.float32)
-        qn = (rq.astype(np.float64) ** 2).sum(axis=1)
-        xn = (rx.astype(np.float64) ** 2).sum(axis=1)
-        mx = np.abs(rq).max(axis=1)
-        invq = np.where(mx > 0, np.float32(448.0) / (np.float32(2.0) * mx),
-                        np.float32(1.0)).astype(np.float32)
-        qh = np.stack([oracle.from_e4m3(oracle.to_e4m3(v, s)) for v, s in zip(rq, invq)])
-        xh = np.stack([oracle.from_e4m3(oracle.to_e4m3(v, il)) for v, il in zip(rx, inv_l)])
-        prod = xh * qh
-        scale = 1.0 / (inv_l.astype(np.float64) * invq.astype(np.float64))
-    dot = prod.sum(axis=1)
-    bound = 2 * np.abs(prod).sum(axis=1) * scale
-    return qn + xn - 2 * scale * dot, qn + xn + bound
 
 
 W_LONG = W.small("sift_window", n_comp=16, nlist=16, slab_size=64)
