@@ -71,6 +71,8 @@ def parse():
                    help="skip the deep-precision (k=100) workload")
     p.add_argument("--no-train", action="store_true",
                    help="skip the quantizer-training measurement")
+    p.add_argument("--no-compact", action="store_true",
+                   help="skip the compaction measurement")
     p.add_argument("--no-zipf", action="store_true",
                    help="skip the Zipf-skewed ingestion workload")
     p.add_argument("--forms", default="fp32,bf16,fp8",
@@ -732,6 +734,62 @@ def run_zipf(torch, sivf, dev, reps=3, n_truth=100, batch=10_000):
     }
 
 
+def run_compact(torch, sivf, dev, frac=0.5, reps=3):
+    """Compaction of partly-live slabs: the SIFT-shaped window (1,000,000
+    vectors d=128, nlist=1024, slab 64, FP8 copy) with a uniformly random
+    half of its ids deleted, then one full pass (min_free 1, no budget):
+    kernel time of the pass (the library's CUDA-event profile), slabs freed,
+    members moved, and the FP8 search (10,000 queries, k=10, nprobe=8)
+    before and after it."""
+    w = W.CONFIGS["sift_window"]
+    n, P = w.window, 8
+    ctr = W.centers(w)
+    S = int(1.25 * (n // w.slab_size + 2 * w.nlist))
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n, S, scan_dtypes=("fp8",))
+    g.set_centroids(torch.from_numpy(W.index_centroids(w, ctr)).to(dev))
+    X = W.vectors_threaded(w, 0, n, ctr)
+    g.add(torch.from_numpy(W.stream_ids(0, n, n)).to(dev), torch.from_numpy(X).to(dev))
+    del X
+    gone = W.sample_ids(w.seed, 14, 0, W.stream_ids(0, n, n), int(frac * n))
+    g.remove(torch.from_numpy(gone).to(dev))
+    g.sync()
+    Qd = torch.from_numpy(W.queries(w, 0, w.n_queries, ctr)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def search_ms():
+        for _ in range(2):
+            g.search(Qd, w.k, P, "fp8")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.search(Qd, w.k, P, "fp8")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    used0 = g.stats()["used_slabs"]
+    before = search_ms()
+    g.profile(True)
+    freed, moved = g.compact(1, 1 << 40, sync=True)
+    pass_ms = g.profile_read("compact")[1]
+    g.profile(False)
+    used1 = g.stats()["used_slabs"]
+    after = search_ms()
+    g.close()
+    del Qd
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"sift_window (1,000,000 vectors, nlist 1024, slab 64) with a random "
+                    f"{frac:.0%} of ids deleted; one compaction pass (min_free 1, no budget); "
+                    f"FP8 search of 10,000 queries, k=10, nprobe=8",
+        "pass_ms": round(pass_ms, 3), "slabs_freed": int(freed), "members_moved": int(moved),
+        "moved_per_s": round(moved / (pass_ms / 1e3), 1) if pass_ms > 0 else None,
+        "slabs_used_before": int(used0), "slabs_used_after": int(used1),
+        "search_ms_before": round(before, 3), "search_ms_after": round(after, 3),
+    }
+
+
 def oracle_zipf_sample(n=100_000):
     """The oracle's ingestion of the first n rows of the skewed stream."""
     import oracle
@@ -998,6 +1056,8 @@ def main():
         line["components"]["train"] = run_train(torch, sivf, dev)
     if not args.no_zipf:
         line["components"]["zipf_ingest"] = run_zipf(torch, sivf, dev)
+    if not args.no_compact:
+        line["components"]["compaction"] = run_compact(torch, sivf, dev)
     if not args.no_serving:
         line["components"]["serving"] = run_serving(
             torch, sivf, dev, args.serving_window, args.serving_seconds)

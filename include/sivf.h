@@ -207,8 +207,9 @@ sivf_status sivf_add(sivf_index *index, const int64_t *ids, const float *x,
 /*
  * sivf_remove -- batched delete (Algorithm 4: address-table lookup, atomic
  * clear of the validity bit, live-count decrement; a slab whose live count
- * reaches zero leaves its list and returns to the free stack).  No
- * compaction.  Absent and repeated ids are no-ops (Theorem 3).
+ * reaches zero leaves its list and returns to the free stack).  Holes are
+ * not refilled here (sivf_compact does that on request).  Absent and
+ * repeated ids are no-ops (Theorem 3).
  *   ids [device] int64[n]; an id outside [0, n_max) rejects the batch with
  *   SIVF_E_ARG and nothing changes.
  * n_removed [host, optional]: if non-NULL the call forces a sync, stores the
@@ -216,6 +217,27 @@ sivf_status sivf_add(sivf_index *index, const int64_t *ids, const float *x,
  */
 sivf_status sivf_remove(sivf_index *index, const int64_t *ids, int64_t n,
                         void *stream, int64_t *n_removed);
+
+/*
+ * sivf_compact -- one pass of compaction of partly-live slabs.  Deletes
+ * leave holes (a slab returns to the pool only when its last vector goes);
+ * the paper names adaptive background compaction as future work
+ * (Conclusion) and gives no algorithm, so this is a reading of it: a list
+ * whose live members would fit in at least `min_free` (>= 1) fewer slabs is
+ * rewritten densely in its member order (slab position, then slot): member
+ * j moves to slot j mod C of the list's (j div C)-th slab, with its FP32
+ * row, reduced-precision copies, norms, id and address-table entry; the
+ * list keeps its first ceil(n / C) slabs (the last one stays open for
+ * appends) and the rest go back on the free stack.  Lists are taken in
+ * index order while the running total of rewritten members stays within
+ * `max_moves` (>= 1); the first list that would pass it ends the pass.
+ * Membership, member order and every search result are unchanged.  Scratch
+ * grows by about max_moves rows (capped at n_max).
+ * n_freed, n_moved [host, optional]: if either is non-NULL the call syncs
+ * and stores the slabs returned to the pool and the members rewritten.
+ */
+sivf_status sivf_compact(sivf_index *index, int32_t min_free, int64_t max_moves,
+                         void *stream, int64_t *n_freed, int64_t *n_moved);
 
 /*
  * sivf_search -- batched k-NN (Algorithm 3 redone list-centrically): coarse

@@ -56,6 +56,7 @@ def load_lib(path: str):
         "oivf_exact_knn": (i32, [p, p, i64, i32, p, p]),
         "oivf_add": (i32, [p, p, p, i64, p]),
         "oivf_remove": (i32, [p, p, i64, p]),
+        "oivf_compact": (i32, [p, i32, i64, p, p]),
         "oivf_ntotal": (i64, [p]),
         "oivf_free_slabs": (i64, [p]),
         "oivf_list_of": (C.c_int32, [p, i64]),
@@ -163,6 +164,15 @@ class OracleIVF:
         if st:
             raise OracleError(st)
         return int(out[0])
+
+    def compact(self, min_free: int = 1, max_moves: int = 1 << 62):
+        """Compaction pass: (slabs freed, members rewritten)."""
+        fr = np.zeros(1, np.int64)
+        mv = np.zeros(1, np.int64)
+        st = self._lib.oivf_compact(self._h, int(min_free), int(max_moves), _ptr(fr), _ptr(mv))
+        if st:
+            raise OracleError(st)
+        return int(fr[0]), int(mv[0])
 
     # -- queries ---------------------------------------------------------
     def assign(self, x) -> np.ndarray:

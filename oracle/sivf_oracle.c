@@ -37,6 +37,15 @@
  *     capacity, (3) remove every kept id that is currently live, (4) append
  *     the kept ids in batch order.  remove(batch) removes each live id once;
  *     absent ids are no-ops.
+ *   - compaction of partly-live slabs (the adaptive background compaction
+ *     the conclusion names as future work; a reading, the paper gives no
+ *     algorithm): a list whose live members would fit in at least
+ *     `min_free` fewer slabs is rewritten densely in its own member order
+ *     -- member j goes to slot j mod C of the list's (j div C)-th slab, the
+ *     list keeps its oldest ceil(n / C) slabs and the rest go back to the
+ *     pool.  Lists are taken in index order while the running total of
+ *     rewritten members stays within `max_moves`; the first list that would
+ *     pass it ends the pass.
  *   - reduced-precision encodings used by the precision path: bfloat16 with
  *     round-to-nearest-even, and FP8 E4M3 (OCP "fn" variant: bias 7, no
  *     infinities, max finite 448) with round-to-nearest-even and saturation
@@ -483,6 +492,52 @@ int oivf_remove(oivf *o, const int64_t *ids, int64_t n, int64_t *n_removed)
         ++cnt;
     }
     if (n_removed) *n_removed = cnt;
+    return O_OK;
+}
+
+/* Compaction (see the header): rewrite list l densely in member order. */
+static void compact_list(oivf *o, int l)
+{
+    olist *L = &o->lists[l];
+    const int64_t keep = (L->n + o->C - 1) / o->C;
+    for (int64_t j = 0; j < L->n; ++j) {
+        L->rec[j] = L->recs[j / o->C];
+        L->slot[j] = (int32_t)(j % o->C);
+    }
+    for (int64_t r = 0; r < L->nrec; ++r) {
+        orec *R = &o->recs[L->recs[r]];
+        if (r < keep) {
+            int64_t f = L->n - r * o->C;
+            R->fill = (int32_t)(f < o->C ? f : o->C);
+            R->live = R->fill;
+        } else {
+            R->list = -1;
+            R->fill = 0;
+            R->live = 0;
+        }
+    }
+    o->free_slabs += L->nrec - keep;
+    L->nrec = keep;
+}
+
+int oivf_compact(oivf *o, int32_t min_free, int64_t max_moves, int64_t *n_freed,
+                 int64_t *n_moved)
+{
+    if (n_freed) *n_freed = 0;
+    if (n_moved) *n_moved = 0;
+    if (min_free < 1 || max_moves < 1) return O_E_ARG;
+    int64_t moved = 0, freed = 0;
+    for (int l = 0; l < o->nlist; ++l) {
+        const olist *L = &o->lists[l];
+        const int64_t keep = (L->n + o->C - 1) / o->C;
+        if (L->nrec - keep < min_free) continue;
+        if (moved + L->n > max_moves) break;
+        moved += L->n;
+        freed += L->nrec - keep;
+        compact_list(o, l);
+    }
+    if (n_freed) *n_freed = freed;
+    if (n_moved) *n_moved = moved;
     return O_OK;
 }
 

@@ -574,6 +574,73 @@ sivf_status sivf_remove(sivf_index *ix, const int64_t *ids, int64_t n, void *str
     return SIVF_OK;
 }
 
+sivf_status sivf_compact(sivf_index *ix, int32_t min_free, int64_t max_moves, void *stream,
+                         int64_t *n_freed, int64_t *n_moved)
+{
+    if (n_freed) *n_freed = 0;
+    if (n_moved) *n_moved = 0;
+    if (!ix) return SIVF_E_ARG;
+    if (min_free < 1 || max_moves < 1) return fail(ix, SIVF_E_ARG, "bad compact arguments");
+    sivf_status st = check_health(ix);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = ix->nlist, d = ix->d;
+    // staged rows: at most max_moves members, and never more than n_max
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(max_moves, ix->n_max));
+    const size_t row = (size_t)d * 4 + (ix->xb16 ? (size_t)d * 2 : 0) + (ix->x8 ? (size_t)d : 0) +
+                       4 + (ix->rnorm ? 4 : 0) + 8;
+    const size_t need = (size_t)L * 4 + (size_t)(L + 1) * 16 + (size_t)ix->n_slabs * 4 +
+                        (size_t)R * row + 10 * 256;
+    Ctx *c;
+    if ((st = get_ctx(ix, stream, need, &c))) return st;
+    Bump b{c->scratch};
+    CompactArgs a;
+    a.L = L;
+    a.C = ix->C;
+    a.W = ix->W;
+    a.d = d;
+    a.n_slabs = ix->n_slabs;
+    a.dir_cap = ix->dir_cap;
+    a.n_max = ix->n_max;
+    a.list_live = ix->list_live;
+    a.nslabs = ix->nslabs;
+    a.dir = ix->dir;
+    a.head = ix->head;
+    a.free_list = ix->free_list;
+    a.free_top = ix->free_top;
+    a.bits = ix->bits;
+    a.meta = ix->meta;
+    a.x32 = ix->x32;
+    a.xnorm = ix->xnorm;
+    a.rnorm = ix->rnorm;
+    a.xb16 = ix->xb16;
+    a.x8 = ix->x8;
+    a.ids = ix->ids;
+    a.att = ix->att;
+    a.sel = b.take<int32_t>(L);
+    a.voff = b.take<int64_t>(L + 1);
+    a.soff = b.take<int64_t>(L + 1);
+    a.sb = b.take<int32_t>(ix->n_slabs);
+    a.t32 = b.take<float>((size_t)R * d);
+    a.t16 = ix->xb16 ? b.take<__nv_bfloat16>((size_t)R * d) : nullptr;
+    a.t8 = ix->x8 ? b.take<uint8_t>((size_t)R * d) : nullptr;
+    a.tn = b.take<float>(R);
+    a.tr = ix->rnorm ? b.take<float>(R) : nullptr;
+    a.ti = b.take<int64_t>(R);
+    a.ctl = c->ctl;
+    a.err = ix->err;
+    CUDA_TRY(ix, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));
+    compact_pass(ix, a, min_free, std::min<int64_t>(max_moves, R), s);
+    CUDA_TRY(ix, cudaGetLastError());
+    if (n_freed || n_moved) {
+        st = read_status(ix, stream, nullptr);
+        if (st) return st;
+        if (n_freed) *n_freed = c->host->demand;
+        if (n_moved) *n_moved = c->host->count;
+    }
+    return SIVF_OK;
+}
+
 }  // extern "C"
 
 namespace sivf {
@@ -855,7 +922,7 @@ sivf_status sivf_profile_read(sivf_index *ix, const char *kernel, int64_t *launc
 {
     if (!ix || !kernel) return fail(ix, SIVF_E_ARG, "null argument");
     static const char *names[PROF_NKIND] = {"coarse", "insert", "remove", "group", "scan",
-                                            "merge", "rerank"};
+                                            "merge", "rerank", "compact"};
     int kind = -1;
     for (int k = 0; k < PROF_NKIND; ++k)
         if (!strcmp(kernel, names[k])) kind = k;

@@ -119,6 +119,35 @@ void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, in
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
 
+// ---- compaction of partly-live slabs (compact.cu)
+struct CompactArgs {
+    int L, C, W, d;
+    int64_t n_slabs, dir_cap, n_max;
+    const int32_t *list_live;
+    int32_t *nslabs, *dir, *head, *free_list, *free_top;
+    uint32_t *bits;
+    SlabMeta *meta;
+    float *x32, *xnorm, *rnorm;
+    __nv_bfloat16 *xb16;
+    uint8_t *x8;
+    int64_t *ids, *att;
+    // scratch: selected lists, their member and slab offsets [L + 1], the
+    // live members before each of their slabs, and the staged rows
+    int32_t *sel;
+    int64_t *voff, *soff;
+    int32_t *sb;
+    float *t32, *tn, *tr;
+    __nv_bfloat16 *t16;
+    uint8_t *t8;
+    int64_t *ti;
+    Ctl *ctl;
+    uint32_t *err;
+};
+// one pass; the control block receives the lists (ntouched), the members
+// rewritten (count) and the slabs freed (demand)
+void compact_pass(sivf_index *ix, const CompactArgs &a, int min_free, int64_t max_moves,
+                  cudaStream_t st);
+
 // ---- C-ABI internals shared with the executor (abi.cu)
 size_t op_need(const sivf_index *ix, const sivf_op &op);   // scratch of one batch
 sivf_status reserve_stream(sivf_index *ix, void *stream, size_t need, int64_t max_add);

@@ -71,7 +71,7 @@ struct PlanEntry {       // per list touched by an insert batch
 
 // Kernel groups timed by the profiler (sivf_profile / sivf_profile_read).
 enum ProfKind { PROF_COARSE = 0, PROF_INSERT, PROF_REMOVE, PROF_GROUP, PROF_SCAN,
-                PROF_MERGE, PROF_RERANK, PROF_NKIND };
+                PROF_MERGE, PROF_RERANK, PROF_COMPACT, PROF_NKIND };
 
 struct ProfEvent {
     int kind;

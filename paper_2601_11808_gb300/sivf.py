@@ -28,7 +28,7 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
     "sivf_train", "sivf_get_centroids", "sivf_save", "sivf_load",
-    "sivf_reserve", "sivf_add", "sivf_remove", "sivf_search",
+    "sivf_reserve", "sivf_add", "sivf_remove", "sivf_compact", "sivf_search",
     "sivf_search_with_probes", "sivf_search_noalloc", "sivf_search_candidates",
     "sivf_assign", "sivf_probe", "sivf_sync",
     "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
@@ -130,6 +130,7 @@ def load(path: str | None = None):
             "sivf_reserve": (i32, [vp, i64, i64, i64, i32, i32, vp]),
             "sivf_add": (i32, [vp, vp, vp, i64, vp, C.POINTER(i64)]),
             "sivf_remove": (i32, [vp, vp, i64, vp, C.POINTER(i64)]),
+            "sivf_compact": (i32, [vp, i32, i64, vp, C.POINTER(i64), C.POINTER(i64)]),
             "sivf_search": (i32, [vp, vp, i64, i32, i32, i32, vp, vp, vp]),
             "sivf_search_with_probes": (i32, [vp, vp, i64, i32, i32, vp, i32, vp, vp, vp]),
             "sivf_search_noalloc": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
@@ -290,6 +291,16 @@ def sivf_remove(h, ids, stream=None, sync=False):
                          C.byref(out) if sync else None)
     _check(lib, h, st)
     return out.value if sync else None
+
+
+def sivf_compact(h, min_free=1, max_moves=1 << 40, stream=None, sync=False):
+    """One compaction pass; with sync, (slabs freed, members rewritten)."""
+    lib = load()
+    fr, mv = C.c_int64(0), C.c_int64(0)
+    st = lib.sivf_compact(h, int(min_free), int(max_moves), _stream(stream),
+                          C.byref(fr) if sync else None, C.byref(mv) if sync else None)
+    _check(lib, h, st)
+    return (fr.value, mv.value) if sync else None
 
 
 def sivf_search(h, q, k, nprobe, dtype=FP32, dist=None, labels=None, stream=None):
@@ -714,6 +725,9 @@ class Index:
 
     def remove(self, ids, stream=None, sync=False):
         return sivf_remove(self.h, ids, stream, sync)
+
+    def compact(self, min_free=1, max_moves=1 << 40, stream=None, sync=True):
+        return sivf_compact(self.h, min_free, max_moves, stream, sync)
 
     def search(self, q, k, nprobe, dtype="fp32", stream=None, dist=None, labels=None):
         return sivf_search(self.h, q, k, nprobe, DTYPES[dtype], dist, labels, stream)

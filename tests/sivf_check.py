@@ -240,6 +240,12 @@ class Pair:
         assert (gst, gg) == (ost, og), f"remove status/count {gst, gg} != oracle {ost, og}"
         return gst
 
+    def compact(self, min_free=1, max_moves=1 << 40):
+        og = self.o.compact(min_free, max_moves)
+        gg = self.g.compact(min_free, max_moves, sync=True)
+        assert gg == og, f"compact (freed, moved) {gg} != oracle {og}"
+        return gg
+
     def check(self):
         compare_state(self.g.dump(), self.o, self.C, self.S)
         assert self.g.stats()["ntotal"] == self.o.ntotal

@@ -4,7 +4,8 @@ catch every one.
 Each mutant is one textual change to ``oracle/sivf_oracle.c`` (a dropped
 coordinate, a wrong sign, ties sent to the wrong index, a top-k off by one,
 first- instead of last-occurrence-wins, an overwrite that forgets the old
-copy, a slab never returned, rounding by truncation, ties away from even).
+copy, a slab never returned, rounding by truncation, ties away from even,
+compaction slots, the last slab's fill, budget or threshold off by one).
 The mutant is compiled into a temporary library, swapped in for the real
 oracle, and the pin tests of ``test_oracle_pins.py`` are run against it: at
 least one must fail.  The real oracle source is never modified.
@@ -30,6 +31,14 @@ MUTANTS = {
     "overwrite_keeps_old_copy": ("if (win[i] && o->where[ids[i]] >= 0) erase(o, ids[i]);",
                                  ";"),
     "slab_never_returned": ("o->free_slabs += 1;", ";"),
+    "compact_slots_reversed": ("L->slot[j] = (int32_t)(j % o->C);",
+                               "L->slot[j] = (int32_t)(o->C - 1 - j % o->C);"),
+    "compact_last_slab_full": ("R->fill = (int32_t)(f < o->C ? f : o->C);",
+                               "R->fill = (int32_t)o->C;"),
+    "compact_budget_exclusive": ("if (moved + L->n > max_moves) break;",
+                                 "if (moved + L->n >= max_moves) break;"),
+    "compact_min_free_off_by_one": ("if (L->nrec - keep < min_free) continue;",
+                                    "if (L->nrec - keep <= min_free) continue;"),
     "bf16_truncates": ("if (lower > 0x8000u || (lower == 0x8000u && (upper & 1u))) upper += 1;",
                        ";"),
     "e4m3_ties_up": ("if (dd < bd || (dd == bd && (c & 1) == 0 && (best & 1) == 1)) {",
@@ -53,6 +62,9 @@ PINS = [
     (pins.test_sliding_window_frees_oldest_slab, {}),
     (pins.test_bf16_matches_torch_rne, {}),
     (pins.test_e4m3_matches_torch_in_range_and_saturates, {}),
+    (pins.test_compact_worked_example, {}),
+    (pins.test_compact_min_free_and_budget_rules, {}),
+    (pins.test_compact_keeps_search_and_members, {}),
 ]
 
 

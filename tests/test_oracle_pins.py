@@ -533,3 +533,91 @@ def test_fp8_list_scales_closed_form():
     np.testing.assert_array_equal(oracle.fp8_list_scales(one), np.float32([448 / 5]))
     np.testing.assert_array_equal(oracle.fp8_list_scales(np.zeros((1, 4), np.float32)),
                                   np.float32([1.0]))
+
+
+# ------------------------------------------------------------ compaction
+def _one_list(C=4, n=10):
+    o = OracleIVF(2, 1, slab_size=C, n_max=64, n_slabs=16)
+    o.set_centroids(np.zeros((1, 2), np.float32))
+    o.add(np.arange(n), np.arange(2 * n, dtype=np.float32).reshape(n, 2))
+    return o
+
+
+def test_compact_worked_example():
+    """C = 4, ids 0..9 appended in order (slabs [0 1 2 3] [4 5 6 7] [8 9]);
+    deleting 0, 1, 2, 5, 8 leaves 5 live members in 3 slabs.  Compaction
+    rewrites them densely in member order -- 3 4 6 7 in slab 0, 9 in slab 1
+    -- and returns slab 2 to the pool; the next insert lands in slab 1,
+    slot 1."""
+    o = _one_list()
+    o.remove([0, 1, 2, 5, 8])
+    free0 = o.free_slabs
+    assert [x.tolist() for x in o.list_slabs(0)] == [[4, 4, 2], [1, 3, 1]]
+    assert o.compact(min_free=1) == (1, 5)
+    ids, seq, slot = o.list_members(0)
+    assert ids.tolist() == [3, 4, 6, 7, 9]
+    assert seq.tolist() == [0, 0, 0, 0, 1]
+    assert slot.tolist() == [0, 1, 2, 3, 0]
+    assert [x.tolist() for x in o.list_slabs(0)] == [[4, 1], [4, 1]]
+    assert o.free_slabs == free0 + 1
+    o.add([10], [[0.5, 0.5]])
+    ids, seq, slot = o.list_members(0)
+    assert (ids[-1], seq[-1], slot[-1]) == (10, 1, 1)
+    assert [x.tolist() for x in o.list_slabs(0)] == [[4, 2], [4, 2]]
+    # nothing left to free: a second pass is a no-op
+    assert o.compact(min_free=1) == (0, 0)
+
+
+def test_compact_min_free_and_budget_rules():
+    """A list is compacted only when it frees at least min_free slabs; lists
+    are taken in index order until the next one would pass max_moves."""
+    o = OracleIVF(1, 2, slab_size=4, n_max=64, n_slabs=32)
+    o.set_centroids(np.array([[0.0], [100.0]], np.float32))
+    o.add(np.arange(16), np.zeros((16, 1), np.float32))            # list 0: 4 slabs
+    o.add(np.arange(16, 32), np.full((16, 1), 100.0, np.float32))  # list 1: 4 slabs
+    o.remove([1, 2, 3, 5, 6, 7])          # list 0: 10 live -> 3 slabs, frees 1
+    o.remove([16, 17, 18, 20, 21, 22, 24, 25, 26])  # list 1: 7 live -> 2 slabs, frees 2
+    assert o.compact(min_free=3) == (0, 0)
+    assert o.compact(min_free=2, max_moves=6) == (0, 0)       # list 1 alone needs 7
+    assert o.compact(min_free=1, max_moves=9) == (0, 0)       # list 0 (10) ends the pass
+    assert o.compact(min_free=1, max_moves=16) == (1, 10)     # list 0 only
+    assert [len(x) for x in o.list_slabs(0)] == [3, 3]
+    assert o.compact(min_free=1, max_moves=7) == (2, 7)       # then list 1
+    assert [x.tolist() for x in o.list_slabs(1)] == [[4, 3], [4, 3]]
+    with pytest.raises(OracleError):
+        o.compact(min_free=0)
+
+
+def test_compact_keeps_search_and_members():
+    """Random inserts and deletes, then compaction: every list's members keep
+    their order and become dense, the freed slab count is the sum over lists
+    of (slabs - ceil(n / C)), and every search returns the same result."""
+    rng = np.random.default_rng(7)
+    d, L, C = 8, 6, 8
+    cent = rng.standard_normal((L, d)).astype(np.float32)
+    o = OracleIVF(d, L, slab_size=C, n_max=4000, n_slabs=800)
+    o.set_centroids(cent)
+    x = (cent[rng.integers(0, L, 3000)] + 0.3 * rng.standard_normal((3000, d))).astype(np.float32)
+    o.add(np.arange(3000), x)
+    o.remove(rng.choice(3000, 1900, replace=False))
+    q = rng.standard_normal((40, d)).astype(np.float32)
+    before = [o.search(q, 7, P) for P in (1, 3, L)]
+    members = [o.list_members(l)[0].copy() for l in range(L)]
+    before_slabs = [o.list_slabs(l)[0].copy() for l in range(L)]
+    expect = sum(len(o.list_slabs(l)[0]) - (o.list_size(l) + C - 1) // C for l in range(L))
+    free0 = o.free_slabs
+    freed, moved = o.compact(min_free=1)
+    assert freed == expect > 0 and o.free_slabs == free0 + freed
+    fragmented = [l for l in range(L)
+                  if len(o.list_slabs(l)[0]) < len(before_slabs[l])]
+    assert moved == sum(o.list_size(l) for l in fragmented)
+    for l in range(L):
+        ids, seq, slot = o.list_members(l)
+        np.testing.assert_array_equal(ids, members[l])
+        j = np.arange(len(ids))
+        np.testing.assert_array_equal(seq, j // C)
+        np.testing.assert_array_equal(slot, j % C)
+    for (bd, bi), P in zip(before, (1, 3, L)):
+        ad, ai = o.search(q, 7, P)
+        np.testing.assert_array_equal(ad, bd)
+        np.testing.assert_array_equal(ai, bi)
