@@ -409,6 +409,8 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
 // 0), accumulator in 256 TMEM columns; four warps read their TMEM lane
 // quarter back.
 constexpr int CT_M = 128, CT_N = 256;
+constexpr int CT_NT = 256;  // threads: 8 warps, two per TMEM lane quarter in the epilogue
+constexpr int CT_AU = 4;    // A chunks each thread loads before converting
 
 __host__ __device__ inline size_t coarse_tc_smem(int d, int split)
 {
@@ -424,11 +426,11 @@ __device__ __forceinline__ void cp_async16_c(void *dst, const void *src, uint32_
 }
 
 template <int SPLIT>
-__global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ x, int m, int d,
-                                                      const uint16_t *__restrict__ cb,
-                                                      const uint16_t *__restrict__ clo,
-                                                      const float *__restrict__ cn, int L,
-                                                      float *__restrict__ out, uint32_t *err)
+__global__ __launch_bounds__(CT_NT, 1) void k_coarse_tc(const float *__restrict__ x, int m, int d,
+                                                        const uint16_t *__restrict__ cb,
+                                                        const uint16_t *__restrict__ clo,
+                                                        const float *__restrict__ cn, int L,
+                                                        float *__restrict__ out, uint32_t *err)
 {
     constexpr int NP = SPLIT == 3 ? 2 : 1;  // hi (and lo) parts
     extern __shared__ unsigned char smem_raw[];
@@ -450,7 +452,7 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
     for (int pp = 0; pp < NP; ++pp) {
         const uint16_t *src0 = pp ? clo : cb;
         unsigned char *Bp = B + (size_t)pp * KC * CT_N * 128;
-        for (int e = tid; e < CT_N * KC * 8; e += 128) {
+        for (int e = tid; e < CT_N * KC * 8; e += CT_NT) {
             const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
             const int k0 = kc * 64 + c * 8;  // first element of the 16-byte chunk
             const bool in = col0 + r < L && k0 < d;
@@ -461,15 +463,31 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
         }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    // A: rows of x rounded to BF16 (round to nearest even); zero past m or d
-    for (int e = tid; e < CT_M * KC * 8; e += 128) {
-        const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
-        const int k0 = kc * 64 + c * 8;
-        uint32_t w[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
-        if (row0 + r < m && k0 < d) {
-            const float4 *xr = reinterpret_cast<const float4 *>(x + (size_t)(row0 + r) * d + k0);
-            const float4 f0 = __ldg(xr), f1 = __ldg(xr + 1);
-            const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    // A: rows of x rounded to BF16 (round to nearest even); zero past m or d.
+    // Each thread loads CT_AU chunks before converting any (loads in flight)
+    const int nA = CT_M * KC * 8;
+    for (int e0 = tid; e0 < nA; e0 += CT_NT * CT_AU) {
+        float4 f0[CT_AU], f1[CT_AU];
+#pragma unroll
+        for (int u = 0; u < CT_AU; ++u) {
+            const int e = e0 + u * CT_NT;
+            const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
+            const int k0 = kc * 64 + c * 8;
+            f0[u] = f1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < nA && row0 + r < m && k0 < d) {
+                const float4 *xr = reinterpret_cast<const float4 *>(x + (size_t)(row0 + r) * d + k0);
+                f0[u] = __ldg(xr);
+                f1[u] = __ldg(xr + 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CT_AU; ++u) {
+            const int e = e0 + u * CT_NT;
+            if (e >= nA) break;
+            const int r = e / (KC * 8), kc = (e >> 3) % KC, c = e & 7;
+            const float f[8] = {f0[u].x, f0[u].y, f0[u].z, f0[u].w,
+                                f1[u].x, f1[u].y, f1[u].z, f1[u].w};
+            uint32_t w[4], wl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * t], f[2 * t + 1]);
@@ -480,13 +498,13 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
                     wl[t] = *reinterpret_cast<uint32_t *>(&l);
                 }
             }
+            const size_t off = (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                               ((c ^ (r & 7)) << 4);
+            *reinterpret_cast<uint4 *>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (NP == 2)
+                *reinterpret_cast<uint4 *>(A + (size_t)KC * CT_M * 128 + off) =
+                    make_uint4(wl[0], wl[1], wl[2], wl[3]);
         }
-        const size_t off = (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
-                           ((c ^ (r & 7)) << 4);
-        *reinterpret_cast<uint4 *>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
-        if (NP == 2)
-            *reinterpret_cast<uint4 *>(A + (size_t)KC * CT_M * 128 + off) =
-                make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     fence_proxy_async_smem();
@@ -514,12 +532,15 @@ __global__ __launch_bounds__(128, 1) void k_coarse_tc(const float *__restrict__ 
     __syncwarp();
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0, err));
     tc_fence_after();
-    const int r = row0 + warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (its lane
+    // quarter) and every other group of 16 columns, starting at w div 4
+    const int q = warp & 3, half = warp >> 2;
+    const int r = row0 + q * 32 + lane;
     const bool vec = (L & 3) == 0;
-    for (int c16 = 0; c16 * 16 < ncol; ++c16) {  // warp-uniform
+    for (int c16 = half; c16 * 16 < ncol; c16 += CT_NT / 128) {  // warp-uniform
         float v[16];
         if (ok) {
-            tmem_ld16(tbase + c16 * 16 + ((uint32_t)(warp * 32) << 16), v);
+            tmem_ld16(tbase + c16 * 16 + ((uint32_t)(q * 32) << 16), v);
             tmem_ld_wait();
         }
         if (!ok || r >= m) continue;
@@ -556,7 +577,10 @@ constexpr int CW_ROWS = 4;     // rows (warps) per block
 constexpr int CW_PMAX = 8;
 constexpr int CW_SCAP = 128;
 constexpr int CW_LMAX = 4096;  // most lists for one warp per row
+constexpr int CW_RG = 4;       // FP32 rechecks in flight per warp
 
+// PM: length of each lane's sorted list (1 when P = 1, else CW_PMAX)
+template <int PM>
 __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 {
     __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP], sDt[CW_ROWS][CW_SCAP];
@@ -584,9 +608,9 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
     // P-th smallest of the values v(i), i < n, each lane keeping its
     // CW_PMAX smallest in a sorted register list
     auto pth_smallest = [&](auto val, int n) {
-        float top[CW_PMAX];
+        float top[PM];
 #pragma unroll
-        for (int k = 0; k < CW_PMAX; ++k) top[k] = INFINITY;
+        for (int k = 0; k < PM; ++k) top[k] = INFINITY;
         constexpr int CU = 8;  // values per lane loaded ahead
         for (int i0 = lane; i0 < n; i0 += 32 * CU) {
             float vv[CU];
@@ -596,7 +620,7 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
             for (int u = 0; u < CU; ++u) {
                 float v = vv[u];
 #pragma unroll
-                for (int k = 0; k < CW_PMAX; ++k) {  // insert into the sorted list
+                for (int k = 0; k < PM; ++k) {  // insert into the sorted list
                     const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
                     top[k] = lo;
                     v = hi;
@@ -618,8 +642,8 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
             T = v;
             if (lane == who) {
 #pragma unroll
-                for (int k = 0; k + 1 < CW_PMAX; ++k) top[k] = top[k + 1];
-                top[CW_PMAX - 1] = INFINITY;
+                for (int k = 0; k + 1 < PM; ++k) top[k] = top[k + 1];
+                top[PM - 1] = INFINITY;
             }
         }
         return T;
@@ -674,24 +698,47 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
         // rebuild T and S with the FP32 bound inside S
         for (int j = lane; j < a.d; j += 32) sX[w][j] = xr[j];
         __syncwarp();
+        // the warp computes CW_RG members' dot products at a time, lanes
+        // over the coordinates (coalesced centroid rows), then a butterfly
         const float4 *x4 = reinterpret_cast<const float4 *>(sX[w]);
-        for (int p = lane; p < ns; p += 32) {
-            const int c = sIdx[w][p];
-            const float4 *c4 = reinterpret_cast<const float4 *>(a.cent + (size_t)c * a.d);
-            float acc = 0.f;
-            for (int j4 = 0; j4 < a.d / 4; ++j4) {
-                const float4 xv = x4[j4], cv = __ldg(c4 + j4);
-                acc = fmaf(xv.x, cv.x, acc);
-                acc = fmaf(xv.y, cv.y, acc);
-                acc = fmaf(xv.z, cv.z, acc);
-                acc = fmaf(xv.w, cv.w, acc);
+        const int n4 = a.d >> 2;
+        for (int p0 = 0; p0 < ns; p0 += CW_RG) {
+            float part[CW_RG];
+#pragma unroll
+            for (int t = 0; t < CW_RG; ++t) {
+                part[t] = 0.f;
+                if (p0 + t >= ns) continue;
+                const float4 *c4 =
+                    reinterpret_cast<const float4 *>(a.cent + (size_t)sIdx[w][p0 + t] * a.d);
+#pragma unroll
+                for (int u = 0; u < kMaxD / 128; ++u) {
+                    const int j4 = lane + 32 * u;
+                    if (j4 >= n4) break;
+                    const float4 xv = x4[j4], cv = __ldg(c4 + j4);
+                    part[t] = fmaf(xv.x, cv.x, part[t]);
+                    part[t] = fmaf(xv.y, cv.y, part[t]);
+                    part[t] = fmaf(xv.z, cv.z, part[t]);
+                    part[t] = fmaf(xv.w, cv.w, part[t]);
+                }
             }
-            const float cnc = __ldg(a.cn + c);
-            const float Dt = fmaf(-2.f, acc, cnc);
-            const float E = bound_of(Dt, cnc, __ldg(a.cnrm_up + c), xn, a.gamma2);
-            sLB[w][p] = lower_of(Dt, E);
-            sUB[w][p] = upper_of(Dt, E);
-            sDt[w][p] = Dt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < CW_RG; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
+            float acc = part[0];
+#pragma unroll
+            for (int t = 1; t < CW_RG; ++t)
+                if (lane == t) acc = part[t];
+            const int p = p0 + lane;
+            if (lane < CW_RG && p < ns) {
+                const int c = sIdx[w][p];
+                const float cnc = __ldg(a.cn + c);
+                const float Dt = fmaf(-2.f, acc, cnc);
+                const float E = bound_of(Dt, cnc, __ldg(a.cnrm_up + c), xn, a.gamma2);
+                sLB[w][p] = lower_of(Dt, E);
+                sUB[w][p] = upper_of(Dt, E);
+                sDt[w][p] = Dt;
+            }
         }
         __syncwarp();
         T = pth_smallest([&](int p) { return sUB[w][p]; }, ns);
@@ -921,7 +968,7 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                                          (int)smem);
                     attr = smem;
                 }
-                k_coarse_tc<1><<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, nullptr,
+                k_coarse_tc<1><<<g, CT_NT, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, nullptr,
                                                       ix->cnorm, L, Dbuf, ix->err);
             } else {
                 static size_t attr = 0;
@@ -930,7 +977,7 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                                          (int)smem);
                     attr = smem;
                 }
-                k_coarse_tc<3><<<g, 128, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cent_lo,
+                k_coarse_tc<3><<<g, CT_NT, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cent_lo,
                                                       ix->cnorm, L, Dbuf, ix->err);
             }
         } else {
@@ -958,10 +1005,13 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.two_level = two;
         a.out = out + r0 * P;
         a.err = ix->err;
-        if (warp_rows)
-            k_coarse_select_w<<<(unsigned)((mc + CW_ROWS - 1) / CW_ROWS), CW_ROWS * 32, 0, st>>>(a);
-        else
+        if (warp_rows) {
+            const unsigned gw = (unsigned)((mc + CW_ROWS - 1) / CW_ROWS);
+            if (P == 1) k_coarse_select_w<1><<<gw, CW_ROWS * 32, 0, st>>>(a);
+            else k_coarse_select_w<CW_PMAX><<<gw, CW_ROWS * 32, 0, st>>>(a);
+        } else {
             k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
+        }
         prof_end(ix, tok, st);
     }
 }

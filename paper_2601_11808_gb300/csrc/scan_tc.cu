@@ -1236,6 +1236,7 @@ void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn
 // scale 448 / (2 max_j |r_j|) (1 when r = 0) and the row E4M3(fl32(r_j *
 // scale)) (round to nearest even, saturated).  One warp per pair; pairs with
 // no list are left untouched (they are never scanned).
+constexpr int PP_V4 = 2;  // float4 of the residual per lane (d <= 256)
 __global__ void k_pair_prep(const float *__restrict__ q, int64_t npairs, int P, int d, int L,
                             const int32_t *__restrict__ probes, const float *__restrict__ cent,
                             float *__restrict__ qn, float *__restrict__ qsc,
@@ -1248,20 +1249,60 @@ __global__ void k_pair_prep(const float *__restrict__ q, int64_t npairs, int P, 
     if (l < 0 || l >= L) return;
     const float *qr = q + (size_t)(e / P) * d;
     const float *cl = cent + (size_t)l * d;
+    unsigned char *o = qcast + (size_t)e * d;
     float ss = 0.f, mx = 0.f;
+    if ((d & 3) == 0 && d <= 32 * 4 * PP_V4) {
+        // the residual held in registers, one float4 per lane and round
+        const int n4 = d >> 2;
+        float4 r4[PP_V4];
+#pragma unroll
+        for (int u = 0; u < PP_V4; ++u) {
+            const int j4 = lane + 32 * u;
+            r4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j4 < n4) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(qr) + j4);
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(cl) + j4);
+                r4[u] = make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y),
+                                    __fsub_rn(a.z, b.z), __fsub_rn(a.w, b.w));
+            }
+            ss = fmaf(r4[u].x, r4[u].x, ss);
+            ss = fmaf(r4[u].y, r4[u].y, ss);
+            ss = fmaf(r4[u].z, r4[u].z, ss);
+            ss = fmaf(r4[u].w, r4[u].w, ss);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(r4[u].x), fabsf(r4[u].y)),
+                                 fmaxf(fabsf(r4[u].z), fabsf(r4[u].w))));
+        }
+        ss = warp_sum(ss);
+        for (int o2 = 16; o2 > 0; o2 >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+        const float sc = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
+        if (lane == 0) {
+            qn[e] = ss;
+            qsc[e] = sc;
+        }
+#pragma unroll
+        for (int u = 0; u < PP_V4; ++u) {
+            const int j4 = lane + 32 * u;
+            if (j4 >= n4) break;
+            const uint32_t lo = __nv_cvt_float2_to_fp8x2(
+                make_float2(__fmul_rn(r4[u].x, sc), __fmul_rn(r4[u].y, sc)), __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(__fmul_rn(r4[u].z, sc), __fmul_rn(r4[u].w, sc)), __NV_SATFINITE, __NV_E4M3);
+            reinterpret_cast<uint32_t *>(o)[j4] = (lo & 0xffffu) | (hi << 16);
+        }
+        return;
+    }
     for (int j = lane; j < d; j += 32) {
         const float r = __fsub_rn(qr[j], cl[j]);
         ss = fmaf(r, r, ss);
         mx = fmaxf(mx, fabsf(r));
     }
     ss = warp_sum(ss);
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
     const float sc = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
     if (lane == 0) {
         qn[e] = ss;
         qsc[e] = sc;
     }
-    unsigned char *o = qcast + (size_t)e * d;
     for (int j = 2 * lane; j < d; j += 64) {
         const float2 p = make_float2(__fmul_rn(__fsub_rn(qr[j], cl[j]), sc),
                                      __fmul_rn(__fsub_rn(qr[j + 1], cl[j + 1]), sc));
