@@ -43,9 +43,13 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # ncu captures of the reduced-precision list scan on this workload (nprobe
-# 8), per scan form: the scan kernel source they were taken of and the mean
-# dram__bytes_read.sum + dram__bytes_write.sum over the search's two launches
-TC_PROFILED = {}
+# 8), per scan form: the hash of the scan kernel's source (scan_tc.cu up to
+# the per-query merge: the kernel and every device helper it calls) they
+# were taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum
+# over the search's two launches
+TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
+TC_PROFILED = {"fp8": ("4b68508e4ec50002", 160_394_240),
+               "bf16": ("4b68508e4ec50002", 300_420_480)}
 
 
 def parse():
@@ -977,7 +981,9 @@ def main():
         import hashlib
         src = os.path.join(ROOT, "paper_2601_11808_gb300", "csrc", "scan_tc.cu")
         sha, nbytes = TC_PROFILED.get(head, (None, None))
-        if sha and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == sha:
+        text = open(src).read()
+        if sha and TC_KERNEL_END in text and \
+                hashlib.sha256(text[:text.index(TC_KERNEL_END)].encode()).hexdigest()[:16] == sha:
             traffic = nbytes
     roofline.update({"traffic": traffic, "launches": scan_n,
                      "ms_per_launch": round(scan_ms / max(scan_n, 1), 4),
