@@ -346,14 +346,31 @@ __device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int 
         }
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
-    uint32_t lo = kmin, hi = kmax;  // smallest v with #(key <= v) >= K
+    // bisection for the smallest v with #(key <= v) >= K; it stops early at
+    // any v with exactly K keys <= v (v then lies between the K-th and the
+    // (K+1)-th smallest key: the kept set is the same and needs no tie
+    // step), which takes about log2(n) rounds instead of one per key bit
+    uint32_t lo = kmin, hi = kmax;
+    bool exact = false;
     while (lo < hi) {  // counts by independent ballots (every lane gets them)
         const uint32_t mid = lo + ((hi - lo) >> 1);
         uint32_t c = 0;
 #pragma unroll
         for (int e = 0; e < EK; ++e) c += __popc(__ballot_sync(0xffffffffu, key[e] <= mid));
-        if (c >= (uint32_t)K) hi = mid;
+        if (c == (uint32_t)K) {
+            lo = mid;
+            exact = true;
+            break;
+        }
+        if (c > (uint32_t)K) hi = mid;
         else lo = mid + 1;
+    }
+    if (exact) {  // keep every key <= lo; the K-th smallest is their maximum
+        uint32_t kk = 0u;
+#pragma unroll
+        for (int e = 0; e < EK; ++e)
+            if (key[e] <= lo) kk = max(kk, key[e]);
+        lo = __reduce_max_sync(0xffffffffu, kk);
     }
     const uint32_t kth = lo;
     uint32_t clt = 0, ceq = 0;
