@@ -48,8 +48,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # were taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum
 # over the search's two launches
 TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
-TC_PROFILED = {"fp8": ("4b68508e4ec50002", 160_394_240),
-               "bf16": ("4b68508e4ec50002", 300_420_480)}
+TC_PROFILED = {"fp8": ("f1611ff8217ff1ec", 160_534_912),
+               "bf16": ("f1611ff8217ff1ec", 300_399_744)}
 
 
 def parse():
