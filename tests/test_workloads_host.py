@@ -53,3 +53,27 @@ def test_bucket_rule():
         assert autotune.bucket(L, nq, 10, P, "fp32") == f"fp32/{b}/0"
     assert autotune.bucket(64, 40, 10, 8, "bf16").endswith("/1")    # 4k = 40 kept
     assert autotune.bucket(64, 40, 100, 8, "bf16").endswith("/3")   # 400 kept
+
+
+def test_zipf_law_and_draws():
+    """The skewed mixture: P(rank r) = r^-s / H(n, s); the rank -> component
+    map is a fixed permutation; empirical component shares follow the law;
+    vectors stay positional (independent of batching)."""
+    w = W.small("tiny_window", n_comp=32, zipf=1.0)
+    p, perm = W.zipf_law(w)
+    h = sum(1.0 / r for r in range(1, 33))
+    np.testing.assert_allclose(p, [1.0 / (r * h) for r in range(1, 33)], rtol=1e-12)
+    assert sorted(perm.tolist()) == list(range(32))
+    np.testing.assert_array_equal(perm, W.zipf_law(w)[1])
+    ctr = W.centers(w)
+    x = W.vectors(w, 0, 40_000, ctr)
+    # nearest center of each vector (sigma 0.1 against centers in [-1, 1]^32:
+    # the component that drew it)
+    d2 = ((x[:, None, :] - ctr[None, :, :]) ** 2).sum(-1)
+    share = np.bincount(d2.argmin(1), minlength=32) / len(x)
+    for rank in (1, 2, 4, 8):
+        assert abs(share[perm[rank - 1]] - p[rank - 1]) < 4 * math.sqrt(p[rank - 1] / len(x)) + 1e-3
+    np.testing.assert_array_equal(W.vectors(w, 1000, 5000, ctr), x[1000:6000])
+    # zipf = 0 is the uniform mixture
+    u = W.small("tiny_window", zipf=0.0)
+    np.testing.assert_array_equal(W.vectors(u, 0, 100), W.vectors(W.CONFIGS["tiny_window"], 0, 100))
