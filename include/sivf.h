@@ -551,7 +551,13 @@ typedef struct {
     int32_t max_query_batch;  /* queries per search launch, >= 1             */
     int32_t max_insert_batch; /* vectors per add launch, >= 1                */
     int32_t max_delete_batch; /* ids per remove launch (evictions included)  */
-    int32_t pad;
+    int32_t compact_min_free; /* > 0: whenever the worker is idle, one
+                                 compaction pass (sivf_compact, at most
+                                 max_insert_batch members) over lists that
+                                 would free at least this many slabs,
+                                 repeated until a pass moves nothing, then
+                                 again after the next mutation batch (the
+                                 first passes run at start); 0: off        */
 } sivf_server_config;
 
 typedef struct {
@@ -571,6 +577,9 @@ typedef struct {
     int64_t deferred;         /* times an insert waited for free slabs       */
     int64_t rejected;         /* requests whose batch was rejected           */
     int64_t max_in_flight;    /* most batches seen in flight at once         */
+    int64_t compact_passes;   /* idle compaction passes that moved members   */
+    int64_t compact_freed;    /* slabs they returned to the pool             */
+    int64_t compact_moved;    /* members they rewrote                        */
 } sivf_server_stats_t;
 
 /*

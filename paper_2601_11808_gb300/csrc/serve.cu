@@ -104,9 +104,12 @@ struct sivf_server {
     int64_t free_known = 0, free_seq = -1, reserved = 0, seq = 0;
     int64_t last_deferred = -1;      // request at the head when an insert last waited
     int in_flight = 0, mut_in_flight = 0;
+    bool compact_dirty = true;       // the index may have changed since the last pass
+                                     // that moved nothing (true at start)
     std::thread worker;
 
     void run();
+    void idle_compact();
     bool reap();
     bool launch();
     void finish(Slot &sl, int32_t status);
@@ -252,7 +255,10 @@ bool sivf_server::launch()
     s.host_status = 0;
     s.reqs.swap(take);
     ++in_flight;
-    if (kind != SIVF_OP_SEARCH) ++mut_in_flight;
+    if (kind != SIVF_OP_SEARCH) {
+        ++mut_in_flight;
+        compact_dirty = true;
+    }
     reserved += s.demand;
 
     const int d = ix->d;
@@ -340,6 +346,31 @@ bool sivf_server::launch()
     return true;
 }
 
+// Background compaction: with nothing pending and nothing in flight, one
+// bounded pass on the first slot's stream (the call syncs it), so a
+// request that arrives meanwhile waits for at most one pass.  Passes repeat
+// while they move members and stop until the next mutation batch.
+void sivf_server::idle_compact()
+{
+    int64_t fr = 0, mv = 0;
+    const sivf_status rc = sivf_compact(ix, cfg.compact_min_free, cfg.max_insert_batch,
+                                        slots[0].s, &fr, &mv);
+    std::lock_guard<std::mutex> lk(mu);
+    if (rc) {
+        fatal = rc;
+        compact_dirty = false;
+        return;
+    }
+    if (mv == 0) {
+        compact_dirty = false;
+        return;
+    }
+    free_known += fr;
+    st.compact_passes += 1;
+    st.compact_freed += fr;
+    st.compact_moved += mv;
+}
+
 void sivf_server::run()
 {
     cudaSetDevice(ix->device);
@@ -349,6 +380,12 @@ void sivf_server::run()
         if (prog) continue;
         std::unique_lock<std::mutex> lk(mu);
         if (stop && pending.empty() && in_flight == 0) break;
+        if (in_flight == 0 && pending.empty() && cfg.compact_min_free > 0 && compact_dirty &&
+            !fatal) {
+            lk.unlock();
+            idle_compact();
+            continue;
+        }
         if (in_flight == 0 && pending.empty())
             cv_work.wait_for(lk, std::chrono::milliseconds(2));
         else {
@@ -390,7 +427,8 @@ sivf_status sivf_server_create(sivf_index *ix, const sivf_server_config *cfg, si
     const sivf_server_config &c = *cfg;
     if (c.depth < 1 || c.depth > 8 || c.k < 1 || c.k > kMaxK || c.nprobe < 1 ||
         c.nprobe > ix->nlist || c.dtype < SIVF_FP32 || c.dtype > SIVF_FP8E4M3 ||
-        c.max_query_batch < 1 || c.max_insert_batch < 1 || c.max_delete_batch < 1)
+        c.max_query_batch < 1 || c.max_insert_batch < 1 || c.max_delete_batch < 1 ||
+        c.compact_min_free < 0)
         return set_error(ix, SIVF_E_ARG, "bad server config");
     if (!ix->have_centroids) return set_error(ix, SIVF_E_STATE, "set_centroids first");
     sivf_server *sv = new (std::nothrow) sivf_server();

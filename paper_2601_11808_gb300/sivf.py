@@ -81,7 +81,7 @@ class sivf_server_config(C.Structure):
     _fields_ = [("k", C.c_int32), ("nprobe", C.c_int32), ("dtype", C.c_int32),
                 ("depth", C.c_int32), ("max_query_batch", C.c_int32),
                 ("max_insert_batch", C.c_int32), ("max_delete_batch", C.c_int32),
-                ("pad", C.c_int32)]
+                ("compact_min_free", C.c_int32)]
 
 
 class sivf_request_info(C.Structure):
@@ -92,7 +92,8 @@ class sivf_request_info(C.Structure):
 class sivf_server_stats_t(C.Structure):
     _fields_ = [("requests", C.c_int64 * 3), ("batches", C.c_int64 * 3),
                 ("items", C.c_int64 * 3), ("deferred", C.c_int64), ("rejected", C.c_int64),
-                ("max_in_flight", C.c_int64)]
+                ("max_in_flight", C.c_int64), ("compact_passes", C.c_int64),
+                ("compact_freed", C.c_int64), ("compact_moved", C.c_int64)]
 
 
 class SivfError(RuntimeError):
@@ -567,14 +568,14 @@ class Server:
     KINDS = {"add": OP_ADD, "remove": OP_REMOVE, "search": OP_SEARCH}
 
     def __init__(self, index, k=10, nprobe=32, dtype="fp32", depth=3, max_query_batch=1024,
-                 max_insert_batch=16384, max_delete_batch=16384):
+                 max_insert_batch=16384, max_delete_batch=16384, compact_min_free=0):
         lib = load()
         self.index = index
         self.h = index.h
         self.k, self.d = int(k), index.d
         cfg = sivf_server_config(self.k, int(nprobe), DTYPES[dtype], int(depth),
                                  int(max_query_batch), int(max_insert_batch),
-                                 int(max_delete_batch), 0)
+                                 int(max_delete_batch), int(compact_min_free))
         out = C.c_void_p()
         _check(lib, self.h, lib.sivf_server_create(self.h, C.byref(cfg), C.byref(out)))
         self.s = out.value
@@ -634,7 +635,8 @@ class Server:
         _check(lib, self.h, lib.sivf_server_stats(self.s, C.byref(st)))
         return {"requests": list(st.requests), "batches": list(st.batches),
                 "items": list(st.items), "deferred": st.deferred, "rejected": st.rejected,
-                "max_in_flight": st.max_in_flight}
+                "max_in_flight": st.max_in_flight, "compact_passes": st.compact_passes,
+                "compact_freed": st.compact_freed, "compact_moved": st.compact_moved}
 
     def close(self) -> None:
         if getattr(self, "s", None):

@@ -252,3 +252,50 @@ def test_bad_requests(torch):
     sv.close()
     with pytest.raises(SivfError):
         Server(g, k=4, nprobe=w.nlist + 1)
+
+
+def test_idle_compaction(torch):
+    """A fragmented index (60 % of its ids deleted at random) handed to a
+    server with background compaction: while idle the worker runs passes of
+    at most max_insert_batch members until one moves nothing.  The passes
+    free and move exactly what the oracle's passes with the same budget do,
+    the final state equals the oracle's bit for bit, and searches served
+    afterwards equal the oracle's."""
+    import time
+    from paper_2601_11808_gb300.sivf import Server
+    w = W.small("tiny_window")
+    S = 2 * (20000 // w.slab_size + w.nlist)
+    g, _, o = _pair(torch, w, S, ())
+    ids0, x0 = W.stream_ids(0, 20000, N_MAX), W.vectors(w, 0, 20000)
+    g.add(cuda(torch, ids0), cuda(torch, x0))
+    o.add(ids0, x0)
+    gone = W.sample_ids(w.seed, 15, 0, ids0, 12000)
+    g.remove(cuda(torch, gone))
+    o.remove(gone)
+    g.sync()
+    budget = 1024
+    sv = Server(g, k=10, nprobe=8, depth=2, max_query_batch=256, max_insert_batch=budget,
+                compact_min_free=1)
+    last, t0 = -1, time.time()
+    while time.time() - t0 < 10:
+        st = sv.stats()
+        if st["compact_passes"] == last and last > 0:
+            break
+        last = st["compact_passes"]
+        time.sleep(0.2)
+    q = W.queries(w, 0, 64)
+    info = sv.wait(sv.search(q))
+    st = sv.stats()
+    sv.close()
+    freed = moved = passes = 0
+    while True:
+        fr, mv = o.compact(1, budget)
+        if mv == 0:
+            break
+        freed, moved, passes = freed + fr, moved + mv, passes + 1
+    assert passes > 1
+    assert (st["compact_passes"], st["compact_freed"], st["compact_moved"]) == (passes, freed, moved)
+    g.sync()
+    compare_state(g.dump(), o, w.slab_size, S)
+    od, oi = o.search(q, 10, 8)
+    compare_topk(info["dist"], info["labels"], od, oi, 1e-5, "served after compaction")
