@@ -289,8 +289,10 @@ sivf_status sivf_search_candidates(sivf_index *index, const float *q, int64_t nq
  *   comes from one array of SIVF_NOALLOC_SCRATCH_BYTES bytes declared in
  *   the library's device code, held by every GPU that loads the library
  *   until the process exits.  A batch whose scratch does not fit (roughly
- *   nq * nprobe * k * 12 bytes plus nlist-sized tables) is refused with
- *   SIVF_E_ARG and a message giving the bytes it needs.
+ *   (nq * nprobe + 2 * 152 * tq * ips) * k * 12 bytes of item outputs, tq
+ *   the queries per scan tile and ips the tile's items per SM, which the
+ *   call lowers to 1 before refusing, plus nlist-sized tables) is refused
+ *   with SIVF_E_ARG and a message giving the bytes it needs.
  *   The first call on a device looks the array's device address up (once
  *   per device, with that device current); make that first call before any
  *   stream capture begins.
