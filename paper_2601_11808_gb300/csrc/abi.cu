@@ -763,7 +763,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             const int64_t sb = (int64_t)ix->C * (ix->d * esz + 4) + ix->C / 8;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
             if (fp8) pair_prep(ix, qq, m, P, probes, sc.pqn, sc.pqsc, sc.qcast, s);
-            else query_prep(ix, dtype, qq, m, sc.qn, sc.qsc, sc.qcast, s);
+            else query_prep(ix, qq, m, sc.qn, sc.qsc, sc.qcast, s);
             const int split = P > 1 && pl.split ? 1 : P;
             group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
             scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);

@@ -174,6 +174,44 @@ __global__ __launch_bounds__(256) void k_cp_bases(CompactArgs a)
     }
 }
 
+// one row's FP32 payload, BF16 / E4M3 codes (d % 4 == 0): float4, 4 x bf16
+// and 4 x e4m3 per lane and round, CP_RV rounds cover d <= 256
+constexpr int CP_RV = 2;
+constexpr int CP_U = 4;  // rows in flight per warp in the gather
+
+struct RowRegs {
+    float4 f[CP_RV];
+    uint2 h[CP_RV];
+    uint32_t b[CP_RV];
+};
+
+__device__ __forceinline__ void row_load(const CompactArgs &a, int64_t src, int lane, RowRegs &v)
+{
+    const int n4 = a.d >> 2;
+#pragma unroll
+    for (int t = 0; t < CP_RV; ++t) {
+        const int j4 = lane + 32 * t;
+        if (j4 >= n4) break;
+        v.f[t] = __ldg(reinterpret_cast<const float4 *>(a.x32 + src * a.d) + j4);
+        if (a.t16) v.h[t] = __ldg(reinterpret_cast<const uint2 *>(a.xb16 + src * a.d) + j4);
+        if (a.t8) v.b[t] = __ldg(reinterpret_cast<const uint32_t *>(a.x8 + src * a.d) + j4);
+    }
+}
+
+__device__ __forceinline__ void row_store(float *f32, __nv_bfloat16 *f16, uint8_t *f8, int64_t dst,
+                                          int d, int lane, const RowRegs &v)
+{
+    const int n4 = d >> 2;
+#pragma unroll
+    for (int t = 0; t < CP_RV; ++t) {
+        const int j4 = lane + 32 * t;
+        if (j4 >= n4) break;
+        reinterpret_cast<float4 *>(f32 + dst * d)[j4] = v.f[t];
+        if (f16) reinterpret_cast<uint2 *>(f16 + dst * d)[j4] = v.h[t];
+        if (f8) reinterpret_cast<uint32_t *>(f8 + dst * d)[j4] = v.b[t];
+    }
+}
+
 __global__ __launch_bounds__(256) void k_cp_gather(CompactArgs a)
 {
     const int nsel = a.ctl->ntouched;
@@ -181,7 +219,6 @@ __global__ __launch_bounds__(256) void k_cp_gather(CompactArgs a)
     const int64_t total = a.soff[nsel];
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
-    const int d = a.d;
     for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; g < total; g += nw) {
         const int k = find_run(a.soff, nsel, g);
         const int l = a.sel[k];
@@ -190,26 +227,40 @@ __global__ __launch_bounds__(256) void k_cp_gather(CompactArgs a)
         int64_t r = a.voff[k] + a.sb[g];
         const int64_t rend = a.voff[k + 1];
         for (int w = 0; w < a.W; ++w) {
-            uint32_t word = a.bits[(size_t)s * a.W + w];
+            uint32_t word = a.bits[(size_t)s * a.W + w];  // the same in every lane
             while (word) {
-                const int b = __ffs(word) - 1;
-                word &= word - 1;
-                if (r >= rend) {  // more bits than the list's live count
+                int slot[CP_U];
+                int nb = 0;
+#pragma unroll
+                for (int u = 0; u < CP_U; ++u) {
+                    slot[u] = -1;
+                    if (word) {
+                        slot[u] = 32 * w + __ffs(word) - 1;
+                        word &= word - 1;
+                        ++nb;
+                    }
+                }
+                if (r + nb > rend) {  // more bits than the list's live count
                     if (lane == 0) atomicOr(a.err, ERR_BAD_SLAB);
+                    word = 0;
                     break;
                 }
-                const int64_t src = (int64_t)s * a.C + 32 * w + b;
-                for (int j = lane; j < d; j += 32) a.t32[r * d + j] = a.x32[src * d + j];
-                if (a.t16)
-                    for (int j = lane; j < d; j += 32) a.t16[r * d + j] = a.xb16[src * d + j];
-                if (a.t8)
-                    for (int j = lane; j < d; j += 32) a.t8[r * d + j] = a.x8[src * d + j];
-                if (lane == 0) {
-                    a.tn[r] = a.xnorm[src];
-                    if (a.tr) a.tr[r] = a.rnorm[src];
-                    a.ti[r] = a.ids[src];
+                RowRegs v[CP_U];
+#pragma unroll
+                for (int u = 0; u < CP_U; ++u)
+                    if (slot[u] >= 0) row_load(a, (int64_t)s * a.C + slot[u], lane, v[u]);
+#pragma unroll
+                for (int u = 0; u < CP_U; ++u) {
+                    if (slot[u] < 0) continue;
+                    const int64_t src = (int64_t)s * a.C + slot[u];
+                    row_store(a.t32, a.t16, a.t8, r + u, a.d, lane, v[u]);
+                    if (lane == 0) {
+                        a.tn[r + u] = a.xnorm[src];
+                        if (a.tr) a.tr[r + u] = a.rnorm[src];
+                        a.ti[r + u] = a.ids[src];
+                    }
                 }
-                ++r;
+                r += nb;
             }
         }
     }
@@ -222,7 +273,6 @@ __global__ __launch_bounds__(256) void k_cp_scatter(CompactArgs a)
     const int64_t total = a.voff[nsel];
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
-    const int d = a.d;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; r < total; r += nw) {
         const int k = find_run(a.voff, nsel, r);
         const int l = a.sel[k];
@@ -231,11 +281,17 @@ __global__ __launch_bounds__(256) void k_cp_scatter(CompactArgs a)
         if (s < 0 || s >= a.n_slabs) continue;
         const int slot = (int)(j % a.C);
         const int64_t dst = (int64_t)s * a.C + slot;
-        for (int jj = lane; jj < d; jj += 32) a.x32[dst * d + jj] = a.t32[r * d + jj];
-        if (a.t16)
-            for (int jj = lane; jj < d; jj += 32) a.xb16[dst * d + jj] = a.t16[r * d + jj];
-        if (a.t8)
-            for (int jj = lane; jj < d; jj += 32) a.x8[dst * d + jj] = a.t8[r * d + jj];
+        RowRegs v;
+        const int n4 = a.d >> 2;
+#pragma unroll
+        for (int t = 0; t < CP_RV; ++t) {
+            const int j4 = lane + 32 * t;
+            if (j4 >= n4) break;
+            v.f[t] = reinterpret_cast<const float4 *>(a.t32 + r * a.d)[j4];
+            if (a.t16) v.h[t] = reinterpret_cast<const uint2 *>(a.t16 + r * a.d)[j4];
+            if (a.t8) v.b[t] = reinterpret_cast<const uint32_t *>(a.t8 + r * a.d)[j4];
+        }
+        row_store(a.x32, a.t16 ? a.xb16 : nullptr, a.t8 ? a.x8 : nullptr, dst, a.d, lane, v);
         if (lane == 0) {
             a.xnorm[dst] = a.tn[r];
             if (a.tr) a.rnorm[dst] = a.tr[r];

@@ -97,8 +97,8 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
 
 // ---- reduced-precision scan + re-rank (scan_tc.cu)
 bool tc_make_maps(sivf_index *ix);
-// ||q||^2, FP8 inverse scale and the row rounded to the scan format `dtype`
-void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn, float *qsc,
+// BF16 form: ||q||^2, unit scale and the row rounded to BF16
+void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
                 unsigned char *qcast, cudaStream_t st);
 // FP8 residual scan: per (query, probe) pair ||q - c_l||^2, scale, E4M3 row
 void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,

@@ -1202,10 +1202,10 @@ __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__
     }
 }
 
-// per query: FP32 ||q||^2, the FP8 inverse scale 448 / (2 max_j |q_j|) and
-// the row in the scan format (dtype 1: BF16, round to nearest even; 2: E4M3
-// of fl32(q_j * scale), round to nearest even, saturated)
-__global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d, int dtype,
+// per query (BF16 form): FP32 ||q||^2, unit scale, and the row rounded to
+// BF16 (round to nearest even).  The FP8 form codes each (query, probe)
+// pair instead (k_pair_prep).
+__global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
                              float *__restrict__ qn, float *__restrict__ qsc,
                              unsigned char *__restrict__ qcast)
 {
@@ -1213,39 +1213,25 @@ __global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d, int
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= nq) return;
     const float *qr = q + (size_t)i * d;
-    float ss = 0.f, mx = 0.f;
+    float ss = 0.f;
+    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(qcast) + (size_t)i * d;
     for (int j = lane; j < d; j += 32) {
         const float v = qr[j];
         ss = fmaf(v, v, ss);
-        mx = fmaxf(mx, fabsf(v));
+        o[j] = __float2bfloat16_rn(v);
     }
     ss = warp_sum(ss);
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const float sc = mx > 0.f ? 448.f / (2.f * mx) : 1.f;
     if (lane == 0) {
         qn[i] = ss;
-        qsc[i] = sc;
-    }
-    if (dtype == SIVF_BF16) {
-        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(qcast) + (size_t)i * d;
-        for (int j = lane; j < d; j += 32) o[j] = __float2bfloat16_rn(qr[j]);
-    } else if (dtype == SIVF_FP8E4M3) {
-        unsigned char *o = qcast + (size_t)i * d;
-        for (int j = 2 * lane; j < d; j += 64) {
-            const float2 p = make_float2(__fmul_rn(qr[j], sc), __fmul_rn(qr[j + 1], sc));
-            const uint32_t two = __nv_cvt_float2_to_fp8x2(p, __NV_SATFINITE, __NV_E4M3);
-            o[j] = (unsigned char)(two & 0xffu);
-            o[j + 1] = (unsigned char)(two >> 8);
-        }
+        qsc[i] = 1.f;
     }
 }
 
-void query_prep(sivf_index *ix, int dtype, const float *q, int64_t nq, float *qn, float *qsc,
+void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qsc,
                 unsigned char *qcast, cudaStream_t st)
 {
     ix->launches += 1;
-    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, dtype, qn, qsc,
-                                                                    qcast);
+    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, qn, qsc, qcast);
 }
 
 // FP8 residual scan: per (query, probe) pair e = q * P + p with list l =
