@@ -459,19 +459,27 @@ sivf_status sivf_autotune(sivf_index *index, const float *q, int64_t nq, int k,
  * batch reads its inputs from, and writes its outputs to, the device
  * addresses given when the queue was recorded, so a caller refills those
  * buffers in place between launches.  The batches run in queue order with
- * the semantics of the single calls (sivf_add, sivf_remove, sivf_search),
+ * the semantics of the single calls (sivf_add, sivf_remove, sivf_search,
+ * sivf_compact: a queue can carry compaction passes between its batches),
  * and the executor records, per batch, its status, its count and a device
  * timestamp.  The paper runs each batch as separate launches; this has no
  * counterpart there.
  * ---------------------------------------------------------------------- */
-typedef enum { SIVF_OP_ADD = 0, SIVF_OP_REMOVE = 1, SIVF_OP_SEARCH = 2 } sivf_op_kind;
+typedef enum {
+    SIVF_OP_ADD = 0,
+    SIVF_OP_REMOVE = 1,
+    SIVF_OP_SEARCH = 2,
+    SIVF_OP_COMPACT = 3  /* executor only: one sivf_compact pass, k = min_free,
+                            n = max_moves; the result's count = members moved */
+} sivf_op_kind;
 
 typedef struct {
     int32_t kind;        /* sivf_op_kind                                     */
     int32_t dtype;       /* search: sivf_scan_dtype                          */
-    int32_t k;           /* search: results per query                        */
+    int32_t k;           /* search: results per query; compact: min_free     */
     int32_t nprobe;      /* search: lists probed per query                   */
-    int64_t n;           /* ids (add, remove) or queries (search), >= 1      */
+    int64_t n;           /* ids (add, remove), queries (search) or the
+                            member budget (compact), >= 1                    */
     const int64_t *ids;  /* add, remove [device] int64[n]                    */
     const float *x;      /* add: vectors, search: queries [device] [n, d]    */
     float *dist;         /* search [device] float32[n, k]                    */

@@ -496,6 +496,22 @@ static size_t search_need(const sivf_index *ix, int64_t nq, int k, int P, int dt
 
 static size_t remove_need(const sivf_index *ix) { return (size_t)ix->nlist * 4 + 512; }
 
+// compaction: staged rows for at most max_moves members (never more than
+// n_max), the selected lists' offsets and the slab bases
+static int64_t compact_rows(const sivf_index *ix, int64_t max_moves)
+{
+    return std::max<int64_t>(1, std::min<int64_t>(max_moves, ix->n_max));
+}
+
+static size_t compact_need(const sivf_index *ix, int64_t max_moves)
+{
+    const size_t d = ix->d, L = ix->nlist;
+    const size_t row = d * 4 + (ix->xb16 ? d * 2 : 0) + (ix->x8 ? d : 0) + 4 +
+                       (ix->rnorm ? 4 : 0) + 8;
+    return L * 4 + (L + 1) * 16 + (size_t)ix->n_slabs * 4 +
+           (size_t)compact_rows(ix, max_moves) * row + 10 * 256;
+}
+
 sivf_status sivf_reserve(sivf_index *ix, int64_t max_add, int64_t max_remove,
                          int64_t max_queries, int max_k, int max_nprobe, void *stream)
 {
@@ -585,12 +601,8 @@ sivf_status sivf_compact(sivf_index *ix, int32_t min_free, int64_t max_moves, vo
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int L = ix->nlist, d = ix->d;
-    // staged rows: at most max_moves members, and never more than n_max
-    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(max_moves, ix->n_max));
-    const size_t row = (size_t)d * 4 + (ix->xb16 ? (size_t)d * 2 : 0) + (ix->x8 ? (size_t)d : 0) +
-                       4 + (ix->rnorm ? 4 : 0) + 8;
-    const size_t need = (size_t)L * 4 + (size_t)(L + 1) * 16 + (size_t)ix->n_slabs * 4 +
-                        (size_t)R * row + 10 * 256;
+    const int64_t R = compact_rows(ix, max_moves);
+    const size_t need = compact_need(ix, max_moves);
     Ctx *c;
     if ((st = get_ctx(ix, stream, need, &c))) return st;
     Bump b{c->scratch};
@@ -649,6 +661,7 @@ size_t op_need(const sivf_index *ix, const sivf_op &op)
     switch (op.kind) {
     case SIVF_OP_ADD: return add_bytes(ix, std::max<int64_t>(op.n, 1));
     case SIVF_OP_REMOVE: return remove_need(ix);
+    case SIVF_OP_COMPACT: return compact_need(ix, op.n);
     default: return search_need(ix, op.n, op.k, op.nprobe, op.dtype);
     }
 }

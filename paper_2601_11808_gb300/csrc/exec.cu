@@ -85,8 +85,11 @@ static sivf_status check_op(sivf_index *ix, const sivf_op &op, int i)
 {
     char b[160];
     const char *why = nullptr;
-    if (op.kind < SIVF_OP_ADD || op.kind > SIVF_OP_SEARCH) why = "unknown kind";
+    if (op.kind < SIVF_OP_ADD || op.kind > SIVF_OP_COMPACT) why = "unknown kind";
     else if (op.n < 1 || op.n > INT32_MAX) why = "n must be in [1, 2^31)";
+    else if (op.kind == SIVF_OP_COMPACT) {
+        if (op.k < 1) why = "compact: min_free (k) must be >= 1";
+    }
     else if (!op.x && op.kind != SIVF_OP_REMOVE) why = "null x";
     else if (!op.ids && op.kind != SIVF_OP_SEARCH) why = "null ids";
     else if (op.kind == SIVF_OP_SEARCH) {
@@ -166,6 +169,8 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
             s2 = sivf_add(ix, op.ids, op.x, op.n, e->cap, nullptr);
         else if (op.kind == SIVF_OP_REMOVE)
             s2 = sivf_remove(ix, op.ids, op.n, e->cap, nullptr);
+        else if (op.kind == SIVF_OP_COMPACT)
+            s2 = sivf_compact(ix, op.k, op.n, e->cap, nullptr, nullptr);
         else
             s2 = sivf_search(ix, op.x, op.n, op.k, op.nprobe, (sivf_scan_dtype)op.dtype,
                              op.dist, op.labels, e->cap);

@@ -40,7 +40,7 @@ EXPORTS = [
     "sivf_server_drain", "sivf_server_stats", "sivf_server_destroy",
 ]
 
-OP_ADD, OP_REMOVE, OP_SEARCH = 0, 1, 2
+OP_ADD, OP_REMOVE, OP_SEARCH, OP_COMPACT = 0, 1, 2, 3
 
 
 class sivf_config(C.Structure):
@@ -493,15 +493,16 @@ def sivf_autotune(h, q, k, nprobe, dtype=FP32, reps=5, stream=None):
 
 
 class Exec:
-    """A recorded queue of add / remove / search batches (sivf_exec).
+    """A recorded queue of add / remove / search / compact batches (sivf_exec).
 
     ``ops`` is a list of dicts: {"kind": "add", "ids": t, "x": t},
     {"kind": "remove", "ids": t}, {"kind": "search", "q": t, "k": k,
-    "nprobe": p, "dtype": "bf16", "dist": t, "labels": t}.  The tensors are
+    "nprobe": p, "dtype": "bf16", "dist": t, "labels": t},
+    {"kind": "compact", "min_free": 1, "max_moves": m}.  The tensors are
     device buffers that stay bound to the queue: refill them in place
     between launches.  The wrapper keeps references to them."""
 
-    KINDS = {"add": OP_ADD, "remove": OP_REMOVE, "search": OP_SEARCH}
+    KINDS = {"add": OP_ADD, "remove": OP_REMOVE, "search": OP_SEARCH, "compact": OP_COMPACT}
 
     def __init__(self, h, ops: list):
         import torch
@@ -513,7 +514,10 @@ class Exec:
             kind = self.KINDS[o["kind"]]
             e = arr[i]
             e.kind = kind
-            if kind == OP_SEARCH:
+            if kind == OP_COMPACT:
+                e.k = int(o.get("min_free", 1))
+                e.n = int(o.get("max_moves", 1 << 30))
+            elif kind == OP_SEARCH:
                 q = _dev(o["q"], torch.float32)
                 e.n = q.shape[0]
                 e.x = _ptr(q)

@@ -364,3 +364,50 @@ def test_tune_cache_round_trip(torch, filled, tmp_path):
         assert g.get_tile(dt, nq, k, P) == got[autotune.bucket(w.nlist, nq, k, P, dt)]["tile"]
     for nq, k, P, dt in shapes:
         g.set_tile(dt, nq, k, P, None)
+
+
+def test_queue_with_compaction_passes(torch):
+    """Compaction passes recorded in a queue between its batches: each pass
+    moves what the oracle's pass moves at the same point (the result's
+    count), searches after it match the oracle, and the final state is
+    bit-exact."""
+    w = WT
+    S = 1500
+    g, cent = _index(torch, w, S)
+    o = _oracle(w, S, cent)
+    st = Stream(w, W.centers(w))
+    ids, x = st.take_add(12000)
+    g.add(cuda(torch, ids), cuda(torch, x))
+    o.add(ids, x)
+    rng = np.random.default_rng(5)
+    r1 = rng.choice(ids, 7000, replace=False)
+    a2, x2 = st.take_add(2000)
+    r2 = rng.choice(np.setdiff1d(ids, r1), 1500, replace=False)
+    q = st.take_queries(50)
+    dist = torch.empty((50, 10), dtype=torch.float32, device="cuda")
+    lab = torch.empty((50, 10), dtype=torch.int64, device="cuda")
+    ops = [{"kind": "remove", "ids": cuda(torch, r1)},
+           {"kind": "compact", "min_free": 1, "max_moves": 1500},
+           {"kind": "compact", "min_free": 2, "max_moves": 1 << 20},
+           {"kind": "search", "q": cuda(torch, q), "k": 10, "nprobe": 8, "dtype": "fp32",
+            "dist": dist, "labels": lab},
+           {"kind": "add", "ids": cuda(torch, a2), "x": cuda(torch, x2)},
+           {"kind": "remove", "ids": cuda(torch, r2)},
+           {"kind": "compact", "min_free": 1, "max_moves": 1 << 20}]
+    ex = g.executor(ops)
+    ex.launch()
+    res = ex.results()
+    ex.close()
+    exp = [(0, o.remove(r1))]
+    exp.append((0, o.compact(1, 1500)[1]))
+    exp.append((0, o.compact(2, 1 << 20)[1]))
+    od, oi = o.search(q, 10, 8)
+    exp.append((0, 50))
+    exp.append((0, o.add(a2, x2)))
+    exp.append((0, o.remove(r2)))
+    exp.append((0, o.compact(1, 1 << 20)[1]))
+    assert [(r[0], r[1]) for r in res] == exp
+    assert exp[1][1] > 0 and exp[6][1] > 0
+    compare_topk(dist.cpu().numpy(), lab.cpu().numpy(), od, oi, 1e-5, "search after passes")
+    g.sync()
+    compare_state(g.dump(), o, w.slab_size, S)
