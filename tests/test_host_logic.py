@@ -107,3 +107,46 @@ def test_sharded_search_equals_unsharded_with_gloo(tmp_path):
     d, i = o.search(q, k, P)
     np.testing.assert_array_equal(np.load(out + "_i.npy"), i)
     np.testing.assert_array_equal(np.load(out + "_d.npy"), d)
+
+
+def _chunk_plan(lcnt, nslabs, tq, chmax, spc, ips):
+    """The scan's chunking rule (k_srch_plan), restated: per probed list
+    nt = ceil(m / tq) query tiles and c = min(chmax, ns, max(1, ceil(ns /
+    target))) slab chunks, target = max(spc, ceil(W / (ips * 152))), W the
+    sum of nt * ns; returns (items, output runs)."""
+    lcnt, nslabs = np.asarray(lcnt, np.int64), np.asarray(nslabs, np.int64)
+    act = (lcnt > 0) & (nslabs > 0)
+    nt = (lcnt + tq - 1) // tq
+    W = int((nt * nslabs)[act].sum())
+    slots = ips * 152
+    target = max(spc, -(-W // slots))
+    c = np.where(act, np.minimum(np.minimum(chmax, nslabs),
+                                 np.maximum(1, -(-nslabs // target))), 0)
+    return int((nt * c).sum()), int((lcnt * c).sum())
+
+
+@pytest.mark.parametrize("shape", ["uniform", "zipf", "one_heavy", "thin"])
+def test_chunk_plan_stays_within_scratch_bounds(shape):
+    """The scratch of a search is sized from the plan's bounds: per launch at
+    most nq*P + L + ips*152 work items and nq*P + tq*ips*152 output runs,
+    whatever the list lengths (a heavy list is split, but its extra chunks
+    are paid for by the work they cover)."""
+    rng = np.random.default_rng({"uniform": 0, "zipf": 1, "one_heavy": 2, "thin": 3}[shape])
+    L = 1024
+    for trial in range(20):
+        if shape == "uniform":
+            ns = rng.integers(1, 40, L)
+        elif shape == "zipf":
+            ns = np.maximum(1, (3000 / np.arange(1, L + 1) ** rng.uniform(0.8, 1.4))).astype(int)
+        elif shape == "one_heavy":
+            ns = np.ones(L, int)
+            ns[rng.integers(L)] = int(rng.integers(1000, 100000))
+        else:
+            ns = rng.integers(1, 5, L)
+        nq, P = int(rng.integers(1, 20000)), int(rng.choice([1, 7, 8, 32, 128]))
+        lcnt = np.bincount(rng.integers(0, L, nq * P), minlength=L)
+        for tq, ips, spc in ((48, 4, 4), (16, 16, 1), (64, 1, 8)):
+            chmax = max(1, min(64, 2048 // P))
+            items, runs = _chunk_plan(lcnt, ns, tq, chmax, spc, ips)
+            assert items <= nq * P + L + ips * 152
+            assert runs <= nq * P + tq * ips * 152
