@@ -206,7 +206,7 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
     __shared__ float red[32];
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_prefix, s_rank;
-    __shared__ int s_ns, s_nsure, s_nb, s_nsel;
+    __shared__ int s_ns, s_nsel;
     __shared__ float sLB[SEL_SCAP], sUB[SEL_SCAP];
     __shared__ int sIdx[SEL_SCAP];
     __shared__ unsigned char sSure[SEL_SCAP];
@@ -285,8 +285,6 @@ __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
     // candidate set S
     if (tid == 0) {
         s_ns = 0;
-        s_nsure = 0;
-        s_nb = 0;
         s_nsel = 0;
     }
     __syncthreads();
