@@ -17,7 +17,6 @@ import json
 import math
 import os
 
-import numpy as np
 
 from . import sivf
 
