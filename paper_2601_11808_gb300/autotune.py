@@ -17,7 +17,6 @@ import json
 import math
 import os
 
-
 from . import sivf
 
 DTYPE_NAMES = {sivf.FP32: "fp32", sivf.BF16: "bf16", sivf.FP8E4M3: "fp8"}
