@@ -75,6 +75,7 @@ def load_lib(path: str):
         "oivf_kmeans_init_rows": (i32, [i64, i32, C.c_uint64, p]),
         "oivf_kmeans": (i32, [p, i64, i32, i32, i32, C.c_uint64, p, p]),
         "oivf_fp8_list_scales": (None, [p, i32, i32, p]),
+        "oivf_approx_dists": (None, [p, p, i64, i32, i32, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +277,31 @@ def dists(q, x) -> np.ndarray:
     out = np.zeros(x.shape[0], np.float64)
     _load().oivf_dists(_ptr(q), _ptr(x), x.shape[0], q.shape[0], _ptr(out))
     return out
+
+
+def approx_dists(q, xs, dtype: str, inv_l=None, cent_l=None):
+    """FP64 value of the reduced-precision scan's approximate distance of
+    one query q to rows xs, and a magnitude for its FP32 accumulation error
+    (see ``oivf_approx_dists``).  BF16: ||q||^2 + ||x||^2 - 2 q^.x^ with the
+    rounded vectors.  FP8: the residuals from each row's list centroid
+    (``cent_l``, one row per member) coded in E4M3, the row's with its
+    list's inverse scale (``inv_l``), the query's with 448 / (2 max|q - c|);
+    the dot product is scaled back by both.  Returns (dist, mag)."""
+    q = _f32(q).reshape(-1)
+    xs = _f32(xs).reshape(-1, q.shape[0])
+    n, d = xs.shape
+    out = np.zeros(n, np.float64)
+    mag = np.zeros(n, np.float64)
+    if dtype == "bf16":
+        _load().oivf_approx_dists(_ptr(q), _ptr(xs), n, d, 0, None, None, _ptr(out), _ptr(mag))
+    elif dtype == "fp8":
+        cent_l = _f32(cent_l).reshape(n, d)
+        inv_l = _f32(inv_l).reshape(n)
+        _load().oivf_approx_dists(_ptr(q), _ptr(xs), n, d, 1, _ptr(cent_l), _ptr(inv_l),
+                                  _ptr(out), _ptr(mag))
+    else:
+        raise ValueError(dtype)
+    return out, mag
 
 
 # -- encodings -----------------------------------------------------------

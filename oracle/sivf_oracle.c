@@ -678,6 +678,86 @@ void oivf_to_e4m3(const float *in, float inv_scale, uint8_t *out, int64_t n)
 }
 
 /* ------------------------------------------------------------------ */
+/* approximate distance of the reduced-precision scan                   */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper scans FP32 payloads only (Algorithm 3).  The precision path of
+ * this build scans a rounded copy of every list, keeps each query's best 4k
+ * members by an approximate distance and re-ranks those exactly in FP32.
+ * This is the FP64 value of that approximate distance for one query q and
+ * rows x (the reading of the precision pattern this build takes; the
+ * paper has no passage for it):
+ *
+ *   mode 0 (BF16): ||q||^2 + ||x||^2 - 2 sum_j bf(q_j) bf(x_j), the norms
+ *     of the unrounded FP32 vectors and bf() the bfloat16 rounding above;
+ *   mode 1 (FP8 E4M3 residual codes): with the row's list centroid c
+ *     (cent, one row of d per x row), r = fl32(q - c), y = fl32(x - c),
+ *     the list's inverse scale t_l (inv_l, one per row) and the query's
+ *     own t_q = fl32(448 / fl32(2 max_j |r_j|)) (1 when r = 0):
+ *     ||r||^2 + ||y||^2 - 2 s sum_j e(r_j, t_q) e(y_j, t_l), where
+ *     e(v, t) is the value of the E4M3 code of fl32(v t) (encoder above)
+ *     and s = 1 / (t_l t_q) undoes both scales.
+ *
+ * mag[i] (optional) = the two norms + 2 s sum_j |code products|: the size
+ * against which an FP32 accumulation of the same terms is judged.
+ */
+static float bf16_round(float v)
+{
+    uint16_t b;
+    float r;
+    oivf_to_bf16(&v, &b, 1);
+    oivf_from_bf16(&b, &r, 1);
+    return r;
+}
+
+static double e4m3_round(float v, float inv_scale)
+{
+    uint8_t c;
+    double r;
+    oivf_to_e4m3(&v, inv_scale, &c, 1);
+    oivf_from_e4m3(&c, &r, 1);
+    return r;
+}
+
+void oivf_approx_dists(const float *q, const float *x, int64_t n, int d, int mode,
+                       const float *cent, const float *inv_l, double *out, double *mag)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const float *xi = x + (size_t)i * d;
+        double qn = 0.0, xn = 0.0, dot = 0.0, ab = 0.0, s = 1.0;
+        if (mode == 0) {
+            for (int j = 0; j < d; ++j) {
+                qn += (double)q[j] * (double)q[j];
+                xn += (double)xi[j] * (double)xi[j];
+                const double p = (double)bf16_round(q[j]) * (double)bf16_round(xi[j]);
+                dot += p;
+                ab += fabs(p);
+            }
+        } else {
+            const float *c = cent + (size_t)i * d;
+            float mx = 0.0f;
+            for (int j = 0; j < d; ++j) {
+                const float r = q[j] - c[j];
+                if (fabsf(r) > mx) mx = fabsf(r);
+            }
+            const float tq = mx > 0.0f ? 448.0f / (2.0f * mx) : 1.0f;
+            for (int j = 0; j < d; ++j) {
+                const float r = q[j] - c[j];
+                const float y = xi[j] - c[j];
+                qn += (double)r * (double)r;
+                xn += (double)y * (double)y;
+                const double p = e4m3_round(r, tq) * e4m3_round(y, inv_l[i]);
+                dot += p;
+                ab += fabs(p);
+            }
+            s = 1.0 / ((double)inv_l[i] * (double)tq);
+        }
+        out[i] = qn + xn - 2.0 * s * dot;
+        if (mag) mag[i] = qn + xn + 2.0 * s * ab;
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* coarse quantizer training                                            */
 /* ------------------------------------------------------------------ */
 /*

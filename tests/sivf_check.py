@@ -146,47 +146,10 @@ def compare_topk(gd, gi, od, oi, rtol: float = 1e-5, what: str = ""):
 
 # ------------------------------------------- reduced-precision candidates
 def approx_oracle(q, xs, dtype, inv_l, cent_l):
-    """FP64 value of the distance the reduced-precision scan approximates,
-    ||q||^2 + ||x||^2 - 2 s q^.x^, for one query q against rows xs, and a
-    magnitude bound for its FP32 accumulation error.  BF16: q^, x^ are the
-    rounded vectors, s = 1.  FP8: q^ and x^ are the E4M3 codes of the
-    residuals from each row's list centroid (cent_l, one row per member),
-    the row's with its list's inverse scale inv_l, the query's with
-    448 / (2 max|q - c_l|); s undoes both scales.  Rows of one list are
-    encoded together."""
-    if dtype == "bf16":
-        q64, x64 = q.astype(np.float64), xs.astype(np.float64)
-        qn = (q64 ** 2).sum()
-        xn = (x64 ** 2).sum(axis=1)
-        qh = oracle.from_bf16(oracle.to_bf16(q)).astype(np.float64)
-        xh = oracle.from_bf16(oracle.to_bf16(xs)).astype(np.float64)
-        prod = xh * qh[None, :]
-        scale = np.ones(len(xs))
-    else:
-        rq = (q[None, :] - cent_l).astype(np.float32)       # per member's list
-        rx = (xs - cent_l).astype(np.float32)
-        qn = (rq.astype(np.float64) ** 2).sum(axis=1)
-        xn = (rx.astype(np.float64) ** 2).sum(axis=1)
-        mx = np.abs(rq).max(axis=1)
-        invq = np.where(mx > 0, np.float32(448.0) / (np.float32(2.0) * mx),
-                        np.float32(1.0)).astype(np.float32)
-        qh = np.empty(rq.shape, np.float64)
-        xh = np.empty(rx.shape, np.float64)
-        crow = np.ascontiguousarray(cent_l, np.float32)
-        rowkey = crow.view(np.dtype((np.void, 4 * crow.shape[1]))).ravel()
-        _, grp = np.unique(rowkey, return_inverse=True)
-        grp = grp.ravel()
-        for gidx in np.unique(grp):
-            sel = np.nonzero(grp == gidx)[0]
-            j = sel[0]
-            assert (inv_l[sel] == inv_l[j]).all()
-            qh[sel] = oracle.from_e4m3(oracle.to_e4m3(rq[j], invq[j]))[None, :]
-            xh[sel] = oracle.from_e4m3(oracle.to_e4m3(rx[sel], inv_l[j]))
-        prod = xh * qh
-        scale = 1.0 / (inv_l.astype(np.float64) * invq.astype(np.float64))
-    dot = prod.sum(axis=1)
-    bound = 2 * np.abs(prod).sum(axis=1) * scale
-    return qn + xn - 2 * scale * dot, qn + xn + bound
+    """The oracle's approximate distance of the reduced-precision scan
+    (``oracle.approx_dists``) and the bound of an FP32 accumulation of it:
+    (FP64 value, norms + 2 s sum |products|)."""
+    return oracle.approx_dists(q, xs, dtype, inv_l, cent_l)
 
 
 # ------------------------------------------------ device index beside oracle

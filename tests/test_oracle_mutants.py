@@ -5,7 +5,10 @@ Each mutant is one textual change to ``oracle/sivf_oracle.c`` (a dropped
 coordinate, a wrong sign, ties sent to the wrong index, a top-k off by one,
 first- instead of last-occurrence-wins, an overwrite that forgets the old
 copy, a slab never returned, rounding by truncation, ties away from even,
-compaction slots, the last slab's fill, budget or threshold off by one).
+compaction slots, the last slab's fill, budget or threshold off by one, a
+row stride in the distance helper, and in the reduced-precision approximate
+distance: a scale not undone, a residual from the wrong centroid, the
+query norm taken from rounded values, the query scale off by two).
 The mutant is compiled into a temporary library, swapped in for the real
 oracle, and the pin tests of ``test_oracle_pins.py`` are run against it: at
 least one must fail.  The real oracle source is never modified.
@@ -18,8 +21,8 @@ import oracle
 import test_oracle_pins as pins
 
 MUTANTS = {
-    "drop_last_coordinate": ("for (int j = 0; j < d; ++j) {",
-                             "for (int j = 0; j < d - 1; ++j) {"),
+    "drop_last_coordinate": ("double acc = 0.0;\n    for (int j = 0; j < d; ++j) {",
+                             "double acc = 0.0;\n    for (int j = 0; j < d - 1; ++j) {"),
     "wrong_sign": ("double t = (double)a[j] - (double)b[j];",
                    "double t = (double)a[j] + (double)b[j];"),
     "ties_to_highest_centroid": ("if (dc < bd) {", "if (dc <= bd) {"),
@@ -43,6 +46,15 @@ MUTANTS = {
                        ";"),
     "e4m3_ties_up": ("if (dd < bd || (dd == bd && (c & 1) == 0 && (best & 1) == 1)) {",
                      "if (dd <= bd) {"),
+    "dists_row_stride": ("out[i] = sqdist(q, x + (size_t)i * d, d);",
+                         "out[i] = sqdist(q, x + (size_t)i, d);"),
+    "approx_scale_not_undone": ("s = 1.0 / ((double)inv_l[i] * (double)tq);",
+                                "s = (double)inv_l[i] * (double)tq;"),
+    "approx_residual_wrong_centroid": ("const float y = xi[j] - c[j];",
+                                       "const float y = xi[j] - cent[j];"),
+    "approx_bf16_norm_of_rounded_query": ("qn += (double)q[j] * (double)q[j];",
+                                          "qn += (double)bf16_round(q[j]) * (double)bf16_round(q[j]);"),
+    "approx_query_scale_from_max": ("448.0f / (2.0f * mx)", "448.0f / mx"),
 }
 
 PINS = [
@@ -65,6 +77,12 @@ PINS = [
     (pins.test_compact_worked_example, {}),
     (pins.test_compact_min_free_and_budget_rules, {}),
     (pins.test_compact_keeps_search_and_members, {}),
+    (pins.test_dists_equal_exact_rational_sums, dict(n=17, d=8, denom=4)),
+    (pins.test_dists_hand_value, {}),
+    (pins.test_approx_bf16_exact_inputs_equal_the_distance, {}),
+    (pins.test_approx_bf16_hand_value, {}),
+    (pins.test_approx_fp8_exact_codes_equal_the_distance, dict(t_l=4.0, qmax=112.0)),
+    (pins.test_approx_fp8_rounding_against_torch_codes, {}),
 ]
 
 

@@ -432,6 +432,115 @@ def test_e4m3_decode_all_codes_matches_torch():
     assert got.max() == 448.0 and got[got > 0].min() == 2.0 ** -9
 
 
+# ------------------------------------------------- distance functions
+@pytest.mark.parametrize("n,d,denom", [(1, 1, 1), (5, 3, 1), (17, 8, 4), (40, 33, 16)])
+def test_dists_equal_exact_rational_sums(n, d, denom):
+    """The FP64 distances every re-rank check compares against: on integer
+    and dyadic rows each term and each partial sum is exact in FP64, so the
+    result must equal the rational sum exactly, row by row (several n and d,
+    so a stride or row-offset mistake shows)."""
+    rng = np.random.default_rng(900 + d)
+    q = grid_points(rng, 1, d, -60, 60, denom)[0]
+    x = grid_points(rng, n, d, -60, 60, denom)
+    got = oracle.dists(q, x)
+    want = [float(exact_sq(q, row)) for row in x]
+    assert got.tolist() == want
+
+
+def test_dists_hand_value():
+    """The rows (1, 2, 2) and (4, -2, 2) from the origin: 1 + 4 + 4 = 9 and
+    16 + 4 + 4 = 24; from (1, 0, 1): 0 + 4 + 1 = 5 and 9 + 4 + 1 = 14."""
+    got = oracle.dists([0, 0, 0], [[1, 2, 2], [4, -2, 2]])
+    assert got.tolist() == [9.0, 24.0]
+    got = oracle.dists([1, 0, 1], [[1, 2, 2], [4, -2, 2]])
+    assert got.tolist() == [5.0, 14.0]
+
+
+def test_approx_bf16_exact_inputs_equal_the_distance():
+    """Integers of magnitude <= 256 are exact in bfloat16, so the expanded
+    form ||q||^2 + ||x||^2 - 2 q^.x^ equals the exact squared distance."""
+    rng = np.random.default_rng(31)
+    for n, d in [(1, 4), (9, 16), (33, 96)]:
+        q = rng.integers(-256, 257, size=d).astype(np.float32)
+        x = rng.integers(-256, 257, size=(n, d)).astype(np.float32)
+        got, mag = oracle.approx_dists(q, x, "bf16")
+        want = [float(exact_sq(q, row)) for row in x]
+        assert got.tolist() == want
+        assert (mag >= got).all()
+
+
+def test_approx_bf16_hand_value():
+    """q = (257), x = (3): 257 lies halfway between the bfloat16 values 256
+    and 258 and rounds to the even one, 256; the norms keep the unrounded
+    257, so the value is 257^2 + 3^2 - 2 * 256 * 3 = 64522 (the exact
+    distance is 254^2 = 64516)."""
+    got, mag = oracle.approx_dists([257.0], [[3.0]], "bf16")
+    assert got.tolist() == [64522.0]
+    assert mag.tolist() == [257.0 ** 2 + 9 + 2 * 768]
+
+
+def _e4m3_exact_rows(rng, n, d, lim):
+    """Rows of small integers in [-lim, lim]: exact in E4M3 (up to 16) and
+    after scaling by 2 or 4 when lim is 8."""
+    return rng.integers(-lim, lim + 1, size=(n, d)).astype(np.float64)
+
+
+@pytest.mark.parametrize("t_l,qmax", [(1.0, 224.0), (4.0, 112.0)])
+def test_approx_fp8_exact_codes_equal_the_distance(t_l, qmax):
+    """Residual codes with no rounding: the rows' residuals are integers in
+    [-8, 8] (times the list scale t_l in {1, 4}: exact E4M3 values), the
+    query's residual has largest magnitude qmax, so its own scale is
+    448 / (2 qmax) in {1, 2} and its codes are exact too.  The scales then
+    cancel and the value is ||(q - c) - (x - c)||^2 = ||q - x||^2 exactly.
+    Each row has its own centroid (a residual taken from another row's
+    centroid breaks the identity), the scale 2 / 4 cases fail if either
+    scale is not undone."""
+    rng = np.random.default_rng(int(t_l))
+    n, d = 12, 16
+    cent = rng.integers(-50, 51, size=(n, d)).astype(np.float64)
+    rq = _e4m3_exact_rows(rng, n, d, 8)
+    rq[:, 3] = qmax                        # the query's largest residual entry
+    # one query q for every row: q = c_i + rq_i must be the same vector, so
+    # the rows' centroids are chosen as q - rq_i
+    q = rng.integers(-40, 41, size=d).astype(np.float64)
+    cent = q[None, :] - rq
+    y = _e4m3_exact_rows(rng, n, d, 8)
+    x = cent + y
+    inv = np.full(n, t_l, np.float32)
+    got, _ = oracle.approx_dists(q.astype(np.float32), x.astype(np.float32), "fp8",
+                                 inv, cent.astype(np.float32))
+    want = [float(exact_sq(q.astype(np.float32), row)) for row in x.astype(np.float32)]
+    assert got.tolist() == want
+
+
+def test_approx_fp8_rounding_against_torch_codes():
+    """General residuals: the value equals the expanded form recomputed
+    from torch's own float8_e4m3fn casts of the scaled residuals (scales
+    computed by hand in float32), within FP64 rounding.  A few residual
+    entries are tiny, so their scaled values fall among the subnormal codes,
+    where a scale off by a power of two changes the rounding."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    n, d = 7, 24
+    q = rng.standard_normal(d).astype(np.float32)
+    cent = rng.standard_normal((n, d)).astype(np.float32)
+    cent[:, :4] = q[:4] - np.float32([3e-5, 1.1e-4, -7e-5, 2.3e-4])
+    x = (cent + 0.3 * rng.standard_normal((n, d))).astype(np.float32)
+    x[:, 4:8] = cent[:, 4:8] + np.float32([5e-5, -1.7e-4, 9e-5, 2e-4])
+    inv = (448.0 / (2.0 * np.abs(x - cent).max(axis=1))).astype(np.float32)
+    got, _ = oracle.approx_dists(q, x, "fp8", inv, cent)
+    for i in range(n):
+        r = (q - cent[i]).astype(np.float32)
+        y = (x[i] - cent[i]).astype(np.float32)
+        tq = np.float32(448.0) / (np.float32(2.0) * np.abs(r).max())
+        cq = torch.from_numpy((r * tq).astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
+        cy = torch.from_numpy((y * inv[i]).astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
+        s = 1.0 / (float(inv[i]) * float(tq))
+        want = (r.astype(np.float64) ** 2).sum() + (y.astype(np.float64) ** 2).sum() \
+            - 2.0 * s * (cq * cy).sum()
+        assert abs(got[i] - want) <= 1e-12 * abs(want) + 1e-12
+
+
 # ------------------------------------------------------ quantizer training
 def _golden_splitmix():
     out = {}
