@@ -403,8 +403,13 @@ sivf_status sivf_profile_read(sivf_index *index, const char *kernel,
  * ---------------------------------------------------------------------- */
 typedef struct {
     int32_t queries_per_tile; /* SIVF_FP32: 8, 16, 32 or 64 queries share
-                                 each slab load; the reduced dtypes use 64
-                                 (the tensor-core tile's N) and ignore it  */
+                                 each slab load.  Reduced dtypes: 64 = the
+                                 vector-row scan (slab rows on the MMA's M,
+                                 up to 48 queries as N; the default), 128 =
+                                 the query-row scan (up to 128 (query,
+                                 probe) pairs of a list on the tensor-memory
+                                 lanes, slab rows as N; only where its
+                                 candidate buffers fit)                    */
     int32_t slabs_per_chunk;  /* 1..16: a list is split into slab chunks
                                  of at least this many slabs              */
     int32_t items_per_sm;     /* 1..16: a list is split into chunks so that
@@ -417,13 +422,21 @@ typedef struct {
                                  for this many slabs of candidates (0: the
                                  built-in width, two slabs while that stays
                                  within 256 entries).  Reduced dtypes,
-                                 0..3: room for this many 128-row tiles of
-                                 candidates beside the best 4k (0: two
-                                 where shared memory keeps three load
-                                 stages, else one)                         */
-    int32_t nearest_first;    /* reduced dtypes: 1 scans each query's
-                                 nearest list in a launch of its own first,
-                                 so the other lists meet a tight bound     */
+                                 vector-row scan, 0..3: room for this many
+                                 128-row tiles of candidates beside the
+                                 held 4k (0: two where shared memory keeps
+                                 three load stages, else one); query-row
+                                 scan, 0..3: the longest candidate buffer
+                                 of one row (0, 1: 255, 2: 1023, 3: 2047)  */
+    int32_t nearest_first;    /* reduced dtypes, queries probing several
+                                 lists: 0 = one launch over every probe;
+                                 1 = each query's nearest list in a launch
+                                 of its own first, so the other lists meet
+                                 a tight bound (the query-row scan reads 1
+                                 as 2); 2 = a seed launch over the first
+                                 128 rows of each query's nearest list
+                                 publishes a bound per query, then one
+                                 launch streams every probed list once     */
 } sivf_tile;
 
 /*

@@ -458,7 +458,7 @@ static int64_t query_chunk(const sivf_index *ix, int P, int k)
     return std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) / per));
 }
 
-// plan of the reduced-precision scan: tiles of 64 queries, K' candidates
+// plan of the reduced-precision scan for K' candidates (the batch's tile)
 static SearchPlan plan_tc(const sivf_index *ix, int dtype, int64_t nq, int P, int Kc)
 {
     return plan_from_tile(ix, dtype, nq, P, Kc, current_tile(ix, dtype, nq, P, Kc));
@@ -473,9 +473,9 @@ static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dty
     SearchPlan pl = plan_tc(ix, dtype, m, P, Kc);
     *plo = pl;
     return coarse_bytes(ix, m) + (size_t)m * P * 4 * 4 + (size_t)(L + 1) * 4 * 4 +
-           (size_t)pl.run_cap * pl.K * 12 + (size_t)m * 4 * 3 + (size_t)m * 16 +
+           (size_t)pl.run_cap * (pl.RK * 12 + 4) + (size_t)m * 4 * 3 + (size_t)m * 16 +
            (size_t)m * pl.K * 12 + (size_t)pl.item_cap * 8 + (size_t)m * ix->d * 2 +
-           (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 22 * 256;
+           (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 23 * 256;
 }
 
 // reduced-precision candidates: the re-rank depth K' = 4k
@@ -733,7 +733,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         Ctx *c;
         if ((st = get_ctx(ix, stream, need, &c))) return st;
         Bump b{c->scratch};
-        SearchScratch sc;
+        SearchScratch sc{};
         int32_t *probes = b.take<int32_t>((size_t)m * P);
         sc.lcnt = b.take<int32_t>(L);
         sc.loff = b.take<int32_t>(L + 1);
@@ -743,8 +743,9 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         sc.qlist = b.take<int32_t>((size_t)m * P);
         sc.prun = b.take<int32_t>((size_t)m * P);
         sc.qrun = b.take<int2>((size_t)2 * m);
-        sc.part_d = b.take<float>((size_t)pl.run_cap * pl.K);
-        sc.part_i = b.take<int64_t>((size_t)pl.run_cap * pl.K);
+        sc.part_d = b.take<float>((size_t)pl.run_cap * pl.RK);
+        sc.part_i = b.take<int64_t>((size_t)pl.run_cap * pl.RK);
+        sc.part_n = tc ? b.take<int32_t>((size_t)pl.run_cap) : nullptr;
         sc.thr = b.take<float>((size_t)m);
         sc.items = b.take<int2>((size_t)pl.item_cap);
         sc.qn = b.take<float>((size_t)m);
@@ -769,27 +770,47 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             scan_lists(ix, qq, m, P, probes, probes_in != nullptr, pl, sc, s);
             merge_topk(ix, m, P, probes, pl, sc, k, dist + q0 * k, labels + q0 * k, s);
         } else {
-            // phase 1: every query's nearest list alone sets a tight bound on
-            // its K'-th distance; phase 2 scans the other lists under it
             const int esz = dtype == SIVF_BF16 ? 2 : 1;
             // per slab: payload copy, ||x||^2 and the validity bitmap
             const int64_t sb = (int64_t)ix->C * (ix->d * esz + 4) + ix->C / 8;
             CUDA_TRY(ix, cudaMemsetAsync(sc.thr, 0x7f, sizeof(float) * m, s));
             if (fp8) pair_prep(ix, qq, m, P, probes, sc.pqn, sc.pqsc, sc.qcast, s);
             else query_prep(ix, qq, m, sc.qn, sc.qsc, sc.qcast, s);
-            const int split = P > 1 && pl.split ? 1 : P;
-            group_pairs(ix, m, P, 0, split, probes, probes_in != nullptr, pl, sc, sb, s);
-            scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
-            if (split < P) {
-                group_pairs(ix, m, P, split, P, probes, probes_in != nullptr, pl, sc, sb, s);
+            int nphase = 1;
+            const bool dd = probes_in != nullptr;
+            const int seed = (128 + ix->C - 1) / ix->C;  // slabs of the first 128 rows
+            if (P > 1 && (pl.split == 2 || (pl.qt && pl.split))) {
+                // a seed launch over the first 128 rows of every query's
+                // nearest list publishes a bound per query (no candidates
+                // kept); the main launch then streams every probed list once
+                group_pairs(ix, m, P, 0, 1, probes, dd, pl, sc, sb, s, false);
+                if (pl.qt) scan_lists_qt(ix, dtype, m, P, Kc, seed, pl.sel, sc, s);
+                else scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s, seed);
+                CUDA_TRY(ix, cudaMemsetAsync(&ix->ctl->nruns, 0, sizeof(int32_t), s));
+                group_pairs(ix, m, P, 0, P, probes, dd, pl, sc, sb, s);
+                if (pl.qt) scan_lists_qt(ix, dtype, m, P, Kc, 0, pl.sel, sc, s);
+                else scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+            } else if (pl.qt) {
+                group_pairs(ix, m, P, 0, P, probes, dd, pl, sc, sb, s);
+                scan_lists_qt(ix, dtype, m, P, Kc, 0, pl.sel, sc, s);
+            } else {
+                // vector-row scan.  With split == 1, phase 1: every query's
+                // nearest list alone sets a tight bound on its K'-th
+                // distance; phase 2 scans the other lists under it
+                const int split = P > 1 && pl.split == 1 ? 1 : P;
+                group_pairs(ix, m, P, 0, split, probes, dd, pl, sc, sb, s);
                 scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+                if (split < P) {
+                    group_pairs(ix, m, P, split, P, probes, dd, pl, sc, sb, s);
+                    scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+                }
+                nphase = split < P ? 2 : 1;
             }
-            const int nphase = split < P ? 2 : 1;
             if (cand_only) {
-                merge_tc(ix, m, nphase, sc, Kc, dist + q0 * k, labels + q0 * k, s);
+                merge_tc(ix, m, nphase, sc, Kc, pl.RK, dist + q0 * k, labels + q0 * k, s);
                 slots_to_ids(ix, labels + q0 * k, m * k, s);
             } else {
-                merge_tc(ix, m, nphase, sc, Kc, cand_d, cand_s, s);
+                merge_tc(ix, m, nphase, sc, Kc, pl.RK, cand_d, cand_s, s);
                 rerank(ix, qq, m, Kc, cand_d, cand_s, k, dist + q0 * k, labels + q0 * k, s);
             }
         }

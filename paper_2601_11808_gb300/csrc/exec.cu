@@ -361,6 +361,7 @@ sivf_status sivf_autotune(sivf_index *ix, const float *q, int64_t nq, int k, int
     static const int sel_v[] = {0, 1, 2, 4};
     static const int nf_v[] = {0, 1};
     static const int tsel_v[] = {0, 1, 2};
+    static const int tqr_v[] = {64, 128};
     struct Knob {
         int32_t sivf_tile::*field;
         const int *v;
@@ -371,6 +372,7 @@ sivf_status sivf_autotune(sivf_index *ix, const float *q, int64_t nq, int k, int
         knobs.push_back({&sivf_tile::queries_per_tile, tq_v, 4});
         knobs.push_back({&sivf_tile::select_slabs, sel_v, 4});
     } else {
+        knobs.push_back({&sivf_tile::queries_per_tile, tqr_v, 2});
         knobs.push_back({&sivf_tile::nearest_first, nf_v, 2});
         knobs.push_back({&sivf_tile::select_slabs, tsel_v, 3});
     }

@@ -3,6 +3,8 @@
 // caller's arena.
 #pragma once
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "sivf_internal.cuh"
@@ -46,8 +48,9 @@ struct SearchScratch {
     int32_t *nch;        // [nlist] slab chunks of each list
     int32_t *prank;      // [nq * P] rank of the pair inside its list group
     int32_t *qlist;      // [nq * P] pairs grouped by list (q * P + p)
-    float *part_d;       // [run_cap * K] item outputs: one run of K per (pair, chunk)
-    int64_t *part_i;     // [run_cap * K]
+    float *part_d;       // [run_cap * RK] item outputs: one run per (pair, chunk)
+    int64_t *part_i;     // [run_cap * RK]
+    int32_t *part_n;     // [run_cap] valid entries of each run (reduced precision)
     float *thr;          // [nq] shared bound of each query's k-th distance
     int32_t *prun;       // [nq * P] run of the pair's chunk 0 (chunk c writes run
                          // prun + c); -1: the pair is not scanned
@@ -68,9 +71,17 @@ struct SearchPlan {
     int ips;             // work items per SM the chunking aims at
     int64_t run_cap;     // output runs of one query chunk (both phases)
     int64_t item_cap;    // work items of one scan launch
-    int K;               // candidates kept per (query, item)
+    int K;               // candidates kept per query (K' for the reduced dtypes)
+    int RK;              // entries of one output run (K for FP32; K' plus the room
+                         // an approximate reduction may keep for the reduced dtypes)
     int M;               // entries of each row's k-select / candidate buffer
-    int split;           // reduced precision: nearest list in a launch of its own
+    int split;           // reduced precision, queries probing several lists: 1 =
+                         // each query's nearest list in a launch of its own, then
+                         // the other lists; 2 = a seed launch over the first 128
+                         // rows of each query's nearest list (bounds only), then
+                         // one launch over every probed list
+    int qt;              // reduced precision: the query-row scan (scan_qt.cu)
+    int sel;             // the tile's select_slabs (query-row scan: buffer cap)
 };
 // tile choice for a batch: the installed one of its bucket, else the default
 int tune_bucket(const sivf_index *ix, int64_t nq, int P);
@@ -88,9 +99,12 @@ int64_t plan_item_cap(int64_t nq, int P, int L, int ips);
 bool scan_fits(const sivf_index *ix, int K);   // shared memory for k = K
 void scan_lists(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                 bool dedupe, const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
+// group the pairs with probe rank in [p0, p1) by list and lay out the work
+// items and output runs; `stats` adds the scan's pairs and bytes to the
+// index's counters (off for the seed launch of the query-row scan)
 void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_t *probes,
                  bool dedupe, const SearchPlan &pl, const SearchScratch &s, int64_t slab_bytes,
-                 cudaStream_t st);
+                 cudaStream_t st, bool stats = true);
 void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
                 const SearchPlan &pl, const SearchScratch &s, int k, float *dist,
                 int64_t *labels, cudaStream_t st);
@@ -109,15 +123,37 @@ bool tc_fits(const sivf_index *ix, int Kc);
 int tc_buf_entries(const sivf_index *ix, int dtype, int Kc, int sel);
 bool tc_buf_fits(const sivf_index *ix, int dtype, int Kc, int M);
 int tc_tile_queries(int Kc);   // 48 (K' <= 64), 32 (<= 128) or 16 (<= 512)
+// seed_slabs > 0: a seed launch over the first seed_slabs slabs of each item
+// that publishes each query's bound and writes no runs
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
-                   const SearchPlan &pl, const SearchScratch &s, cudaStream_t st);
+                   const SearchPlan &pl, const SearchScratch &s, cudaStream_t st,
+                   int seed_slabs = 0);
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st);
 // per query: the best Kc (distance, slot) of its reduced-precision item
 // outputs (the runs of `nphase` scan phases), sorted ascending
-void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc,
+void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc, int RK,
               float *out_d, int64_t *out_s, cudaStream_t st);
+int tc_run_len(int Kc);  // RK of the vector-row scan for K' = Kc
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
+
+// ---- reduced-precision scan, queries on the tensor-memory lanes (scan_qt.cu)
+struct QtShape {
+    bool ok;             // the shape fits for this dtype, d, slab size and K'
+    int KC;              // 128-byte chunks of a row in the scan format
+    int NV;              // slab rows per B tile (128 / KC)
+    int nst;             // B stages
+    int ME;              // entries of a query row's candidate buffer
+    size_t smem;         // dynamic shared memory of the CTA
+};
+QtShape qt_shape(const sivf_index *ix, int dtype, int Kc);
+bool qt_make_maps(sivf_index *ix, PFN_cuTensorMapEncodeTiled_v12000 enc);
+// one launch over the grouped items; seed_slabs > 0 scans only the first
+// seed_slabs slabs of each item and publishes the bounds, writing no runs;
+// select_slabs is the tile's buffer-length knob (qt_mecap)
+void scan_lists_qt(sivf_index *ix, int dtype, int64_t nq, int P, int Kc, int seed_slabs,
+                   int select_slabs, const SearchScratch &s, cudaStream_t st);
+int qt_mecap(int select_slabs);
 
 // ---- compaction of partly-live slabs (compact.cu)
 struct CompactArgs {

@@ -135,7 +135,7 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
     Carve c{reinterpret_cast<char *>(base), 0, kNoallocBytes};
     Ctl *ctl = c.take<Ctl>(1);
     int32_t *probes = c.take<int32_t>((size_t)nq * P);
-    SearchScratch sc;
+    SearchScratch sc{};
     sc.lcnt = c.take<int32_t>(L);
     sc.loff = c.take<int32_t>(L + 1);
     sc.ibase = c.take<int32_t>(L + 1);

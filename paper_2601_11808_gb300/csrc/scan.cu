@@ -100,9 +100,9 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
             ubytes += (unsigned long long)ns * slab_bytes;
         }
     }
-    if (pairs) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 1), pairs);
-    if (bytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 2), bytes);
-    if (ubytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 3), ubytes);
+    if (stat && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 1), pairs);
+    if (stat && bytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 2), bytes);
+    if (stat && ubytes) atomicAdd(reinterpret_cast<unsigned long long *>(stat + 3), ubytes);
     sa[tid] = ca;
     sb[tid] = cb;
     __syncthreads();
@@ -784,6 +784,7 @@ sivf_tile default_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K
         t.select_slabs = 0;
         t.nearest_first = 0;
     } else {
+        // the vector-row scan (the query-row scan, 128, is a tile option)
         t.queries_per_tile = 64;
         t.slabs_per_chunk = 4;
         t.items_per_sm = 4;
@@ -805,9 +806,12 @@ bool tile_valid(const sivf_index *ix, int dtype, const sivf_tile &t, int K)
         return scan_smem(tq, ix->C, ix->d, fp32_width(K, ix->C, t.select_slabs)).total <=
                220 * 1024;
     }
+    if (t.nearest_first < 0 || t.nearest_first > 2) return false;
+    if (t.queries_per_tile == 128)
+        return t.select_slabs >= 0 && t.select_slabs <= 3 && qt_shape(ix, dtype, K).ok;
+    if (t.queries_per_tile != 64) return false;
     if (t.select_slabs < 0 || t.select_slabs > 3) return false;
-    if (!tc_buf_fits(ix, dtype, K, tc_buf_entries(ix, dtype, K, t.select_slabs))) return false;
-    return t.nearest_first == 0 || t.nearest_first == 1;
+    return tc_buf_fits(ix, dtype, K, tc_buf_entries(ix, dtype, K, t.select_slabs));
 }
 
 sivf_tile current_tile(const sivf_index *ix, int dtype, int64_t nq, int P, int K)
@@ -822,11 +826,15 @@ SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, in
 {
     SearchPlan pl;
     const bool fp32 = dtype == SIVF_FP32;
-    pl.tq = fp32 ? t.queries_per_tile : tc_tile_queries(K);
+    pl.qt = !fp32 && t.queries_per_tile == 128;
+    pl.tq = fp32 ? t.queries_per_tile : pl.qt ? 128 : tc_tile_queries(K);
     pl.K = K;
-    pl.M = fp32 ? fp32_width(K, ix->C, t.select_slabs)
-                : tc_buf_entries(ix, dtype, K, t.select_slabs);
+    pl.M = fp32  ? fp32_width(K, ix->C, t.select_slabs)
+           : pl.qt ? qt_shape(ix, dtype, K).ME
+                   : tc_buf_entries(ix, dtype, K, t.select_slabs);
     pl.split = fp32 ? 0 : t.nearest_first;
+    pl.sel = t.select_slabs;
+    pl.RK = (fp32 || pl.qt) ? K : tc_run_len(K);
     // slab chunks: a list is split when its items would be long against the
     // launch's work per SM (decided on the device from the grouped pairs);
     // at most 2048 runs per query reach the merge
@@ -863,7 +871,7 @@ bool scan_fits(const sivf_index *ix, int K)
 
 void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_t *probes,
                  bool dedupe, const SearchPlan &pl, const SearchScratch &s, int64_t slab_bytes,
-                 cudaStream_t st)
+                 cudaStream_t st, bool stats)
 {
     const int L = ix->nlist;
     cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
@@ -874,7 +882,8 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
     k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
     k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
                                     pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff,
-                                    s.ibase, s.nch, s.items, ix->ctl, ix->stat, ix->err);
+                                    s.ibase, s.nch, s.items, ix->ctl, stats ? ix->stat : nullptr,
+                                    ix->err);
     k_srch_scatter<<<gq, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
                                        s.prun, s.qrun, ix->ctl, pl.run_cap, ix->err);
     prof_end(ix, tg, st);

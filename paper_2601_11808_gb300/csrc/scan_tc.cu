@@ -79,6 +79,8 @@ struct TcArgs {
     int per_pair;                // qn, qsc, qcast are per (query, probe) pair (FP8)
     float *part_d;
     int64_t *part_i;  // global slot (slab * C + slot) of each candidate
+    int32_t *part_n;  // candidates in each run (at most RK)
+    int RK;           // run length: K' plus room an approximate reduction may keep
     float *thr;
     const float *xnorm;
     const uint32_t *bits;
@@ -89,6 +91,8 @@ struct TcArgs {
     int L, d, C, KC;  // KC = 128-byte K chunks per row
     int nst;          // A-tile stages
     int pf_tiles;     // A tiles prefetched into L2 ahead of the loads
+    int seed_slabs;   // > 0: seed launch: the first seed_slabs slabs of each
+                      // item, bounds published, no runs written
     Ctl *ctl;
     uint32_t *err;
 };
@@ -258,13 +262,13 @@ __device__ __forceinline__ void warp_radix_kth(KeyF key, int n, int K, uint32_t 
 }
 
 // Keep in bd/bs[0, K) the K smallest (distance, slot) entries of the two
-// unsorted runs [0, nb) and [K, K + nc), with nb + nc > K; the kept
+// unsorted runs [0, nb) and [PB, PB + nc) (PB >= K), with nb + nc > K; the kept
 // entries stay unsorted (a slot appears once per buffer, so the keys are
 // distinct).  Returns the largest kept distance.
-__device__ float warp_select_keep(float *bd, int32_t *bs, int K, int nb, int nc,
+__device__ float warp_select_keep(float *bd, int32_t *bs, int K, int PB, int nb, int nc,
                                   uint32_t *hist, int lane)
 {
-    auto at = [&](int i) { return i < nb ? i : K + (i - nb); };
+    auto at = [&](int i) { return i < nb ? i : PB + (i - nb); };
     uint64_t prefix, mask;
     warp_radix_kth([&](int i) { return ds_key(bd[at(i)], bs[at(i)]); }, nb + nc, K, hist, lane,
                    prefix, mask);
@@ -293,7 +297,7 @@ __device__ float warp_select_keep(float *bd, int32_t *bs, int K, int nb, int nc,
         __syncwarp();
     }
     for (int i0 = 0; i0 < nc; i0 += 32) {
-        const int i = K + i0 + lane;
+        const int i = PB + i0 + lane;
         float dv = 0.f;
         int32_t sv = 0;
         bool take = false;
@@ -318,14 +322,18 @@ __device__ float warp_select_keep(float *bd, int32_t *bs, int K, int nb, int nc,
     return dmax;
 }
 
-// Binary-search form of warp_select_keep for nb + nc <= 32 * EK: the 32-bit
-// distance keys and the slots live in registers; the K-th smallest key is
-// found by bisection on the key value, each step one compare and one ballot
-// per register (no shared memory); distance ties at the K-th
-// place keep the lowest slots (a second bisection on the slot).  The kept
-// entries are written back from registers.
+// Reduce the two unsorted runs [0, nb) and [PB, PB + nc) of one row
+// (nb + nc <= 32 * EK, more than Kw entries) to between K and Kw of their
+// smallest (distance, slot) entries, written unsorted to [0, kept); returns
+// the largest kept distance, a bound on the row's K-th smallest.  The
+// 32-bit distance keys and the slots live in registers; a bisection on the
+// key value with ballot counts stops at the first value with between K and
+// Kw keys at or below it, which takes a few rounds where the exact K-th
+// needs one per key bit.  Only when ties at the K-th key span past Kw is
+// the cut made exact (K kept, ties to the lower slots).
 template <int EK>
-__device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int nc, int lane)
+__device__ float warp_select_window(float *bd, int32_t *bs, int K, int Kw, int PB, int nb,
+                                    int nc, int lane, int &kept)
 {
     const int n = nb + nc;
     uint32_t key[EK];
@@ -333,7 +341,7 @@ __device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int 
 #pragma unroll
     for (int e = 0; e < EK; ++e) {
         const int i = lane + 32 * e;
-        const int ai = i < nb ? i : K + (i - nb);
+        const int ai = i < nb ? i : PB + (i - nb);
         key[e] = i < n ? fkey(bd[ai]) : 0xffffffffu;
         slt[e] = i < n ? bs[ai] : 0x7fffffff;
     }
@@ -346,51 +354,43 @@ __device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int 
         }
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
-    // bisection for the smallest v with #(key <= v) >= K; it stops early at
-    // any v with exactly K keys <= v (v then lies between the K-th and the
-    // (K+1)-th smallest key: the kept set is the same and needs no tie
-    // step), which takes about log2(n) rounds instead of one per key bit
-    uint32_t lo = kmin, hi = kmax;
-    bool exact = false;
-    while (lo < hi) {  // counts by independent ballots (every lane gets them)
+    // invariant: #(key <= hi) >= K; stop at any value with K..Kw keys below
+    uint32_t lo = kmin, hi = kmax, cnt = 0;
+    bool found = false;
+    while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
         uint32_t c = 0;
 #pragma unroll
         for (int e = 0; e < EK; ++e) c += __popc(__ballot_sync(0xffffffffu, key[e] <= mid));
-        if (c == (uint32_t)K) {
+        if (c >= (uint32_t)K && c <= (uint32_t)Kw) {
             lo = mid;
-            exact = true;
+            cnt = c;
+            found = true;
             break;
         }
-        if (c > (uint32_t)K) hi = mid;
+        if (c > (uint32_t)Kw) hi = mid;
         else lo = mid + 1;
     }
-    if (exact) {  // keep every key <= lo; the K-th smallest is their maximum
-        uint32_t kk = 0u;
+    const uint32_t v = lo;  // found: K..Kw keys <= v; else v is the K-th key
+    if (!found) {
+        uint32_t c = 0;
 #pragma unroll
-        for (int e = 0; e < EK; ++e)
-            if (key[e] <= lo) kk = max(kk, key[e]);
-        lo = __reduce_max_sync(0xffffffffu, kk);
+        for (int e = 0; e < EK; ++e) c += __popc(__ballot_sync(0xffffffffu, key[e] <= v));
+        cnt = c;
     }
-    const uint32_t kth = lo;
-    uint32_t clt = 0, ceq = 0;
+    int32_t cut = 0x7fffffff;  // entries equal to v kept: slot <= cut
+    if (cnt > (uint32_t)Kw) {  // ties at v span past Kw: keep exactly K
+        uint32_t clt = 0;
 #pragma unroll
-    for (int e = 0; e < EK; ++e) {
-        clt += key[e] < kth;
-        ceq += key[e] == kth;
-    }
-    clt = __reduce_add_sync(0xffffffffu, clt);
-    ceq = __reduce_add_sync(0xffffffffu, ceq);
-    const uint32_t need = (uint32_t)K - clt;  // 1 <= need <= ceq
-    int32_t cut = 0x7fffffff;                 // tied entries kept: slot <= cut
-    if (ceq > need) {
+        for (int e = 0; e < EK; ++e) clt += __popc(__ballot_sync(0xffffffffu, key[e] < v));
+        const uint32_t need = (uint32_t)K - clt;
         int32_t slo = 0, shi = 0x7fffffff;
         while (slo < shi) {
             const int32_t mid = slo + ((shi - slo) >> 1);
             uint32_t c = 0;
 #pragma unroll
             for (int e = 0; e < EK; ++e)
-                c += __popc(__ballot_sync(0xffffffffu, key[e] == kth && slt[e] <= mid));
+                c += __popc(__ballot_sync(0xffffffffu, key[e] == v && slt[e] <= mid));
             if (c >= need) shi = mid;
             else slo = mid + 1;
         }
@@ -398,40 +398,46 @@ __device__ float warp_select_keep_bs(float *bd, int32_t *bs, int K, int nb, int 
     }
     __syncwarp();  // every lane has read its entries before any is written
     int w = 0;
+    uint32_t kk = 0u;
 #pragma unroll
     for (int e = 0; e < EK; ++e) {
-        const bool take = key[e] < kth || (key[e] == kth && slt[e] <= cut);
+        const bool take = key[e] < v || (key[e] == v && slt[e] <= cut);
         const uint32_t mk = __ballot_sync(0xffffffffu, take);
         if (take) {
             const int p = w + __popc(mk & lanemask_lt());
             bd[p] = fkey_inv(key[e]);
             bs[p] = slt[e];
+            kk = max(kk, key[e]);
         }
         w += __popc(mk);
     }
     __syncwarp();
-    return fkey_inv(kth);
+    kept = w;
+    return fkey_inv(__reduce_max_sync(0xffffffffu, kk));
 }
 
-// Fold the nc pending candidates of one row into its best set: keep the
-// best K' of the union (unsorted); move them down when they fit whole.
-// Returns the new K'-th distance (+inf while fewer than K' are held).
-__device__ __forceinline__ float fold_row(float *bd, int32_t *bs, int K, int &nb, int nc,
-                                          uint32_t *hist, int lane)
+// Fold the nc pending candidates of one row (at [PB, PB + nc)) into its
+// held set [0, nb): when the union holds more than Kw entries it is reduced
+// to between K and Kw of its smallest (exactly K for long buffers, by the
+// radix select), else the pending entries move down whole.  Returns a bound
+// on the row's K-th smallest distance (+inf while fewer than K are held).
+__device__ __forceinline__ float fold_row(float *bd, int32_t *bs, int K, int Kw, int PB, int &nb,
+                                          int nc, uint32_t *hist, int lane)
 {
-    if (nb + nc > K) {
-        const int n = nb + nc;
-        const float kd = n <= 64    ? warp_select_keep_bs<2>(bd, bs, K, nb, nc, lane)
-                         : n <= 128 ? warp_select_keep_bs<4>(bd, bs, K, nb, nc, lane)
-                         : n <= 192 ? warp_select_keep_bs<6>(bd, bs, K, nb, nc, lane)
-                         : n <= 320 ? warp_select_keep_bs<10>(bd, bs, K, nb, nc, lane)
-                                    : warp_select_keep(bd, bs, K, nb, nc, hist, lane);
-        nb = K;
+    const int n = nb + nc;
+    if (n > Kw) {
+        int kept = K;
+        const float kd = n <= 64    ? warp_select_window<2>(bd, bs, K, Kw, PB, nb, nc, lane, kept)
+                         : n <= 128 ? warp_select_window<4>(bd, bs, K, Kw, PB, nb, nc, lane, kept)
+                         : n <= 192 ? warp_select_window<6>(bd, bs, K, Kw, PB, nb, nc, lane, kept)
+                         : n <= 320 ? warp_select_window<10>(bd, bs, K, Kw, PB, nb, nc, lane, kept)
+                                    : warp_select_keep(bd, bs, K, PB, nb, nc, hist, lane);
+        nb = kept;
         return kd;
     }
-    for (int i = lane; i < nc; i += 32) {  // write index < K <= read index
-        const float dv = bd[K + i];
-        const int32_t sv = bs[K + i];
+    for (int i = lane; i < nc; i += 32) {  // write index < PB <= read index
+        const float dv = bd[PB + i];
+        const int32_t sv = bs[PB + i];
         bd[nb + i] = dv;
         bs[nb + i] = sv;
     }
@@ -612,6 +618,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                     }
                     s0 = (int)((int64_t)ns_total * chunk / nc_l);
                     ns = (int)((int64_t)ns_total * (chunk + 1) / nc_l) - s0;
+                    if (a.seed_slabs > 0) ns = chunk == 0 ? min(ns, a.seed_slabs) : 0;
                     nsub = max(1, (ns + TC_META - 1) / TC_META);
                     sub = 0;
                     qb = a.loff[l] + r0;
@@ -817,9 +824,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             if (flags & CF_STOP) break;
             const int m = h[1], sns = h[3], nblk = h[4], ME = h[5], chunk = h[7];
             const float inv_l = __int_as_float(h[9]);
-            // a row's pending candidates are folded into its best K' once a
-            // tile leaves more than FT of them: FT plus one tile always fits
-            const int FT = min(ME - K, 256) - TC_M;
+            // a row holds [0, nb) (at most RK) and appends at RK; its pending
+            // candidates are folded once a tile leaves more than FT of them:
+            // FT plus one tile always fits.  A fold keeps K' .. Kw.
+            const int RK = a.RK, Kw = K + ((RK - K) >> 1);
+            const int FT = min(ME - RK, 256) - TC_M;
             const int32_t *qp = c_qpair(j);
             const float *cqn = c_qn(j), *cqsc = c_qsc(j), *ckd = c_kd0(j);
             const int32_t *sl = c_sl(j);
@@ -908,7 +917,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                             const int n = c0 + i;
                             const int base = __shfl_sync(0xffffffffu, mybase, i);
                             if ((mk[i] >> lane) & 1u) {
-                                const int p = K + base + __popc(mk[i] & lanemask_lt());
+                                const int p = RK + base + __popc(mk[i] & lanemask_lt());
                                 BD[(size_t)n * ME + p] = fmaf(-s_sc[n], dv[i], cqn[n] + xn);
                                 BS[(size_t)n * ME + p] = gslot;
                             }
@@ -923,8 +932,8 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                         const int cc = s_cnt[n];
                         if (cc <= FT) continue;
                         int nb = s_nb[n];
-                        const float kd = fold_row(BD + (size_t)n * ME, BS + (size_t)n * ME, K, nb,
-                                                  cc, hist, lane);
+                        const float kd = fold_row(BD + (size_t)n * ME, BS + (size_t)n * ME, K, Kw,
+                                                  RK, nb, cc, hist, lane);
                         if (lane == 0) {
                             s_nb[n] = nb;
                             s_cnt[n] = 0;
@@ -943,9 +952,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                 break;
             }
             if (flags & CF_LAST) {
-                // each row's best K' (unsorted; the per-query merge sorts),
-                // padded with (+inf, -1); its K'-th distance becomes a bound
-                // of the query for the items that follow
+                // each row's run: between K' and RK of its smallest
+                // candidates (all of them when fewer), unsorted, with their
+                // count (the per-query merge selects and sorts the best K');
+                // a bound on its K'-th distance becomes a bound of the query
+                // for the items that follow
                 named_bar_sync(1, EPI);
                 for (int n = ew; n < m; n += EW) {
                     const int cc = s_cnt[n];
@@ -953,13 +964,14 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                     float *bd = BD + (size_t)n * ME;
                     int32_t *bs = BS + (size_t)n * ME;
                     float kd = s_kd[n];
-                    if (cc > 0) kd = fminf(kd, fold_row(bd, bs, K, nb, cc, hist, lane));
-                    const int run = a.prun[qp[n]];
-                    const int64_t base = ((int64_t)run + chunk) * K;
-                    for (int i = lane; i < K && run >= 0; i += 32) {
-                        a.part_d[base + i] = i < nb ? bd[i] : INFINITY;
-                        a.part_i[base + i] = i < nb ? (int64_t)bs[i] : -1;
+                    if (cc > 0) kd = fminf(kd, fold_row(bd, bs, K, RK, RK, nb, cc, hist, lane));
+                    const int run = a.seed_slabs > 0 ? -1 : a.prun[qp[n]];
+                    const int64_t base = ((int64_t)run + chunk) * RK;
+                    for (int i = lane; i < nb && run >= 0; i += 32) {
+                        a.part_d[base + i] = bd[i];
+                        a.part_i[base + i] = (int64_t)bs[i];
                     }
+                    if (lane == 0 && run >= 0) a.part_n[run + chunk] = nb;
                     if (lane == 0 && kd >= 0.f && kd < INFINITY)
                         atomicMin(reinterpret_cast<int *>(a.thr) + qp[n] / a.P, __float_as_int(kd));
                     __syncwarp();
@@ -977,58 +989,137 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
 
 // ------------------------------------------------------- per-query merge
 // One warp per query: the best K' (distance, slot) of the query's item
-// outputs (runs of K' unsorted entries, valid ones first, padded with
-// (+inf, -1); the runs of one scan phase are contiguous, qrun[phase][q] =
+// outputs (runs of RK entries of which the first part_n[run] are valid,
+// unsorted; the runs of one scan phase are contiguous, qrun[phase][q] =
 // (first run, runs)) by a radix select over the 64-bit (distance, slot)
-// keys, then sorted ascending, padded with (+inf, -1).
+// keys of the valid entries, then sorted ascending, padded with (+inf, -1).
 constexpr int MT_NT = 128;
 template <int E>
 __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qrun, int64_t nq,
-                                                    int nphase, int K,
+                                                    int nphase, int K, int RK,
+                                                    const int32_t *__restrict__ part_n,
                                                     const float *__restrict__ part_d,
                                                     const int64_t *__restrict__ part_i,
                                                     float *__restrict__ out_d,
                                                     int64_t *__restrict__ out_s)
 {
     constexpr int NW = MT_NT / 32;
-    __shared__ uint32_t hist[NW][TC_HIST];
+    __shared__ uint32_t hist_s[NW][TC_HIST];
     __shared__ float sd[NW][32 * E];
     __shared__ int32_t ss[NW][32 * E];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
     if (q >= nq) return;  // whole warps
+    uint32_t *hist = hist_s[warp];
     const int2 r0 = qrun[q];
     const int2 r1 = nphase > 1 ? qrun[nq + q] : make_int2(0, 0);
-    const int N0 = r0.y * K, N = N0 + r1.y * K;
-    // entry i of the query's runs -> its place in part_d / part_i
-    auto at = [&](int i) -> int64_t {
-        return i < N0 ? (int64_t)r0.x * K + i : (int64_t)r1.x * K + (i - N0);
-    };
-    auto key = [&](int i) -> uint64_t {
-        const int64_t e = at(i);
-        const int64_t sl = part_i[e];
-        return sl < 0 ? ~0ull : ds_key(part_d[e], (int32_t)sl);
+    const int NR = r0.y + r1.y;
+    auto run_of = [&](int t) -> int64_t { return t < r0.y ? r0.x + t : r1.x + (t - r0.y); };
+    auto key_at = [&](int64_t e) -> uint64_t { return ds_key(part_d[e], (int32_t)part_i[e]); };
+    // visit every valid entry: f(valid, index) for 32 entries at a time,
+    // called by the whole warp (the loops are warp-uniform)
+    auto each = [&](auto f) {
+        for (int t = 0; t < NR; ++t) {
+            const int64_t rb = run_of(t);
+            const int c = min(part_n[rb], RK);
+            for (int j0 = 0; j0 < c; j0 += 32) f(j0 + lane < c, rb * RK + j0 + lane);
+        }
     };
     int nv = 0;
-    for (int i = lane; i < N; i += 32) nv += key(i) != ~0ull;
+    for (int t = lane; t < NR; t += 32) nv += min(part_n[run_of(t)], RK);
     for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
     uint64_t prefix = ~0ull, mask = 0ull;  // keep every valid entry
-    if (nv > K) warp_radix_kth(key, N, K, hist[warp], lane, prefix, mask);
+    if (nv > K) {
+        // radix select: 8 bits per pass from the highest bit where the keys
+        // differ, stopping at the first pass whose chosen bin is taken whole
+        uint64_t kmin = ~0ull, kmax = 0ull;
+        each([&](bool ok, int64_t e) {
+            if (ok) {
+                const uint64_t k = key_at(e);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
+        });
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmin, o));
+            kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmax, o));
+        }
+        const uint64_t diff = kmin ^ kmax;
+        const int top = diff ? 63 - __clzll((long long)diff) : 0;
+        mask = top >= 63 ? 0ull : ~((2ull << top) - 1ull);
+        prefix = kmin & mask;
+        uint32_t need = (uint32_t)K;
+        for (int hi = top; hi >= 0; hi -= 8) {
+            const int shift = max(hi - 7, 0);
+            const uint32_t bmask = (1u << (hi - shift + 1)) - 1u;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0u;
+            __syncwarp();
+            each([&](bool ok, int64_t e) {
+                if (ok) {
+                    const uint64_t k = key_at(e);
+                    if ((k & mask) == prefix) atomicAdd(&hist[(uint32_t)(k >> shift) & bmask], 1u);
+                }
+            });
+            __syncwarp();
+            uint32_t loc[8], sum = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                loc[b] = hist[lane * 8 + b];
+                sum += loc[b];
+            }
+            uint32_t incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t tv = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += tv;
+            }
+            const uint32_t excl = incl - sum;
+            const bool mine = excl < need && incl >= need;
+            uint32_t bin = 0, below = 0, cnt = 0;
+            if (mine) {
+                uint32_t cum = excl;
+                for (int b = 0; b < 8; ++b) {
+                    if (cum + loc[b] >= need) {
+                        bin = (uint32_t)(lane * 8 + b);
+                        below = cum;
+                        cnt = loc[b];
+                        break;
+                    }
+                    cum += loc[b];
+                }
+            }
+            const uint32_t who = __ballot_sync(0xffffffffu, mine);
+            const int src = who ? __ffs(who) - 1 : 0;
+            bin = __shfl_sync(0xffffffffu, bin, src);
+            below = __shfl_sync(0xffffffffu, below, src);
+            cnt = __shfl_sync(0xffffffffu, cnt, src);
+            prefix |= (uint64_t)bin << shift;
+            mask |= (uint64_t)bmask << shift;
+            need -= below;
+            __syncwarp();
+            if (cnt == need) break;
+        }
+    }
     int w = 0;
-    for (int i0 = 0; i0 < N; i0 += 32) {
-        const int i = i0 + lane;
-        const uint64_t k = i < N ? key(i) : ~0ull;
-        const bool take = k != ~0ull && (k & mask) <= prefix;
+    each([&](bool ok, int64_t e) {
+        bool take = false;
+        float dv = 0.f;
+        int32_t sv = 0;
+        if (ok) {
+            dv = part_d[e];
+            sv = (int32_t)part_i[e];
+            take = (ds_key(dv, sv) & mask) <= prefix;
+        }
         const uint32_t mk = __ballot_sync(0xffffffffu, take);
         if (take) {
             const int p = w + __popc(mk & lanemask_lt());
             if (p < 32 * E) {
-                sd[warp][p] = part_d[at(i)];
-                ss[warp][p] = (int32_t)part_i[at(i)];
+                sd[warp][p] = dv;
+                ss[warp][p] = sv;
             }
         }
         w += __popc(mk);
-    }
+    });
     __syncwarp();
     const int nk = min(w, K);
     float v[E];
@@ -1050,14 +1141,14 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qru
     }
 }
 
-void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc,
+void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, int Kc, int RK,
               float *out_d, int64_t *out_s, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
-#define SIVF_MTC(E_)                                                                    \
-    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, s.part_d, s.part_i, \
-                                             out_d, out_s)
+#define SIVF_MTC(E_)                                                                         \
+    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, RK, s.part_n, s.part_d, \
+                                             s.part_i, out_d, out_s)
     if (Kc <= 32) SIVF_MTC(1);
     else if (Kc <= 64) SIVF_MTC(2);
     else if (Kc <= 128) SIVF_MTC(4);
@@ -1381,12 +1472,16 @@ bool tc_make_maps(sivf_index *ix)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
-    return true;
+    return qt_make_maps(ix, enc);
 }
 
-// a row's candidate buffer: its best K' plus room for `tiles` tiles of
+// a row's run and held set: K' plus the room an approximate reduction may
+// keep beyond it (a quarter of K', at least 32), a multiple of 8
+int tc_run_len(int K) { return (K + max(32, K / 4) + 7) / 8 * 8; }
+
+// a row's candidate buffer: its held set plus room for `tiles` tiles of
 // candidates (TC_M each)
-static int tc_buf_len(int K, int tiles) { return (K + tiles * TC_M + 7) / 8 * 8; }
+static int tc_buf_len(int K, int tiles) { return tc_run_len(K) + tiles * TC_M; }
 
 // queries per tile of the reduced-precision scan for K' candidates
 int tc_tile_queries(int Kc)
@@ -1466,7 +1561,7 @@ static void launch_tc(const unsigned char *tmap, TcArgs a, cudaStream_t st)
 }
 
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
-                   const SearchPlan &pl, const SearchScratch &s, cudaStream_t st)
+                   const SearchPlan &pl, const SearchScratch &s, cudaStream_t st, int seed_slabs)
 {
     TcArgs a;
     a.q = q;
@@ -1482,6 +1577,8 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.nch = s.nch;
     a.part_d = s.part_d;
     a.part_i = s.part_i;
+    a.part_n = s.part_n;
+    a.RK = pl.RK;
     a.thr = s.thr;
     a.items = s.items;
     a.per_pair = dtype == SIVF_FP8E4M3;
@@ -1505,6 +1602,7 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.pf_tiles = std::max(2, TC_PF_BYTES / (TC_M * ix->d * esz));
     a.ctl = ix->ctl;
     a.err = ix->err;
+    a.seed_slabs = seed_slabs;
     const int tn = tc_tile_queries(Kc);
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {

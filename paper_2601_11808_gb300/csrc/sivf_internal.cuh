@@ -128,6 +128,9 @@ struct sivf_index {
     // TMA descriptors (CUtensorMap, 128 bytes) of the BF16 / FP8 copies
     alignas(64) unsigned char tmap_bf16[128];
     alignas(64) unsigned char tmap_fp8[128];
+    // the same copies with boxes of min(C, 64) rows (query-row scan)
+    alignas(64) unsigned char tmap_qt_bf16[128];
+    alignas(64) unsigned char tmap_qt_fp8[128];
     bool tmaps_ready;
 
     // address translation table (Sec. 3.4)

@@ -256,7 +256,9 @@ def _t(tq, spc, ips, sel, nf=0):
 # (d = 128, slab 64, k = 10): all fit in shared memory
 FP32_TILES = [_t(8, 1, 1, 1), _t(16, 2, 16, 4), _t(8, 8, 4, 8), _t(32, 16, 2, 2),
               _t(64, 4, 8, 1)]
-TC_TILES = [_t(64, 1, 16, 0, 0), _t(64, 8, 1, 0, 1)]
+# vector-row scan one launch / nearest list first / seeded; query-row scan
+TC_TILES = [_t(64, 1, 16, 0, 0), _t(64, 8, 1, 0, 1), _t(64, 4, 4, 0, 2), _t(128, 4, 4, 0, 1),
+            _t(128, 2, 8, 2, 0)]
 
 
 @pytest.fixture(scope="module")
@@ -312,8 +314,9 @@ def test_bad_tiles_rejected(torch, filled):
               _t(32, 1, 1, 4)]:          # the last needs 274 KB of shared memory
         with pytest.raises(SivfError):
             g.set_tile("fp32", 100, 10, 8, t)
-    with pytest.raises(SivfError):
-        g.set_tile("bf16", 100, 10, 8, _t(64, 1, 1, 0, 2))
+    for t in [_t(64, 1, 1, 0, 3), _t(48, 1, 1, 0, 1), _t(128, 1, 1, 4, 1)]:
+        with pytest.raises(SivfError):
+            g.set_tile("bf16", 100, 10, 8, t)
 
 
 @pytest.mark.parametrize("dtype", ["fp32", "bf16"])
