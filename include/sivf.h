@@ -25,8 +25,11 @@
  *    changes, and the status is reported by the call itself when it syncs,
  *    otherwise by the next sivf_sync().
  *  - A device loop that hits its bound (a corrupt directory) records a
- *    sticky error and returns; nothing traps.  Every later call returns
- *    SIVF_E_CORRUPT.
+ *    sticky error and returns; nothing traps.  A device wait that runs out
+ *    of time (2 s by default, sivf_set_wait_limit) records a sticky
+ *    timeout the same way.  The next synchronising call returns
+ *    SIVF_E_CORRUPT / SIVF_E_TIMEOUT and every later call returns
+ *    SIVF_E_CORRUPT without enqueuing anything.
  *  - One index is driven by one host thread at a time.  Calls on the same
  *    stream are ordered; the library does not order calls across streams.
  *  - Scratch memory grows on demand with cudaMalloc; call sivf_reserve()
@@ -372,6 +375,27 @@ sivf_status sivf_dump_payload(sivf_index *index, void *stream, float *x32,
  * sizes [host] int32[nlist].
  */
 sivf_status sivf_list_sizes(sivf_index *index, void *stream, int32_t *sizes);
+
+/*
+ * sivf_set_wait_limit -- the time after which a device wait inside the list
+ * scan (a TMA copy, an MMA, a stage hand-over between the roles of a CTA)
+ * gives up: it records a sticky timeout bit, stops every role of the scan
+ * (copies already in flight are drained first) and the next synchronising
+ * call returns SIVF_E_TIMEOUT, after which the index refuses work.  ns = 0
+ * restores the default, 2 s (far above any healthy wait, a slow scan of a
+ * long list included).  The paper has no counterpart: it names a traversal
+ * bound and fail-fast errors (Sec. 3.2, Sec. 3.3) but no timing.
+ */
+sivf_status sivf_set_wait_limit(sivf_index *index, int64_t ns);
+
+/*
+ * sivf_debug_set_error_bits -- test hook: ORs `bits` into the index's sticky
+ * device error word (forces a sync), as a device-side bound or timeout
+ * would, so the failure paths can be exercised without a device fault.
+ * bits: 1 a bad slab reference, 2 a directory past its capacity, 4 the free
+ * stack, 8 a timeout, 16 the coarse selection, 32 a search plan.
+ */
+sivf_status sivf_debug_set_error_bits(sivf_index *index, uint32_t bits, void *stream);
 
 /*
  * sivf_profile -- tracing.  enable != 0 starts recording a CUDA event pair

@@ -238,6 +238,7 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
     ix->n_slabs = cfg->n_slabs;
     ix->dir_cap = cfg->dir_cap ? std::min(cfg->dir_cap, cfg->n_slabs) : cfg->n_slabs;
     ix->dtypes = cfg->scan_dtypes;
+    ix->wait_ns = kWaitNs;
     cudaGetDevice(&ix->device);
     ix->nblk_max = 64;
     const size_t S = (size_t)ix->n_slabs, rows = S * C;
@@ -696,6 +697,8 @@ sivf_status set_error(sivf_index *ix, sivf_status st, const char *what)
 }
 
 void mark_corrupt(sivf_index *ix) { ex(ix).corrupt = true; }
+
+sivf_status index_health(sivf_index *ix) { return check_health(ix); }
 }  // namespace sivf
 
 extern "C" {
@@ -939,6 +942,24 @@ sivf_status sivf_dump(sivf_index *ix, void *stream, int32_t *list_nslabs, int32_
     if (free_stack && top > 0)
         CUDA_TRY(ix, cudaMemcpy(free_stack, ix->free_list, (size_t)std::min<int64_t>(top, S) * 4,
                                 cudaMemcpyDeviceToHost));
+    return SIVF_OK;
+}
+
+sivf_status sivf_set_wait_limit(sivf_index *ix, int64_t ns)
+{
+    if (!ix || ns < 0) return fail(ix, SIVF_E_ARG, "negative wait limit");
+    ix->wait_ns = ns == 0 ? kWaitNs : (uint64_t)ns;
+    return SIVF_OK;
+}
+
+sivf_status sivf_debug_set_error_bits(sivf_index *ix, uint32_t bits, void *stream)
+{
+    if (!ix) return SIVF_E_ARG;
+    CUDA_TRY(ix, cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t word = 0;
+    CUDA_TRY(ix, cudaMemcpy(&word, ix->err, 4, cudaMemcpyDeviceToHost));
+    word |= bits;
+    CUDA_TRY(ix, cudaMemcpy(ix->err, &word, 4, cudaMemcpyHostToDevice));
     return SIVF_OK;
 }
 

@@ -63,15 +63,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`, giving up after `limit` polls (each
-// try_wait itself suspends for a hardware-defined time).  Returns false and
-// sets ERR_TIMEOUT when the limit is hit.
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t gtimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+
+// Wait for phase `parity` of `bar`, giving up once `limit_ns` of global
+// time has passed since the first unsuccessful poll (each try_wait itself
+// suspends for a hardware-defined time; a poll count of 2^30 is a second
+// limit in case the timer stalls).  Returns false and sets ERR_TIMEOUT
+// when a limit is hit.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   uint32_t *err,
-                                                  uint32_t limit = 4000000u)
+                                                  uint64_t limit_ns = kWaitNs)
 {
-    for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer_ns();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (gtimer_ns() - t0 > limit_ns) break;
+    }
     atomicOr(err, ERR_TIMEOUT);
     return false;
 }

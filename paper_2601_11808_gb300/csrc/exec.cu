@@ -121,6 +121,7 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
     *out = nullptr;
     if (nops < 1 || !ops) return set_error(ix, SIVF_E_ARG, "empty queue");
     if (!ix->have_centroids) return set_error(ix, SIVF_E_STATE, "set_centroids first");
+    if (sivf_status hs = index_health(ix)) return hs;
     size_t need = 0;
     int64_t max_add = 1;
     for (int i = 0; i < nops; ++i) {
@@ -219,6 +220,7 @@ sivf_status sivf_exec_launch(sivf_exec *e, void *stream)
 {
     if (!e) return SIVF_E_ARG;
     sivf_index *ix = e->ix;
+    if (sivf_status hs = index_health(ix)) return hs;
     cudaError_t ce = cudaGraphLaunch(e->gexec, (cudaStream_t)stream);
     if (ce != cudaSuccess) return set_error(ix, SIVF_E_CUDA, cudaGetErrorString(ce));
     ix->launches += e->kernels;

@@ -191,5 +191,8 @@ Ctl *stream_ctl(sivf_index *ix, void *stream);
 void release_stream(sivf_index *ix, void *stream);        // free a stream's scratch
 sivf_status set_error(sivf_index *ix, sivf_status st, const char *what);
 void mark_corrupt(sivf_index *ix);
+// SIVF_E_CORRUPT once a synchronising call has seen a device error bit (the
+// index then refuses further work), else SIVF_OK
+sivf_status index_health(sivf_index *ix);
 
 }  // namespace sivf

@@ -91,6 +91,8 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
         (nq > 0 && (!q || !dist || !labels)))
         return fail(SIVF_E_ARG, "bad search arguments");
     if (!ix->have_centroids) return fail(SIVF_E_STATE, "set_centroids first");
+    const sivf_status health = index_health(ix);
+    if (health != SIVF_OK) return health;
     if (nq == 0) return SIVF_OK;
     if (!scan_fits(ix, k)) return fail(SIVF_E_ARG, "k too large for this slab shape");
 
@@ -152,13 +154,19 @@ extern "C" sivf_status sivf_search_noalloc(sivf_index *ix, const float *q, int64
     if (!c.ok()) return fail(SIVF_E_ARG, "scratch carve-up overflow");
 
     // the control block starts at zero on every call (lcnt is cleared by
-    // the grouping step itself)
+    // the grouping step itself); the kernels take the index's control
+    // block pointer at launch, so the index's own one is put back after
+    // the launches are enqueued
+    Ctl *own = ix->ctl;
     ix->ctl = ctl;
-    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess)
+    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) {
+        ix->ctl = own;
         return fail(SIVF_E_CUDA, "cudaMemsetAsync failed");
+    }
     coarse_topP(ix, q, nq, P, probes, Dbuf, rows, s);
     scan_lists(ix, q, nq, P, probes, false, pl, sc, s);
     merge_topk(ix, nq, P, probes, pl, sc, k, dist, labels, s);
+    ix->ctl = own;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SIVF_E_CUDA, cudaGetErrorString(e));
     return SIVF_OK;

@@ -95,6 +95,7 @@ struct QtArgs {
     int d, C, KC, NV, nst;
     int seed_slabs;             // > 0: seed launch over the first slabs of each item
     int mecap;                  // longest candidate buffer of one row (odd)
+    uint64_t wait_ns;           // time after which a wait of the scan gives up
     int pf_tiles;               // B tiles prefetched into L2 ahead of the loads
     Ctl *ctl;
     uint32_t *err;
@@ -343,14 +344,18 @@ __device__ __forceinline__ float qt_fold_any(float *bd, int32_t *bs, int n, int 
     return qt_radix_keep(bd, bs, n, K, hist, lane);
 }
 
-// mbarrier wait bounded by an iteration limit that also gives up as soon
-// as another role of the CTA has stopped (abort flag in shared memory)
+// mbarrier wait bounded in time (the index's wait limit) that also gives
+// up as soon as another role of the CTA has stopped (abort flag in shared
+// memory); a wait that runs out sets ERR_TIMEOUT and the abort flag
 __device__ __forceinline__ bool qt_wait(uint64_t *bar, uint32_t parity, uint32_t *err,
-                                        volatile int *abort_flag)
+                                        volatile int *abort_flag, uint64_t limit_ns)
 {
-    for (uint32_t it = 0; it < 4000000u; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer_ns();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 127u) == 127u && *abort_flag) return false;
+        if ((it & 63u) == 0u && *abort_flag) return false;
+        if (gtimer_ns() - t0 > limit_ns) break;
     }
     atomicOr(err, ERR_TIMEOUT);
     *abort_flag = 1;
@@ -450,7 +455,7 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
         for (int it = 0;; ++it) {
             const int j = it % QT_CTX;
             const uint32_t cu = (uint32_t)(it / QT_CTX);
-            bool ok = cu == 0 || qt_wait(&cempty[j], (cu - 1) & 1, a.err, s_abort);
+            bool ok = cu == 0 || qt_wait(&cempty[j], (cu - 1) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             int32_t *h = hdr(j);
             bool stop = false;
@@ -544,11 +549,11 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
         // ---- query tiles (A operand), rounded and swizzled
         for (int it = 0;; ++it) {
             const int j = it % QT_CTX;
-            bool ok = qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort);
+            bool ok = qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             if (hdr(j)[8] & QF_STOP) break;
             ok = it < QT_CTX ||
-                 qt_wait(&afree[j], (uint32_t)(it / QT_CTX - 1) & 1, a.err, s_abort);
+                 qt_wait(&afree[j], (uint32_t)(it / QT_CTX - 1) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             const int32_t *cqi = c_qi(j);
             const int m = hdr(j)[1];
@@ -582,7 +587,7 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
             const int LPT = NV / Cb;  // loads per B tile
             for (int it = 0;; ++it) {
                 const int j = it % QT_CTX;
-                if (!qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort)) break;
+                if (!qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort, a.wait_ns)) break;
                 const int32_t *h = hdr(j);
                 if (h[8] & QF_STOP) break;
                 const int sns = h[3], nblk = h[4];
@@ -590,11 +595,11 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
                 bool ab = false;
                 for (int b = 0; b < nblk; ++b, ++g) {
                     const uint32_t st = g % NST, u = g / NST, xs = g % QT_XR, xu = g / QT_XR;
-                    if (u >= 1 && !qt_wait(&empty[st], (u - 1) & 1, a.err, s_abort)) {
+                    if (u >= 1 && !qt_wait(&empty[st], (u - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
-                    if (xu >= 1 && !qt_wait(&xempty[xs], (xu - 1) & 1, a.err, s_abort)) {
+                    if (xu >= 1 && !qt_wait(&xempty[xs], (xu - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
@@ -644,19 +649,19 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
             uint32_t g = 0;
             for (int it = 0;; ++it) {
                 const int j = it % QT_CTX;
-                if (!qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort)) break;
+                if (!qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort, a.wait_ns)) break;
                 if (hdr(j)[8] & QF_STOP) break;
                 const int nblk = hdr(j)[4];
-                if (!qt_wait(&afull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort)) break;
+                if (!qt_wait(&afull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort, a.wait_ns)) break;
                 const uint32_t abase = smem_u32(A + (size_t)j * KC * QT_M * 128);
                 bool ab = false;
                 for (int b = 0; b < nblk; ++b, ++g) {
                     const uint32_t st = g % NST, u = g / NST, buf = g % QT_NB, ub = g / QT_NB;
-                    if (!qt_wait(&full[st], u & 1, a.err, s_abort)) {
+                    if (!qt_wait(&full[st], u & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
-                    if (ub >= 1 && !qt_wait(&tempty[buf], (ub - 1) & 1, a.err, s_abort)) {
+                    if (ub >= 1 && !qt_wait(&tempty[buf], (ub - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
@@ -710,7 +715,7 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
         };
         for (int it = 0;; ++it) {
             const int j = it % QT_CTX;
-            const bool ok = qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort);
+            const bool ok = qt_wait(&cfull[j], (uint32_t)(it / QT_CTX) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             const int32_t *h = hdr(j);
             const int flags = h[8];
@@ -742,8 +747,8 @@ __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CU
             bool run_ok = true;
             for (int b = 0; b < nblk; ++b, ++g) {
                 const uint32_t buf = g % QT_NB, ub = g / QT_NB, xs = g % QT_XR, xu = g / QT_XR;
-                bool wok = qt_wait(&xfull[xs], xu & 1, a.err, s_abort);
-                wok = wok && qt_wait(&tfull[buf], ub & 1, a.err, s_abort);
+                bool wok = qt_wait(&xfull[xs], xu & 1, a.err, s_abort, a.wait_ns);
+                wok = wok && qt_wait(&tfull[buf], ub & 1, a.err, s_abort, a.wait_ns);
                 wok = __all_sync(0xffffffffu, wok);  // tcgen05.ld is warp-aligned
                 if (!wok) {
                     run_ok = false;
@@ -997,6 +1002,7 @@ void scan_lists_qt(sivf_index *ix, int dtype, int64_t nq, int P, int Kc, int see
     a.nst = sh.nst;
     a.seed_slabs = seed_slabs;
     a.mecap = qt_mecap(select_slabs);
+    a.wait_ns = ix->wait_ns;
     a.pf_tiles = std::max(2, QT_PF_BYTES / (sh.NV * ix->d * esz));
     a.ctl = ix->ctl;
     a.err = ix->err;

@@ -91,6 +91,7 @@ struct TcArgs {
     int L, d, C, KC;  // KC = 128-byte K chunks per row
     int nst;          // A-tile stages
     int pf_tiles;     // A tiles prefetched into L2 ahead of the loads
+    uint64_t wait_ns; // time after which a wait of the scan gives up
     int seed_slabs;   // > 0: seed launch: the first seed_slabs slabs of each
                       // item, bounds published, no runs written
     Ctl *ctl;
@@ -450,14 +451,20 @@ __device__ __forceinline__ float fold_row(float *bd, int32_t *bs, int K, int Kw,
     return dmax;
 }
 
-// mbarrier wait bounded by an iteration limit that also gives up as soon
-// as another role of the CTA has stopped (abort flag in shared memory).
+// mbarrier wait bounded in time (the index's wait limit) that also gives
+// up as soon as another role of the CTA has stopped (abort flag in shared
+// memory); a wait that runs out sets ERR_TIMEOUT and the abort flag.
+// Copies already in flight are drained by the producer with the default
+// limit before the CTA exits.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, uint32_t *err,
-                                             volatile int *abort_flag)
+                                             volatile int *abort_flag, uint64_t limit_ns)
 {
-    for (uint32_t it = 0; it < 4000000u; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer_ns();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 127u) == 127u && *abort_flag) return false;
+        if ((it & 63u) == 0u && *abort_flag) return false;
+        if (gtimer_ns() - t0 > limit_ns) break;
     }
     atomicOr(err, ERR_TIMEOUT);
     *abort_flag = 1;
@@ -590,7 +597,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
         for (int it = 0;; ++it) {
             const int j = it % TC_CTX;
             const uint32_t cu = (uint32_t)(it / TC_CTX);
-            bool ok = cu == 0 || mbar_wait_ab(&cempty[j], (cu - 1) & 1, a.err, s_abort);
+            bool ok = cu == 0 || mbar_wait_ab(&cempty[j], (cu - 1) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             int32_t *h = hdr(j);
             bool stop = false;
@@ -682,10 +689,10 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
         // ---- query tiles (B operand), rounded and swizzled
         for (int it = 0;; ++it) {
             const int j = it % TC_CTX, bb = it & 1;
-            bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort);
+            bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             if (hdr(j)[8] & CF_STOP) break;
-            ok = it < 2 || mbar_wait_ab(&bfree[bb], (uint32_t)((it >> 1) - 1) & 1, a.err, s_abort);
+            ok = it < 2 || mbar_wait_ab(&bfree[bb], (uint32_t)((it >> 1) - 1) & 1, a.err, s_abort, a.wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             const int32_t *cqi = c_qi(j);
             const int m = hdr(j)[1];
@@ -714,7 +721,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             const uint32_t pay_bytes = (uint32_t)(C * d * ESZ);
             for (int it = 0;; ++it) {
                 const int j = it % TC_CTX;
-                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort)) break;
+                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort, a.wait_ns)) break;
                 const int32_t *h = hdr(j);
                 if (h[8] & CF_STOP) break;
                 const int sns = h[3], nblk = h[4];
@@ -722,11 +729,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                 bool ab = false;
                 for (int b = 0; b < nblk; ++b, ++g) {
                     const uint32_t st = g % NST, u = g / NST, xs = g % TC_XR, xu = g / TC_XR;
-                    if (u >= 1 && !mbar_wait_ab(&empty[st], (u - 1) & 1, a.err, s_abort)) {
+                    if (u >= 1 && !mbar_wait_ab(&empty[st], (u - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
-                    if (xu >= 1 && !mbar_wait_ab(&xempty[xs], (xu - 1) & 1, a.err, s_abort)) {
+                    if (xu >= 1 && !mbar_wait_ab(&xempty[xs], (xu - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
@@ -769,19 +776,19 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             uint32_t g = 0;
             for (int it = 0;; ++it) {
                 const int j = it % TC_CTX, bb = it & 1;
-                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort)) break;
+                if (!mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort, a.wait_ns)) break;
                 if (hdr(j)[8] & CF_STOP) break;
                 const int nblk = hdr(j)[4];
-                if (!mbar_wait_ab(&bfull[bb], (uint32_t)(it >> 1) & 1, a.err, s_abort)) break;
+                if (!mbar_wait_ab(&bfull[bb], (uint32_t)(it >> 1) & 1, a.err, s_abort, a.wait_ns)) break;
                 const uint32_t bbase = smem_u32(B + (size_t)bb * KC * TN * 128);
                 bool ab = false;
                 for (int b = 0; b < nblk; ++b, ++g) {
                     const uint32_t st = g % NST, u = g / NST, buf = g & 1, ub = g >> 1;
-                    if (!mbar_wait_ab(&full[st], u & 1, a.err, s_abort)) {
+                    if (!mbar_wait_ab(&full[st], u & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
-                    if (ub >= 1 && !mbar_wait_ab(&tempty[buf], (ub - 1) & 1, a.err, s_abort)) {
+                    if (ub >= 1 && !mbar_wait_ab(&tempty[buf], (ub - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
@@ -817,7 +824,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
         uint32_t g = 0;
         for (int it = 0;; ++it) {
             const int j = it % TC_CTX;
-            const bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort);
+            const bool ok = mbar_wait_ab(&cfull[j], (uint32_t)(it / TC_CTX) & 1, a.err, s_abort, a.wait_ns);
             if (!named_bar_and(1, EPI, ok && !*s_abort)) break;
             const int32_t *h = hdr(j);
             const int flags = h[8];
@@ -853,11 +860,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                 const int s = jr < nsl ? sl[mi] : -1;
                 const bool live = s >= 0 && ((bt[mi * 4 + (slot >> 5)] >> (slot & 31)) & 1u);
                 const int32_t gslot = s * C + slot;
-                bool wok = mbar_wait_ab(&xfull[xs], xu & 1, a.err, s_abort);
+                bool wok = mbar_wait_ab(&xfull[xs], xu & 1, a.err, s_abort, a.wait_ns);
                 const float xn = XN[xs * TC_M + v];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&xempty[xs]);
-                wok = wok && mbar_wait_ab(&tfull[buf], ub & 1, a.err, s_abort);
+                wok = wok && mbar_wait_ab(&tfull[buf], ub & 1, a.err, s_abort, a.wait_ns);
                 wok = __all_sync(0xffffffffu, wok);  // tcgen05.ld is warp-aligned
                 tc_fence_after();
                 const bool cols = c0 < m;           // warp-uniform
@@ -1603,6 +1610,7 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.ctl = ix->ctl;
     a.err = ix->err;
     a.seed_slabs = seed_slabs;
+    a.wait_ns = ix->wait_ns;
     const int tn = tc_tile_queries(Kc);
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {

@@ -431,6 +431,7 @@ sivf_status sivf_server_create(sivf_index *ix, const sivf_server_config *cfg, si
         c.compact_min_free < 0)
         return set_error(ix, SIVF_E_ARG, "bad server config");
     if (!ix->have_centroids) return set_error(ix, SIVF_E_STATE, "set_centroids first");
+    if (sivf_status hs = index_health(ix)) return hs;
     sivf_server *sv = new (std::nothrow) sivf_server();
     if (!sv) return SIVF_E_NOMEM;
     sv->ix = ix;

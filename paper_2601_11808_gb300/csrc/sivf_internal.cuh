@@ -21,6 +21,9 @@ constexpr int kMaxK = 1024;         // largest k of one search
 constexpr int kRankTile = 1024;     // vectors per block of the stable ranking
 constexpr int kMaxChunks = 64;      // most slab chunks one list is split into
 constexpr size_t kMaxStageBytes = 160 * 1024;  // two slab stages in shared memory
+// default time a device wait may take before it gives up: far above any
+// healthy wait (a slow scan of a long list included)
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 // sticky device error bits (index->err)
 enum : uint32_t {
@@ -145,6 +148,7 @@ struct sivf_index {
 
     sivf::Ctl *ctl;                // control block of the current call's stream
     uint32_t *err;                 // sticky error bits
+    uint64_t wait_ns;              // time after which a list-scan wait gives up
     int64_t *stat;                 // [4] persistent counters: [0] live vectors,
                                    // [1] (query, vector) pairs scanned,
                                    // [2] slab bytes streamed by list scans

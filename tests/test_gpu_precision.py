@@ -158,3 +158,61 @@ def test_reduced_dtype_needs_its_copy(torch):
         g.search(q, 5, 2, "fp8")
     with pytest.raises(SivfError):
         g.search(q, 129, 2, "bf16")       # 4k > 512
+
+
+# ------------------------------------------ full-size SIFT-shaped window
+def test_sift_window_full_size_reduced_sampled(torch):
+    """The benchmark's exact launch on the SIFT-shaped window (1,000,000
+    vectors d=128, nlist=1024, slab 64, after two +10,000 / -10,000 steps;
+    10,000 queries in one call, k=10) with the BF16 and FP8 scans and the
+    FP32 re-rank, at nprobe 1 (the benchmark's operating point) and 8.
+    For 100 sampled queries the oracle's FP64 IVF top-k at the same nprobe
+    is recomputed one by one (walking the window in ascending FP64
+    distance and asking the oracle for each vector's list) and compared
+    with compare_topk: distances within 1e-5, ids equal except at ties."""
+    from sivf_check import compare_topk
+    w = W.CONFIGS["sift_window"]
+    ctr = W.centers(w)
+    cent = W.index_centroids(w, ctr)
+    n_max = w.window + 4 * w.step
+    S = int(1.25 * (w.window // w.slab_size + 2 * w.nlist))
+    from paper_2601_11808_gb300.sivf import Index
+    g = Index(w.d, w.nlist, w.slab_size, n_max, S, scan_dtypes=("bf16", "fp8"))
+    g.set_centroids(torch.from_numpy(cent).cuda())
+    X = W.vectors_threaded(w, 0, w.window + 2 * w.step, ctr)
+    for b in range(0, w.window, 100_000):
+        g.add(torch.from_numpy(W.stream_ids(b, 100_000, n_max)).cuda(),
+              torch.from_numpy(X[b:b + 100_000]).cuda())
+    for s in range(2):
+        new = w.window + s * w.step
+        g.add(torch.from_numpy(W.stream_ids(new, w.step, n_max)).cuda(),
+              torch.from_numpy(X[new:new + w.step]).cuda())
+        g.remove(torch.from_numpy(W.stream_ids(s * w.step, w.step, n_max)).cuda())
+    assert g.sync() == w.step
+    live = np.arange(2 * w.step, w.window + 2 * w.step)
+    Xl = X[live]
+    o = oracle.OracleIVF(w.d, w.nlist, n_max=10, n_slabs=10)
+    o.set_centroids(cent)
+    Q = W.queries(w, 0, w.n_queries, ctr)
+    Qd = torch.from_numpy(Q).cuda()
+    rng = np.random.default_rng(3)
+    sample = rng.choice(w.n_queries, 100, replace=False)
+    walks = {}
+    for r in sample:
+        dd = oracle.dists(Q[r], Xl)
+        order = np.argsort(dd, kind="stable")[:4000]
+        walks[r] = (dd, order, o.assign(Xl[order]))
+    for P in (1, 8):
+        want = {}
+        for r in sample:
+            pr = set(o.probe(Q[r:r + 1], P)[0].tolist())
+            dd, order, lists = walks[r]
+            keep = [j for j, l in zip(order, lists) if int(l) in pr][:w.k]
+            assert len(keep) == w.k
+            want[r] = (np.array([dd[keep]]), np.array([live[keep] % n_max]))
+        for form in ("bf16", "fp8"):
+            gd, gi = g.search(Qd, w.k, P, form)
+            gd, gi = gd.cpu().numpy(), gi.cpu().numpy()
+            for r in sample:
+                compare_topk(gd[r:r + 1], gi[r:r + 1], *want[r], 1e-5, f"{form} P{P} q{r}")
+    g.close()

@@ -73,15 +73,17 @@ def test_noalloc_does_not_allocate_and_refuses_oversize(torch):
     q = torch.from_numpy(W.queries(w, 0, 64, ctr)).cuda()
     d = torch.empty((64, 10), dtype=torch.float32, device="cuda")
     i = torch.empty((64, 10), dtype=torch.int64, device="cuda")
-    stream = torch.cuda.Stream()       # a stream sivf_search never used
+    # the regular search of the same shape loads the kernels both paths
+    # share (so lazy module loading cannot show up as memory taken below)
+    g.search(q, 10, 8)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()       # a stream neither search has used
+    free0 = torch.cuda.mem_get_info()[0]
     with torch.cuda.stream(stream):
-        sivf.sivf_search_noalloc(g.h, q, 10, 8, d, i)
-        torch.cuda.synchronize()
-        free0 = torch.cuda.mem_get_info()[0]
-        for _ in range(2):
+        for _ in range(3):             # the first call on the stream included
             sivf.sivf_search_noalloc(g.h, q, 10, 8, d, i)
         torch.cuda.synchronize()
-        free1 = torch.cuda.mem_get_info()[0]
+    free1 = torch.cuda.mem_get_info()[0]
     assert free1 == free0
     big = torch.zeros((20_000, w.d), dtype=torch.float32, device="cuda")
     bd = torch.empty((20_000, 64), dtype=torch.float32, device="cuda")
@@ -89,3 +91,42 @@ def test_noalloc_does_not_allocate_and_refuses_oversize(torch):
     with pytest.raises(sivf.SivfError) as e:
         sivf.sivf_search_noalloc(g.h, big, 64, 64, bd, bi)
     assert e.value.status == sivf.E_ARG and "scratch" in str(e.value)
+
+
+def _need_bytes(nq, P, k, L, tq, ips, rows):
+    """The allocation-free search's scratch bytes for a plan (the same sum,
+    each part rounded up to 256 bytes, as the library's carve-up)."""
+    run_cap = nq * P + 2 * tq * ips * 152
+    item_cap = nq * P + L + ips * 152
+    parts = [64, nq * P * 4, L * 4, (L + 1) * 4, (L + 1) * 4, L * 4, nq * P * 4, nq * P * 4,
+             run_cap * k * 4, run_cap * k * 8, nq * 4, nq * P * 4, nq * 16, item_cap * 8,
+             rows * L * 4]
+    b = 0
+    for n in parts:
+        b = ((b + 255) & ~255) + n
+    return b
+
+
+def test_noalloc_narrows_a_plan_that_does_not_fit(torch):
+    """A batch whose default plan needs more than the fixed array but fits
+    once the work items per SM are lowered: the call narrows the plan
+    (items per SM, then coarse rows) and still returns sivf_search's
+    results."""
+    from paper_2601_11808_gb300 import sivf
+    w = W.CONFIGS["tiny_window"]
+    g, ctr = _index(torch, w, 20_000)
+    nq, k, P = 3000, 48, 8
+    t = g.get_tile("fp32", nq, k, P)
+    cap = 32 << 20
+    rows = min(nq, max(1, (8 << 20) // (4 * w.nlist)))
+    ips = t["items_per_sm"]
+    assert _need_bytes(nq, P, k, w.nlist, t["queries_per_tile"], ips, rows) > cap
+    while _need_bytes(nq, P, k, w.nlist, t["queries_per_tile"], ips, rows) > cap and ips > 1:
+        ips >>= 1
+    while _need_bytes(nq, P, k, w.nlist, t["queries_per_tile"], ips, rows) > cap and rows > 1:
+        rows >>= 1
+    assert ips < t["items_per_sm"]
+    assert _need_bytes(nq, P, k, w.nlist, t["queries_per_tile"], ips, rows) <= cap
+    q = W.queries(w, 0, nq, ctr)
+    for _ in range(2):
+        compare_topk(*_both(torch, g, q, k, P), RTOL, "noalloc narrowed plan")
