@@ -5,7 +5,9 @@ sliding window (1,000,000 live vectors, d=128, nlist=1024, slab 64):
 insert 10,000 new vectors (coarse assignment + slot claim + append), delete
 the 10,000 oldest (address-table lookup, bit clear, slab reclaim), and search
 10,000 fresh queries (coarse probe selection, list scan, top-10) at the
-smallest nprobe of {8, 16, 32, 64, 128} whose recall@10 reaches 0.95.
+smallest nprobe of {1, 2, 3, 4, 6, 8, 16, 32, 64, 128} whose recall@10,
+against the FP64 oracle's exact k nearest neighbours of 1,000 sampled
+queries, reaches 0.95.
 Each scan form is measured (FP32 direct form; BF16 and FP8 scans on the
 tensor cores with an FP32 re-rank of the best 4k); the headline is the
 fastest form that reaches recall 0.95, and every form is reported.
@@ -38,7 +40,8 @@ sys.path.insert(0, ROOT)
 from paper_2601_11808_gb300 import workloads as W  # noqa: E402
 
 METRIC = "QPS@recall@10=0.95; insert/delete vec/s; p99 update ms (1×GB300)"
-NPROBES = (8, 16, 32, 64, 128)
+NPROBES = (1, 2, 3, 4, 6, 8, 16, 32, 64, 128)
+N_TRUTH = 1000          # sampled queries with FP64 exact ground truth
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -60,6 +63,9 @@ def parse():
     p.add_argument("--impl", default="sivf", choices=["sivf", "reference"])
     p.add_argument("--workload", default="sift_window")
     p.add_argument("--nprobe", type=int, default=0, help="0 = calibrate for recall 0.95")
+    p.add_argument("--gpu-truth", action="store_true",
+                   help="recall against the GPU's FP32 search over every list instead of "
+                        "the FP64 oracle (quick runs only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true",
@@ -77,6 +83,8 @@ def parse():
                    help="skip the quantizer-training measurement")
     p.add_argument("--no-compact", action="store_true",
                    help="skip the compaction measurement")
+    p.add_argument("--no-delete-window", action="store_true",
+                   help="skip the delete-latency-vs-window-size component")
     p.add_argument("--no-zipf", action="store_true",
                    help="skip the Zipf-skewed ingestion workload")
     p.add_argument("--forms", default="fp32,bf16,fp8",
@@ -160,10 +168,9 @@ def make_data(w: W.Workload, n_steps: int, n_calib: int, rank: int):
     return cent, X, Q
 
 
-def oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps):
-    """FP64 oracle on the host cores: full window built with all cores
-    (untimed), then `steps` bounded samples of a step (n_ins inserts, n_del
-    deletes of the oldest, n_q queries), each scaled to the full step."""
+def oracle_window(w, cent, X, n_max):
+    """The FP64 oracle holding the initial window (positions 0 .. window),
+    built with every host core; returns (oracle, cores, seconds)."""
     import oracle
     cores = oracle.num_threads(os.cpu_count() or 1)
     S = int(1.25 * (w.window // w.slab_size + 2 * w.nlist))
@@ -172,23 +179,40 @@ def oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps):
     t0 = time.time()
     for b in range(0, w.window, 100_000):
         o.add(W.stream_ids(b, 100_000, n_max), X[b:b + 100_000])
-    build_s = time.time() - t0
+    return o, cores, time.time() - t0
+
+
+def oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps, o=None,
+                  threads=0, at=(0, 0, 0)):
+    """FP64 oracle on the host cores: full window built with all cores
+    (untimed, or the given oracle holding it), then `steps` bounded samples
+    of a step (n_ins inserts, n_del deletes of the oldest, n_q queries) with
+    `threads` OpenMP threads (0 = every core), each scaled to the full
+    step.  `at` = (inserted, deleted, queried) by earlier samples on the
+    same oracle: the stream continues from there."""
+    import oracle
+    build_s = 0.0
+    if o is None:
+        o, _, build_s = oracle_window(w, cent, X, n_max)
+    cores = oracle.num_threads(threads or (os.cpu_count() or 1))
     per_step = []
     for s in range(steps):
-        new = w.window + s * n_ins
+        new = w.window + at[0] + s * n_ins
         t0 = time.time()
         o.add(W.stream_ids(new, n_ins, n_max), X[new:new + n_ins])
         t_ins = time.time() - t0
         t0 = time.time()
-        o.remove(W.stream_ids(s * n_del, n_del, n_max))
+        o.remove(W.stream_ids(at[1] + s * n_del, n_del, n_max))
         t_del = time.time() - t0
         t0 = time.time()
-        o.search(Q[s * n_q:(s + 1) * n_q], w.k, nprobe)
+        q0 = at[2] + s * n_q
+        o.search(Q[q0:q0 + n_q], w.k, nprobe)
         t_q = time.time() - t0
         per_step.append((t_ins * w.step / n_ins, t_del * w.step / n_del,
                          t_q * w.n_queries / n_q))
     a = np.array(per_step)
     step_s = a.sum(axis=1)
+    oracle.num_threads(os.cpu_count() or 1)
     return {
         "qps": float(w.n_queries / np.mean(step_s)),
         "search_qps": float(w.n_queries / np.mean(a[:, 2])),
@@ -379,6 +403,23 @@ def run_mixed(torch, sivf, dev, stream, replays, warmup, form="bf16"):
     torch.cuda.synchronize()
     eager_ms = e0.elapsed_time(e1)
     g.sync()
+    # the scans of the queue's small query batches (under 256 queries, the
+    # memory-bound regime) against the HBM roof: each batch searched once
+    # more on its own with the library's CUDA events; unique bytes of the
+    # lists its scan probed over the scan launches' device time
+    small = [op for op in ops if op["kind"] == "search" and op["q"].shape[0] < 256]
+    sb, sms, sn = 0, 0.0, 0
+    for op in small:
+        st0 = g.stats()
+        g.profile(True)
+        g.search(op["q"], op["k"], op["nprobe"], op["dtype"], dist=op["dist"],
+                 labels=op["labels"])
+        n1, ms1 = g.profile_read("scan")
+        g.profile(False)
+        sb += g.stats()["list_bytes_scanned"] - st0["list_bytes_scanned"]
+        sms += ms1
+        sn += n1
+    small_gbs = sb / (sms / 1e3) / 1e9 if sms > 0 else 0.0
     kernels = ex.kernels
     ex.close()
     live = g.stats()["ntotal"]
@@ -400,9 +441,88 @@ def run_mixed(torch, sivf, dev, stream, replays, warmup, form="bf16"):
         "queries_per_s": round(nq / (gm / 1e3), 1),
         "ops_per_s": round((nq + n_ins + nd) / (gm / 1e3), 1),
         "per_batch_device_ms": pct, "replays": replays,
+        "small_query_scans": {"batches": len(small), "launches": int(sn), "ms": round(sms, 3),
+                              "unique_list_bytes": int(sb), "achieved_gbs": round(small_gbs, 1),
+                              "frac_of_hbm": round(small_gbs / peaks().get("hbm_gbs", 6695.5),
+                                                   4)},
         "tuned_buckets": len(tuned), "tune_s": round(t_tune, 2), "record_s": round(t_rec, 3),
         "prefill_s": round(t_fill, 1), "live_after": int(live),
     }
+
+
+# ------------------------------------------------- delete vs window size
+def run_delete_window(torch, sivf, dev, windows=(1_000_000, 10_000_000, 100_000_000),
+                      batches=(1000, 10_000), steps=200):
+    """Delete latency as the window grows (the paper's O(1) delete, Sec.
+    3.5.2, and its tail-latency table for batches of 1,000, Sec. 5.5): the
+    serving workload's vectors (d=128, 16,384-component mixture, nlist
+    16384, slab 128) in one index grown from 1 M to 10 M to 100 M live
+    vectors; at each size and batch B, `steps` sliding-window steps insert
+    B new vectors and delete the B oldest; the delete alone is timed with
+    CUDA events on its stream (device time, p50 / p99 / max)."""
+    w = W.CONFIGS["serving"]
+    top = max(windows)
+    n_max = top + (1 << 22)
+    S = int(1.02 * top / w.slab_size) + 3 * w.nlist + (1 << 14)
+    ctr = W.centers(w)
+    pool = W.noise_pool(w, 1 << 20)
+    g = sivf.Index(w.d, w.nlist, w.slab_size, n_max, S)
+    g.set_centroids(torch.from_numpy(W.index_centroids(w, ctr)).to(dev))
+    ctr_d, pool_d = torch.from_numpy(ctr).to(dev), torch.from_numpy(pool).to(dev)
+    sig = float(np.float32(w.sigma))
+    stream = torch.cuda.current_stream()
+
+    def add_range(b, n):
+        for c0 in range(b, b + n, 2_000_000):
+            m = min(2_000_000, b + n - c0)
+            c, r = W.pooled_parts(w, c0, m, len(pool))
+            x = ctr_d[torch.from_numpy(c).to(dev)] + pool_d[torch.from_numpy(r).to(dev)] * sig
+            g.add(torch.from_numpy(W.stream_ids(c0, m, n_max)).to(dev), x)
+
+    lo, hi, out = 0, 0, {}
+    t_fill = time.time()
+    for Wn in sorted(windows):
+        add_range(hi, Wn - (hi - lo))
+        hi = lo + Wn
+        g.sync()
+        res = {}
+        for B in batches:
+            ms = []
+            for st in range(steps + 3):
+                add_range(hi, B)
+                hi += B
+                ids = torch.from_numpy(W.stream_ids(lo, B, n_max)).to(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.remove(ids)
+                e1.record(stream)
+                lo += B
+                e1.synchronize()
+                if st >= 3:
+                    ms.append(e0.elapsed_time(e1))
+            a = np.array(ms)
+            res[f"B{B}"] = {"p50_ms": round(float(np.percentile(a, 50)), 4),
+                            "p99_ms": round(float(np.percentile(a, 99)), 4),
+                            "max_ms": round(float(a.max()), 4),
+                            "delete_vec_s": round(B / (a.mean() / 1e3), 1)}
+        assert g.sync() >= 0
+        res["live"] = int(g.stats()["ntotal"])
+        out[f"W{Wn}"] = res
+    t_fill = time.time() - t_fill
+    g.close()
+    del ctr_d, pool_d
+    torch.cuda.empty_cache()
+    lo_w, hi_w = f"W{min(windows)}", f"W{max(windows)}"
+    out["p99_ratio_largest_vs_smallest"] = {
+        f"B{B}": round(out[hi_w][f"B{B}"]["p99_ms"] / out[lo_w][f"B{B}"]["p99_ms"], 3)
+        for B in batches}
+    out["workload"] = ("serving mixture (d=128, 16,384 components, nlist=16384, slab 128), one "
+                       "index grown 1M -> 10M -> 100M live vectors; per size and batch B, "
+                       f"{steps} steps of insert B new + delete the B oldest, the delete timed "
+                       "with CUDA events (device time)")
+    out["seconds"] = round(t_fill, 1)
+    return out
 
 
 # ----------------------------------------------------------- serving loop
@@ -471,6 +591,8 @@ def run_serving(torch, sivf, dev, window=0, seconds=2.0, loads=(0.5, 0.8, 0.95))
 
     def run(n_req, rate, stream):
         t_off, kinds, sizes = W.request_stream(n_req, rate, seed=w.seed, stream=stream)
+        g.profile(True)          # CUDA events around the library's kernel groups
+        gs0 = g.stats()
         st0 = sv.stats()
         t0 = sivf.Server.now_ns() + 2_000_000
         reqs = []
@@ -502,6 +624,16 @@ def run_serving(torch, sivf, dev, window=0, seconds=2.0, loads=(0.5, 0.8, 0.95))
         out["max_in_flight"] = st1["max_in_flight"]
         bad = [i for _, i in infos if i["status"] != 0]
         out["failed"] = len(bad)
+        # the query scans against the HBM roof: unique bytes of the lists
+        # the scans probed over the scan launches' summed device time
+        gs1 = g.stats()
+        n_scan, scan_ms = g.profile_read("scan")
+        g.profile(False)
+        ub = gs1["list_bytes_scanned"] - gs0["list_bytes_scanned"]
+        gbs = ub / (scan_ms / 1e3) / 1e9 if scan_ms > 0 else 0.0
+        out["scan"] = {"launches": int(n_scan), "ms": round(scan_ms, 3),
+                       "unique_list_bytes": int(ub), "achieved_gbs": round(gbs, 1),
+                       "frac_of_hbm": round(gbs / peaks().get("hbm_gbs", 6695.5), 4)}
         return out
 
     # saturation: a burst with every arrival at once
@@ -827,7 +959,7 @@ def main():
     forms = [f for f in args.forms.split(",") if f]
     K, Wm = args.steps, args.warmup
     n_steps = Wm + (len(forms) + 1) * K + 1
-    n_calib = 1000
+    n_calib = N_TRUTH
     cent, X, Q = make_data(w, n_steps, n_calib, rank)
     n_max = w.window + (n_steps + 2) * w.step
     S = int(1.25 * (w.window // w.slab_size + 2 * w.nlist))
@@ -842,14 +974,29 @@ def main():
               torch.from_numpy(X[b:b + 100_000]).to(dev))
     g.sync()
 
-    # per form: the smallest nprobe with recall@10 >= 0.95 against exact
-    # search (nprobe = nlist, FP32)
-    Qc = torch.from_numpy(Q[-n_calib:]).to(dev)
-    _, gt = g.search(Qc, w.k, w.nlist)
-    gt = gt.cpu().numpy()
+    # per form: the smallest nprobe of the sweep whose recall@10 reaches
+    # 0.95 against the exact k nearest neighbours of N_TRUTH sampled queries
+    # (the FP64 oracle's brute force over the same window, computed on the
+    # host cores outside any timed region), and the nprobe interpolated
+    # linearly between the last sweep point below the target and the first
+    # at or above it
+    Qc_h = Q[-n_calib:]
+    Qc = torch.from_numpy(Qc_h).to(dev)
+    orc = None
+    t_truth = time.time()
+    if args.gpu_truth or args.impl != "sivf" or world > 1:
+        _, gt = g.search(Qc, w.k, w.nlist)
+        gt = gt.cpu().numpy()
+        truth = "the GPU's FP32 search over every list"
+    else:
+        orc, _, _ = oracle_window(w, cent, X, n_max)
+        _, gt = orc.exact_knn(Qc_h, w.k)
+        truth = (f"exact FP64 k nearest neighbours (the oracle's brute force) of {n_calib} "
+                 "sampled queries over the initial window")
+    t_truth = time.time() - t_truth
     calib = {}
     for f in forms:
-        rec, chosen = {}, None
+        rec, chosen, interp, prev = {}, None, None, None
         for P in ([args.nprobe] if args.nprobe else NPROBES):
             _, got = g.search(Qc, w.k, P, f)
             got = got.cpu().numpy()
@@ -857,8 +1004,16 @@ def main():
                                     for a, b in zip(got.tolist(), gt.tolist())]))
             if chosen is None and rec[P] >= 0.95:
                 chosen = P
+                if prev is None:
+                    interp = float(P)
+                else:
+                    p0, r0 = prev
+                    interp = p0 + (0.95 - r0) / max(rec[P] - r0, 1e-12) * (P - p0)
+            if chosen is None:
+                prev = (P, rec[P])
         calib[f] = {"recall_by_nprobe": rec, "nprobe": chosen or NPROBES[-1],
-                    "meets_target": chosen is not None}
+                    "nprobe_interpolated": interp, "meets_target": chosen is not None,
+                    "recall_at_10": rec[chosen or NPROBES[-1]]}
 
     def step_inputs(s):
         new = w.window + s * w.step
@@ -1000,15 +1155,20 @@ def main():
         "data": "synthetic: seeded 1,024-component Gaussian mixture shaped like SIFT "
                 "(d=128, integers 0..255); stands in for SIFT1M",
         "config": config_of(w, nprobe, head),
+        "recall_at_10": calib[head]["recall_at_10"],
+        "nprobe": nprobe,
+        "recall_truth": truth,
         "components": {
             **{k: round(r[k], 4) for k in ("search_qps", "insert_vec_s", "delete_vec_s",
                                            "p50_update_ms", "p99_update_ms", "insert_ms",
                                            "delete_ms", "search_ms")},
-            "recall_at_10": calib[head]["recall_by_nprobe"][nprobe],
+            "truth_s": round(t_truth, 1),
             "kernel_ms_per_step": r["kernel_ms_per_step"],
             "forms": {f: {"qps": round(results[f]["qps"], 1),
                           "search_qps": round(results[f]["search_qps"], 1),
                           "nprobe": calib[f]["nprobe"],
+                          "nprobe_interpolated": calib[f]["nprobe_interpolated"],
+                          "recall_at_10": calib[f]["recall_at_10"],
                           "meets_recall_0.95": calib[f]["meets_target"],
                           "recall_by_nprobe": calib[f]["recall_by_nprobe"],
                           "scan_ms": round(results[f]["scan"][1] / K, 4)} for f in forms},
@@ -1064,22 +1224,35 @@ def main():
         line["components"]["zipf_ingest"] = run_zipf(torch, sivf, dev)
     if not args.no_compact:
         line["components"]["compaction"] = run_compact(torch, sivf, dev)
+    if not args.no_delete_window:
+        line["components"]["delete_vs_window"] = run_delete_window(torch, sivf, dev)
+        torch.cuda.empty_cache()
     if not args.no_serving:
         line["components"]["serving"] = run_serving(
             torch, sivf, dev, args.serving_window, args.serving_seconds)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_ins, n_del, n_q = 1000, 1000, 200
-        rr = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2)
+        if orc is None:
+            orc, _, _ = oracle_window(w, cent, X, n_max)
+        rr = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, 2, o=orc)
+        r1 = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins // 2, n_del // 2, n_q // 2, 1,
+                           o=orc, threads=1, at=(2 * n_ins, 2 * n_del, 2 * n_q))
         line["cpu_baseline"] = {
             "value": round(rr["qps"], 3), "unit": "queries/s", "cores": rr["cores"],
             "kind": "oracle",
             "sample": (f"FP64 oracle holding the full {w.window:,}-vector window (built with "
-                       f"{rr['cores']} threads in {rr['build_s']:.1f} s, untimed); 2 steps of "
-                       f"{n_ins} inserts, {n_del} deletes of the oldest and {n_q} queries "
-                       f"(k={w.k}, nprobe={nprobe}), each scaled to the full step"),
+                       f"every core, untimed); 2 steps of {n_ins} inserts, {n_del} deletes of "
+                       f"the oldest and {n_q} queries (k={w.k}, nprobe={nprobe}), each scaled "
+                       f"to the full step"),
             "components": {k: round(rr[k], 3) for k in ("search_qps", "insert_vec_s",
                                                         "delete_vec_s", "p99_update_ms")},
+            "single_thread": {
+                "value": round(r1["qps"], 3), "unit": "queries/s", "cores": r1["cores"],
+                "sample": (f"the same oracle on one thread: 1 step of {n_ins // 2} inserts, "
+                           f"{n_del // 2} deletes and {n_q // 2} queries, scaled to the full "
+                           f"step"),
+                **{k: round(r1[k], 3) for k in ("search_qps", "insert_vec_s", "delete_vec_s")}},
         }
         if not args.no_train:
             line["cpu_baseline"]["components"]["train"] = oracle_train_sample()
