@@ -798,27 +798,3 @@ class Index:
     def dump_payload(self, bf16=False, fp8=False, stream=None):
         return sivf_dump_payload(self.h, self.n_slabs, self.slab_size, self.d, self.nlist,
                                  True, bf16, fp8, stream)
-
-
-# ------------------------------------------------------------ host logic
-def slab_header_overhead(d: int, slab_size: int = 32, header_bytes: int = 128,
-                         payload_bytes: int = 4) -> float:
-    """Fraction of slab memory spent on the per-slab header: the space model
-    of Sec. 3.5.3 (metadata amortised over C vectors of d floats)."""
-    return header_bytes / (slab_size * d * payload_bytes)
-
-
-def merge_topk_host(dists, ids, k: int):
-    """Merge per-shard top-k lists (shape [shards, nq, k']) into one top-k by
-    (distance, id), the gather step of the paper's scatter-gather search
-    (Sec. 4.2).  Padding (+inf, -1) sorts last."""
-    d = np.concatenate(list(dists), axis=1)
-    i = np.concatenate(list(ids), axis=1)
-    key_i = np.where(i < 0, np.iinfo(np.int64).max, i)
-    out_d = np.empty((d.shape[0], k), d.dtype)
-    out_i = np.empty((d.shape[0], k), np.int64)
-    for r in range(d.shape[0]):
-        order = np.lexsort((key_i[r], d[r]))[:k]
-        out_d[r] = d[r][order]
-        out_i[r] = i[r][order]
-    return out_d, out_i

@@ -40,13 +40,13 @@ def test_create_rejects_bad_config_without_gpu():
 def test_slab_header_overhead_matches_paper():
     """Sec. 5.6.2 reports 0.77% (d=128) and 0.10% (d=960) for a 128-byte
     header amortised over 32 FP32 vectors."""
-    from paper_2601_11808_gb300.sivf import slab_header_overhead
+    from sivf_check import slab_header_overhead
     assert abs(slab_header_overhead(128) - 0.0077) < 0.0002
     assert abs(slab_header_overhead(960) - 0.0010) < 0.00005
 
 
 def test_merge_topk_host_ties_and_padding():
-    from paper_2601_11808_gb300.sivf import merge_topk_host
+    from sivf_check import merge_topk_host
     d = np.array([[[1.0, 3.0, np.inf]], [[1.0, 2.0, 3.0]]])
     i = np.array([[[9, 4, -1]], [[5, 7, 2]]])
     od, oi = merge_topk_host(d, i, 5)
@@ -58,7 +58,7 @@ def _shard_worker(rank, world, port, q, x, ids, cent, k, P, out):
     import torch.distributed as dist
     import torch
     from oracle import OracleIVF
-    from paper_2601_11808_gb300.sivf import merge_topk_host
+    from sivf_check import merge_topk_host
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
