@@ -45,14 +45,12 @@ N_TRUTH = 1000          # sampled queries with FP64 exact ground truth
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# ncu captures of the reduced-precision list scan on this workload (nprobe
-# 8), per scan form: the hash of the scan kernel's source (scan_tc.cu up to
-# the per-query merge: the kernel and every device helper it calls) they
-# were taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum
-# over the search's two launches
-TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
-TC_PROFILED = {"fp8": ("f1611ff8217ff1ec", 160_534_912),
-               "bf16": ("f1611ff8217ff1ec", 300_399_744)}
+# ncu capture of the reduced-precision list scan on this workload (nprobe
+# 1, FP8): the hash of the scan kernel's source (scan_tc.cu up to the
+# per-query merge: the kernel and every device helper it calls) it was
+# taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum per
+# launch
+TC_PROFILED = {"fp8": ("82474eda9311eabe", 149_619_840)}
 
 
 def parse():
