@@ -50,6 +50,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # per-query merge: the kernel and every device helper it calls) it was
 # taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum per
 # launch
+TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
 TC_PROFILED = {"fp8": ("82474eda9311eabe", 149_619_840)}
 
 
