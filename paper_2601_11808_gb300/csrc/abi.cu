@@ -296,6 +296,7 @@ sivf_status sivf_create(const sivf_config *cfg, sivf_index **out)
         ix->free_list, ix->meta, (int64_t)S);
     if (cudaDeviceSynchronize() != cudaSuccess) return bad(SIVF_E_CUDA);
     if ((ix->xb16 || ix->x8) && !tc_make_maps(ix)) return bad(SIVF_E_CUDA);
+    ix->tmap_cent_ok = coarse_make_map(ix);
     ix->tmaps_ready = true;
     *out = ix;
     return SIVF_OK;

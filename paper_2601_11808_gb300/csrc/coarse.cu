@@ -147,6 +147,10 @@ struct SelArgs {
     float gamma2;          // 2 * gamma_d
     float gamma2_first;    // the same factor for the first-stage distances D
     int two_level;         // D is the BF16 tensor-core stage: recheck S in FP32
+    const int32_t *S;      // instead of D: per-row candidate lists of the fused
+    int s_stride;          // first stage ([n, lists...], n = -1: redo the row)
+    const int32_t *hard;   // the rows the fused first stage left undecided
+    const int *nhard;      // (their number, on the device)
     int32_t *out;          // [m, P]
     uint32_t *err;
 };
@@ -564,13 +568,386 @@ __global__ __launch_bounds__(CT_NT, 1) void k_coarse_tc(const float *__restrict_
     if (warp == 0) tmem_dealloc(tbase, CT_N);
 }
 
+// ------------------------------- fused BF16 first stage for assignment
+// P = 1, one CTA per 128 rows of x against ALL centroids, without writing
+// the distance matrix.  The BF16 centroids pass in chunks of CT_N = 256 rows
+// (TMA boxes of 64 columns x 256 rows, 128-byte swizzle, into two buffers),
+// one tcgen05.mma group per chunk into one of two 256-column TMEM buffers,
+// so that the MMA of the next step and the copy of the one after run under
+// each epilogue.  The chunks pass twice (recomputing a chunk's products
+// costs far less than keeping them):
+//   pass 1: per row Dmin = min_c Dt_c and A = max_c |Dt_c|.  With
+//           Ebig >= E_c for every c (the bound of the selection evaluated
+//           at max ||c||^2, A and max ||c||, rounded up), T = Dmin + Ebig
+//           (rounded up) is >= the smallest upper bound Dt_c + E_c;
+//   pass 2: the lists with lower bound Dt_c - E_c <= T, a superset of the
+//           selection's set S.  A list with Dt_c above thr = T + Ebig plus
+//           one unit in the last place of T (rounded up) cannot qualify and
+//           is rejected by one comparison; the rest take the exact test.
+// Pass 1 also keeps the row's second smallest Dt: when it is above thr only
+// the argmin can qualify, so the argmin is the answer; a tile whose rows
+// are all decided that way skips pass 2.
+// A row left with one list has its answer (S holds the nearest list): it
+// is written to `out1` directly.  Any other row is appended to `hard` and
+// leaves [n, list_0 .. list_{n-1}] for the finishing selection, n = -1 when
+// one of its four threads had more than CF_CAP lists (the row is then
+// redone from all lists).  ||x|| is bounded from the FP32 sum of squares
+// s of the tile's rows (relative error <= d u) as RU(sqrt(RU(s (1 + 4 d u)))).
+// One thread issues the copies and MMAs and waits for them; a block barrier
+// per step releases the others.
+constexpr int CF_CAP = 8;                   // lists per thread
+constexpr int CF_SUB = 4;                   // threads per row
+constexpr int CF_STRIDE = CF_SUB * CF_CAP + 1;  // ints per row of the output
+constexpr int CF_NT = 128 * CF_SUB;
+
+__host__ __device__ inline size_t coarse_fused_smem(int d)
+{
+    const int KC = (d * 2 + 127) / 128;
+    return (size_t)KC * (CT_M + 2 * CT_N) * 128 + (size_t)CF_CAP * CF_NT * 4 + 1024;
+}
+
+template <int KC>
+__global__ __launch_bounds__(CF_NT, 1) void k_coarse_fused1(
+    const __grid_constant__ CUtensorMap tmB, const float *__restrict__ x, int m, int d,
+    const float *__restrict__ cn, const float *__restrict__ cnrm_up, int L, float g1,
+    int32_t *__restrict__ out1, int32_t *__restrict__ outS, int32_t *__restrict__ hard,
+    int *nhard, uint32_t *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    __shared__ uint64_t fullb[2], mmab[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ float sxn[CT_M], sMin[CF_SUB][CT_M], sSec[CF_SUB][CT_M], sMax[CF_SUB][CT_M];
+    __shared__ int sn[CF_SUB][CT_M], sArg[CF_SUB][CT_M];
+    __shared__ uint32_t smax[2];  // max ||c||^2, max ||c|| (bits of non-negative floats)
+    constexpr uint32_t BBYTES = KC * CT_N * 128;
+    unsigned char *A = smem;                                  // KC x 128 rows x 128 B
+    unsigned char *B = smem + (size_t)KC * CT_M * 128;        // 2 x KC x 256 rows x 128 B
+    int *rc = reinterpret_cast<int *>(B + 2 * BBYTES);        // [CF_CAP][CF_NT] lists
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, sub = warp >> 2, rloc = q * 32 + lane;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&fullb[i], 1);
+            mbar_init(&mmab[i], 1);
+        }
+        fence_mbar_init();
+        smax[0] = smax[1] = 0u;
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 2 * CT_N);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    {
+        float a0 = 0.f, a1 = 0.f;
+        for (int c = tid; c < L; c += CF_NT) {
+            a0 = fmaxf(a0, __ldg(cn + c));
+            a1 = fmaxf(a1, __ldg(cnrm_up + c));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 = fmaxf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+            a1 = fmaxf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        }
+        if (lane == 0) {
+            atomicMax(&smax[0], __float_as_uint(a0));
+            atomicMax(&smax[1], __float_as_uint(a1));
+        }
+    }
+    const uint32_t tbase = tmem_base;
+    const uint32_t idesc = mma_idesc(1, 1, CT_M, CT_N);
+    const int nch = (L + CT_N - 1) / CT_N, nsteps = 2 * nch, ntiles = (m + CT_M - 1) / CT_M;
+    // thread 0's bookkeeping, bit b for buffer b: phases, and copies / MMAs
+    // issued but not waited for
+    uint32_t fph = 0u, mph = 0u, fpend = 0u, mpend = 0u;
+    bool ok = true;
+
+    auto load_b = [&](int j, int b) {  // chunk j -> B buffer b
+        mbar_arrive_expect_tx(&fullb[b], BBYTES);
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc)
+            tma_load_2d(B + (size_t)b * BBYTES + (size_t)kc * CT_N * 128, &tmB, kc * 64, j * CT_N,
+                        &fullb[b]);
+        fpend |= 1u << b;
+    };
+    auto wait_full = [&](int b) {
+        const bool g = mbar_wait_bounded(&fullb[b], (fph >> b) & 1u, err);
+        fph ^= 1u << b;
+        fpend &= ~(1u << b);
+        return g;
+    };
+    auto issue_mma = [&](int b) {  // B buffer b -> TMEM buffer b
+        const uint32_t abase = smem_u32(A), bbase = smem_u32(B + (size_t)b * BBYTES);
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_bf16(tbase + b * CT_N, smem_desc_sw128(abase + kc * CT_M * 128 + ks * 32, 1024),
+                         smem_desc_sw128(bbase + kc * CT_N * 128 + ks * 32, 1024), idesc,
+                         (kc | ks) != 0);
+        mma_commit(&mmab[b]);
+        mpend |= 1u << b;
+    };
+    auto wait_mma = [&](int b) {
+        const bool g = mbar_wait_bounded(&mmab[b], (mph >> b) & 1u, err);
+        mph ^= 1u << b;
+        mpend &= ~(1u << b);
+        return g;
+    };
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int row0 = tile * CT_M;
+        if (tid == 0) {
+            load_b(0, 0);
+            load_b(1 % nch, 1);
+        }
+        // A: the tile's rows rounded to BF16, zero past m or d.  The KC * 8
+        // chunks of a row sit in consecutive lanes: their sums of squares
+        // reduce by shuffles into the row's ||x|| bound
+        constexpr int nA = CT_M * KC * 8, W = KC * 8;
+        const float fx = 1.f + 4.f * (float)d * 5.9604645e-08f;
+        static_assert(nA % CF_NT == 0 || CF_NT % nA == 0, "whole warps per A pass");
+        for (int e0 = tid; e0 < nA; e0 += CF_NT * CT_AU) {
+            float4 f0[CT_AU], f1[CT_AU];
+#pragma unroll
+            for (int u = 0; u < CT_AU; ++u) {
+                const int e = e0 + u * CF_NT;
+                const int r = e / W, kc = (e >> 3) % KC, c = e & 7;
+                const int k0 = kc * 64 + c * 8;
+                f0[u] = f1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < nA && row0 + r < m && k0 < d) {
+                    const float4 *xr = reinterpret_cast<const float4 *>(x + (size_t)(row0 + r) * d + k0);
+                    f0[u] = __ldg(xr);
+                    f1[u] = __ldg(xr + 1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CT_AU; ++u) {
+                const int e = e0 + u * CF_NT;
+                if (e >= nA) break;  // warp-uniform: nA is a multiple of CF_NT / 2
+                const int r = e / W, kc = (e >> 3) % KC, c = e & 7;
+                const float f[8] = {f0[u].x, f0[u].y, f0[u].z, f0[u].w,
+                                    f1[u].x, f1[u].y, f1[u].z, f1[u].w};
+                uint32_t w[4];
+                float sq = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * t], f[2 * t + 1]);
+                    w[t] = *reinterpret_cast<uint32_t *>(&h);
+                    sq = fmaf(f[2 * t], f[2 * t], sq);
+                    sq = fmaf(f[2 * t + 1], f[2 * t + 1], sq);
+                }
+                *reinterpret_cast<uint4 *>(A + (size_t)kc * CT_M * 128 + (size_t)(r >> 3) * 1024 +
+                                           (r & 7) * 128 + ((c ^ (r & 7)) << 4)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                for (int o = W >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if ((lane & (W - 1)) == 0) sxn[r] = __fsqrt_ru(__fmul_ru(sq, fx));
+            }
+        }
+        fence_proxy_async_smem();  // A (generic stores) is read by the MMAs
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        bool got = true;  // thread 0: every wait so far succeeded
+        if (tid == 0) {
+            got = wait_full(0);
+            if (got) issue_mma(0);
+        }
+        const float xn = sxn[rloc];
+        // pass 1: smallest, second smallest and largest Dt, the smallest's list
+        float d1 = INFINITY, d2 = INFINITY, dmax = -INFINITY, T = INFINITY, thr = -INFINITY;
+        int c1 = -1, n = 0;
+        bool ovf = false, done = false;
+        for (int s = 0; s < nsteps; ++s) {
+            const int b = s & 1, j = s % nch;
+            if (tid == 0 && got) got = wait_mma(b);
+            // MMA s is done and every thread has finished epilogue s - 1
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            if (tid == 0) {
+                if (s + 1 < nsteps) {  // TMEM buffer b ^ 1 is free: MMA s + 1 under this epilogue
+                    got = wait_full(b ^ 1);
+                    if (got) issue_mma(b ^ 1);
+                }
+                if (got && s + 2 < nsteps) load_b((s + 2) % nch, b);  // MMA s has read buffer b
+            }
+            for (int c16 = sub; c16 < CT_N / 16; c16 += CF_SUB) {  // warp-uniform
+                const int cb0 = j * CT_N + c16 * 16;
+                if (cb0 >= L) break;
+                const int nv = min(16, L - cb0);
+                float v[16], cv[16];
+                tmem_ld16(tbase + b * CT_N + c16 * 16 + ((uint32_t)(q * 32) << 16), v);
+                if (nv == 16) {
+#pragma unroll
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const float4 t = __ldg(reinterpret_cast<const float4 *>(cn + cb0) + i4);
+                        cv[4 * i4] = t.x;
+                        cv[4 * i4 + 1] = t.y;
+                        cv[4 * i4 + 2] = t.z;
+                        cv[4 * i4 + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) cv[i] = i < nv ? __ldg(cn + cb0 + i) : 0.f;
+                }
+                tmem_ld_wait(v);
+                if (s < nch) {
+                    auto see = [&](float Dt, int c) {
+                        const bool lt = Dt < d1;
+                        d2 = fminf(d2, lt ? d1 : Dt);
+                        c1 = lt ? c : c1;
+                        d1 = fminf(d1, Dt);
+                        dmax = fmaxf(dmax, Dt);
+                    };
+                    if (nv == 16) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) see(fmaf(-2.f, v[i], cv[i]), cb0 + i);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (i < nv) see(fmaf(-2.f, v[i], cv[i]), cb0 + i);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float Dt = fmaf(-2.f, v[i], cv[i]);
+                        if (!(i < nv && Dt <= thr)) continue;
+                        const int c = cb0 + i;
+                        const float E = bound_of(Dt, cv[i], __ldg(cnrm_up + c), xn, g1);
+                        if (!(lower_of(Dt, E) <= T)) continue;
+                        if (n < CF_CAP) rc[n * CF_NT + tid] = c;
+                        else ovf = true;
+                        ++n;
+                    }
+                }
+            }
+            if (s == nch - 1) {  // end of pass 1: the row's T and quick-reject threshold
+                sMin[sub][rloc] = d1;
+                sSec[sub][rloc] = d2;
+                sMax[sub][rloc] = dmax;
+                sArg[sub][rloc] = c1;
+                __syncthreads();
+                int kmin = 0;
+                float mn = sMin[0][rloc], mx = sMax[0][rloc];
+#pragma unroll
+                for (int k = 1; k < CF_SUB; ++k) {
+                    if (sMin[k][rloc] < mn) kmin = k;
+                    mn = fminf(mn, sMin[k][rloc]);
+                    mx = fmaxf(mx, sMax[k][rloc]);
+                }
+                float second = sSec[kmin][rloc];
+#pragma unroll
+                for (int k = 0; k < CF_SUB; ++k)
+                    if (k != kmin) second = fminf(second, sMin[k][rloc]);
+                const float ab = fmaxf(fabsf(mn), fabsf(mx));
+                // Ebig: the bound at the maxima, every step rounded up, times
+                // 1 + 2^-10 (covers the roundings of the bound itself)
+                const float t1 = __fmul_ru(5.9604645e-08f, __fadd_ru(__uint_as_float(smax[0]), ab));
+                const float t2 = __fmul_ru(__fmul_ru(g1, xn), __uint_as_float(smax[1]));
+                const float eb = __fadd_ru(
+                    __fmul_ru(__fmul_ru(2.f, __fadd_ru(t1, t2)), 1.f + 1.f / 1024.f), 1e-30f);
+                T = __fadd_ru(mn, eb);
+                // RN(Dt - E) <= T needs Dt < T + E + ulp(T) <= thr
+                thr = __fadd_ru(__fadd_ru(T, eb), __fadd_ru(__fmul_ru(fabsf(T), 1.2e-7f), 1e-30f));
+                // decided: no list but the argmin has Dt <= thr
+                const bool decided = !(second <= thr) && mn <= thr;
+                if (!__syncthreads_or(!decided && row0 + rloc < m)) {
+                    if (sub == 0 && row0 + rloc < m) out1[row0 + rloc] = sArg[kmin][rloc];
+                    if (tid == 0)  // the pass-2 copy and MMA already issued are waited for
+                        for (int i = 0; i < 2; ++i) {
+                            if ((fpend >> i) & 1u) got &= wait_full(i);
+                            if ((mpend >> i) & 1u) got &= wait_mma(i);
+                        }
+                    done = true;
+                    break;
+                }
+            }
+            tc_fence_before();
+        }
+        if (!ok) break;
+        if (done) {
+            if (__syncthreads_or(!got)) ok = false;  // a drain wait ran out
+            continue;                                // sMin ... are rewritten after a barrier
+        }
+        sn[sub][rloc] = ovf ? -1 : n;
+        __syncthreads();
+        const int r = row0 + rloc;
+        if (r < m) {
+            int32_t *o = outS + (size_t)r * CF_STRIDE;
+            int before = 0, total = 0;
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < CF_SUB; ++k) {
+                const int nk = sn[k][rloc];
+                bad |= nk < 0;
+                before += k < sub ? nk : 0;
+                total += nk;
+            }
+            if (!bad && total == 1) {
+                if (n == 1) out1[r] = rc[tid];
+            } else {
+                if (bad) {
+                    if (sub == 0) o[0] = -1;
+                } else {
+                    for (int k = 0; k < n; ++k) o[1 + before + k] = rc[k * CF_NT + tid];
+                    if (sub == 0) o[0] = total;
+                }
+                if (sub == 0) hard[atomicAdd(nhard, 1)] = r;
+            }
+        }
+        __syncthreads();  // sxn, sMin, sMax, sn, the lists and A are reused by the next tile
+    }
+    if (!ok) {
+        // a wait ran out: thread 0 waits (bounded) for its copies and MMAs
+        // still in flight; every row of this CTA's tiles goes to the full
+        // selection
+        if (tid == 0)
+            for (int i = 0; i < 2; ++i) {
+                if ((fpend >> i) & 1u) wait_full(i);
+                if ((mpend >> i) & 1u) wait_mma(i);
+            }
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+            for (int r = tile * CT_M + tid; r < min(m, tile * CT_M + CT_M); r += CF_NT) {
+                outS[(size_t)r * CF_STRIDE] = -1;
+                hard[atomicAdd(nhard, 1)] = r;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tbase, 2 * CT_N);
+}
+
+// TMA descriptor of the BF16 centroids for the fused first stage: boxes of
+// 64 columns x CT_N rows, 128-byte swizzle; rows past nlist read as zero.
+bool coarse_make_map(sivf_index *ix)
+{
+    const int d = ix->d;
+    if (!ix->cent_bf16 || d < 64 || d > 128 || d % 16) return false;
+    auto enc = tmap_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)ix->nlist};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)CT_N};
+    cuuint32_t es[2] = {1, 1};
+    return enc(reinterpret_cast<CUtensorMap *>(ix->tmap_cent), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               ix->cent_bf16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // ----------------------------------------------- warp-per-row selection
 // The same selection for P <= CW_PMAX with one warp per row and no block
 // barriers: each lane keeps the CW_PMAX smallest upper bounds of its lists
 // (sorted, in registers), the warp extracts the P-th smallest of their
 // union as T, then gathers S, tests the sure members and re-decides the
 // rest in FP64 exactly as above.  Rows whose S exceeds CW_SCAP take the
-// serial FP64 path.
+// serial FP64 path.  FROM_S: the candidate set comes from the fused first
+// stage (a superset of S for its BF16 bound); a row it marked as overflowed
+// is selected from all lists with FP32 distances computed here.
 constexpr int CW_ROWS = 4;     // rows (warps) per block
 constexpr int CW_PMAX = 8;
 constexpr int CW_SCAP = 128;
@@ -578,7 +955,7 @@ constexpr int CW_LMAX = 4096;  // most lists for one warp per row
 constexpr int CW_RG = 4;       // FP32 rechecks in flight per warp
 
 // PM: length of each lane's sorted list (1 when P = 1, else CW_PMAX)
-template <int PM>
+template <int PM, bool FROM_S>
 __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 {
     __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP], sDt[CW_ROWS][CW_SCAP];
@@ -590,233 +967,235 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
     __shared__ double sHd[CW_ROWS][CW_PMAX];
     __shared__ __align__(16) float sX[CW_ROWS][kMaxD];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * CW_ROWS + w;
-    if (row >= a.m) return;  // whole warps
     const int L = a.L, P = a.P;
-    const float *Dr = a.D + (size_t)row * L;
-    const float *xr = a.x + (size_t)row * a.d;
-    const float g1 = a.two_level ? a.gamma2_first : a.gamma2;
+    const int nrows = FROM_S ? *a.nhard : a.m;
+    for (int it = blockIdx.x * CW_ROWS + w; it < nrows; it += gridDim.x * CW_ROWS) {  // whole warps
+        const int row = FROM_S ? a.hard[it] : it;
+        const float *Dr = FROM_S ? nullptr : a.D + (size_t)row * L;
+        const float *xr = a.x + (size_t)row * a.d;
+        int two_level = a.two_level;
+        float g1 = two_level ? a.gamma2_first : a.gamma2;
 
-    // ||x|| upper bound from an FP64 sum
-    double part = 0.0;
-    for (int j = lane; j < a.d; j += 32) part += (double)xr[j] * (double)xr[j];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const float xn = __double2float_ru(sqrt(part) * (1.0 + 1e-12));
+        // ||x|| upper bound from an FP64 sum
+        double part = 0.0;
+        for (int j = lane; j < a.d; j += 32) part += (double)xr[j] * (double)xr[j];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const float xn = __double2float_ru(sqrt(part) * (1.0 + 1e-12));
 
-    // P-th smallest of the values v(i), i < n, each lane keeping its
-    // CW_PMAX smallest in a sorted register list
-    auto pth_smallest = [&](auto val, int n) {
-        float top[PM];
-#pragma unroll
-        for (int k = 0; k < PM; ++k) top[k] = INFINITY;
-        constexpr int CU = 8;  // values per lane loaded ahead
-        for (int i0 = lane; i0 < n; i0 += 32 * CU) {
-            float vv[CU];
-#pragma unroll
-            for (int u = 0; u < CU; ++u) vv[u] = i0 + 32 * u < n ? val(i0 + 32 * u) : INFINITY;
-#pragma unroll
-            for (int u = 0; u < CU; ++u) {
-                float v = vv[u];
-#pragma unroll
-                for (int k = 0; k < PM; ++k) {  // insert into the sorted list
-                    const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
-                    top[k] = lo;
-                    v = hi;
-                }
+        // first-stage distance of list c: the approximate matrix, or for a row
+        // the fused first stage could not record, an FP32 dot product (one lane)
+        int ns = 0;
+        bool have_s = false;
+        if (FROM_S) {
+            for (int j = lane; j < a.d; j += 32) sX[w][j] = xr[j];
+            const int32_t *Sr = a.S + (size_t)row * a.s_stride;
+            const int n0 = Sr[0];
+            if (n0 >= 0 && n0 <= CW_SCAP) {
+                for (int p = lane; p < n0; p += 32) sIdx[w][p] = Sr[1 + p];
+                ns = n0;
+                have_s = true;
+            } else {
+                two_level = 0;
+                g1 = a.gamma2;
             }
-        }
-        float T = INFINITY;
-        for (int t = 0; t < P; ++t) {
-            float v = top[0];
-            int who = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                const int ow = __shfl_xor_sync(0xffffffffu, who, o);
-                if (ov < v || (ov == v && ow < who)) {
-                    v = ov;
-                    who = ow;
-                }
-            }
-            T = v;
-            if (lane == who) {
-#pragma unroll
-                for (int k = 0; k + 1 < PM; ++k) top[k] = top[k + 1];
-                top[PM - 1] = INFINITY;
-            }
-        }
-        return T;
-    };
-
-    // T = P-th smallest upper bound over all lists
-    float T = pth_smallest([&](int c) {
-        const float Dt = __ldg(Dr + c);
-        return upper_of(Dt, bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1));
-    }, L);
-
-    // candidate set S = {c : lower bound <= T}
-    int ns = 0;
-    constexpr int CU = 8;
-    for (int c00 = 0; c00 < L; c00 += 32 * CU) {
-        float lbv[CU], ubv[CU], dtv[CU];
-#pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            const int c = c00 + 32 * u + lane;
-            lbv[u] = INFINITY;
-            ubv[u] = INFINITY;
-            dtv[u] = 0.f;
-            if (c < L) {
-                const float Dt = __ldg(Dr + c);
-                const float E = bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1);
-                lbv[u] = lower_of(Dt, E);
-                ubv[u] = upper_of(Dt, E);
-                dtv[u] = Dt;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            const int c = c00 + 32 * u + lane;
-            const bool in = c < L && lbv[u] <= T;
-            const uint32_t mk = __ballot_sync(0xffffffffu, in);
-            if (in) {
-                const int p = ns + __popc(mk & lanemask_lt());
-                if (p < CW_SCAP) {
-                    sLB[w][p] = lbv[u];
-                    sUB[w][p] = ubv[u];
-                    sDt[w][p] = dtv[u];
-                    sIdx[w][p] = c;
-                }
-            }
-            ns += __popc(mk);
-        }
-    }
-    __syncwarp();
-    if (a.two_level && ns <= CW_SCAP) {
-        // S holds every list that can be among the top P (BF16-stage
-        // bound); recompute their distances in FP32, one list per lane,
-        // rebuild T and S with the FP32 bound inside S
-        for (int j = lane; j < a.d; j += 32) sX[w][j] = xr[j];
-        __syncwarp();
-        // the warp computes CW_RG members' dot products at a time, lanes
-        // over the coordinates (coalesced centroid rows), then a butterfly
-        const float4 *x4 = reinterpret_cast<const float4 *>(sX[w]);
-        const int n4 = a.d >> 2;
-        for (int p0 = 0; p0 < ns; p0 += CW_RG) {
-            float part[CW_RG];
-#pragma unroll
-            for (int t = 0; t < CW_RG; ++t) {
-                part[t] = 0.f;
-                if (p0 + t >= ns) continue;
-                const float4 *c4 =
-                    reinterpret_cast<const float4 *>(a.cent + (size_t)sIdx[w][p0 + t] * a.d);
-#pragma unroll
-                for (int u = 0; u < kMaxD / 128; ++u) {
-                    const int j4 = lane + 32 * u;
-                    if (j4 >= n4) break;
-                    const float4 xv = x4[j4], cv = __ldg(c4 + j4);
-                    part[t] = fmaf(xv.x, cv.x, part[t]);
-                    part[t] = fmaf(xv.y, cv.y, part[t]);
-                    part[t] = fmaf(xv.z, cv.z, part[t]);
-                    part[t] = fmaf(xv.w, cv.w, part[t]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int t = 0; t < CW_RG; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
-            float acc = part[0];
-#pragma unroll
-            for (int t = 1; t < CW_RG; ++t)
-                if (lane == t) acc = part[t];
-            const int p = p0 + lane;
-            if (lane < CW_RG && p < ns) {
-                const int c = sIdx[w][p];
-                const float cnc = __ldg(a.cn + c);
-                const float Dt = fmaf(-2.f, acc, cnc);
-                const float E = bound_of(Dt, cnc, __ldg(a.cnrm_up + c), xn, a.gamma2);
-                sLB[w][p] = lower_of(Dt, E);
-                sUB[w][p] = upper_of(Dt, E);
-                sDt[w][p] = Dt;
-            }
-        }
-        __syncwarp();
-        T = pth_smallest([&](int p) { return sUB[w][p]; }, ns);
-        int n2 = 0;
-        for (int p0 = 0; p0 < ns; p0 += 32) {
-            const int p = p0 + lane;
-            const bool keep = p < ns && sLB[w][p] <= T;
-            float lb = 0.f, ub = 0.f, dt = 0.f;
-            int c = 0;
-            if (keep) {
-                lb = sLB[w][p];
-                ub = sUB[w][p];
-                dt = sDt[w][p];
-                c = sIdx[w][p];
-            }
-            const uint32_t mk = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
-            if (keep) {  // write index <= read index
-                const int q = n2 + __popc(mk & lanemask_lt());
-                sLB[w][q] = lb;
-                sUB[w][q] = ub;
-                sDt[w][q] = dt;
-                sIdx[w][q] = c;
-            }
-            n2 += __popc(mk);
             __syncwarp();
         }
-        ns = n2;
-    }
-    int32_t *outr = a.out + (size_t)row * P;
-    int nsel = 0;
-    if (ns <= CW_SCAP) {
-        // sure members
-        for (int p0 = 0; p0 < ns; p0 += 32) {
-            const int p = p0 + lane;
-            bool sure = false;
-            if (p < ns) {
-                const float ub = sUB[w][p];
-                int cnt = 0;
-                for (int q = 0; q < ns; ++q) cnt += (q != p && sLB[w][q] <= ub);
-                sure = ub <= T && cnt < P;
-                sSure[w][p] = sure;
+        auto dt_of = [&](int c) -> float {
+            if (!FROM_S) return __ldg(Dr + c);
+            const float4 *x4 = reinterpret_cast<const float4 *>(sX[w]);
+            const float4 *c4 = reinterpret_cast<const float4 *>(a.cent + (size_t)c * a.d);
+            float acc = 0.f;
+            for (int j4 = 0; j4 < (a.d >> 2); ++j4) {
+                const float4 xv = x4[j4], cv = __ldg(c4 + j4);
+                acc = fmaf(xv.x, cv.x, acc);
+                acc = fmaf(xv.y, cv.y, acc);
+                acc = fmaf(xv.z, cv.z, acc);
+                acc = fmaf(xv.w, cv.w, acc);
             }
-            const uint32_t mk = __ballot_sync(0xffffffffu, sure);
-            if (sure) {
-                const int s = nsel + __popc(mk & lanemask_lt());
-                if (s < CW_PMAX) {
-                    sSel[w][s] = sIdx[w][p];
-                    sSelDt[w][s] = sDt[w][p];
-                }
-            }
-            nsel += __popc(mk);
-        }
-        __syncwarp();
-        const int r = P - nsel, nb = ns - nsel;
-        if (r > 0) {
-            // boundary members: exact FP64 distances, rank among them
-            if (nb > r) {
-                for (int p = lane; p < ns; p += 32)
-                    if (!sSure[w][p]) sDx[w][p] = exact_dist(xr, a.cent + (size_t)sIdx[w][p] * a.d, a.d);
-                __syncwarp();
-            }
-            for (int p0 = 0; p0 < ns; p0 += 32) {
-                const int p = p0 + lane;
-                bool take = false;
-                if (p < ns && !sSure[w][p]) {
-                    take = true;
-                    if (nb > r) {
-                        const double Dc = sDx[w][p];
-                        const int c = sIdx[w][p];
-                        int rank = 0;
-                        for (int q = 0; q < ns; ++q) {
-                            if (q == p || sSure[w][q]) continue;
-                            rank += (sDx[w][q] < Dc || (sDx[w][q] == Dc && sIdx[w][q] < c));
-                        }
-                        take = rank < r;
+            for (int j = a.d & ~3; j < a.d; ++j)
+                acc = fmaf(sX[w][j], __ldg(a.cent + (size_t)c * a.d + j), acc);
+            return fmaf(-2.f, acc, __ldg(a.cn + c));
+        };
+
+        // P-th smallest of the values v(i), i < n, each lane keeping its
+        // CW_PMAX smallest in a sorted register list
+        auto pth_smallest = [&](auto val, int n) {
+            float top[PM];
+#pragma unroll
+            for (int k = 0; k < PM; ++k) top[k] = INFINITY;
+            constexpr int CU = 8;  // values per lane loaded ahead
+            for (int i0 = lane; i0 < n; i0 += 32 * CU) {
+                float vv[CU];
+#pragma unroll
+                for (int u = 0; u < CU; ++u) vv[u] = i0 + 32 * u < n ? val(i0 + 32 * u) : INFINITY;
+#pragma unroll
+                for (int u = 0; u < CU; ++u) {
+                    float v = vv[u];
+#pragma unroll
+                    for (int k = 0; k < PM; ++k) {  // insert into the sorted list
+                        const float lo = fminf(top[k], v), hi = fmaxf(top[k], v);
+                        top[k] = lo;
+                        v = hi;
                     }
                 }
-                const uint32_t mk = __ballot_sync(0xffffffffu, take);
-                if (take) {
+            }
+            float T = INFINITY;
+            for (int t = 0; t < P; ++t) {
+                float v = top[0];
+                int who = lane;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    const int ow = __shfl_xor_sync(0xffffffffu, who, o);
+                    if (ov < v || (ov == v && ow < who)) {
+                        v = ov;
+                        who = ow;
+                    }
+                }
+                T = v;
+                if (lane == who) {
+#pragma unroll
+                    for (int k = 0; k + 1 < PM; ++k) top[k] = top[k + 1];
+                    top[PM - 1] = INFINITY;
+                }
+            }
+            return T;
+        };
+
+        // T = P-th smallest upper bound over all lists
+        float T = INFINITY;
+        if (!have_s) T = pth_smallest([&](int c) {
+            const float Dt = dt_of(c);
+            return upper_of(Dt, bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1));
+        }, L);
+
+        // candidate set S = {c : lower bound <= T}
+        constexpr int CU = 8;
+        for (int c00 = 0; c00 < (have_s ? 0 : L); c00 += 32 * CU) {
+            float lbv[CU], ubv[CU], dtv[CU];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int c = c00 + 32 * u + lane;
+                lbv[u] = INFINITY;
+                ubv[u] = INFINITY;
+                dtv[u] = 0.f;
+                if (c < L) {
+                    const float Dt = dt_of(c);
+                    const float E = bound_of(Dt, __ldg(a.cn + c), __ldg(a.cnrm_up + c), xn, g1);
+                    lbv[u] = lower_of(Dt, E);
+                    ubv[u] = upper_of(Dt, E);
+                    dtv[u] = Dt;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int c = c00 + 32 * u + lane;
+                const bool in = c < L && lbv[u] <= T;
+                const uint32_t mk = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    const int p = ns + __popc(mk & lanemask_lt());
+                    if (p < CW_SCAP) {
+                        sLB[w][p] = lbv[u];
+                        sUB[w][p] = ubv[u];
+                        sDt[w][p] = dtv[u];
+                        sIdx[w][p] = c;
+                    }
+                }
+                ns += __popc(mk);
+            }
+        }
+        __syncwarp();
+        if (two_level && ns <= CW_SCAP) {
+            // S holds every list that can be among the top P (BF16-stage
+            // bound); recompute their distances in FP32, one list per lane,
+            // rebuild T and S with the FP32 bound inside S
+            for (int j = lane; j < a.d; j += 32) sX[w][j] = xr[j];
+            __syncwarp();
+            // the warp computes CW_RG members' dot products at a time, lanes
+            // over the coordinates (coalesced centroid rows), then a butterfly
+            const float4 *x4 = reinterpret_cast<const float4 *>(sX[w]);
+            const int n4 = a.d >> 2;
+            for (int p0 = 0; p0 < ns; p0 += CW_RG) {
+                float part[CW_RG];
+#pragma unroll
+                for (int t = 0; t < CW_RG; ++t) {
+                    part[t] = 0.f;
+                    if (p0 + t >= ns) continue;
+                    const float4 *c4 =
+                        reinterpret_cast<const float4 *>(a.cent + (size_t)sIdx[w][p0 + t] * a.d);
+#pragma unroll
+                    for (int u = 0; u < kMaxD / 128; ++u) {
+                        const int j4 = lane + 32 * u;
+                        if (j4 >= n4) break;
+                        const float4 xv = x4[j4], cv = __ldg(c4 + j4);
+                        part[t] = fmaf(xv.x, cv.x, part[t]);
+                        part[t] = fmaf(xv.y, cv.y, part[t]);
+                        part[t] = fmaf(xv.z, cv.z, part[t]);
+                        part[t] = fmaf(xv.w, cv.w, part[t]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int t = 0; t < CW_RG; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
+                float acc = part[0];
+#pragma unroll
+                for (int t = 1; t < CW_RG; ++t)
+                    if (lane == t) acc = part[t];
+                const int p = p0 + lane;
+                if (lane < CW_RG && p < ns) {
+                    const int c = sIdx[w][p];
+                    const float cnc = __ldg(a.cn + c);
+                    const float Dt = fmaf(-2.f, acc, cnc);
+                    const float E = bound_of(Dt, cnc, __ldg(a.cnrm_up + c), xn, a.gamma2);
+                    sLB[w][p] = lower_of(Dt, E);
+                    sUB[w][p] = upper_of(Dt, E);
+                    sDt[w][p] = Dt;
+                }
+            }
+            __syncwarp();
+            T = pth_smallest([&](int p) { return sUB[w][p]; }, ns);
+            int n2 = 0;
+            for (int p0 = 0; p0 < ns; p0 += 32) {
+                const int p = p0 + lane;
+                const bool keep = p < ns && sLB[w][p] <= T;
+                float lb = 0.f, ub = 0.f, dt = 0.f;
+                int c = 0;
+                if (keep) {
+                    lb = sLB[w][p];
+                    ub = sUB[w][p];
+                    dt = sDt[w][p];
+                    c = sIdx[w][p];
+                }
+                const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+                __syncwarp();
+                if (keep) {  // write index <= read index
+                    const int q = n2 + __popc(mk & lanemask_lt());
+                    sLB[w][q] = lb;
+                    sUB[w][q] = ub;
+                    sDt[w][q] = dt;
+                    sIdx[w][q] = c;
+                }
+                n2 += __popc(mk);
+                __syncwarp();
+            }
+            ns = n2;
+        }
+        int32_t *outr = a.out + (size_t)row * P;
+        int nsel = 0;
+        if (ns <= CW_SCAP) {
+            // sure members
+            for (int p0 = 0; p0 < ns; p0 += 32) {
+                const int p = p0 + lane;
+                bool sure = false;
+                if (p < ns) {
+                    const float ub = sUB[w][p];
+                    int cnt = 0;
+                    for (int q = 0; q < ns; ++q) cnt += (q != p && sLB[w][q] <= ub);
+                    sure = ub <= T && cnt < P;
+                    sSure[w][p] = sure;
+                }
+                const uint32_t mk = __ballot_sync(0xffffffffu, sure);
+                if (sure) {
                     const int s = nsel + __popc(mk & lanemask_lt());
                     if (s < CW_PMAX) {
                         sSel[w][s] = sIdx[w][p];
@@ -825,53 +1204,90 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
                 }
                 nsel += __popc(mk);
             }
-        }
-    } else {
-        // pathological (more than CW_SCAP candidates, e.g. many identical
-        // centroids): exact FP64 insertion into a sorted array of P, lists
-        // in index order (keeps the lowest index among ties)
-        if (lane == 0) {
-            int n = 0;
-            for (int c = 0; c < L; ++c) {
-                const float Dt = Dr[c];
-                const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, g1);
-                if (lower_of(Dt, E) > T) continue;
-                const double Dc = exact_dist(xr, a.cent + (size_t)c * a.d, a.d);
-                if (n == P && !(Dc < sHd[w][n - 1])) continue;
-                int pos = n < P ? n : P - 1;
-                while (pos > 0 && Dc < sHd[w][pos - 1]) {
-                    sHd[w][pos] = sHd[w][pos - 1];
-                    sSel[w][pos] = sSel[w][pos - 1];
-                    --pos;
+            __syncwarp();
+            const int r = P - nsel, nb = ns - nsel;
+            if (r > 0) {
+                // boundary members: exact FP64 distances, rank among them
+                if (nb > r) {
+                    for (int p = lane; p < ns; p += 32)
+                        if (!sSure[w][p]) sDx[w][p] = exact_dist(xr, a.cent + (size_t)sIdx[w][p] * a.d, a.d);
+                    __syncwarp();
                 }
-                sHd[w][pos] = Dc;
-                sSel[w][pos] = c;
-                if (n < P) ++n;
+                for (int p0 = 0; p0 < ns; p0 += 32) {
+                    const int p = p0 + lane;
+                    bool take = false;
+                    if (p < ns && !sSure[w][p]) {
+                        take = true;
+                        if (nb > r) {
+                            const double Dc = sDx[w][p];
+                            const int c = sIdx[w][p];
+                            int rank = 0;
+                            for (int q = 0; q < ns; ++q) {
+                                if (q == p || sSure[w][q]) continue;
+                                rank += (sDx[w][q] < Dc || (sDx[w][q] == Dc && sIdx[w][q] < c));
+                            }
+                            take = rank < r;
+                        }
+                    }
+                    const uint32_t mk = __ballot_sync(0xffffffffu, take);
+                    if (take) {
+                        const int s = nsel + __popc(mk & lanemask_lt());
+                        if (s < CW_PMAX) {
+                            sSel[w][s] = sIdx[w][p];
+                            sSelDt[w][s] = sDt[w][p];
+                        }
+                    }
+                    nsel += __popc(mk);
+                }
             }
-            for (int i = 0; i < n; ++i) sSelDt[w][i] = (float)sHd[w][i];
-            nsel = n;
-        }
-        nsel = __shfl_sync(0xffffffffu, nsel, 0);
-    }
-    __syncwarp();
-    // the selected set nearest first: ascending approximate distance, ties
-    // to the lower list index (the set itself is the exact one)
-    if (nsel != P && lane == 0) atomicOr(a.err, ERR_SELECT);
-    nsel = min(nsel, P);
-    if (lane < P) {
-        if (lane >= nsel) {
-            outr[lane] = -1;
         } else {
-            const int c = sSel[w][lane];
-            const float dc = sSelDt[w][lane];
-            int pos = 0;
-            for (int q = 0; q < nsel; ++q) {
-                const int c2 = sSel[w][q];
-                const float d2 = sSelDt[w][q];
-                pos += d2 < dc || (d2 == dc && c2 < c);
+            // pathological (more than CW_SCAP candidates, e.g. many identical
+            // centroids): exact FP64 insertion into a sorted array of P, lists
+            // in index order (keeps the lowest index among ties)
+            if (lane == 0) {
+                int n = 0;
+                for (int c = 0; c < L; ++c) {
+                    const float Dt = dt_of(c);
+                    const float E = bound_of(Dt, a.cn[c], a.cnrm_up[c], xn, g1);
+                    if (lower_of(Dt, E) > T) continue;
+                    const double Dc = exact_dist(xr, a.cent + (size_t)c * a.d, a.d);
+                    if (n == P && !(Dc < sHd[w][n - 1])) continue;
+                    int pos = n < P ? n : P - 1;
+                    while (pos > 0 && Dc < sHd[w][pos - 1]) {
+                        sHd[w][pos] = sHd[w][pos - 1];
+                        sSel[w][pos] = sSel[w][pos - 1];
+                        --pos;
+                    }
+                    sHd[w][pos] = Dc;
+                    sSel[w][pos] = c;
+                    if (n < P) ++n;
+                }
+                for (int i = 0; i < n; ++i) sSelDt[w][i] = (float)sHd[w][i];
+                nsel = n;
             }
-            outr[pos] = c;
+            nsel = __shfl_sync(0xffffffffu, nsel, 0);
         }
+        __syncwarp();
+        // the selected set nearest first: ascending approximate distance, ties
+        // to the lower list index (the set itself is the exact one)
+        if (nsel != P && lane == 0) atomicOr(a.err, ERR_SELECT);
+        nsel = min(nsel, P);
+        if (lane < P) {
+            if (lane >= nsel) {
+                outr[lane] = -1;
+            } else {
+                const int c = sSel[w][lane];
+                const float dc = sSelDt[w][lane];
+                int pos = 0;
+                for (int q = 0; q < nsel; ++q) {
+                    const int c2 = sSel[w][q];
+                    const float d2 = sSelDt[w][q];
+                    pos += d2 < dc || (d2 == dc && c2 < c);
+                }
+                outr[pos] = c;
+            }
+        }
+        __syncwarp();  // the warp's shared rows are reused by its next row
     }
 }
 
@@ -953,10 +1369,52 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
     // addition, over d (single) or 3 d (split) terms
     const double ub = 1.0 / 256.0;
     const double gacc = (split == 3 ? 3.0 * d : (double)d) * std::ldexp(1.0, -22);
+    // |acc - x.c| / (||x|| ||c||): single: 2 ub + ub^2 (both roundings)
+    // plus the accumulation; split: the dropped products xl cl, and the
+    // roundings of xl and cl (each ub^2 relative), 3.1 ub^2 in all, plus
+    // the accumulation
+    const double rel = split == 3 ? 3.1 * ub * ub + gacc * (1 + 2 * ub)
+                                  : (2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub);
+    const float gamma2_first = (float)(2.0 * rel * (1.0 + 1e-6));
+    // assignment with the single BF16 product: the fused first stage keeps
+    // only each row's candidate lists (needs CF_STRIDE ints per row of the
+    // distance buffer, and d <= 128 for its shared memory)
+    const bool fused = split == 1 && ix->tmap_cent_ok &&
+                       (size_t)32 + (size_t)rows_per_chunk * (CF_STRIDE + 1) <=
+                           (size_t)rows_per_chunk * L;
+    int nsm = 0;
+    if (fused) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        nsm = std::max(nsm, 1);
+    }
     for (int64_t r0 = 0; r0 < m; r0 += rows_per_chunk) {
         int mc = (int)std::min<int64_t>(rows_per_chunk, m - r0);
         const int tok = prof_begin(ix, PROF_COARSE, 2, st);
-        if (two) {
+        if (fused) {
+            const size_t smem = coarse_fused_smem(d);
+            // the distance buffer holds the undecided-row count, the
+            // undecided rows and the candidate lists
+            int32_t *nh = reinterpret_cast<int32_t *>(Dbuf);
+            cudaMemsetAsync(nh, 0, sizeof(int32_t), st);
+            const int nt = (mc + CT_M - 1) / CT_M;
+            const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(ix->tmap_cent);
+            // shared memory opted in once per instantiation (index KC - 1)
+            static size_t attr[2] = {0, 0};
+            auto go = [&](auto kern, int kc) {
+                if (smem > attr[kc - 1]) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                    attr[kc - 1] = smem;
+                }
+                kern<<<std::min(nt, nsm), CF_NT, smem, st>>>(
+                    tm, x + r0 * d, mc, d, ix->cnorm, ix->cnrm_up, L, gamma2_first, out + r0,
+                    nh + 32 + mc, nh + 32, nh, ix->err);
+            };
+            if (d <= 64) go(k_coarse_fused1<1>, 1);
+            else go(k_coarse_fused1<2>, 2);
+        } else if (two) {
             const size_t smem = coarse_tc_smem(d, split);
             dim3 g((mc + CT_M - 1) / CT_M, (L + CT_N - 1) / CT_N);
             if (split == 1) {
@@ -983,7 +1441,11 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
             k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
         }
         SelArgs a;
-        a.D = Dbuf;
+        a.D = fused ? nullptr : Dbuf;
+        a.S = fused ? reinterpret_cast<const int32_t *>(Dbuf) + 32 + mc : nullptr;
+        a.s_stride = CF_STRIDE;
+        a.hard = reinterpret_cast<const int32_t *>(Dbuf) + 32;
+        a.nhard = reinterpret_cast<const int *>(Dbuf);
         a.m = mc;
         a.L = L;
         a.P = P;
@@ -993,20 +1455,17 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         a.cn = ix->cnorm;
         a.cnrm_up = ix->cnrm_up;
         a.gamma2 = (float)(2.0 * gd * (1.0 + 1e-6));
-        // |acc - x.c| / (||x|| ||c||): single: 2 ub + ub^2 (both roundings)
-        // plus the accumulation; split: the dropped products xl cl, and the
-        // roundings of xl and cl (each ub^2 relative), 3.1 ub^2 in all, plus
-        // the accumulation
-        const double rel = split == 3 ? 3.1 * ub * ub + gacc * (1 + 2 * ub)
-                                      : (2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub);
-        a.gamma2_first = (float)(2.0 * rel * (1.0 + 1e-6));
+        a.gamma2_first = gamma2_first;
         a.two_level = two;
         a.out = out + r0 * P;
         a.err = ix->err;
         if (warp_rows) {
             const unsigned gw = (unsigned)((mc + CW_ROWS - 1) / CW_ROWS);
-            if (P == 1) k_coarse_select_w<1><<<gw, CW_ROWS * 32, 0, st>>>(a);
-            else k_coarse_select_w<CW_PMAX><<<gw, CW_ROWS * 32, 0, st>>>(a);
+            if (fused)  // loops over the undecided rows, usually none
+                k_coarse_select_w<1, true>
+                    <<<std::min<unsigned>(gw, 2u * (unsigned)nsm), CW_ROWS * 32, 0, st>>>(a);
+            else if (P == 1) k_coarse_select_w<1, false><<<gw, CW_ROWS * 32, 0, st>>>(a);
+            else k_coarse_select_w<CW_PMAX, false><<<gw, CW_ROWS * 32, 0, st>>>(a);
         } else {
             k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
         }

@@ -148,6 +148,11 @@ struct QtShape {
 };
 QtShape qt_shape(const sivf_index *ix, int dtype, int Kc);
 bool qt_make_maps(sivf_index *ix, PFN_cuTensorMapEncodeTiled_v12000 enc);
+// the driver's cuTensorMapEncodeTiled (null when unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn();
+// TMA descriptor of the BF16 centroids for the fused coarse first stage;
+// false when the shape does not take that stage
+bool coarse_make_map(sivf_index *ix);
 // one launch over the grouped items; seed_slabs > 0 scans only the first
 // seed_slabs slabs of each item and publishes the bounds, writing no runs;
 // select_slabs is the tile's buffer-length knob (qt_mecap)

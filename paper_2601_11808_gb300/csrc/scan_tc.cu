@@ -833,9 +833,11 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             const float inv_l = __int_as_float(h[9]);
             // a row holds [0, nb) (at most RK) and appends at RK; its pending
             // candidates are folded once a tile leaves more than FT of them:
-            // FT plus one tile always fits.  A fold keeps K' .. Kw.
+            // FT plus one tile always fits.  A fold keeps K' .. Kw.  Past
+            // 224 pending rows a fold costs more than the extra folds that a
+            // lower trigger brings (measured: 224 beats 256, 192 and 160).
             const int RK = a.RK, Kw = K + ((RK - K) >> 1);
-            const int FT = min(ME - RK, 256) - TC_M;
+            const int FT = min(ME - RK, 224) - TC_M;
             const int32_t *qp = c_qpair(j);
             const float *cqn = c_qn(j), *cqsc = c_qsc(j), *ckd = c_kd0(j);
             const int32_t *sl = c_sl(j);
@@ -1438,7 +1440,7 @@ void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st)
 }
 
 // --------------------------------------------------------------- host side
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -1454,7 +1456,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 bool tc_make_maps(sivf_index *ix)
 {
-    auto enc = encode_fn();
+    auto enc = tmap_encode_fn();
     if (!enc) return false;
     const cuuint64_t rows = (cuuint64_t)ix->n_slabs * ix->C;
     if (ix->xb16) {

@@ -134,6 +134,9 @@ struct sivf_index {
     // the same copies with boxes of min(C, 64) rows (query-row scan)
     alignas(64) unsigned char tmap_qt_bf16[128];
     alignas(64) unsigned char tmap_qt_fp8[128];
+    // the BF16 centroids in boxes of 64 x 256 (fused coarse first stage)
+    alignas(64) unsigned char tmap_cent[128];
+    bool tmap_cent_ok;
     bool tmaps_ready;
 
     // address translation table (Sec. 3.4)

@@ -129,6 +129,19 @@ __device__ __forceinline__ void tmem_ld_wait()
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// The same wait, with the 16 loaded values as in/out operands: arithmetic
+// on them cannot be scheduled above it, so other work may sit between the
+// load and the wait.
+__device__ __forceinline__ void tmem_ld_wait(float (&v)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                   "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]),
+                   "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
+                 :
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ TMA
 // 2-D tiled load of the box at (c0, c1) (elements, innermost first) of the
 // tensor described by `tmap` into shared memory, completing on `bar`.

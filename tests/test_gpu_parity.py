@@ -52,6 +52,27 @@ def _assign_cases():
         rng.standard_normal((2000, 16)).astype(np.float32)
     yield "int_ties_d32", rng.integers(-2, 3, (300, 32)).astype(np.float32), \
         rng.integers(-2, 3, (3000, 32)).astype(np.float32)
+    # the fused first stage for assignment (64 <= d <= 128): more row tiles
+    # of 128 than SMs (each CTA loops over tiles), 300 lists in two chunks
+    # of 256 (the second ragged)
+    c64 = rng.standard_normal((300, 64)).astype(np.float32)
+    yield "many_rows_d64", c64, \
+        (c64[rng.integers(0, 300, 25000)]
+         + 0.3 * rng.standard_normal((25000, 64))).astype(np.float32)
+    # d = 96: the second 64-column TMA box is half outside the rows
+    c96 = rng.standard_normal((700, 96)).astype(np.float32)
+    yield "d96", c96, (c96[rng.integers(0, 700, 3000)]
+                       + 0.5 * rng.standard_normal((3000, 96))).astype(np.float32)
+    # 200 copies of one centroid among 100 others: the fused stage's
+    # per-thread lists overflow, the row is redone from all lists (and its
+    # set of more than 128 candidates takes the serial FP64 path)
+    one = rng.standard_normal((1, 64)).astype(np.float32)
+    oth = rng.standard_normal((100, 64)).astype(np.float32)
+    yield "identical_200_d64", np.concatenate([oth[:50], np.repeat(one, 200, 0), oth[50:]]), \
+        (one + 0.05 * rng.standard_normal((500, 64))).astype(np.float32)
+    # integer grid: exact ties between lists, several candidates per row
+    yield "int_ties_d64", rng.integers(-1, 2, (400, 64)).astype(np.float32), \
+        rng.integers(-1, 2, (3000, 64)).astype(np.float32)
 
 
 @pytest.mark.parametrize("case", [c[0] for c in _assign_cases()])
