@@ -1170,11 +1170,16 @@ void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, in
 // ---------------------------------------------------------------- re-rank
 // One warp per query: exact FP32 direct-form distances of the K' merged
 // candidates (global slots) from the FP32 payload, then the best k by
-// (distance, id).  Candidate c belongs to lane c % 32 (register c / 32),
-// which reads its whole payload row with 16-byte loads, so the warp has 32
-// rows in flight; the query row is staged in shared memory.
+// (distance, id).  Eight lanes share a candidate row: lane t of a group
+// holds query chunks t, t + 8, ... (16 bytes each) in registers and reads
+// the same chunks of the row, so one load instruction of the warp covers
+// four whole 128-byte lines; RK_UNR rounds of four candidates are loaded
+// before any is reduced (the group's partial sums meet by shuffles).  The
+// candidates' slots are staged in shared memory first; their ids are read
+// into the owning lanes' registers then and used only by the sort.
 constexpr int RK_NT = 128;
-template <int E>
+constexpr int RK_UNR = 4;  // measured best of 2, 4, 5, 8 and 10
+template <int E, int NQ>  // E: candidates per lane in the sort; NQ: chunks per lane (d <= 32 NQ)
 __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, int64_t nq, int d,
                                                 int Kc, const float *__restrict__ cand_d,
                                                 const int64_t *__restrict__ cand_s,
@@ -1182,45 +1187,71 @@ __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, i
                                                 const int64_t *__restrict__ ids, int k,
                                                 float *__restrict__ dist, int64_t *__restrict__ labels)
 {
-    __shared__ __align__(16) float sq[RK_NT / 32][kMaxD];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ int64_t sgs[RK_NT / 32][32 * E];
+    __shared__ float sd[RK_NT / 32][32 * E];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 3, t = lane & 7;
     const int64_t qi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (qi >= nq) return;  // whole warps
-    const float *qr = q + (size_t)qi * d;
-    for (int j = lane; j < d; j += 32) sq[w][j] = qr[j];
-    __syncwarp();
-    const float4 *q4 = reinterpret_cast<const float4 *>(sq[w]);
-    float v[E];
+    const int n4 = d >> 2;
+    // candidate slots (-1: none); ids into registers, read by the sort
     int64_t id[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int c = lane + 32 * e;
-        v[e] = INFINITY;
-        id[e] = -1;
-        if (c >= Kc) continue;
-        const int64_t gs = cand_s[qi * Kc + c];
-        if (gs < 0 || !(cand_d[qi * Kc + c] < INFINITY)) continue;
-        const float4 *x4 = reinterpret_cast<const float4 *>(x32 + (size_t)gs * d);
-        float acc = 0.f;
-        for (int j4 = 0; j4 < d / 4; j4 += 4) {  // d % 16 == 0
-            float4 xv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = __ldg(x4 + j4 + u);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float4 qv = q4[j4 + u];
-                float t = qv.x - xv[u].x;
-                acc = fmaf(t, t, acc);
-                t = qv.y - xv[u].y;
-                acc = fmaf(t, t, acc);
-                t = qv.z - xv[u].z;
-                acc = fmaf(t, t, acc);
-                t = qv.w - xv[u].w;
-                acc = fmaf(t, t, acc);
-            }
+        int64_t gs = -1;
+        if (c < Kc) {
+            gs = cand_s[qi * Kc + c];
+            if (!(cand_d[qi * Kc + c] < INFINITY)) gs = -1;
         }
-        v[e] = acc;
-        id[e] = __ldg(ids + gs);
+        sgs[w][c] = gs;
+        id[e] = gs >= 0 ? __ldg(ids + gs) : -1;
+    }
+    const float4 *q4 = reinterpret_cast<const float4 *>(q + (size_t)qi * d);
+    float4 qv[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+        qv[u] = t + 8 * u < n4 ? __ldg(q4 + t + 8 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    const float4 *x4 = reinterpret_cast<const float4 *>(x32);
+    for (int c0 = 0; c0 < Kc; c0 += 4 * RK_UNR) {
+        float4 xv[RK_UNR][NQ];
+        int64_t gs[RK_UNR];
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            const int c = c0 + 4 * r + g;
+            gs[r] = c < Kc ? sgs[w][c] : -1;
+#pragma unroll
+            for (int u = 0; u < NQ; ++u)
+                xv[r][u] = gs[r] >= 0 && t + 8 * u < n4 ? __ldg(x4 + gs[r] * n4 + t + 8 * u)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                float dd = qv[u].x - xv[r][u].x;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].y - xv[r][u].y;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].z - xv[r][u].z;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].w - xv[r][u].w;
+                acc = fmaf(dd, dd, acc);
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            const int c = c0 + 4 * r + g;
+            if (t == 0 && c < Kc) sd[w][c] = gs[r] >= 0 ? acc : INFINITY;
+        }
+    }
+    __syncwarp();
+    float v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = lane + 32 * e;
+        v[e] = c < Kc && id[e] >= 0 ? sd[w][c] : INFINITY;
     }
     warp_bitonic_sort<E>(v, id, lane);
 #pragma unroll
@@ -1632,13 +1663,20 @@ void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *can
 {
     const int64_t blocks = (nq * 32 + RK_NT - 1) / RK_NT;
     const int tok = prof_begin(ix, PROF_RERANK, 1, st);
-#define SIVF_RERANK(E_)                                                                  \
-    k_rerank<E_><<<(unsigned)blocks, RK_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32, \
-                                                   ix->ids, k, dist, labels)
-    if (Kc <= 32) SIVF_RERANK(1);
-    else if (Kc <= 64) SIVF_RERANK(2);
-    else if (Kc <= 128) SIVF_RERANK(4);
-    else
+#define SIVF_RERANK(E_, NQ_)                                                            \
+    k_rerank<E_, NQ_><<<(unsigned)blocks, RK_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, \
+                                                        ix->x32, ix->ids, k, dist, labels)
+    const bool wide = ix->d > 128;  // chunks per lane: 4 (d <= 128) or 8 (d <= 256)
+    if (Kc <= 32) {
+        if (wide) SIVF_RERANK(1, 8);
+        else SIVF_RERANK(1, 4);
+    } else if (Kc <= 64) {
+        if (wide) SIVF_RERANK(2, 8);
+        else SIVF_RERANK(2, 4);
+    } else if (Kc <= 128) {
+        if (wide) SIVF_RERANK(4, 8);
+        else SIVF_RERANK(4, 4);
+    } else
         k_rerank_wide<<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
                                                       ix->ids, k, dist, labels);
 #undef SIVF_RERANK
