@@ -452,14 +452,6 @@ static size_t search_bytes(const sivf_index *ix, int64_t nq, int k, int P, Searc
            (size_t)pl.item_cap * 8 + 19 * 256;
 }
 
-static int64_t query_chunk(const sivf_index *ix, int P, int k)
-{
-    (void)ix;
-    // keep the per-chunk candidate buffers near 2 GB
-    int64_t per = (int64_t)P * k * 12 * 8;
-    return std::max<int64_t>(256, std::min<int64_t>(65536, ((int64_t)2 << 30) / per));
-}
-
 // plan of the reduced-precision scan for K' candidates (the batch's tile)
 static SearchPlan plan_tc(const sivf_index *ix, int dtype, int64_t nq, int P, int Kc)
 {
@@ -480,6 +472,25 @@ static size_t chunk_need(const sivf_index *ix, int64_t m, int P, int Kc, int dty
            (dtype == SIVF_FP8E4M3 ? (size_t)m * P * (ix->d + 8) : 0) + 23 * 256;
 }
 
+// Queries per chunk of a search of nq queries: all of them (at most 65536)
+// when their scratch fits kChunkBytes, else the most (at least 256) that
+// fit.  Each chunk streams the lists its queries probe, so fewer, larger
+// chunks read each list fewer times.
+constexpr size_t kChunkBytes = (size_t)6 << 30;
+static int64_t query_chunk(const sivf_index *ix, int64_t nq, int P, int Kc, int dtype)
+{
+    SearchPlan pl;
+    const int64_t top = std::min<int64_t>(std::max<int64_t>(nq, 1), 65536);
+    if (top <= 256 || chunk_need(ix, top, P, Kc, dtype, &pl) <= kChunkBytes) return top;
+    int64_t lo = 256, hi = top;  // need(lo) is taken to fit, need(hi) does not
+    while (hi - lo > 64) {
+        const int64_t mid = (lo + hi) / 2;
+        if (chunk_need(ix, mid, P, Kc, dtype, &pl) <= kChunkBytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // reduced-precision candidates: the re-rank depth K' = 4k
 static int rerank_depth(int k) { return 4 * k; }
 
@@ -489,7 +500,7 @@ static size_t search_need(const sivf_index *ix, int64_t nq, int k, int P, int dt
 {
     if (nq <= 0) return 0;
     const int Kc = dtype == SIVF_FP32 ? k : rerank_depth(k);
-    const int64_t qc = query_chunk(ix, P, std::max(k, Kc));
+    const int64_t qc = query_chunk(ix, nq, P, Kc, dtype);
     SearchPlan pl;
     size_t need = chunk_need(ix, std::min(qc, nq), P, Kc, dtype, &pl);
     if (nq > qc && nq % qc) need = std::max(need, chunk_need(ix, nq % qc, P, Kc, dtype, &pl));
@@ -729,7 +740,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
     cudaStream_t s = (cudaStream_t)stream;
     const int P = nprobe, L = ix->nlist;
     if (!tc && !scan_fits(ix, k)) return fail(ix, SIVF_E_ARG, "k too large for this slab shape");
-    const int64_t qc = query_chunk(ix, P, std::max(k, Kc));
+    const int64_t qc = query_chunk(ix, nq, P, Kc, dtype);
     for (int64_t q0 = 0; q0 < nq; q0 += qc) {
         const int64_t m = std::min(qc, nq - q0);
         SearchPlan pl;

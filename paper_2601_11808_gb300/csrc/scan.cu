@@ -135,27 +135,28 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
     }
 }
 
-// One thread per query, whole warps together: each pair goes to its list's
+// One warp per query, SC_Q queries per block: each pair goes to its list's
 // group (qlist), and the query's pairs of this phase reserve consecutive
-// output runs (one per slab chunk of the pair's list; one atomic per warp).
+// output runs in probe order (one per slab chunk of the pair's list; one
+// atomic per block).  The warp's lanes take the probes p0 + lane + 32 j.
 // prun = the pair's first run (-1: not scanned); qrun[phase][q] = (first
 // run, runs) of the query.  A reservation past run_cap (the plan's bound
 // makes this impossible) sets ERR_PLAN and leaves the query's runs out.
-__global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, int P, int p0,
-                               int p1, const int32_t *__restrict__ prank,
-                               const int32_t *__restrict__ loff, const int32_t *__restrict__ nch,
-                               int32_t *__restrict__ qlist, int32_t *__restrict__ prun,
-                               int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap,
-                               uint32_t *err)
+constexpr int SC_Q = 8;
+__global__ __launch_bounds__(SC_Q * 32) void k_srch_scatter(
+    const int32_t *__restrict__ probes, int64_t nq, int P, int p0, int p1,
+    const int32_t *__restrict__ prank, const int32_t *__restrict__ loff,
+    const int32_t *__restrict__ nch, int32_t *__restrict__ qlist, int32_t *__restrict__ prun,
+    int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap, uint32_t *err)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); q0 < nq;
-         q0 += stride) {
-        const int64_t q = q0 + lane;
+    __shared__ int s_cnt[SC_Q];
+    __shared__ int s_base;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t qb = (int64_t)blockIdx.x * SC_Q; qb < nq; qb += (int64_t)gridDim.x * SC_Q) {
+        const int64_t q = qb + w;
         int cnt = 0;
         if (q < nq)
-            for (int p = p0; p < p1; ++p) {
+            for (int p = p0 + lane; p < p1; p += 32) {
                 const int64_t e = q * P + p;
                 const int r = prank[e];
                 int c = 0;
@@ -167,26 +168,36 @@ __global__ void k_srch_scatter(const int32_t *__restrict__ probes, int64_t nq, i
                 prun[e] = c;
                 cnt += c;
             }
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) s_cnt[w] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < SC_Q; ++k) tot += s_cnt[k];
+            s_base = atomicAdd(&ctl->nruns, tot);
         }
-        int base = 0;
-        if (lane == 31) base = atomicAdd(&ctl->nruns, incl);
-        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+        __syncthreads();
+        int base = s_base;
+        for (int k = 0; k < w; ++k) base += s_cnt[k];
         if (q < nq) {
             const bool fits = base >= 0 && (int64_t)base + cnt <= run_cap;
-            if (!fits) atomicOr(err, ERR_PLAN);
+            if (!fits && lane == 0) atomicOr(err, ERR_PLAN);
             int run = base;
-            for (int p = p0; p < p1; ++p) {
+            for (int pb = p0; pb < p1; pb += 32) {  // warp-uniform
+                const int p = pb + lane;
                 const int64_t e = q * P + p;
-                const int c = prun[e];
-                prun[e] = (c > 0 && fits) ? run : -1;
-                run += c;
+                const int c = p < p1 ? prun[e] : 0;  // this lane's own count from above
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (p < p1) prun[e] = (c > 0 && fits) ? run + incl - c : -1;
+                run += __shfl_sync(0xffffffffu, incl, 31);
             }
-            qrun[(p0 > 0 ? nq : 0) + q] = fits ? make_int2(base, cnt) : make_int2(0, 0);
+            if (lane == 0) qrun[(p0 > 0 ? nq : 0) + q] = fits ? make_int2(base, cnt) : make_int2(0, 0);
         }
+        __syncthreads();  // s_cnt and s_base are reused by the next queries
     }
 }
 
@@ -877,15 +888,16 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
     cudaMemsetAsync(s.lcnt, 0, sizeof(int32_t) * L, st);
     const int64_t n = nq * (p1 - p0);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
-    const int gq = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, 152 * 16));
     const int tg = prof_begin(ix, PROF_GROUP, 3, st);
     k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
     k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
                                     pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff,
                                     s.ibase, s.nch, s.items, ix->ctl, stats ? ix->stat : nullptr,
                                     ix->err);
-    k_srch_scatter<<<gq, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch, s.qlist,
-                                       s.prun, s.qrun, ix->ctl, pl.run_cap, ix->err);
+    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nq + SC_Q - 1) / SC_Q, 152 * 16));
+    k_srch_scatter<<<gs, SC_Q * 32, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
+                                             s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap,
+                                             ix->err);
     prof_end(ix, tg, st);
 }
 
