@@ -135,10 +135,61 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
     }
 }
 
-// One warp per query, SC_Q queries per block: each pair goes to its list's
+// One thread per query, whole warps together: each pair goes to its list's
 // group (qlist), and the query's pairs of this phase reserve consecutive
-// output runs in probe order (one per slab chunk of the pair's list; one
-// atomic per block).  The warp's lanes take the probes p0 + lane + 32 j.
+// output runs (one per slab chunk of the pair's list; one atomic per warp).
+__global__ void k_srch_scatter_t(const int32_t *__restrict__ probes, int64_t nq, int P, int p0,
+                                 int p1, const int32_t *__restrict__ prank,
+                                 const int32_t *__restrict__ loff, const int32_t *__restrict__ nch,
+                                 int32_t *__restrict__ qlist, int32_t *__restrict__ prun,
+                                 int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap,
+                                 uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); q0 < nq;
+         q0 += stride) {
+        const int64_t q = q0 + lane;
+        int cnt = 0;
+        if (q < nq)
+            for (int p = p0; p < p1; ++p) {
+                const int64_t e = q * P + p;
+                const int r = prank[e];
+                int c = 0;
+                if (r >= 0) {
+                    const int l = probes[e];
+                    qlist[loff[l] + r] = (int32_t)e;
+                    c = nch[l];
+                }
+                prun[e] = c;
+                cnt += c;
+            }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&ctl->nruns, incl);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+        if (q < nq) {
+            const bool fits = base >= 0 && (int64_t)base + cnt <= run_cap;
+            if (!fits) atomicOr(err, ERR_PLAN);
+            int run = base;
+            for (int p = p0; p < p1; ++p) {
+                const int64_t e = q * P + p;
+                const int c = prun[e];
+                prun[e] = (c > 0 && fits) ? run : -1;
+                run += c;
+            }
+            qrun[(p0 > 0 ? nq : 0) + q] = fits ? make_int2(base, cnt) : make_int2(0, 0);
+        }
+    }
+}
+
+// The same with one warp per query, SC_Q queries per block, for phases of
+// many probes: the warp's lanes take the probes p0 + lane + 32 j, runs are
+// assigned in probe order (one atomic per block).
 // prun = the pair's first run (-1: not scanned); qrun[phase][q] = (first
 // run, runs) of the query.  A reservation past run_cap (the plan's bound
 // makes this impossible) sets ERR_PLAN and leaves the query's runs out.
@@ -894,10 +945,17 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
                                     pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff,
                                     s.ibase, s.nch, s.items, ix->ctl, stats ? ix->stat : nullptr,
                                     ix->err);
-    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nq + SC_Q - 1) / SC_Q, 152 * 16));
-    k_srch_scatter<<<gs, SC_Q * 32, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
+    if (p1 - p0 >= 8) {
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nq + SC_Q - 1) / SC_Q, 152 * 16));
+        k_srch_scatter<<<gs, SC_Q * 32, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
+                                                 s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap,
+                                                 ix->err);
+    } else {
+        const int gq = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, 152 * 16));
+        k_srch_scatter_t<<<gq, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
                                              s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap,
                                              ix->err);
+    }
     prof_end(ix, tg, st);
 }
 

@@ -22,11 +22,12 @@
 //           scales and bounds, its slab ids and validity bitmaps, and
 //           prefetches the first slabs into L2 (two contexts in flight);
 //   warp 3  builds the rounded, swizzled query tile (two B buffers);
-//   warp 0  (one lane) TMA loads of the A tiles and bulk copies of the
-//           rows' ||x||^2, plus L2 prefetches further ahead in the list;
+//   warp 0  (one lane) TMA loads of the A tiles, plus L2 prefetches of
+//           the payload rows and their ||x||^2 further ahead in the list;
 //   warp 1  (one lane) issues the MMAs; warp 2 also owns the TMEM;
 //   warps 4.. the epilogue: TN / 16 warps per TMEM lane quarter, 16
-//           query columns each.
+//           query columns each; each thread reads its row's ||x||^2 from
+//           global memory (L2) before it waits for the accumulator.
 // A tile's passing rows are appended to their query's buffer at positions
 // reserved by one shared atomic per (warp, query); a buffer is reduced to
 // its best K' (radix select, left unsorted) only after a tile that leaves
@@ -47,7 +48,6 @@ constexpr int TC_M = 128;       // rows per A tile (MMA M)
 constexpr int TC_NCOL = 16;     // query columns per epilogue warp
 constexpr int TC_META = 256;    // slabs of one sub-item (ids and bitmaps staged together)
 constexpr int TC_CTX = 2;       // item contexts in flight
-constexpr int TC_XR = 8;        // entries of the ||x||^2 ring (one per A tile)
 constexpr int TC_MAXST = 4;     // most A-tile stages
 constexpr int TC_HIST = 256;    // radix-select bins per epilogue warp
 constexpr int TC_PF_BYTES = 192 * 1024;  // L2 prefetch distance per CTA
@@ -119,8 +119,8 @@ __host__ __device__ inline TcSmem tc_smem(int KC, int M, int nst)
     TcSmem s;
     s.a = 0;                                             // nst x KC x 16 KB
     s.b = s.a + (size_t)nst * KC * TC_M * 128;           // 2 x KC x TN rows x 128 B
-    s.xn = s.b + (size_t)2 * KC * TN * 128;              // TC_XR x 128 floats
-    s.bd = s.xn + (size_t)TC_XR * TC_M * 4;
+    s.xn = s.b + (size_t)2 * KC * TN * 128;              // (no norm ring)
+    s.bd = s.xn;
     s.bs = s.bd + (size_t)TN * M * 4;
     s.ctx = s.bs + (size_t)TN * M * 4;
     s.hist = s.ctx + (size_t)TC_CTX * tc_ctx_bytes(TN);
@@ -531,14 +531,13 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
     const TcSmem L = tc_smem<TN>(KC, M, NST);
     unsigned char *A = smem + L.a;
     unsigned char *B = smem + L.b;
-    float *XN = reinterpret_cast<float *>(smem + L.xn);
     float *BD = reinterpret_cast<float *>(smem + L.bd);
     int32_t *BS = reinterpret_cast<int32_t *>(smem + L.bs);
     unsigned char *CTX = smem + L.ctx;
     uint32_t *Hist = reinterpret_cast<uint32_t *>(smem + L.hist);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *full = bars, *empty = bars + 4, *tfull = bars + 8, *tempty = bars + 10,
-             *xfull = bars + 12, *xempty = bars + 20, *cfull = bars + 28, *cempty = bars + 30,
+             *cfull = bars + 28, *cempty = bars + 30,
              *bfull = bars + 32, *bfree = bars + 34;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(bars + 40);
     volatile int *s_abort = reinterpret_cast<volatile int *>(bars + 41);
@@ -572,10 +571,6 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             mbar_init(&tempty[i], EW);
             mbar_init(&bfull[i], 32);
             mbar_init(&bfree[i], 1);
-        }
-        for (int i = 0; i < TC_XR; ++i) {
-            mbar_init(&xfull[i], 1);
-            mbar_init(&xempty[i], EW);
         }
         for (int i = 0; i < TC_CTX; ++i) {
             mbar_init(&cfull[i], 32);
@@ -728,12 +723,8 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                 const int32_t *sl = c_sl(j);
                 bool ab = false;
                 for (int b = 0; b < nblk; ++b, ++g) {
-                    const uint32_t st = g % NST, u = g / NST, xs = g % TC_XR, xu = g / TC_XR;
+                    const uint32_t st = g % NST, u = g / NST;
                     if (u >= 1 && !mbar_wait_ab(&empty[st], (u - 1) & 1, a.err, s_abort, a.wait_ns)) {
-                        ab = true;
-                        break;
-                    }
-                    if (xu >= 1 && !mbar_wait_ab(&xempty[xs], (xu - 1) & 1, a.err, s_abort, a.wait_ns)) {
                         ab = true;
                         break;
                     }
@@ -741,7 +732,6 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                     int okc = 0;
                     for (int jj = 0; jj < nsl; ++jj) okc += sl[b * SPB + jj] >= 0;
                     mbar_arrive_expect_tx(&full[st], (uint32_t)(okc * KC * C * 128));
-                    mbar_arrive_expect_tx(&xfull[xs], (uint32_t)(okc * C * 4));
                     for (int jj = 0; jj < nsl; ++jj) {
                         const int s = sl[b * SPB + jj];
                         if (s < 0) continue;
@@ -749,8 +739,6 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                             tma_load_2d(A + (size_t)st * KC * TC_M * 128 + (size_t)kc * TC_M * 128 +
                                             (size_t)jj * C * 128,
                                         &tmap, kc * EPC, s * C, &full[st]);
-                        bulk_g2s(XN + (size_t)xs * TC_M + jj * C, a.xnorm + (size_t)s * C,
-                                 (uint32_t)(C * 4), &xfull[xs]);
                     }
                     const int bp = b + a.pf_tiles;  // keep the L2 prefetch ahead
                     if (bp < nblk)
@@ -766,8 +754,6 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             // the copies of the last tiles issued have landed before exit
             for (uint32_t t = g > (uint32_t)NST ? g - NST : 0; t < g; ++t)
                 mbar_wait_bounded(&full[t % NST], (t / NST) & 1, a.err);
-            for (uint32_t t = g > (uint32_t)TC_XR ? g - TC_XR : 0; t < g; ++t)
-                mbar_wait_bounded(&xfull[t % TC_XR], (t / TC_XR) & 1, a.err);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -854,19 +840,28 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             }
             named_bar_sync(1, EPI);
             bool run = true;
+            // this thread's row's slab in A tile bb of the item, and that
+            // row's ||x||^2 read one tile ahead (its L2 latency hides behind
+            // the tile before)
+            auto row_slab = [&](int bb) {
+                return v / C < min(SPB, sns - bb * SPB) ? sl[bb * SPB + v / C] : -1;
+            };
+            const int s_first = nblk > 0 ? row_slab(0) : -1;
+            float xn_next = s_first >= 0 ? __ldg(a.xnorm + (size_t)s_first * C + v % C) : 0.f;
             for (int b = 0; b < nblk; ++b, ++g) {
-                const uint32_t buf = g & 1, ub = g >> 1, xs = g % TC_XR, xu = g / TC_XR;
+                const uint32_t buf = g & 1, ub = g >> 1;
                 // row of this thread in the tile
                 const int nsl = min(SPB, sns - b * SPB);
                 const int jr = v / C, slot = v % C, mi = b * SPB + jr;
                 const int s = jr < nsl ? sl[mi] : -1;
                 const bool live = s >= 0 && ((bt[mi * 4 + (slot >> 5)] >> (slot & 31)) & 1u);
                 const int32_t gslot = s * C + slot;
-                bool wok = mbar_wait_ab(&xfull[xs], xu & 1, a.err, s_abort, a.wait_ns);
-                const float xn = XN[xs * TC_M + v];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&xempty[xs]);
-                wok = wok && mbar_wait_ab(&tfull[buf], ub & 1, a.err, s_abort, a.wait_ns);
+                const float xn = xn_next;
+                if (b + 1 < nblk) {
+                    const int s2 = row_slab(b + 1);
+                    xn_next = s2 >= 0 ? __ldg(a.xnorm + (size_t)s2 * C + slot) : 0.f;
+                }
+                bool wok = mbar_wait_ab(&tfull[buf], ub & 1, a.err, s_abort, a.wait_ns);
                 wok = __all_sync(0xffffffffu, wok);  // tcgen05.ld is warp-aligned
                 tc_fence_after();
                 const bool cols = c0 < m;           // warp-uniform
