@@ -51,7 +51,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum per
 # launch
 TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
-TC_PROFILED = {"fp8": ("82474eda9311eabe", 149_619_840)}
+TC_PROFILED = {"fp8": ("46ea39274c3e8deb", 149_659_520)}
 
 
 def parse():
@@ -76,6 +76,10 @@ def parse():
     p.add_argument("--serving-window", type=int, default=0,
                    help="live vectors of the serving window (0 = 100,000,000)")
     p.add_argument("--serving-seconds", type=float, default=2.0)
+    p.add_argument("--deep-vectors", type=int, default=None,
+                   help="precision component on a reduced copy of this many vectors (profiling)")
+    p.add_argument("--deep-queries", type=int, default=None,
+                   help="precision component with this many queries (profiling)")
     p.add_argument("--no-deep", action="store_true",
                    help="skip the deep-precision (k=100) workload")
     p.add_argument("--no-train", action="store_true",
@@ -694,7 +698,7 @@ def oracle_train_sample(n=10_000, iters=2):
             "row_iters_per_s": round(n * iters / s, 1)}
 
 
-def run_deep(torch, sivf, dev, steps=3, n_truth=100):
+def run_deep(torch, sivf, dev, steps=3, n_truth=100, n_vec=None, n_q=None):
     """The precision workload: 10,000,000 unit-norm vectors d=96 from a
     4,096-component mixture, nlist=4096, slab 32, with FP32, BF16 and FP8
     E4M3 (per-list scale) payloads; 10,000 queries, k=100, nprobe=64; the
@@ -703,7 +707,8 @@ def run_deep(torch, sivf, dev, steps=3, n_truth=100):
     sample of queries, and the largest relative error of the returned
     distances against their FP64 values."""
     w = W.CONFIGS["deep_precision"]
-    n, k, P = w.window, w.k, w.nprobes[0]
+    n, k, P = n_vec or w.window, w.k, w.nprobes[0]
+    nq = n_q or w.n_queries
     ctr = W.centers(w)
     cent = W.index_centroids(w, ctr)
     S = int(1.05 * (n // w.slab_size)) + 2 * w.nlist
@@ -718,7 +723,7 @@ def run_deep(torch, sivf, dev, steps=3, n_truth=100):
               torch.from_numpy(X[b:b + ch]).to(dev))
     g.sync()
     t_fill = time.time() - t_fill
-    Q = W.vectors_threaded(w, 0, w.n_queries, ctr, stream=2)
+    Q = W.vectors_threaded(w, 0, nq, ctr, stream=2)
     Qd = torch.from_numpy(Q).to(dev)
     # exact FP64 top-k of a query sample (brute force, ties to the lower id)
     t_gt = time.time()
@@ -739,8 +744,8 @@ def run_deep(torch, sivf, dev, steps=3, n_truth=100):
     out = {}
     stream = torch.cuda.current_stream()
     for form in ("fp32", "bf16", "fp8"):
-        dist = torch.empty((w.n_queries, k), dtype=torch.float32, device=dev)
-        lab = torch.empty((w.n_queries, k), dtype=torch.int64, device=dev)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        lab = torch.empty((nq, k), dtype=torch.int64, device=dev)
         for _ in range(2):
             g.search(Qd, k, P, form, dist=dist, labels=lab)
         torch.cuda.synchronize()
@@ -760,15 +765,15 @@ def run_deep(torch, sivf, dev, steps=3, n_truth=100):
             ok = gi[r] >= 0
             ex = ((X[gi[r][ok]].astype(np.float64) - Q[r].astype(np.float64)) ** 2).sum(1)
             err = max(err, float(np.max(np.abs(gd[r][ok] - ex) / np.maximum(ex, 1e-30))))
-        out[form] = {"qps": round(w.n_queries / (ms / 1e3), 1), "ms_per_search": round(ms, 3),
+        out[form] = {"qps": round(nq / (ms / 1e3), 1), "ms_per_search": round(ms, 3),
                      "recall_at_100": round(rec, 4), "max_rel_dist_err": err}
     g.close()
     del X
     torch.cuda.empty_cache()
     out.update({
-        "workload": "deep_precision: 10,000,000 unit-norm vectors d=96 (4,096-component "
+        "workload": f"deep_precision: {n:,} unit-norm vectors d=96 (4,096-component "
                     "mixture, sigma 0.02), nlist=4096, slab 32, FP32 + BF16 + FP8 E4M3 payloads; "
-                    "10,000 queries, k=100, nprobe=64, re-rank depth 400",
+                    f"{nq:,} queries, k=100, nprobe=64, re-rank depth 400",
         "truth": f"exact FP64 brute force over all vectors for {n_truth} sampled queries",
         "prefill_s": round(t_fill, 1), "truth_s": round(t_gt, 1)})
     return out
@@ -1216,7 +1221,8 @@ def main():
             args.mixed_form)
         torch.cuda.empty_cache()
     if not args.no_deep:
-        line["components"]["deep_precision"] = run_deep(torch, sivf, dev)
+        line["components"]["deep_precision"] = run_deep(torch, sivf, dev, n_vec=args.deep_vectors,
+                                                        n_q=args.deep_queries)
     if not args.no_train:
         line["components"]["train"] = run_train(torch, sivf, dev)
     if not args.no_zipf:
