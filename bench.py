@@ -56,6 +56,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # per-query merge: the kernel and every device helper it calls) it was
 # taken of, and the mean dram__bytes_read.sum + dram__bytes_write.sum per
 # launch
+E2E_PASSES = 3
 TC_KERNEL_END = "// ------------------------------------------------------- per-query merge"
 TC_PROFILED = {"fp8": ("46ea39274c3e8deb", 149_659_520)}
 
@@ -970,7 +971,7 @@ def main():
     K, Wm = args.steps, args.warmup
     # warm-up, then per form an instrumented eager pass, two graph warm-up
     # steps and the graph pass, then the e2e pass
-    n_steps = Wm + len(forms) * (2 * K + 2) + K + 1
+    n_steps = Wm + len(forms) * (2 * K + 2) + E2E_PASSES * K + 1
     n_calib = N_TRUTH
     cent, X, Q = make_data(w, n_steps, n_calib, rank)
     n_max = w.window + (n_steps + 2) * w.step
@@ -1264,34 +1265,42 @@ def main():
 
     if not args.no_e2e:
         host = []
-        for s in range(K):
+        for s in range(E2E_PASSES * K):
             host.append([x.cpu().pin_memory() for x in step_inputs(step_no + s)])
-        step_no += K
+        step_no += E2E_PASSES * K
         ex, bufs = execs[head]
         hd = torch.empty((w.n_queries, w.k), dtype=torch.float32).pin_memory()
         hl = torch.empty((w.n_queries, w.k), dtype=torch.int64).pin_memory()
         h2d = sum(x.numel() * x.element_size() for x in host[0])
         d2h = hd.numel() * 4 + hl.numel() * 8
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for s in range(K):
-            for dst, src in zip(bufs, host[s]):  # into the executor's input buffers
-                dst.copy_(src, non_blocking=True)
-            ex.launch(stream)
-            hd.copy_(dist_out, non_blocking=True)
-            hl.copy_(lab_out, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
+        # E2E_PASSES passes of K steps (fresh inputs each), the median pass
+        # reported: the host-to-device copies share the machine's host
+        # memory with other jobs, so a single pass can catch a transient
+        passes = []
+        for pss in range(E2E_PASSES):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s in range(pss * K, (pss + 1) * K):
+                for dst, src in zip(bufs, host[s]):  # into the executor's input buffers
+                    dst.copy_(src, non_blocking=True)
+                ex.launch(stream)
+                hd.copy_(dist_out, non_blocking=True)
+                hl.copy_(lab_out, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            passes.append(e0.elapsed_time(e1))
+        e2e_ms = float(np.median(passes))
         if world > 1:
             t = torch.tensor([e2e_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(t.item())
         line["e2e"] = {"value": round(world * K * w.n_queries / (e2e_ms / 1e3), 3),
                        "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
-                       "d2h_bytes_per_step": int(d2h)}
+                       "d2h_bytes_per_step": int(d2h),
+                       "passes_ms": [round(x, 3) for x in passes],
+                       "timing": f"median of {E2E_PASSES} passes of {K} steps"}
 
     for ex, _ in execs.values():
         ex.close()

@@ -825,8 +825,8 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
                 merge_tc(ix, m, nphase, sc, Kc, pl.RK, dist + q0 * k, labels + q0 * k, s);
                 slots_to_ids(ix, labels + q0 * k, m * k, s);
             } else {
-                merge_tc(ix, m, nphase, sc, Kc, pl.RK, cand_d, cand_s, s);
-                rerank(ix, qq, m, Kc, cand_d, cand_s, k, dist + q0 * k, labels + q0 * k, s);
+                merge_rerank(ix, qq, m, nphase, sc, Kc, pl.RK, k, cand_d, cand_s, dist + q0 * k,
+                             labels + q0 * k, s);
             }
         }
         CUDA_TRY(ix, cudaGetLastError());

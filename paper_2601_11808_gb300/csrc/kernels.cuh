@@ -136,6 +136,11 @@ void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, in
 int tc_run_len(int Kc);  // RK of the vector-row scan for K' = Kc
 void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *cand_d,
             const int64_t *cand_s, int k, float *dist, int64_t *labels, cudaStream_t st);
+// merge of the reduced-precision scan's runs and FP32 re-rank, fused into
+// one kernel for K' <= 128 (cand_d / cand_s are used only beyond that)
+void merge_rerank(sivf_index *ix, const float *q, int64_t nq, int nphase,
+                  const SearchScratch &s, int Kc, int RK, int k, float *cand_d,
+                  int64_t *cand_s, float *dist, int64_t *labels, cudaStream_t st);
 
 // ---- reduced-precision scan, queries on the tensor-memory lanes (scan_qt.cu)
 struct QtShape {

@@ -998,23 +998,15 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
 // (first run, runs)) by a radix select over the 64-bit (distance, slot)
 // keys of the valid entries, then sorted ascending, padded with (+inf, -1).
 constexpr int MT_NT = 128;
+// The selection of one query (one warp): its best K' valid entries, unsorted,
+// into sd / ss (32 E entries of the warp's shared memory); returns their
+// number, min(valid entries, K').  hist: TC_HIST words of shared memory.
 template <int E>
-__global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qrun, int64_t nq,
-                                                    int nphase, int K, int RK,
-                                                    const int32_t *__restrict__ part_n,
-                                                    const float *__restrict__ part_d,
-                                                    const int64_t *__restrict__ part_i,
-                                                    float *__restrict__ out_d,
-                                                    int64_t *__restrict__ out_s)
+__device__ int merge_select(const int2 *__restrict__ qrun, int64_t nq, int64_t q, int nphase,
+                            int K, int RK, const int32_t *__restrict__ part_n,
+                            const float *__restrict__ part_d, const int64_t *__restrict__ part_i,
+                            uint32_t *hist, float *sd, int32_t *ss, int lane)
 {
-    constexpr int NW = MT_NT / 32;
-    __shared__ uint32_t hist_s[NW][TC_HIST];
-    __shared__ float sd[NW][32 * E];
-    __shared__ int32_t ss[NW][32 * E];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t q = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
-    if (q >= nq) return;  // whole warps
-    uint32_t *hist = hist_s[warp];
     const int2 r0 = qrun[q];
     const int2 r1 = nphase > 1 ? qrun[nq + q] : make_int2(0, 0);
     const int NR = r0.y + r1.y;
@@ -1118,14 +1110,35 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qru
         if (take) {
             const int p = w + __popc(mk & lanemask_lt());
             if (p < 32 * E) {
-                sd[warp][p] = dv;
-                ss[warp][p] = sv;
+                sd[p] = dv;
+                ss[p] = sv;
             }
         }
         w += __popc(mk);
     });
     __syncwarp();
-    const int nk = min(w, K);
+    return min(w, K);
+}
+
+template <int E>
+__global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qrun, int64_t nq,
+                                                    int nphase, int K, int RK,
+                                                    const int32_t *__restrict__ part_n,
+                                                    const float *__restrict__ part_d,
+                                                    const int64_t *__restrict__ part_i,
+                                                    float *__restrict__ out_d,
+                                                    int64_t *__restrict__ out_s)
+{
+    constexpr int NW = MT_NT / 32;
+    __shared__ uint32_t hist_s[NW][TC_HIST];
+    __shared__ float sd[NW][32 * E];
+    __shared__ int32_t ss[NW][32 * E];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
+    if (q >= nq) return;  // whole warps
+    uint32_t *hist = hist_s[warp];
+    const int nk = merge_select<E>(qrun, nq, q, nphase, K, RK, part_n, part_d, part_i, hist,
+                                   sd[warp], ss[warp], lane);
     float v[E];
     int32_t sv[E];
 #pragma unroll
@@ -1247,6 +1260,94 @@ __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, i
     for (int e = 0; e < E; ++e) {
         const int c = lane + 32 * e;
         v[e] = c < Kc && id[e] >= 0 ? sd[w][c] : INFINITY;
+    }
+    warp_bitonic_sort<E>(v, id, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < k) {
+            dist[qi * k + i] = id[e] >= 0 ? v[e] : INFINITY;
+            labels[qi * k + i] = id[e];
+        }
+    }
+}
+
+// The per-query merge and the re-rank in one warp per query (K' <= 128):
+// merge_select leaves the query's best K' (distance, slot) entries in shared
+// memory, and the warp re-ranks those slots exactly as k_rerank does (eight
+// lanes per candidate row, RK_UNR rounds of four, the query in registers),
+// so the candidate lists never go through global memory and nothing sorts
+// them by approximate distance.
+template <int E, int NQ>
+__global__ __launch_bounds__(MT_NT) void k_merge_rerank(
+    const int2 *__restrict__ qrun, int64_t nq, int nphase, int K, int RK,
+    const int32_t *__restrict__ part_n, const float *__restrict__ part_d,
+    const int64_t *__restrict__ part_i, const float *__restrict__ q, int d,
+    const float *__restrict__ x32, const int64_t *__restrict__ ids, int k,
+    float *__restrict__ dist, int64_t *__restrict__ labels)
+{
+    constexpr int NW = MT_NT / 32;
+    __shared__ uint32_t hist_s[NW][TC_HIST];
+    __shared__ float sd[NW][32 * E];
+    __shared__ int32_t ss[NW][32 * E];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 3, t = lane & 7;
+    const int64_t qi = (blockIdx.x * (int64_t)MT_NT + threadIdx.x) >> 5;
+    if (qi >= nq) return;  // whole warps
+    const int nk = merge_select<E>(qrun, nq, qi, nphase, K, RK, part_n, part_d, part_i,
+                                   hist_s[warp], sd[warp], ss[warp], lane);
+    int64_t id[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = lane + 32 * e;
+        id[e] = c < nk ? __ldg(ids + ss[warp][c]) : -1;
+    }
+    const int n4 = d >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q + (size_t)qi * d);
+    float4 qv[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+        qv[u] = t + 8 * u < n4 ? __ldg(q4 + t + 8 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x32);
+    for (int c0 = 0; c0 < nk; c0 += 4 * RK_UNR) {
+        float4 xv[RK_UNR][NQ];
+        int64_t gs[RK_UNR];
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            const int c = c0 + 4 * r + g;
+            gs[r] = c < nk ? (int64_t)ss[warp][c] : -1;
+#pragma unroll
+            for (int u = 0; u < NQ; ++u)
+                xv[r][u] = gs[r] >= 0 && t + 8 * u < n4 ? __ldg(x4 + gs[r] * n4 + t + 8 * u)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                float dd = qv[u].x - xv[r][u].x;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].y - xv[r][u].y;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].z - xv[r][u].z;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].w - xv[r][u].w;
+                acc = fmaf(dd, dd, acc);
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            const int c = c0 + 4 * r + g;
+            __syncwarp();
+            if (t == 0 && c < nk) sd[warp][c] = acc;  // the approximate distance is no longer needed
+        }
+    }
+    __syncwarp();
+    float v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = lane + 32 * e;
+        v[e] = c < nk ? sd[warp][c] : INFINITY;
     }
     warp_bitonic_sort<E>(v, id, lane);
 #pragma unroll
@@ -1650,6 +1751,38 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
         else if (tn == 32) launch_tc<1, 32>(ix->tmap_fp8, a, st);
         else launch_tc<1, 16>(ix->tmap_fp8, a, st);
     }
+    prof_end(ix, tok, st);
+}
+
+// merge and re-rank of a search: fused for K' <= 128 (d <= 256), else the
+// merge into cand_d / cand_s followed by the wide re-rank
+void merge_rerank(sivf_index *ix, const float *q, int64_t nq, int nphase,
+                  const SearchScratch &s, int Kc, int RK, int k, float *cand_d,
+                  int64_t *cand_s, float *dist, int64_t *labels, cudaStream_t st)
+{
+    if (Kc > 128) {
+        merge_tc(ix, nq, nphase, s, Kc, RK, cand_d, cand_s, st);
+        rerank(ix, q, nq, Kc, cand_d, cand_s, k, dist, labels, st);
+        return;
+    }
+    const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
+    const int tok = prof_begin(ix, PROF_RERANK, 1, st);
+#define SIVF_MRR(E_, NQ_)                                                                 \
+    k_merge_rerank<E_, NQ_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, RK, s.part_n, \
+                                                    s.part_d, s.part_i, q, ix->d, ix->x32,  \
+                                                    ix->ids, k, dist, labels)
+    const bool wide = ix->d > 128;
+    if (Kc <= 32) {
+        if (wide) SIVF_MRR(1, 8);
+        else SIVF_MRR(1, 4);
+    } else if (Kc <= 64) {
+        if (wide) SIVF_MRR(2, 8);
+        else SIVF_MRR(2, 4);
+    } else {
+        if (wide) SIVF_MRR(4, 8);
+        else SIVF_MRR(4, 4);
+    }
+#undef SIVF_MRR
     prof_end(ix, tok, st);
 }
 
