@@ -398,6 +398,17 @@ sivf_status sivf_set_wait_limit(sivf_index *index, int64_t ns);
 sivf_status sivf_debug_set_error_bits(sivf_index *index, uint32_t bits, void *stream);
 
 /*
+ * sivf_set_chunk_bytes -- the scratch budget of one query chunk of a search:
+ * a batch whose scratch (per-pair candidate runs, coarse rows, plans) would
+ * exceed it is searched in chunks of as many queries as fit (at least 256),
+ * each chunk streaming the lists its queries probe.  bytes = 0 restores the
+ * default, 6 GiB; a smaller budget trades list re-reads for device memory.
+ * Results do not depend on the chunking.  Returns SIVF_E_ARG for bytes < 0.
+ * The paper has no counterpart (its batches fit its scratch).
+ */
+sivf_status sivf_set_chunk_bytes(sivf_index *index, int64_t bytes);
+
+/*
  * sivf_profile -- tracing.  enable != 0 starts recording a CUDA event pair
  * on the launching stream around every kernel group the index enqueues
  * (forces a device sync and clears earlier records); enable == 0 stops.

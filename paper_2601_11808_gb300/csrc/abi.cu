@@ -480,12 +480,13 @@ constexpr size_t kChunkBytes = (size_t)6 << 30;
 static int64_t query_chunk(const sivf_index *ix, int64_t nq, int P, int Kc, int dtype)
 {
     SearchPlan pl;
+    const size_t budget = ix->chunk_bytes > 0 ? (size_t)ix->chunk_bytes : kChunkBytes;
     const int64_t top = std::min<int64_t>(std::max<int64_t>(nq, 1), 65536);
-    if (top <= 256 || chunk_need(ix, top, P, Kc, dtype, &pl) <= kChunkBytes) return top;
+    if (top <= 256 || chunk_need(ix, top, P, Kc, dtype, &pl) <= budget) return top;
     int64_t lo = 256, hi = top;  // need(lo) is taken to fit, need(hi) does not
     while (hi - lo > 64) {
         const int64_t mid = (lo + hi) / 2;
-        if (chunk_need(ix, mid, P, Kc, dtype, &pl) <= kChunkBytes) lo = mid;
+        if (chunk_need(ix, mid, P, Kc, dtype, &pl) <= budget) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -954,6 +955,14 @@ sivf_status sivf_dump(sivf_index *ix, void *stream, int32_t *list_nslabs, int32_
     if (free_stack && top > 0)
         CUDA_TRY(ix, cudaMemcpy(free_stack, ix->free_list, (size_t)std::min<int64_t>(top, S) * 4,
                                 cudaMemcpyDeviceToHost));
+    return SIVF_OK;
+}
+
+sivf_status sivf_set_chunk_bytes(sivf_index *ix, int64_t bytes)
+{
+    if (!ix) return SIVF_E_ARG;
+    if (bytes < 0) return fail(ix, SIVF_E_ARG, "chunk bytes must be >= 0");
+    ix->chunk_bytes = bytes;
     return SIVF_OK;
 }
 

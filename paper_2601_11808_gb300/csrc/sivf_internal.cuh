@@ -152,6 +152,7 @@ struct sivf_index {
     sivf::Ctl *ctl;                // control block of the current call's stream
     uint32_t *err;                 // sticky error bits
     uint64_t wait_ns;              // time after which a list-scan wait gives up
+    int64_t chunk_bytes;           // query-chunk scratch budget (0: the default)
     int64_t *stat;                 // [4] persistent counters: [0] live vectors,
                                    // [1] (query, vector) pairs scanned,
                                    // [2] slab bytes streamed by list scans

@@ -33,7 +33,7 @@ EXPORTS = [
     "sivf_assign", "sivf_probe", "sivf_sync",
     "sivf_stats", "sivf_dump", "sivf_dump_payload", "sivf_list_sizes",
     "sivf_profile", "sivf_profile_read", "sivf_last_error", "sivf_version",
-    "sivf_set_wait_limit", "sivf_debug_set_error_bits",
+    "sivf_set_wait_limit", "sivf_debug_set_error_bits", "sivf_set_chunk_bytes",
     "sivf_set_tile", "sivf_get_tile", "sivf_autotune",
     "sivf_exec_create", "sivf_exec_launch", "sivf_exec_results", "sivf_exec_kernels",
     "sivf_exec_destroy",
@@ -146,6 +146,7 @@ def load(path: str | None = None):
             "sivf_list_sizes": (i32, [vp, vp, vp]),
             "sivf_profile": (i32, [vp, i32]),
             "sivf_set_wait_limit": (i32, [vp, i64]),
+            "sivf_set_chunk_bytes": (i32, [vp, i64]),
             "sivf_debug_set_error_bits": (i32, [vp, C.c_uint32, vp]),
             "sivf_profile_read": (i32, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)]),
             "sivf_last_error": (C.c_char_p, [vp]),
@@ -455,6 +456,11 @@ def sivf_list_sizes(h, nlist, stream=None) -> np.ndarray:
 def sivf_set_wait_limit(h, ns: int) -> None:
     lib = load()
     _check(lib, h, lib.sivf_set_wait_limit(h, int(ns)))
+
+
+def sivf_set_chunk_bytes(h, nbytes: int) -> None:
+    lib = load()
+    _check(lib, h, lib.sivf_set_chunk_bytes(h, int(nbytes)))
 
 
 def sivf_debug_set_error_bits(h, bits: int, stream=None) -> None:
