@@ -1273,6 +1273,14 @@ def main():
         hl = torch.empty((w.n_queries, w.k), dtype=torch.int64).pin_memory()
         h2d = sum(x.numel() * x.element_size() for x in host[0])
         d2h = hd.numel() * 4 + hl.numel() * 8
+        # one untimed copy of every pinned buffer first: the first DMA to or
+        # from a freshly pinned buffer pays its one-time mapping
+        for hs in host:
+            for dst, src in zip(bufs, hs):
+                dst.copy_(src, non_blocking=True)
+        hd.copy_(dist_out, non_blocking=True)
+        hl.copy_(lab_out, non_blocking=True)
+        torch.cuda.synchronize()
         # E2E_PASSES passes of K steps (fresh inputs each), the median pass
         # reported: the host-to-device copies share the machine's host
         # memory with other jobs, so a single pass can catch a transient

@@ -13,8 +13,9 @@
 //   rank      per block of 1024 vectors: stable sort by list, local ranks,
 //             run counts per (list, block)
 //   plan      per touched list: prefix of run counts over blocks, slab demand
-//   admit     all-or-nothing admission against the free stack
-//   overwrite delete-then-insert for kept ids that are live
+//   overwrite all-or-nothing admission against the free stack (derived by
+//             every thread, recorded once), then delete-then-insert for kept
+//             ids that are live
 //   reclaim   lists that lost a slab: directory compaction, slab to the stack
 //   alloc     per touched list: fill the head, pop fresh slabs
 //   append    per vector: payload + copies + id + table, fence, bit
@@ -276,19 +277,29 @@ __global__ __launch_bounds__(512) void k_ins_rank(IndexView V, const int64_t *__
     }
 }
 
+// one warp per touched list: exclusive scan of its run counts over the
+// rank blocks (lanes over blocks), then its slab demand
 __global__ void k_ins_plan(IndexView V, int nblk, const int32_t *__restrict__ touched,
                            int32_t *__restrict__ bcnt)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= V.ctl->ntouched) return;
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= V.ctl->ntouched) return;  // whole warps
     const int l = touched[t];
     int32_t *rc = V.runcnt + (size_t)l * V.nblk_max;
     int acc = 0;
-    for (int b = 0; b < nblk; ++b) {
-        const int c = rc[b];
-        rc[b] = acc;
-        acc += c;
+    for (int b0 = 0; b0 < nblk; b0 += 32) {  // warp-uniform
+        const int b = b0 + lane;
+        const int c = b < nblk ? rc[b] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (b < nblk) rc[b] = acc + incl - c;
+        acc += __shfl_sync(0xffffffffu, incl, 31);
     }
+    if (lane != 0) return;
     bcnt[t] = acc;
     const int h = V.head[l];
     const int avail = h >= 0 ? V.C - V.meta[h].fill : 0;
@@ -298,20 +309,26 @@ __global__ void k_ins_plan(IndexView V, int nblk, const int32_t *__restrict__ to
     atomicAdd(reinterpret_cast<unsigned long long *>(&V.ctl->count), (unsigned long long)acc);
 }
 
-__global__ void k_ins_admit(IndexView V)
+// all-or-nothing admission of the batch against the free stack, from the
+// plan's totals (every thread of the overwrite kernel derives it; the
+// first records it for the kernels that follow and for the host)
+__device__ __forceinline__ int admission(const IndexView &V)
 {
-    Ctl *c = V.ctl;
-    int st = SIVF_OK;
-    if (c->flags & FLAG_BAD_ID) st = SIVF_E_ARG;
-    else if ((c->flags & FLAG_DIR_FULL) || c->demand > (int64_t)*V.free_top) st = SIVF_E_NOMEM;
-    c->status = st;
-    if (st != SIVF_OK) c->count = 0;
+    const Ctl *c = V.ctl;
+    if (c->flags & FLAG_BAD_ID) return SIVF_E_ARG;
+    if ((c->flags & FLAG_DIR_FULL) || c->demand > (int64_t)*V.free_top) return SIVF_E_NOMEM;
+    return SIVF_OK;
 }
 
 __global__ void k_ins_overwrite(IndexView V, const int64_t *__restrict__ ids, int64_t n,
                                 const int32_t *__restrict__ rloc, int32_t *__restrict__ affected)
 {
-    if (V.ctl->status != SIVF_OK) return;
+    const int st = admission(V);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        V.ctl->status = st;
+        if (st != SIVF_OK) V.ctl->count = 0;
+    }
+    if (st != SIVF_OK) return;
     GRID_STRIDE(i, n)
     {
         if (rloc[i] < 0) continue;
@@ -480,11 +497,11 @@ void insert_batch(sivf_index *ix, const int64_t *ids, const float *x, int64_t n,
     IndexView V = view_of(ix);
     const int nblk = (int)((n + kRankTile - 1) / kRankTile);
     const int tmax = (int)std::min<int64_t>(n, ix->nlist);
-    const int tok = prof_begin(ix, PROF_INSERT, 9, st);
+    const int tok = prof_begin(ix, PROF_INSERT, 8, st);
     k_ins_claim<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n);
     k_ins_rank<<<nblk, 512, 0, st>>>(V, ids, s.lab, n, s.rloc, s.touched);
-    k_ins_plan<<<(tmax + 127) / 128, 128, 0, st>>>(V, nblk, s.touched, s.bcnt);
-    k_ins_admit<<<1, 1, 0, st>>>(V);
+    k_ins_plan<<<(unsigned)(((int64_t)tmax * 32 + 127) / 128), 128, 0, st>>>(V, nblk, s.touched,
+                                                                           s.bcnt);
     k_ins_overwrite<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n, s.rloc, s.affected);
     k_reclaim<<<grid_for((int64_t)tmax * 32, 256), 256, 0, st>>>(V, s.affected);
     k_ins_alloc<<<(tmax + 127) / 128, 128, 0, st>>>(V, s.touched, s.bcnt, s.plan);
