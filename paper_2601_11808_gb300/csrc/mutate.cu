@@ -369,8 +369,11 @@ __global__ void k_ins_alloc(IndexView V, const int32_t *__restrict__ touched,
         }
         const int rem = cnt - a;
         int s = -1;
+        // the reserved stack entries from the top down: on a fresh pool (slab
+        // 0 on top) a list receives ascending consecutive slabs, which the
+        // list scan fetches as one 128-row box
         for (int j = 0; j < need; ++j) {
-            s = V.free_list[top - need + j];
+            s = V.free_list[top - 1 - j];
             const int f = min(C, rem - j * C);
             V.meta[s].list = l;
             V.meta[s].fill = f;

@@ -94,6 +94,8 @@ struct TcArgs {
     uint64_t wait_ns; // time after which a wait of the scan gives up
     int seed_slabs;   // > 0: seed launch: the first seed_slabs slabs of each
                       // item, bounds published, no runs written
+    int tile_box;     // the 128-row map is valid: a tile of consecutive slabs
+                      // is one TMA box
     Ctl *ctl;
     uint32_t *err;
 };
@@ -518,7 +520,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 
 template <int DT, int TN>  // DT: 0 = BF16, 1 = FP8 E4M3; TN: queries per tile
 __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
-    const __grid_constant__ CUtensorMap tmap, TcArgs a)
+    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_t,
+    TcArgs a)
 {
     using S = TcShape<TN>;
     constexpr int EW = S::EW, EPI = S::EPI, TB = S::TB;
@@ -732,22 +735,45 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
                     int okc = 0;
                     for (int jj = 0; jj < nsl; ++jj) okc += sl[b * SPB + jj] >= 0;
                     mbar_arrive_expect_tx(&full[st], (uint32_t)(okc * KC * C * 128));
-                    for (int jj = 0; jj < nsl; ++jj) {
-                        const int s = sl[b * SPB + jj];
-                        if (s < 0) continue;
+                    // a whole tile of consecutive slabs s0 .. s0 + SPB - 1 is one
+                    // 128-row box (the same bytes, the same swizzled layout)
+                    auto consecutive = [&](int bb, int ns) {
+                        const int s0 = sl[bb * SPB];
+                        bool r = a.tile_box && ns == SPB && s0 >= 0;
+                        for (int jj = 1; jj < ns && r; ++jj) r = sl[bb * SPB + jj] == s0 + jj;
+                        return r;
+                    };
+                    if (consecutive(b, nsl)) {
+                        const int s0 = sl[b * SPB];
                         for (int kc = 0; kc < KC; ++kc)
-                            tma_load_2d(A + (size_t)st * KC * TC_M * 128 + (size_t)kc * TC_M * 128 +
-                                            (size_t)jj * C * 128,
-                                        &tmap, kc * EPC, s * C, &full[st]);
+                            tma_load_2d(A + (size_t)st * KC * TC_M * 128 + (size_t)kc * TC_M * 128,
+                                        &tmap_t, kc * EPC, s0 * C, &full[st]);
+                    } else {
+                        for (int jj = 0; jj < nsl; ++jj) {
+                            const int s = sl[b * SPB + jj];
+                            if (s < 0) continue;
+                            for (int kc = 0; kc < KC; ++kc)
+                                tma_load_2d(A + (size_t)st * KC * TC_M * 128 +
+                                                (size_t)kc * TC_M * 128 + (size_t)jj * C * 128,
+                                            &tmap, kc * EPC, s * C, &full[st]);
+                        }
                     }
                     const int bp = b + a.pf_tiles;  // keep the L2 prefetch ahead
-                    if (bp < nblk)
-                        for (int jj = 0; jj < min(SPB, sns - bp * SPB); ++jj) {
-                            const int s = sl[bp * SPB + jj];
-                            if (s < 0) continue;
-                            prefetch_l2(a.pay + (size_t)s * pay_bytes, pay_bytes);
-                            prefetch_l2(a.xnorm + (size_t)s * C, (uint32_t)(C * 4));
+                    if (bp < nblk) {
+                        const int nsp = min(SPB, sns - bp * SPB);
+                        if (consecutive(bp, nsp)) {
+                            const int s0 = sl[bp * SPB];
+                            prefetch_l2(a.pay + (size_t)s0 * pay_bytes, (uint32_t)(SPB * pay_bytes));
+                            prefetch_l2(a.xnorm + (size_t)s0 * C, (uint32_t)(SPB * C * 4));
+                        } else {
+                            for (int jj = 0; jj < nsp; ++jj) {
+                                const int s = sl[bp * SPB + jj];
+                                if (s < 0) continue;
+                                prefetch_l2(a.pay + (size_t)s * pay_bytes, pay_bytes);
+                                prefetch_l2(a.xnorm + (size_t)s * C, (uint32_t)(C * 4));
+                            }
                         }
+                    }
                 }
                 if (ab) break;
             }
@@ -1608,6 +1634,34 @@ bool tc_make_maps(sivf_index *ix)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
+    // 128-row boxes for tiles whose slabs are consecutive in the pool
+    ix->tmap_tile_ok = false;
+    if (ix->C < TC_M && TC_M % ix->C == 0) {
+        bool ok = true;
+        if (ix->xb16) {
+            cuuint64_t dims[2] = {(cuuint64_t)ix->d, rows};
+            cuuint64_t strides[1] = {(cuuint64_t)ix->d * 2};
+            cuuint32_t box[2] = {64, (cuuint32_t)TC_M};
+            cuuint32_t es[2] = {1, 1};
+            ok = ok && enc(reinterpret_cast<CUtensorMap *>(ix->tmap_bf16_t),
+                           CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ix->xb16, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        if (ix->x8) {
+            cuuint64_t dims[2] = {(cuuint64_t)ix->d, rows};
+            cuuint64_t strides[1] = {(cuuint64_t)ix->d};
+            cuuint32_t box[2] = {128, (cuuint32_t)TC_M};
+            cuuint32_t es[2] = {1, 1};
+            ok = ok && enc(reinterpret_cast<CUtensorMap *>(ix->tmap_fp8_t),
+                           CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ix->x8, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        ix->tmap_tile_ok = ok;
+    }
     return qt_make_maps(ix, enc);
 }
 
@@ -1682,7 +1736,8 @@ bool tc_fits(const sivf_index *ix, int Kc)
 }
 
 template <int DT, int TN>
-static void launch_tc(const unsigned char *tmap, TcArgs a, cudaStream_t st)
+static void launch_tc(const unsigned char *tmap, const unsigned char *tmap_t, TcArgs a,
+                      cudaStream_t st)
 {
     a.nst = tc_stages<TN>(a.KC, a.M);
     const size_t smem = tc_smem<TN>(a.KC, a.M, a.nst).total;
@@ -1693,7 +1748,8 @@ static void launch_tc(const unsigned char *tmap, TcArgs a, cudaStream_t st)
         attr = smem;
     }
     k_scan_tc<DT, TN><<<152, TcShape<TN>::NT, smem, st>>>(
-        *reinterpret_cast<const CUtensorMap *>(tmap), a);
+        *reinterpret_cast<const CUtensorMap *>(tmap), *reinterpret_cast<const CUtensorMap *>(tmap_t),
+        a);
 }
 
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
@@ -1736,6 +1792,7 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.KC = (ix->d * esz + 127) / 128;
     a.nst = 2;
     a.pf_tiles = std::max(2, TC_PF_BYTES / (TC_M * ix->d * esz));
+    a.tile_box = ix->tmap_tile_ok ? 1 : 0;
     a.ctl = ix->ctl;
     a.err = ix->err;
     a.seed_slabs = seed_slabs;
@@ -1743,13 +1800,13 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     const int tn = tc_tile_queries(Kc);
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {
-        if (tn == 48) launch_tc<0, 48>(ix->tmap_bf16, a, st);
-        else if (tn == 32) launch_tc<0, 32>(ix->tmap_bf16, a, st);
-        else launch_tc<0, 16>(ix->tmap_bf16, a, st);
+        if (tn == 48) launch_tc<0, 48>(ix->tmap_bf16, ix->tmap_bf16_t, a, st);
+        else if (tn == 32) launch_tc<0, 32>(ix->tmap_bf16, ix->tmap_bf16_t, a, st);
+        else launch_tc<0, 16>(ix->tmap_bf16, ix->tmap_bf16_t, a, st);
     } else {
-        if (tn == 48) launch_tc<1, 48>(ix->tmap_fp8, a, st);
-        else if (tn == 32) launch_tc<1, 32>(ix->tmap_fp8, a, st);
-        else launch_tc<1, 16>(ix->tmap_fp8, a, st);
+        if (tn == 48) launch_tc<1, 48>(ix->tmap_fp8, ix->tmap_fp8_t, a, st);
+        else if (tn == 32) launch_tc<1, 32>(ix->tmap_fp8, ix->tmap_fp8_t, a, st);
+        else launch_tc<1, 16>(ix->tmap_fp8, ix->tmap_fp8_t, a, st);
     }
     prof_end(ix, tok, st);
 }

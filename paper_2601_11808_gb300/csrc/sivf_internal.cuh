@@ -131,6 +131,11 @@ struct sivf_index {
     // TMA descriptors (CUtensorMap, 128 bytes) of the BF16 / FP8 copies
     alignas(64) unsigned char tmap_bf16[128];
     alignas(64) unsigned char tmap_fp8[128];
+    // the same copies with boxes of 128 rows (a tile of consecutive slabs,
+    // slabs of fewer than 128 rows only; tmap_tile_ok when made)
+    alignas(64) unsigned char tmap_bf16_t[128];
+    alignas(64) unsigned char tmap_fp8_t[128];
+    bool tmap_tile_ok;
     // the same copies with boxes of min(C, 64) rows (query-row scan)
     alignas(64) unsigned char tmap_qt_bf16[128];
     alignas(64) unsigned char tmap_qt_fp8[128];
