@@ -1387,11 +1387,14 @@ __global__ __launch_bounds__(MT_NT) void k_merge_rerank(
 }
 
 // Deep re-rank (K' up to 512): one block per query; its warps compute the
-// candidates' exact FP32 direct-form distances into shared memory, then
+// candidates' exact FP32 direct-form distances into shared memory (eight
+// lanes per candidate row with 16-byte loads, RK_UNR rounds of four rows
+// per warp loaded before they are reduced, the query in registers), then
 // the block sorts them by (distance, id) with a bitonic network and writes
 // the best k.
 constexpr int RR_NT = 256;
 constexpr int RR_MAX = 512;
+template <int NQ>  // 16-byte chunks of the row per lane (d <= 32 NQ)
 __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__ q, int64_t nq,
                                                        int d, int Kc,
                                                        const float *__restrict__ cand_d,
@@ -1404,30 +1407,56 @@ __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__
     __shared__ float sd[RR_MAX];
     __shared__ int64_t si[RR_MAX];
     const int64_t qi = blockIdx.x;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 3, t = lane & 7;
     const int64_t PAD = 0x7fffffffffffffffLL;  // pads sort after every id
     int N = 32;
     while (N < Kc) N <<= 1;
-    const float *qr = q + (size_t)qi * d;
-    for (int c = warp; c < N; c += RR_NT / 32) {
-        float acc = INFINITY;
-        int64_t lab = PAD;
-        if (c < Kc) {
-            const int64_t gs = cand_s[qi * Kc + c];
-            if (gs >= 0 && cand_d[qi * Kc + c] < INFINITY) {
-                const float *xr = x32 + (size_t)gs * d;
-                float a = 0.f;
-                for (int j = lane; j < d; j += 32) {
-                    const float t = qr[j] - xr[j];
-                    a = fmaf(t, t, a);
-                }
-                acc = warp_sum(a);
-                lab = ids[gs];
+    const int n4 = d >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(q + (size_t)qi * d);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x32);
+    float4 qv[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+        qv[u] = t + 8 * u < n4 ? __ldg(q4 + t + 8 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int CPW = 4 * RK_UNR;  // candidates per warp and batch
+    for (int c0 = warp * CPW; c0 < N; c0 += (RR_NT / 32) * CPW) {
+        float4 xv[RK_UNR][NQ];
+        int64_t gs[RK_UNR];
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            const int c = c0 + 4 * r + g;
+            gs[r] = -1;
+            if (c < Kc) {
+                const int64_t s0 = cand_s[qi * Kc + c];
+                if (s0 >= 0 && cand_d[qi * Kc + c] < INFINITY) gs[r] = s0;
             }
+#pragma unroll
+            for (int u = 0; u < NQ; ++u)
+                xv[r][u] = gs[r] >= 0 && t + 8 * u < n4 ? __ldg(x4 + gs[r] * n4 + t + 8 * u)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (lane == 0) {
-            sd[c] = acc;
-            si[c] = lab;
+#pragma unroll
+        for (int r = 0; r < RK_UNR; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                float dd = qv[u].x - xv[r][u].x;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].y - xv[r][u].y;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].z - xv[r][u].z;
+                acc = fmaf(dd, dd, acc);
+                dd = qv[u].w - xv[r][u].w;
+                acc = fmaf(dd, dd, acc);
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            const int c = c0 + 4 * r + g;
+            if (t == 0 && c < N) {
+                sd[c] = gs[r] >= 0 ? acc : INFINITY;
+                si[c] = gs[r] >= 0 ? __ldg(ids + gs[r]) : PAD;
+            }
         }
     }
     __syncthreads();
@@ -1861,9 +1890,14 @@ void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *can
     } else if (Kc <= 128) {
         if (wide) SIVF_RERANK(4, 8);
         else SIVF_RERANK(4, 4);
-    } else
-        k_rerank_wide<<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, ix->x32,
-                                                      ix->ids, k, dist, labels);
+    } else {
+        if (ix->d > 128)
+            k_rerank_wide<8><<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s,
+                                                             ix->x32, ix->ids, k, dist, labels);
+        else
+            k_rerank_wide<4><<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s,
+                                                             ix->x32, ix->ids, k, dist, labels);
+    }
 #undef SIVF_RERANK
     prof_end(ix, tok, st);
 }
