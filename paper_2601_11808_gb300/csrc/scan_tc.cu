@@ -1388,14 +1388,17 @@ __global__ __launch_bounds__(MT_NT) void k_merge_rerank(
 
 // Deep re-rank (K' up to 512): one block per query; its warps compute the
 // candidates' exact FP32 direct-form distances into shared memory (eight
-// lanes per candidate row with 16-byte loads, RK_UNR rounds of four rows
+// lanes per candidate row with 16-byte loads, RR_UNR rounds of four rows
 // per warp loaded before they are reduced, the query in registers), then
 // the block sorts them by (distance, id) with a bitonic network and writes
-// the best k.
+// the best k.  Two rounds per batch keep the registers low enough for four
+// blocks per SM: the gather is bound by loads in flight, i.e. by resident
+// warps.
 constexpr int RR_NT = 256;
 constexpr int RR_MAX = 512;
+constexpr int RR_UNR = 2;
 template <int NQ>  // 16-byte chunks of the row per lane (d <= 32 NQ)
-__global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__ q, int64_t nq,
+__global__ __launch_bounds__(RR_NT, NQ <= 4 ? 4 : 1) void k_rerank_wide(const float *__restrict__ q, int64_t nq,
                                                        int d, int Kc,
                                                        const float *__restrict__ cand_d,
                                                        const int64_t *__restrict__ cand_s,
@@ -1418,12 +1421,12 @@ __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__
 #pragma unroll
     for (int u = 0; u < NQ; ++u)
         qv[u] = t + 8 * u < n4 ? __ldg(q4 + t + 8 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
-    constexpr int CPW = 4 * RK_UNR;  // candidates per warp and batch
+    constexpr int CPW = 4 * RR_UNR;  // candidates per warp and batch
     for (int c0 = warp * CPW; c0 < N; c0 += (RR_NT / 32) * CPW) {
-        float4 xv[RK_UNR][NQ];
-        int64_t gs[RK_UNR];
+        float4 xv[RR_UNR][NQ];
+        int64_t gs[RR_UNR];
 #pragma unroll
-        for (int r = 0; r < RK_UNR; ++r) {
+        for (int r = 0; r < RR_UNR; ++r) {
             const int c = c0 + 4 * r + g;
             gs[r] = -1;
             if (c < Kc) {
@@ -1436,7 +1439,7 @@ __global__ __launch_bounds__(RR_NT) void k_rerank_wide(const float *__restrict__
                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int r = 0; r < RK_UNR; ++r) {
+        for (int r = 0; r < RR_UNR; ++r) {
             float acc = 0.f;
 #pragma unroll
             for (int u = 0; u < NQ; ++u) {
