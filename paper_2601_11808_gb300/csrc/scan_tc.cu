@@ -1304,8 +1304,11 @@ __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, i
 // lanes per candidate row, RK_UNR rounds of four, the query in registers),
 // so the candidate lists never go through global memory and nothing sorts
 // them by approximate distance.
+// rounds of four candidate rows per warp batch of the re-ranks that run with
+// more resident warps (fused merge + re-rank, wide re-rank)
+constexpr int RR_UNR = 2;
 template <int E, int NQ>
-__global__ __launch_bounds__(MT_NT) void k_merge_rerank(
+__global__ __launch_bounds__(MT_NT, NQ <= 4 ? 8 : 2) void k_merge_rerank(
     const int2 *__restrict__ qrun, int64_t nq, int nphase, int K, int RK,
     const int32_t *__restrict__ part_n, const float *__restrict__ part_d,
     const int64_t *__restrict__ part_i, const float *__restrict__ q, int d,
@@ -1334,11 +1337,11 @@ __global__ __launch_bounds__(MT_NT) void k_merge_rerank(
     for (int u = 0; u < NQ; ++u)
         qv[u] = t + 8 * u < n4 ? __ldg(q4 + t + 8 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 *x4 = reinterpret_cast<const float4 *>(x32);
-    for (int c0 = 0; c0 < nk; c0 += 4 * RK_UNR) {
-        float4 xv[RK_UNR][NQ];
-        int64_t gs[RK_UNR];
+    for (int c0 = 0; c0 < nk; c0 += 4 * RR_UNR) {
+        float4 xv[RR_UNR][NQ];
+        int64_t gs[RR_UNR];
 #pragma unroll
-        for (int r = 0; r < RK_UNR; ++r) {
+        for (int r = 0; r < RR_UNR; ++r) {
             const int c = c0 + 4 * r + g;
             gs[r] = c < nk ? (int64_t)ss[warp][c] : -1;
 #pragma unroll
@@ -1347,7 +1350,7 @@ __global__ __launch_bounds__(MT_NT) void k_merge_rerank(
                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int r = 0; r < RK_UNR; ++r) {
+        for (int r = 0; r < RR_UNR; ++r) {
             float acc = 0.f;
 #pragma unroll
             for (int u = 0; u < NQ; ++u) {
@@ -1396,7 +1399,6 @@ __global__ __launch_bounds__(MT_NT) void k_merge_rerank(
 // warps.
 constexpr int RR_NT = 256;
 constexpr int RR_MAX = 512;
-constexpr int RR_UNR = 2;
 template <int NQ>  // 16-byte chunks of the row per lane (d <= 32 NQ)
 __global__ __launch_bounds__(RR_NT, NQ <= 4 ? 4 : 1) void k_rerank_wide(const float *__restrict__ q, int64_t nq,
                                                        int d, int Kc,
