@@ -817,8 +817,11 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
                 group_pairs(ix, m, P, 0, split, probes, dd, pl, sc, sb, s);
                 scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
                 if (split < P) {
-                    group_pairs(ix, m, P, split, P, probes, dd, pl, sc, sb, s);
-                    scan_lists_tc(ix, dtype, qq, m, P, Kc, pl, sc, s);
+                    SearchPlan pl2 = pl;  // the other lists: the plan's phase-2 tile
+                    pl2.tq = pl.tq2;
+                    pl2.M = pl.M2;
+                    group_pairs(ix, m, P, split, P, probes, dd, pl2, sc, sb, s);
+                    scan_lists_tc(ix, dtype, qq, m, P, Kc, pl2, sc, s);
                 }
                 nphase = split < P ? 2 : 1;
             }

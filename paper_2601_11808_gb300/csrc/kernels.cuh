@@ -82,6 +82,9 @@ struct SearchPlan {
                          // one launch over every probed list
     int qt;              // reduced precision: the query-row scan (scan_qt.cu)
     int sel;             // the tile's select_slabs (query-row scan: buffer cap)
+    int tq2, M2;         // split 1, the other lists: queries per tile and buffer
+                         // entries (32 and one tile of room for K' > 128 when
+                         // that fits beside two stages; else tq and M)
 };
 // tile choice for a batch: the installed one of its bucket, else the default
 int tune_bucket(const sivf_index *ix, int64_t nq, int P);
@@ -118,6 +121,9 @@ void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qs
 void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t *probes,
                float *qn, float *qsc, unsigned char *qcast, cudaStream_t st);
 bool tc_fits(const sivf_index *ix, int Kc);
+// buffer entries of 32-query tiles for K' > 128 with one tile of room and
+// two A stages, or 0 when they do not fit
+int tc_wide_entries(const sivf_index *ix, int dtype, int Kc);
 // entries of a row's candidate buffer (sel: tiles of room, 0 = default) and
 // whether a buffer of M entries fits in shared memory
 int tc_buf_entries(const sivf_index *ix, int dtype, int Kc, int sel);

@@ -903,7 +903,19 @@ SearchPlan plan_from_tile(const sivf_index *ix, int dtype, int64_t nq, int P, in
     pl.ch = std::max(1, std::min(kMaxChunks, 2048 / std::max(P, 1)));
     pl.slabs_per_chunk = t.slabs_per_chunk;
     pl.ips = t.items_per_sm;
-    pl.run_cap = plan_run_cap(nq, P, pl.tq, pl.ips);
+    // the other lists of split 1 run under the bounds of the nearest, so few
+    // rows reach a buffer: K' > 128 takes 32-query tiles with one tile of
+    // room there (half the tiles of 16)
+    pl.tq2 = pl.tq;
+    pl.M2 = pl.M;
+    if (!fp32 && !pl.qt && pl.split == 1 && P > 1) {
+        const int m2 = tc_wide_entries(ix, dtype, K);
+        if (m2 > 0) {
+            pl.tq2 = 32;
+            pl.M2 = m2;
+        }
+    }
+    pl.run_cap = plan_run_cap(nq, P, std::max(pl.tq, pl.tq2), pl.ips);
     pl.item_cap = plan_item_cap(nq, P, ix->nlist, pl.ips);
     return pl;
 }

@@ -1757,6 +1757,15 @@ bool tc_buf_fits(const sivf_index *ix, int dtype, int Kc, int M)
     return (tn != 16 || Kc <= TcShape<16>::KMAX) && tc_total(tn, KC, M, 2) <= kTcSmemMax;
 }
 
+int tc_wide_entries(const sivf_index *ix, int dtype, int Kc)
+{
+    if (Kc <= TcShape<32>::KMAX || Kc > TcShape<16>::KMAX) return 0;
+    const int esz = dtype == SIVF_BF16 ? 2 : 1;
+    const int KC = (ix->d * esz + 127) / 128;
+    const int M = tc_buf_len(Kc, 1);
+    return tc_smem<32>(KC, M, 2).total <= kTcSmemMax ? M : 0;
+}
+
 bool tc_fits(const sivf_index *ix, int Kc)
 {
     const int esz = 2;  // the larger of the two formats
@@ -1831,7 +1840,7 @@ void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P,
     a.err = ix->err;
     a.seed_slabs = seed_slabs;
     a.wait_ns = ix->wait_ns;
-    const int tn = tc_tile_queries(Kc);
+    const int tn = pl.tq;  // the plan's tile: 48 / 32 / 16 (tc_tile_queries), 32 wide
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
     if (dtype == SIVF_BF16) {
         if (tn == 48) launch_tc<0, 48>(ix->tmap_bf16, ix->tmap_bf16_t, a, st);
