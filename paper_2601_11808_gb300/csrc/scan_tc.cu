@@ -845,11 +845,13 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
             const float inv_l = __int_as_float(h[9]);
             // a row holds [0, nb) (at most RK) and appends at RK; its pending
             // candidates are folded once a tile leaves more than FT of them:
-            // FT plus one tile always fits.  A fold keeps K' .. Kw.  Past
-            // 224 pending rows a fold costs more than the extra folds that a
-            // lower trigger brings (measured: 224 beats 256, 192 and 160).
+            // FT plus one tile always fits.  A fold keeps K' .. Kw.  For
+            // K' <= 128, past 224 pending rows a fold costs more than the
+            // extra folds that a lower trigger brings (measured at K' = 40:
+            // 224 beats 256, 192 and 160); deeper sets fold only when the
+            // room is full (the held K' dominate a fold's cost)
             const int RK = a.RK, Kw = K + ((RK - K) >> 1);
-            const int FT = min(ME - RK, 224) - TC_M;
+            const int FT = min(ME - RK, K > 128 ? ME - RK : 224) - TC_M;
             const int32_t *qp = c_qpair(j);
             const float *cqn = c_qn(j), *cqsc = c_qsc(j), *ckd = c_kd0(j);
             const int32_t *sl = c_sl(j);
@@ -1734,16 +1736,21 @@ static size_t tc_total(int tn, int KC, int M, int nst)
 }
 
 // Entries of a row's candidate buffer.  A row folds its pending candidates
-// into its best K' once more than (room - 1) tiles of them wait, so with
-// room for one tile any candidate at all costs a fold per tile; the default
-// takes room for two tiles where three A stages still fit beside it (FP8
-// rows), else one.  sel > 0 asks for sel tiles of room.
+// into its best K' once more than (room - 1) tiles of them wait (for
+// K' <= 128 also past 224), so with room for one tile any candidate at all
+// costs a fold per tile; the default takes room for three tiles (K' > 128)
+// or two where three A stages still fit beside it, else one.  sel > 0 asks
+// for sel tiles of room.
 int tc_buf_entries(const sivf_index *ix, int dtype, int Kc, int sel)
 {
     if (sel > 0) return tc_buf_len(Kc, sel);
     const int esz = dtype == SIVF_BF16 ? 2 : 1;
     const int KC = (ix->d * esz + 127) / 128;
     const int tn = tc_tile_queries(Kc);
+    // K' > 128: three tiles of room where they fit, so a fold (dominated by
+    // the held K') comes every third tile while no bound prunes
+    if (Kc > 128 && tc_total(tn, KC, tc_buf_len(Kc, 3), 3) <= kTcSmemMax)
+        return tc_buf_len(Kc, 3);
     if (tc_total(tn, KC, tc_buf_len(Kc, 2), 3) <= kTcSmemMax) return tc_buf_len(Kc, 2);
     return tc_buf_len(Kc, 1);
 }
