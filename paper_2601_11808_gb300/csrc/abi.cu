@@ -106,18 +106,6 @@ sivf_status get_ctx(sivf_index *ix, void *stream, size_t need, Ctx **out)
     return SIVF_OK;
 }
 
-int64_t coarse_rows(const sivf_index *ix, int64_t n)
-{
-    // approximate-distance rows per chunk: at most 64 MB of scratch
-    int64_t r = ((int64_t)64 << 20) / (4 * (int64_t)ix->nlist);
-    return std::max<int64_t>(1, std::min<int64_t>(n, std::max<int64_t>(r, 128)));
-}
-
-size_t coarse_bytes(const sivf_index *ix, int64_t n)
-{
-    return (size_t)coarse_rows(ix, n) * ix->nlist * 4 + 256;
-}
-
 sivf_status grow_rank_rows(sivf_index *ix, int64_t n, void *stream)
 {
     int need = (int)((n + kRankTile - 1) / kRankTile);
@@ -174,6 +162,19 @@ sivf_status read_status(sivf_index *ix, void *stream, int64_t *count)
 }  // namespace
 
 namespace sivf {
+
+int64_t coarse_rows(const sivf_index *ix, int64_t n)
+{
+    // approximate-distance rows per chunk: at most 64 MB of scratch
+    int64_t r = ((int64_t)64 << 20) / (4 * (int64_t)ix->nlist);
+    return std::max<int64_t>(1, std::min<int64_t>(n, std::max<int64_t>(r, 128)));
+}
+
+size_t coarse_bytes(const sivf_index *ix, int64_t n)
+{
+    return (size_t)coarse_rows(ix, n) * ix->nlist * 4 + 256;
+}
+
 int prof_begin(sivf_index *ix, int k, int n, cudaStream_t st)
 {
     ix->launches += n;
@@ -718,7 +719,8 @@ extern "C" {
 
 static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k, int nprobe,
                                const int32_t *probes_in, sivf_scan_dtype dtype, float *dist,
-                               int64_t *labels, void *stream, int cand_only = 0)
+                               int64_t *labels, void *stream, int cand_only = 0,
+                               bool probes_unique = false)
 {
     if (!ix) return SIVF_E_ARG;
     if (nq < 0 || k < 1 || k > kMaxK || nprobe < 1 ||
@@ -783,7 +785,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
         else
             coarse_topP(ix, qq, m, P, probes, Dbuf, rows, s);
         if (!tc) {
-            scan_lists(ix, qq, m, P, probes, probes_in != nullptr, pl, sc, s);
+            scan_lists(ix, qq, m, P, probes, probes_in != nullptr && !probes_unique, pl, sc, s);
             merge_topk(ix, m, P, probes, pl, sc, k, dist + q0 * k, labels + q0 * k, s);
         } else {
             const int esz = dtype == SIVF_BF16 ? 2 : 1;
@@ -793,7 +795,7 @@ static sivf_status search_impl(sivf_index *ix, const float *q, int64_t nq, int k
             if (fp8) pair_prep(ix, qq, m, P, probes, sc.pqn, sc.pqsc, sc.qcast, s);
             else query_prep(ix, qq, m, sc.qn, sc.qsc, sc.qcast, s);
             int nphase = 1;
-            const bool dd = probes_in != nullptr;
+            const bool dd = probes_in != nullptr && !probes_unique;  // repeated probes dropped
             const int seed = (128 + ix->C - 1) / ix->C;  // slabs of the first 128 rows
             if (P > 1 && (pl.split == 2 || (pl.qt && pl.split))) {
                 // a seed launch over the first 128 rows of every query's
@@ -851,6 +853,19 @@ sivf_status sivf_search_candidates(sivf_index *ix, const float *q, int64_t nq, i
     if (dtype == SIVF_FP32) return fail(ix, SIVF_E_ARG, "candidates need a reduced-precision dtype");
     return search_impl(ix, q, nq, kc, nprobe, nullptr, dtype, dist, labels, stream, 1);
 }
+
+}  // extern "C"
+
+// a search whose probes come from the library's own selection (distinct
+// lists per query): the executor selects them on a side stream
+sivf_status sivf::search_probed(sivf_index *ix, const float *q, int64_t nq, int k, int nprobe,
+                                const int32_t *probes, sivf_scan_dtype dtype, float *dist,
+                                int64_t *labels, void *stream)
+{
+    return search_impl(ix, q, nq, k, nprobe, probes, dtype, dist, labels, stream, 0, true);
+}
+
+extern "C" {
 
 sivf_status sivf_search_with_probes(sivf_index *ix, const float *q, int64_t nq, int k,
                                     int nprobe, const int32_t *probes, sivf_scan_dtype dtype,

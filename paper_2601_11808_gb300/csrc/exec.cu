@@ -4,7 +4,10 @@
 // The executor records a queue of uneven add / remove / search batches into
 // one CUDA graph on a private stream, whose scratch arena is reserved for
 // the largest batch before recording starts, so nothing inside the graph
-// allocates or waits on the host.  After every batch a one-thread kernel
+// allocates or waits on the host.  The probe selection of every search batch
+// reads only its queries and the centroids, not the lists, so it is recorded
+// on a second stream forked at the start of the queue: it runs under the
+// batches before it, and each search waits only for its own probes.  After every batch a one-thread kernel
 // copies the batch's status and count out of the stream's control block
 // together with a %globaltimer stamp.  The autotuner times searches of one
 // batch shape over a set of tiles by coordinate descent and installs the
@@ -65,6 +68,10 @@ struct sivf_exec {
     uint64_t *t0 = nullptr;          // device, queue start stamp
     OpRecord *host = nullptr;        // pinned [nops + 1]
     int64_t kernels = 0;
+    cudaStream_t side = nullptr;     // probe selection of the search batches
+    std::vector<int32_t *> probes;   // device, per op (search batches only)
+    float *cbuf = nullptr;           // device, the coarse selection's scratch
+    std::vector<cudaEvent_t> evs;    // fork, per search, join
 };
 
 static void exec_free(sivf_exec *e)
@@ -77,6 +84,11 @@ static void exec_free(sivf_exec *e)
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->rec) cudaFree(e->rec);
     if (e->t0) cudaFree(e->t0);
+    if (e->side) cudaStreamDestroy(e->side);
+    for (int32_t *p : e->probes)
+        if (p) cudaFree(p);
+    if (e->cbuf) cudaFree(e->cbuf);
+    for (cudaEvent_t ev : e->evs) cudaEventDestroy(ev);
     if (e->host) cudaFreeHost(e->host);
     delete e;
 }
@@ -149,6 +161,22 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
         exec_free(e);
         return set_error(ix, SIVF_E_CUDA, "executor scratch missing");
     }
+    // probe buffers of the search batches and the coarse selection's scratch
+    e->probes.assign(nops, nullptr);
+    size_t cneed = 0;
+    int nsearch = 0;
+    for (int i = 0; i < nops; ++i)
+        if (ops[i].kind == SIVF_OP_SEARCH) {
+            EXEC_TRY(cudaMalloc(&e->probes[i], sizeof(int32_t) * ops[i].n * ops[i].nprobe));
+            cneed = std::max(cneed, coarse_bytes(ix, ops[i].n));
+            ++nsearch;
+        }
+    if (nsearch) {
+        EXEC_TRY(cudaMalloc(&e->cbuf, cneed));
+        EXEC_TRY(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking));
+        e->evs.assign(nops + 2, nullptr);
+        for (auto &ev : e->evs) EXEC_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     EXEC_TRY(cudaStreamSynchronize(e->cap));
     EXEC_TRY(cudaDeviceSynchronize());
 
@@ -161,6 +189,19 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
         EXEC_TRY(ce);
     }
     k_stamp<<<1, 1, 0, e->cap>>>(e->t0);
+    if (nsearch) {
+        // fork: the probe selection of every search batch, in queue order
+        cudaEventRecord(e->evs[nops], e->cap);
+        cudaStreamWaitEvent(e->side, e->evs[nops], 0);
+        for (int i = 0; i < nops; ++i) {
+            const sivf_op &op = e->ops[i];
+            if (op.kind != SIVF_OP_SEARCH) continue;
+            coarse_topP(ix, op.x, op.n, op.nprobe, e->probes[i], e->cbuf, coarse_rows(ix, op.n),
+                        e->side);
+            cudaEventRecord(e->evs[i], e->side);
+        }
+        cudaEventRecord(e->evs[nops + 1], e->side);
+    }
     sivf_status bad = SIVF_OK;
     int bad_i = -1;
     for (int i = 0; i < nops && !bad; ++i) {
@@ -172,9 +213,11 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
             s2 = sivf_remove(ix, op.ids, op.n, e->cap, nullptr);
         else if (op.kind == SIVF_OP_COMPACT)
             s2 = sivf_compact(ix, op.k, op.n, e->cap, nullptr, nullptr);
-        else
-            s2 = sivf_search(ix, op.x, op.n, op.k, op.nprobe, (sivf_scan_dtype)op.dtype,
-                             op.dist, op.labels, e->cap);
+        else {
+            cudaStreamWaitEvent(e->cap, e->evs[i], 0);  // this batch's probes
+            s2 = search_probed(ix, op.x, op.n, op.k, op.nprobe, e->probes[i],
+                               (sivf_scan_dtype)op.dtype, op.dist, op.labels, e->cap);
+        }
         if (s2) {
             bad = s2;
             bad_i = i;
@@ -188,6 +231,7 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
         }
         k_op_record<<<1, 1, 0, e->cap>>>(ctl, e->rec + i, op.kind == SIVF_OP_SEARCH, op.n);
     }
+    if (nsearch) cudaStreamWaitEvent(e->cap, e->evs[nops + 1], 0);  // join the side stream
     cudaGraph_t g = nullptr;
     ce = cudaStreamEndCapture(e->cap, &g);
     ix->capturing = false;

@@ -15,6 +15,14 @@ namespace sivf {
 void centroid_prep(sivf_index *ix, cudaStream_t st);
 // exact top-P set of each row of x, in ascending list index; Dbuf holds
 // rows_per_chunk * nlist floats
+// rows of one coarse chunk and the scratch of a coarse selection of n rows
+int64_t coarse_rows(const sivf_index *ix, int64_t n);
+size_t coarse_bytes(const sivf_index *ix, int64_t n);
+// the search of sivf_search_with_probes for probes the library selected
+// itself (distinct per query, so not de-duplicated)
+sivf_status search_probed(sivf_index *ix, const float *q, int64_t nq, int k, int nprobe,
+                          const int32_t *probes, sivf_scan_dtype dtype, float *dist,
+                          int64_t *labels, void *stream);
 void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                  float *Dbuf, int64_t rows_per_chunk, cudaStream_t st);
 
