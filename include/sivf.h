@@ -132,9 +132,28 @@ sivf_status sivf_load(const char *path, sivf_index **out);
  * every list's FP8 inverse scale to fl32(448 / R_l), R_l the distance from
  * c_l to its nearest other centroid (FP64); with one list or R_l = 0,
  * fl32(448 / (2 * max_j |c_lj|)) (1.0 when the centroid is zero);
- * sivf_set_list_scales overrides it.
+ * sivf_set_list_scales overrides it.  Then picks the first stage of
+ * nearest-list assignment (sivf_assign_stage) from the centroid spacing
+ * and synchronizes `stream`.
  */
 sivf_status sivf_set_centroids(sivf_index *index, const float *c, void *stream);
+
+/*
+ * sivf_assign_stage -- the first stage that nearest-list assignment (the
+ * insert's coarse step, sivf_assign, probe selection at nprobe 1) takes on
+ * the current centroids: 1 the single BF16 tensor-core product, 3 the split
+ * BF16 products (x_hi c_hi + x_hi c_lo + x_lo c_hi), 0 FP32; -1 for NULL or
+ * an index without centroids.  Every stage gives the same assignment (the
+ * FP64 nearest centroid, ties to the lowest index, Sec. 3.3): a row whose
+ * first-stage bound does not isolate one list is re-decided exactly.  The
+ * single product is taken unless twice its bound at the largest centroid
+ * norm, 4 gamma max ||c||^2 with gamma = 2 (2 u + u^2 + d 2^-22 (1 + u)^2),
+ * u = 2^-8, exceeds half the median over lists of the squared distance from
+ * a centroid to its nearest other centroid (FP32): then most rows would need
+ * the re-decision and the split stage (a bound about 60x tighter) is taken.
+ * Chosen by sivf_set_centroids, sivf_train and sivf_load.
+ */
+int32_t sivf_assign_stage(const sivf_index *index);
 
 /*
  * sivf_train -- train the coarse quantizer by Lloyd's k-means and install

@@ -347,6 +347,7 @@ sivf_status sivf_set_centroids(sivf_index *ix, const float *c, void *stream)
                                  cudaMemcpyDeviceToDevice, s));
     centroid_prep(ix, s);
     CUDA_TRY(ix, cudaGetLastError());
+    CUDA_TRY(ix, assign_stage_choose(ix, s));
     ix->have_centroids = true;
     return SIVF_OK;
 }
@@ -404,14 +405,24 @@ sivf_status sivf_train(sivf_index *ix, const float *x, int64_t n, int iters, uin
     CUDA_TRY(ix, cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));
     train_gather(ix, x, rows_dev, s);
     centroid_prep(ix, s);
+    // the assignment's first stage is chosen on the initial centroids and
+    // again on the trained ones
+    CUDA_TRY(ix, assign_stage_choose(ix, s));
     for (int it = 0; it < iters; ++it) {
         coarse_topP(ix, x, n, 1, lab, Dbuf, crows, s);
         train_step(ix, x, n, lab, sum, cnt, s);
         centroid_prep(ix, s);
     }
     CUDA_TRY(ix, cudaGetLastError());
+    CUDA_TRY(ix, assign_stage_choose(ix, s));
     ix->have_centroids = true;
     return SIVF_OK;
+}
+
+int32_t sivf_assign_stage(const sivf_index *ix)
+{
+    if (!ix || !ix->have_centroids) return -1;
+    return first_stage_split(ix, 1);
 }
 
 sivf_status sivf_get_centroids(sivf_index *ix, float *c, void *stream)

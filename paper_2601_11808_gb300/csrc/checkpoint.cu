@@ -176,7 +176,9 @@ sivf_status sivf_load(const char *path, sivf_index **out)
     }
     if (h.have_centroids) {
         sivf::centroid_prep(ix, 0);
-        if (cudaDeviceSynchronize() != cudaSuccess) return bad(SIVF_E_CUDA, "centroid preparation failed");
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            sivf::assign_stage_choose(ix, 0) != cudaSuccess)
+            return bad(SIVF_E_CUDA, "centroid preparation failed");
         ix->have_centroids = true;
     }
     if (cudaMemcpy(ix->inv_scale8, scales.data(), scales.size() * 4, cudaMemcpyHostToDevice) !=

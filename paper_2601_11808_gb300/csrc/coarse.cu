@@ -31,6 +31,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <cmath>
+
 #include "device_utils.cuh"
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -1343,6 +1345,107 @@ void centroid_prep(sivf_index *ix, cudaStream_t st)
     }
 }
 
+// Squared distance from each centroid to its nearest other centroid, FP32
+// (a statistic that picks the first stage, never a result).  One warp per
+// list, its lanes striding over the other centroids.
+__global__ void k_cent_gap(const float *__restrict__ cent, int L, int d,
+                           float *__restrict__ gap2)
+{
+    const int lane = threadIdx.x & 31;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= L) return;
+    const float *cl = cent + (size_t)l * d;
+    float best = INFINITY;
+    for (int o = lane; o < L; o += 32) {
+        if (o == l) continue;
+        const float *co = cent + (size_t)o * d;
+        float s0 = 0.f, s1 = 0.f;
+        int j = 0;
+        for (; j + 1 < d; j += 2) {
+            const float t0 = cl[j] - co[j], t1 = cl[j + 1] - co[j + 1];
+            s0 = fmaf(t0, t0, s0);
+            s1 = fmaf(t1, t1, s1);
+        }
+        if (j < d) {
+            const float t0 = cl[j] - co[j];
+            s0 = fmaf(t0, t0, s0);
+        }
+        best = fminf(best, s0 + s1);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) gap2[l] = best;
+}
+
+// relative error of the BF16 first stage's dot products, |acc - x.c| /
+// (||x|| ||c||): unit roundoff of BF16 ub = 2^-8; the FP32 accumulation of
+// the exact BF16 products is taken as up to two ulps per addition, over d
+// (single) or 3 d (split) terms.  Single: 2 ub + ub^2 (both roundings) plus
+// the accumulation; split: the dropped products xl cl, and the roundings of
+// xl and cl (each ub^2 relative), 3.1 ub^2 in all, plus the accumulation.
+static double first_stage_rel(int d, int split)
+{
+    const double ub = 1.0 / 256.0;
+    const double gacc = (split == 3 ? 3.0 * d : (double)d) * std::ldexp(1.0, -22);
+    return split == 3 ? 3.1 * ub * ub + gacc * (1 + 2 * ub)
+                      : (2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub);
+}
+
+// Which first stage nearest-list assignment takes.  The single BF16 product
+// decides a row on its own when the row's second-nearest list is farther
+// than its nearest by more than twice the bound E <= gamma ||x|| ||c||
+// (gamma = 2 first_stage_rel); otherwise the row's candidates are recorded
+// and re-decided, and a row with more candidates than its records hold is
+// redone from every list.  For a point near its centroid that gap is about
+// the squared distance R^2 from the centroid to its nearest neighbour, so
+// when 2 E (taken at ||x|| = max ||c||) exceeds half the median R^2, most
+// rows would be undecided and the split first stage (bound about 60x
+// tighter) is taken instead.  Both give the same assignment.  Synchronizes
+// `st`.
+cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st)
+{
+    ix->assign_split = false;
+    const int L = ix->nlist, d = ix->d;
+    if (!ix->cent_bf16 || !ix->cent_lo || L < 2 || L > CW_LMAX || d % 16 || d > 128)
+        return cudaSuccess;
+    float *gap2 = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&gap2), sizeof(float) * L, st);
+    if (e != cudaSuccess) return e;
+    ix->launches += 1;
+    k_cent_gap<<<(L * 32 + 127) / 128, 128, 0, st>>>(ix->cent, L, d, gap2);
+    std::vector<float> g((size_t)L), cn((size_t)L);
+    e = cudaMemcpyAsync(g.data(), gap2, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cn.data(), ix->cnorm, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(gap2, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    std::nth_element(g.begin(), g.begin() + L / 2, g.end());
+    const double med = g[(size_t)L / 2];
+    const double c2 = *std::max_element(cn.begin(), cn.end());
+    const double two_e = 4.0 * first_stage_rel(d, 1) * c2;
+    ix->assign_split = std::isfinite(med) && two_e > 0.5 * med;
+    return cudaSuccess;
+}
+
+// First stage of the selection of P lists: 1 the single BF16 product, 3
+// the split BF16 products, 0 FP32.  The single product is within a few
+// percent of ||x|| ||c||: tight enough to isolate the nearest centroid
+// (assignment, P = 1) unless the centroids are close together against
+// their norms (assign_stage_choose), but not to separate the P-th from the
+// (P+1)-th of a dense shell of far centroids; probe selection takes the
+// split form (three products, ~1e-4 of ||x|| ||c||), which needs twice the
+// shared memory (d <= 128).  One warp per row suits up to a few thousand
+// lists; beyond, the block kernel (256 threads per row) selects, from the
+// FP32 first stage.
+int first_stage_split(const sivf_index *ix, int P)
+{
+    const int d = ix->d;
+    if (P > CW_PMAX || ix->nlist > CW_LMAX || d % 16) return 0;
+    const bool single = P == 1 && !ix->assign_split;
+    if (single) return ix->cent_bf16 && d <= kMaxD ? 1 : 0;
+    return ix->cent_lo && d <= 128 ? 3 : 0;
+}
+
 // rows [0, m) of x -> out[m, P]; `Dbuf` holds at least rows_per_chunk * L
 // floats.
 void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
@@ -1351,31 +1454,10 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
     const int L = ix->nlist, d = ix->d;
     const double u = 5.9604644775390625e-08;
     const double gd = d * u / (1.0 - d * u);
-    // The single BF16 product is within a few percent of ||x|| ||c||: tight
-    // enough to isolate the nearest centroid (assignment, P = 1) but not to
-    // separate the P-th from the (P+1)-th of a dense shell of far centroids;
-    // probe selection takes the split form (three products, ~1e-4 of
-    // ||x|| ||c||), which needs twice the shared memory (d <= 128)
-    // one warp per row suits up to a few thousand lists; beyond, the block
-    // kernel (256 threads per row) selects, from the FP32 first stage
     const bool warp_rows = P <= CW_PMAX && L <= CW_LMAX;
-    const int split = !warp_rows ? 0
-                      : (ix->cent_bf16 && P == 1 && d % 16 == 0 && d <= kMaxD) ? 1
-                      : (ix->cent_lo && P > 1 && d % 16 == 0 && d <= 128)      ? 3
-                                                                                : 0;
+    const int split = first_stage_split(ix, P);
     const bool two = split != 0;
-    // BF16 first stage: unit roundoff of BF16 ub = 2^-8; the FP32
-    // accumulation of the exact BF16 products is taken as up to two ulps per
-    // addition, over d (single) or 3 d (split) terms
-    const double ub = 1.0 / 256.0;
-    const double gacc = (split == 3 ? 3.0 * d : (double)d) * std::ldexp(1.0, -22);
-    // |acc - x.c| / (||x|| ||c||): single: 2 ub + ub^2 (both roundings)
-    // plus the accumulation; split: the dropped products xl cl, and the
-    // roundings of xl and cl (each ub^2 relative), 3.1 ub^2 in all, plus
-    // the accumulation
-    const double rel = split == 3 ? 3.1 * ub * ub + gacc * (1 + 2 * ub)
-                                  : (2 * ub + ub * ub) + gacc * (1 + ub) * (1 + ub);
-    const float gamma2_first = (float)(2.0 * rel * (1.0 + 1e-6));
+    const float gamma2_first = (float)(2.0 * first_stage_rel(d, split) * (1.0 + 1e-6));
     // assignment with the single BF16 product: the fused first stage keeps
     // only each row's candidate lists (needs CF_STRIDE ints per row of the
     // distance buffer, and d <= 128 for its shared memory)

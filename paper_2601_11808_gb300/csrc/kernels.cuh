@@ -13,6 +13,8 @@ namespace sivf {
 
 // ---- coarse quantizer (coarse.cu)
 void centroid_prep(sivf_index *ix, cudaStream_t st);
+cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st);
+int first_stage_split(const sivf_index *ix, int P);
 // exact top-P set of each row of x, in ascending list index; Dbuf holds
 // rows_per_chunk * nlist floats
 // rows of one coarse chunk and the scratch of a coarse selection of n rows

@@ -142,6 +142,9 @@ struct sivf_index {
     // the BF16 centroids in boxes of 64 x 256 (fused coarse first stage)
     alignas(64) unsigned char tmap_cent[128];
     bool tmap_cent_ok;
+    // nearest-list assignment takes the split-BF16 first stage (the single
+    // BF16 product's bound is wide against the centroid spacing)
+    bool assign_split;
     bool tmaps_ready;
 
     // address translation table (Sec. 3.4)

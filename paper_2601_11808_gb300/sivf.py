@@ -27,7 +27,7 @@ DTYPES = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 # every symbol include/sivf.h declares
 EXPORTS = [
     "sivf_create", "sivf_destroy", "sivf_set_centroids", "sivf_set_list_scales",
-    "sivf_train", "sivf_get_centroids", "sivf_save", "sivf_load",
+    "sivf_train", "sivf_get_centroids", "sivf_assign_stage", "sivf_save", "sivf_load",
     "sivf_reserve", "sivf_add", "sivf_remove", "sivf_compact", "sivf_search",
     "sivf_search_with_probes", "sivf_search_noalloc", "sivf_search_candidates",
     "sivf_assign", "sivf_probe", "sivf_sync",
@@ -126,6 +126,7 @@ def load(path: str | None = None):
             "sivf_set_centroids": (i32, [vp, vp, vp]),
             "sivf_train": (i32, [vp, vp, i64, i32, C.c_uint64, vp]),
             "sivf_get_centroids": (i32, [vp, vp, vp]),
+            "sivf_assign_stage": (i32, [vp]),
             "sivf_save": (i32, [vp, C.c_char_p, vp]),
             "sivf_load": (i32, [C.c_char_p, C.POINTER(vp)]),
             "sivf_set_list_scales": (i32, [vp, vp, vp]),
@@ -259,6 +260,10 @@ def sivf_get_centroids(h, out, stream=None) -> None:
     import torch
     lib = load()
     _check(lib, h, lib.sivf_get_centroids(h, _ptr(_dev(out, torch.float32)), _stream(stream)))
+
+
+def sivf_assign_stage(h) -> int:
+    return int(load().sivf_assign_stage(h))
 
 
 def sivf_set_list_scales(h, inv_scale, stream=None) -> None:

@@ -63,16 +63,28 @@ def _assign_cases():
     c96 = rng.standard_normal((700, 96)).astype(np.float32)
     yield "d96", c96, (c96[rng.integers(0, 700, 3000)]
                        + 0.5 * rng.standard_normal((3000, 96))).astype(np.float32)
-    # 200 copies of one centroid among 100 others: the fused stage's
-    # per-thread lists overflow, the row is redone from all lists (and its
-    # set of more than 128 candidates takes the serial FP64 path)
+    # 150 copies of one centroid among 400 others (the median spacing keeps
+    # the single BF16 stage): the fused stage's per-thread lists overflow,
+    # the row is redone from all lists (and its set of more than 128
+    # candidates takes the serial FP64 path)
     one = rng.standard_normal((1, 64)).astype(np.float32)
-    oth = rng.standard_normal((100, 64)).astype(np.float32)
-    yield "identical_200_d64", np.concatenate([oth[:50], np.repeat(one, 200, 0), oth[50:]]), \
+    oth = rng.standard_normal((400, 64)).astype(np.float32)
+    yield "identical_150_d64", np.concatenate([oth[:200], np.repeat(one, 150, 0), oth[200:]]), \
         (one + 0.05 * rng.standard_normal((500, 64))).astype(np.float32)
     # integer grid: exact ties between lists, several candidates per row
     yield "int_ties_d64", rng.integers(-1, 2, (400, 64)).astype(np.float32), \
         rng.integers(-1, 2, (3000, 64)).astype(np.float32)
+    # 2,048 lists around 64 mixture centers (sigma 0.1, d = 128): the single
+    # BF16 bound is wider than the centroid spacing, so assignment takes the
+    # split first stage
+    w = W.small("mixed_batches")
+    yield "clustered_d128", W.index_centroids(w), W.vectors(w, 0, 3000)
+
+
+# first stage of assignment (sivf_assign_stage) the centroids above select:
+# 1 single BF16, 3 split BF16
+STAGE = {"sift": 1, "int_ties_d32": 1, "many_rows_d64": 1, "d96": 1, "identical_150_d64": 1,
+         "int_ties_d64": 1, "clustered_d128": 3}
 
 
 @pytest.mark.parametrize("case", [c[0] for c in _assign_cases()])
@@ -85,6 +97,9 @@ def test_assign_bit_exact(torch, case):
     o.set_centroids(cent)
     got = g.assign(cuda(torch, x)).cpu().numpy()
     np.testing.assert_array_equal(got, o.assign(x))
+    if case in STAGE:
+        from paper_2601_11808_gb300.sivf import sivf_assign_stage
+        assert sivf_assign_stage(g.h) == STAGE[case]
 
 
 @pytest.mark.parametrize("P", [1, 5, 8])
