@@ -60,6 +60,7 @@ cudaError_t dalloc(T **p, size_t n)
 
 __global__ void k_init_pool(int32_t *free_list, SlabMeta *meta, int64_t S)
 {
+    pdl_begin();
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
          s += (int64_t)gridDim.x * blockDim.x) {
         free_list[s] = (int32_t)(S - 1 - s);  // slab 0 on top

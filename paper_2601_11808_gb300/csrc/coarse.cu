@@ -45,6 +45,7 @@ __global__ void k_centroid_norms(const float *__restrict__ cent, int L, int d,
                                  float *__restrict__ inv_scale8, uint16_t *__restrict__ cb,
                                  uint16_t *__restrict__ clo)
 {
+    pdl_begin();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L) return;
     const float *v = cent + (size_t)c * d;
@@ -78,6 +79,7 @@ __global__ __launch_bounds__(256) void k_coarse_gemm(const float *__restrict__ x
                                                      const float *__restrict__ cn, int L,
                                                      float *__restrict__ out)
 {
+    pdl_begin();
     __shared__ __align__(16) float As[GBK][GBM];
     __shared__ __align__(16) float Bs[GBK][GBN];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -203,6 +205,7 @@ __device__ float block_min(float v, float *red)
 
 __global__ __launch_bounds__(SEL_NT) void k_coarse_select(SelArgs a)
 {
+    pdl_begin();
     const int row = blockIdx.x;
     if (row >= a.m) return;
     const int tid = threadIdx.x;
@@ -436,6 +439,7 @@ __global__ __launch_bounds__(CT_NT, 1) void k_coarse_tc(const float *__restrict_
                                                         const float *__restrict__ cn, int L,
                                                         float *__restrict__ out, uint32_t *err)
 {
+    pdl_begin();
     constexpr int NP = SPLIT == 3 ? 2 : 1;  // hi (and lo) parts
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -615,6 +619,7 @@ __global__ __launch_bounds__(CF_NT, 1) void k_coarse_fused1(
     int32_t *__restrict__ out1, int32_t *__restrict__ outS, int32_t *__restrict__ hard,
     int *nhard, uint32_t *err)
 {
+    pdl_begin();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     __shared__ uint64_t fullb[2], mmab[2];
@@ -960,6 +965,7 @@ constexpr int CW_RG = 4;       // FP32 rechecks in flight per warp
 template <int PM, bool FROM_S>
 __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 {
+    pdl_begin();
     __shared__ float sLB[CW_ROWS][CW_SCAP], sUB[CW_ROWS][CW_SCAP], sDt[CW_ROWS][CW_SCAP];
     __shared__ int sIdx[CW_ROWS][CW_SCAP];
     __shared__ double sDx[CW_ROWS][CW_SCAP];
@@ -1302,6 +1308,7 @@ __global__ __launch_bounds__(CW_ROWS * 32) void k_coarse_select_w(SelArgs a)
 __global__ void k_fp8_scales(const float *__restrict__ cent, int L, int d,
                              float *__restrict__ inv_scale8)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= L) return;
@@ -1335,13 +1342,12 @@ __global__ void k_fp8_scales(const float *__restrict__ cent, int L, int d,
 void centroid_prep(sivf_index *ix, cudaStream_t st)
 {
     ix->launches += 1;
-    k_centroid_norms<<<(ix->nlist + 127) / 128, 128, 0, st>>>(
-        ix->cent, ix->nlist, ix->d, ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16,
-        ix->cent_lo);
+    launch_pdl(k_centroid_norms, (ix->nlist + 127) / 128, 128, 0, st, ix->cent, ix->nlist, ix->d,
+               ix->cnorm, ix->cnrm_up, ix->inv_scale8, ix->cent_bf16, ix->cent_lo);
     if (ix->x8) {
         ix->launches += 1;
-        k_fp8_scales<<<(ix->nlist * 32 + 127) / 128, 128, 0, st>>>(ix->cent, ix->nlist, ix->d,
-                                                                    ix->inv_scale8);
+        launch_pdl(k_fp8_scales, (ix->nlist * 32 + 127) / 128, 128, 0, st, ix->cent, ix->nlist,
+                   ix->d, ix->inv_scale8);
     }
 }
 
@@ -1351,6 +1357,7 @@ void centroid_prep(sivf_index *ix, cudaStream_t st)
 __global__ void k_cent_gap(const float *__restrict__ cent, int L, int d,
                            float *__restrict__ gap2)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= L) return;
@@ -1411,7 +1418,7 @@ cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st)
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&gap2), sizeof(float) * L, st);
     if (e != cudaSuccess) return e;
     ix->launches += 1;
-    k_cent_gap<<<(L * 32 + 127) / 128, 128, 0, st>>>(ix->cent, L, d, gap2);
+    launch_pdl(k_cent_gap, (L * 32 + 127) / 128, 128, 0, st, ix->cent, L, d, gap2);
     std::vector<float> g((size_t)L), cn((size_t)L);
     e = cudaMemcpyAsync(g.data(), gap2, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
@@ -1490,9 +1497,9 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                                          (int)smem);
                     attr[kc - 1] = smem;
                 }
-                kern<<<std::min(nt, nsm), CF_NT, smem, st>>>(
-                    tm, x + r0 * d, mc, d, ix->cnorm, ix->cnrm_up, L, gamma2_first, out + r0,
-                    nh + 32 + mc, nh + 32, nh, ix->err);
+                launch_pdl(kern, std::min(nt, nsm), CF_NT, smem, st, tm, x + r0 * d, mc, d,
+                           ix->cnorm, ix->cnrm_up, L, gamma2_first, out + r0, nh + 32 + mc, nh + 32,
+                           nh, ix->err);
             };
             if (d <= 64) go(k_coarse_fused1<1>, 1);
             else go(k_coarse_fused1<2>, 2);
@@ -1506,8 +1513,8 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                                          (int)smem);
                     attr = smem;
                 }
-                k_coarse_tc<1><<<g, CT_NT, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, nullptr,
-                                                      ix->cnorm, L, Dbuf, ix->err);
+                launch_pdl(k_coarse_tc<1>, g, CT_NT, smem, st, x + r0 * d, mc, d, ix->cent_bf16,
+                           nullptr, ix->cnorm, L, Dbuf, ix->err);
             } else {
                 static size_t attr = 0;
                 if (smem > attr) {
@@ -1515,12 +1522,13 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
                                          (int)smem);
                     attr = smem;
                 }
-                k_coarse_tc<3><<<g, CT_NT, smem, st>>>(x + r0 * d, mc, d, ix->cent_bf16, ix->cent_lo,
-                                                      ix->cnorm, L, Dbuf, ix->err);
+                launch_pdl(k_coarse_tc<3>, g, CT_NT, smem, st, x + r0 * d, mc, d, ix->cent_bf16,
+                           ix->cent_lo, ix->cnorm, L, Dbuf, ix->err);
             }
         } else {
             dim3 g((L + GBN - 1) / GBN, (mc + GBM - 1) / GBM);
-            k_coarse_gemm<<<g, 256, 0, st>>>(x + r0 * d, mc, d, ix->cent, ix->cnorm, L, Dbuf);
+            launch_pdl(k_coarse_gemm, g, 256, 0, st, x + r0 * d, mc, d, ix->cent, ix->cnorm, L,
+                       Dbuf);
         }
         SelArgs a;
         a.D = fused ? nullptr : Dbuf;
@@ -1544,12 +1552,12 @@ void coarse_topP(sivf_index *ix, const float *x, int64_t m, int P, int32_t *out,
         if (warp_rows) {
             const unsigned gw = (unsigned)((mc + CW_ROWS - 1) / CW_ROWS);
             if (fused)  // loops over the undecided rows, usually none
-                k_coarse_select_w<1, true>
-                    <<<std::min<unsigned>(gw, 2u * (unsigned)nsm), CW_ROWS * 32, 0, st>>>(a);
-            else if (P == 1) k_coarse_select_w<1, false><<<gw, CW_ROWS * 32, 0, st>>>(a);
-            else k_coarse_select_w<CW_PMAX, false><<<gw, CW_ROWS * 32, 0, st>>>(a);
+                launch_pdl(k_coarse_select_w<1, true>, std::min<unsigned>(gw, 2u * (unsigned)nsm),
+                           CW_ROWS * 32, 0, st, a);
+            else if (P == 1) launch_pdl(k_coarse_select_w<1, false>, gw, CW_ROWS * 32, 0, st, a);
+            else launch_pdl(k_coarse_select_w<CW_PMAX, false>, gw, CW_ROWS * 32, 0, st, a);
         } else {
-            k_coarse_select<<<mc, SEL_NT, 0, st>>>(a);
+            launch_pdl(k_coarse_select, mc, SEL_NT, 0, st, a);
         }
         prof_end(ix, tok, st);
     }

@@ -63,6 +63,7 @@ __device__ int64_t block_incl_scan(int64_t v, int64_t *sh)
 __global__ __launch_bounds__(CP_PLAN_NT) void k_cp_plan(CompactArgs a, int min_free,
                                                         int64_t max_moves)
 {
+    pdl_begin();
     __shared__ int64_t sh[CP_PLAN_NT];
     const int tid = threadIdx.x;
     const int per = (a.L + CP_PLAN_NT - 1) / CP_PLAN_NT;
@@ -132,6 +133,7 @@ __device__ __forceinline__ int find_run(const int64_t *off, int n, int64_t g)
 
 __global__ __launch_bounds__(256) void k_cp_bases(CompactArgs a)
 {
+    pdl_begin();
     __shared__ int32_t wsum[8];
     __shared__ int32_t s_run;
     const int nsel = a.ctl->ntouched;
@@ -214,6 +216,7 @@ __device__ __forceinline__ void row_store(float *f32, __nv_bfloat16 *f16, uint8_
 
 __global__ __launch_bounds__(256) void k_cp_gather(CompactArgs a)
 {
+    pdl_begin();
     const int nsel = a.ctl->ntouched;
     if (nsel == 0) return;
     const int64_t total = a.soff[nsel];
@@ -268,6 +271,7 @@ __global__ __launch_bounds__(256) void k_cp_gather(CompactArgs a)
 
 __global__ __launch_bounds__(256) void k_cp_scatter(CompactArgs a)
 {
+    pdl_begin();
     const int nsel = a.ctl->ntouched;
     if (nsel == 0) return;
     const int64_t total = a.voff[nsel];
@@ -305,6 +309,7 @@ __global__ __launch_bounds__(256) void k_cp_scatter(CompactArgs a)
 
 __global__ __launch_bounds__(256) void k_cp_finish(CompactArgs a)
 {
+    pdl_begin();
     const int nsel = a.ctl->ntouched;
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x / 32);
@@ -352,12 +357,12 @@ void compact_pass(sivf_index *ix, const CompactArgs &a, int min_free, int64_t ma
                   cudaStream_t st)
 {
     const int tok = prof_begin(ix, PROF_COMPACT, 5, st);
-    k_cp_plan<<<1, CP_PLAN_NT, 0, st>>>(a, min_free, max_moves);
+    launch_pdl(k_cp_plan, 1, CP_PLAN_NT, 0, st, a, min_free, max_moves);
     const int grid = 152 * 4;
-    k_cp_bases<<<grid, 256, 0, st>>>(a);
-    k_cp_gather<<<grid, 256, 0, st>>>(a);
-    k_cp_scatter<<<grid, 256, 0, st>>>(a);
-    k_cp_finish<<<grid, 256, 0, st>>>(a);
+    launch_pdl(k_cp_bases, grid, 256, 0, st, a);
+    launch_pdl(k_cp_gather, grid, 256, 0, st, a);
+    launch_pdl(k_cp_scatter, grid, 256, 0, st, a);
+    launch_pdl(k_cp_finish, grid, 256, 0, st, a);
     prof_end(ix, tok, st);
 }
 

@@ -25,6 +25,9 @@
 
 using namespace sivf;
 
+// set while this thread records an executor's queue (ordinary kernel edges)
+thread_local bool sivf::tl_recording = false;
+
 namespace {
 
 struct OpRecord {        // device, one per batch
@@ -41,11 +44,16 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-__global__ void k_stamp(uint64_t *t) { *t = global_ns(); }
+__global__ void k_stamp(uint64_t *t)
+{
+    pdl_begin();
+    *t = global_ns();
+}
 
 // the batch just finished on this stream: its status and count
 __global__ void k_op_record(const Ctl *ctl, OpRecord *r, int is_search, int64_t nq)
 {
+    pdl_begin();
     OpRecord o;
     int st = is_search ? (int)SIVF_OK : ctl->status;
     if (!is_search && (ctl->flags & FLAG_BAD_ID)) st = SIVF_E_ARG;
@@ -183,12 +191,14 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
     // record the queue
     const int64_t launches0 = ix->launches;
     ix->capturing = true;
+    tl_recording = true;
     cudaError_t ce = cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal);
     if (ce != cudaSuccess) {
         ix->capturing = false;
+        tl_recording = false;
         EXEC_TRY(ce);
     }
-    k_stamp<<<1, 1, 0, e->cap>>>(e->t0);
+    launch_pdl(k_stamp, 1, 1, 0, e->cap, e->t0);
     if (nsearch) {
         // fork: the probe selection of every search batch, in queue order
         cudaEventRecord(e->evs[nops], e->cap);
@@ -229,12 +239,13 @@ sivf_status sivf_exec_create(sivf_index *ix, const sivf_op *ops, int nops, sivf_
             bad_i = i;
             break;
         }
-        k_op_record<<<1, 1, 0, e->cap>>>(ctl, e->rec + i, op.kind == SIVF_OP_SEARCH, op.n);
+        launch_pdl(k_op_record, 1, 1, 0, e->cap, ctl, e->rec + i, op.kind == SIVF_OP_SEARCH, op.n);
     }
     if (nsearch) cudaStreamWaitEvent(e->cap, e->evs[nops + 1], 0);  // join the side stream
     cudaGraph_t g = nullptr;
     ce = cudaStreamEndCapture(e->cap, &g);
     ix->capturing = false;
+    tl_recording = false;
     ix->launches = launches0;  // recorded, not run
     if (bad) {
         if (g) cudaGraphDestroy(g);

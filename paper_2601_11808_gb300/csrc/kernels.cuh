@@ -6,10 +6,51 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "sivf_internal.cuh"
 
 namespace sivf {
+
+// ---- programmatic dependent launch
+// Every kernel of the library is launched with launch_pdl: outside a graph
+// recording the hardware may make its blocks resident while the kernel
+// before it on the stream still runs, so its launch latency hides under
+// that kernel's tail (a single insert of 10,000 vectors: 0.058 -> 0.038 ms).
+// Each kernel therefore begins with pdl_begin(): wait until the previous
+// kernel has completed and its writes are visible (nothing is read or
+// written before), then allow the next kernel to be scheduled in turn.
+// While a sivf_exec records its queue (tl_recording) the kernels keep
+// ordinary dependencies: a graph already launches its nodes ahead, and
+// programmatic edges made the replayed benchmark step slower (0.382
+// against 0.368 ms).  Launched the ordinary way, both instructions do
+// nothing.
+extern thread_local bool tl_recording;
+
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       A &&...args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = tl_recording ? 0 : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // a failed launch is left in the runtime's last error, which every
+    // caller checks after its launches
+    (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // ---- coarse quantizer (coarse.cu)
 void centroid_prep(sivf_index *ix, cudaStream_t st);

@@ -133,6 +133,7 @@ __device__ __forceinline__ void delete_one(const IndexView &V, int64_t id,
 // emptied slabs reset and pushed on the free stack
 __global__ void k_reclaim(IndexView V, const int32_t *__restrict__ affected)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * blockDim.x / 32;
     const int na = V.ctl->naffected;
@@ -180,6 +181,7 @@ __global__ void k_reclaim(IndexView V, const int32_t *__restrict__ affected)
 // ------------------------------------------------------------- delete
 __global__ void k_rm_validate(IndexView V, const int64_t *__restrict__ ids, int64_t n)
 {
+    pdl_begin();
     GRID_STRIDE(i, n)
     {
         const int64_t id = ids[i];
@@ -190,6 +192,7 @@ __global__ void k_rm_validate(IndexView V, const int64_t *__restrict__ ids, int6
 __global__ void k_rm_phase1(IndexView V, const int64_t *__restrict__ ids, int64_t n,
                             int32_t *__restrict__ affected)
 {
+    pdl_begin();
     if (V.ctl->flags & FLAG_BAD_ID) return;
     GRID_STRIDE(i, n) delete_one(V, ids[i], affected, true);
 }
@@ -197,6 +200,7 @@ __global__ void k_rm_phase1(IndexView V, const int64_t *__restrict__ ids, int64_
 // ------------------------------------------------------------- insert
 __global__ void k_ins_claim(IndexView V, const int64_t *__restrict__ ids, int64_t n)
 {
+    pdl_begin();
     GRID_STRIDE(i, n)
     {
         const int64_t id = ids[i];
@@ -212,6 +216,7 @@ __global__ __launch_bounds__(512) void k_ins_rank(IndexView V, const int64_t *__
                                                   int32_t *__restrict__ rloc,
                                                   int32_t *__restrict__ touched)
 {
+    pdl_begin();
     static_assert(kRankTile == 1024, "rank tile");
     __shared__ uint32_t key[1024];
     __shared__ int32_t rs[1024];
@@ -282,6 +287,7 @@ __global__ __launch_bounds__(512) void k_ins_rank(IndexView V, const int64_t *__
 __global__ void k_ins_plan(IndexView V, int nblk, const int32_t *__restrict__ touched,
                            int32_t *__restrict__ bcnt)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= V.ctl->ntouched) return;  // whole warps
@@ -323,6 +329,7 @@ __device__ __forceinline__ int admission(const IndexView &V)
 __global__ void k_ins_overwrite(IndexView V, const int64_t *__restrict__ ids, int64_t n,
                                 const int32_t *__restrict__ rloc, int32_t *__restrict__ affected)
 {
+    pdl_begin();
     const int st = admission(V);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         V.ctl->status = st;
@@ -340,6 +347,7 @@ __global__ void k_ins_overwrite(IndexView V, const int64_t *__restrict__ ids, in
 __global__ void k_ins_alloc(IndexView V, const int32_t *__restrict__ touched,
                             const int32_t *__restrict__ bcnt, PlanEntry *__restrict__ plan)
 {
+    pdl_begin();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (V.ctl->status != SIVF_OK || t >= V.ctl->ntouched) return;
     const int l = touched[t];
@@ -394,6 +402,7 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
                              const int32_t *__restrict__ lab, const int32_t *__restrict__ rloc,
                              const PlanEntry *__restrict__ plan)
 {
+    pdl_begin();
     if (V.ctl->status != SIVF_OK) return;
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
@@ -473,6 +482,7 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
 __global__ void k_ins_cleanup(IndexView V, const int64_t *__restrict__ ids, int64_t n, int nblk,
                               const int32_t *__restrict__ touched)
 {
+    pdl_begin();
     GRID_STRIDE(i, n)
     {
         const int64_t id = ids[i];
@@ -501,16 +511,17 @@ void insert_batch(sivf_index *ix, const int64_t *ids, const float *x, int64_t n,
     const int nblk = (int)((n + kRankTile - 1) / kRankTile);
     const int tmax = (int)std::min<int64_t>(n, ix->nlist);
     const int tok = prof_begin(ix, PROF_INSERT, 8, st);
-    k_ins_claim<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n);
-    k_ins_rank<<<nblk, 512, 0, st>>>(V, ids, s.lab, n, s.rloc, s.touched);
-    k_ins_plan<<<(unsigned)(((int64_t)tmax * 32 + 127) / 128), 128, 0, st>>>(V, nblk, s.touched,
-                                                                           s.bcnt);
-    k_ins_overwrite<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n, s.rloc, s.affected);
-    k_reclaim<<<grid_for((int64_t)tmax * 32, 256), 256, 0, st>>>(V, s.affected);
-    k_ins_alloc<<<(tmax + 127) / 128, 128, 0, st>>>(V, s.touched, s.bcnt, s.plan);
-    k_ins_append<<<grid_for(n * 32, 256), 256, 0, st>>>(V, ids, x, n, s.lab, s.rloc, s.plan);
-    k_ins_cleanup<<<grid_for(std::max<int64_t>(n, (int64_t)tmax * nblk), 256), 256, 0, st>>>(
-        V, ids, n, nblk, s.touched);
+    launch_pdl(k_ins_claim, grid_for(n, 256), 256, 0, st, V, ids, n);
+    launch_pdl(k_ins_rank, nblk, 512, 0, st, V, ids, s.lab, n, s.rloc, s.touched);
+    launch_pdl(k_ins_plan, (unsigned)(((int64_t)tmax * 32 + 127) / 128), 128, 0, st, V, nblk,
+               s.touched, s.bcnt);
+    launch_pdl(k_ins_overwrite, grid_for(n, 256), 256, 0, st, V, ids, n, s.rloc, s.affected);
+    launch_pdl(k_reclaim, grid_for((int64_t)tmax * 32, 256), 256, 0, st, V, s.affected);
+    launch_pdl(k_ins_alloc, (tmax + 127) / 128, 128, 0, st, V, s.touched, s.bcnt, s.plan);
+    launch_pdl(k_ins_append, grid_for(n * 32, 256), 256, 0, st, V, ids, x, n, s.lab, s.rloc,
+               s.plan);
+    launch_pdl(k_ins_cleanup, grid_for(std::max<int64_t>(n, (int64_t)tmax * nblk), 256), 256, 0, st,
+               V, ids, n, nblk, s.touched);
     prof_end(ix, tok, st);
 }
 
@@ -519,10 +530,10 @@ void remove_batch(sivf_index *ix, const int64_t *ids, int64_t n, int32_t *affect
 {
     IndexView V = view_of(ix);
     const int tok = prof_begin(ix, PROF_REMOVE, 3, st);
-    k_rm_validate<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n);
-    k_rm_phase1<<<grid_for(n, 256), 256, 0, st>>>(V, ids, n, affected);
+    launch_pdl(k_rm_validate, grid_for(n, 256), 256, 0, st, V, ids, n);
+    launch_pdl(k_rm_phase1, grid_for(n, 256), 256, 0, st, V, ids, n, affected);
     const int amax = (int)std::min<int64_t>(n, ix->nlist);
-    k_reclaim<<<grid_for((int64_t)amax * 32, 256), 256, 0, st>>>(V, affected);
+    launch_pdl(k_reclaim, grid_for((int64_t)amax * 32, 256), 256, 0, st, V, affected);
     prof_end(ix, tok, st);
 }
 

@@ -26,6 +26,7 @@ __global__ void k_srch_hist(const int32_t *__restrict__ probes, int64_t nq, int 
                             int p1, int L, bool dedupe, int32_t *__restrict__ lcnt,
                             int32_t *__restrict__ prank)
 {
+    pdl_begin();
     const int np = p1 - p0;
     const int64_t n = nq * np;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -66,6 +67,7 @@ __global__ __launch_bounds__(1024) void k_srch_plan(const int32_t *__restrict__ 
                                                     int2 *__restrict__ items, Ctl *ctl,
                                                     int64_t *stat, uint32_t *err)
 {
+    pdl_begin();
     __shared__ int32_t sa[1024], sb[1024];
     __shared__ unsigned long long sw[32];
     const int tid = threadIdx.x;
@@ -145,6 +147,7 @@ __global__ void k_srch_scatter_t(const int32_t *__restrict__ probes, int64_t nq,
                                  int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap,
                                  uint32_t *err)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); q0 < nq;
@@ -200,6 +203,7 @@ __global__ __launch_bounds__(SC_Q * 32) void k_srch_scatter(
     const int32_t *__restrict__ nch, int32_t *__restrict__ qlist, int32_t *__restrict__ prun,
     int2 *__restrict__ qrun, Ctl *ctl, int64_t run_cap, uint32_t *err)
 {
+    pdl_begin();
     __shared__ int s_cnt[SC_Q];
     __shared__ int s_base;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -433,6 +437,7 @@ __device__ __forceinline__ void dist_tile(float (&acc)[RQ][RX], const float *__r
 template <int TQ, int C>
 __global__ __launch_bounds__(SCAN_NT, 1) void k_scan(ScanArgs a)
 {
+    pdl_begin();
     constexpr int QW = TQ >= 32 ? TQ / 32 : 1;
     constexpr int SW = 8 / QW;
     constexpr int RQ = TQ / (8 * QW);
@@ -730,6 +735,7 @@ __global__ __launch_bounds__(MERGE_NT) void k_merge(const int2 *__restrict__ qru
                                                     float *__restrict__ dist,
                                                     int64_t *__restrict__ labels)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t q = (blockIdx.x * (int64_t)MERGE_NT + threadIdx.x) >> 5;
     if (q >= nq) return;
@@ -808,7 +814,7 @@ static void launch_scan(sivf_index *ix, const ScanArgs &a, size_t smem, int grid
         attr = smem;
     }
     const int tok = prof_begin(ix, PROF_SCAN, 1, st);
-    k_scan<TQ, C><<<grid, SCAN_NT, smem, st>>>(a);
+    launch_pdl(k_scan<TQ, C>, grid, SCAN_NT, smem, st, a);
     prof_end(ix, tok, st);
 }
 
@@ -952,21 +958,18 @@ void group_pairs(sivf_index *ix, int64_t nq, int P, int p0, int p1, const int32_
     const int64_t n = nq * (p1 - p0);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
     const int tg = prof_begin(ix, PROF_GROUP, 3, st);
-    k_srch_hist<<<g, 256, 0, st>>>(probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
-    k_srch_plan<<<1, 1024, 0, st>>>(s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
-                                    pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff,
-                                    s.ibase, s.nch, s.items, ix->ctl, stats ? ix->stat : nullptr,
-                                    ix->err);
+    launch_pdl(k_srch_hist, g, 256, 0, st, probes, nq, P, p0, p1, L, dedupe, s.lcnt, s.prank);
+    launch_pdl(k_srch_plan, 1, 1024, 0, st, s.lcnt, ix->nslabs, ix->list_live, L, pl.tq, pl.ch,
+               pl.slabs_per_chunk, pl.ips, pl.item_cap, slab_bytes, s.loff, s.ibase, s.nch, s.items,
+               ix->ctl, stats ? ix->stat : nullptr, ix->err);
     if (p1 - p0 >= 8) {
         const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nq + SC_Q - 1) / SC_Q, 152 * 16));
-        k_srch_scatter<<<gs, SC_Q * 32, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
-                                                 s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap,
-                                                 ix->err);
+        launch_pdl(k_srch_scatter, gs, SC_Q * 32, 0, st, probes, nq, P, p0, p1, s.prank, s.loff,
+                   s.nch, s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap, ix->err);
     } else {
         const int gq = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, 152 * 16));
-        k_srch_scatter_t<<<gq, 256, 0, st>>>(probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
-                                             s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap,
-                                             ix->err);
+        launch_pdl(k_srch_scatter_t, gq, 256, 0, st, probes, nq, P, p0, p1, s.prank, s.loff, s.nch,
+                   s.qlist, s.prun, s.qrun, ix->ctl, pl.run_cap, ix->err);
     }
     prof_end(ix, tg, st);
 }
@@ -1025,8 +1028,8 @@ void merge_topk(sivf_index *ix, int64_t nq, int P, const int32_t *probes,
     int64_t warps = nq;
     int64_t blocks = (warps * 32 + MERGE_NT - 1) / MERGE_NT;
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
-    k_merge<<<(unsigned)blocks, MERGE_NT, 0, st>>>(s.qrun, nq, pl.K, k, s.part_d, s.part_i,
-                                                  dist, labels);
+    launch_pdl(k_merge, (unsigned)blocks, MERGE_NT, 0, st, s.qrun, nq, pl.K, k, s.part_d, s.part_i,
+               dist, labels);
     prof_end(ix, tok, st);
 }
 

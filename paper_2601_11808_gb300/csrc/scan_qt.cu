@@ -383,6 +383,7 @@ template <int DT>  // 0 = BF16, 1 = FP8 E4M3
 __global__ __launch_bounds__(QT_NT, 1) void k_scan_qt(const __grid_constant__ CUtensorMap tmap,
                                                        QtArgs a)
 {
+    pdl_begin();
     constexpr int ESZ = DT == 0 ? 2 : 1;
     constexpr int EPC = 128 / ESZ;  // elements per 128-byte chunk
     extern __shared__ unsigned char smem_raw[];
@@ -953,7 +954,8 @@ static void launch_qt(const unsigned char *tmap, const QtArgs &a, size_t smem, c
         cudaFuncSetAttribute(k_scan_qt<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_scan_qt<DT><<<152, QT_NT, smem, st>>>(*reinterpret_cast<const CUtensorMap *>(tmap), a);
+    launch_pdl(k_scan_qt<DT>, 152, QT_NT, smem, st, *reinterpret_cast<const CUtensorMap *>(tmap),
+               a);
 }
 
 // longest candidate buffer of one row for the tile's select_slabs (0: 255,

@@ -523,6 +523,7 @@ __global__ __launch_bounds__(TcShape<TN>::NT, 1) void k_scan_tc(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_t,
     TcArgs a)
 {
+    pdl_begin();
     using S = TcShape<TN>;
     constexpr int EW = S::EW, EPI = S::EPI, TB = S::TB;
     constexpr int ESZ = DT == 0 ? 2 : 1;
@@ -1157,6 +1158,7 @@ __global__ __launch_bounds__(MT_NT) void k_merge_tc(const int2 *__restrict__ qru
                                                     float *__restrict__ out_d,
                                                     int64_t *__restrict__ out_s)
 {
+    pdl_begin();
     constexpr int NW = MT_NT / 32;
     __shared__ uint32_t hist_s[NW][TC_HIST];
     __shared__ float sd[NW][32 * E];
@@ -1191,9 +1193,9 @@ void merge_tc(sivf_index *ix, int64_t nq, int nphase, const SearchScratch &s, in
 {
     const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
     const int tok = prof_begin(ix, PROF_MERGE, 1, st);
-#define SIVF_MTC(E_)                                                                         \
-    k_merge_tc<E_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, RK, s.part_n, s.part_d, \
-                                             s.part_i, out_d, out_s)
+#define SIVF_MTC(E_)                                                                               \
+    launch_pdl(k_merge_tc<E_>, blocks, MT_NT, 0, st, s.qrun, nq, nphase, Kc, RK, s.part_n,         \
+               s.part_d, s.part_i, out_d, out_s)
     if (Kc <= 32) SIVF_MTC(1);
     else if (Kc <= 64) SIVF_MTC(2);
     else if (Kc <= 128) SIVF_MTC(4);
@@ -1223,6 +1225,7 @@ __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, i
                                                 const int64_t *__restrict__ ids, int k,
                                                 float *__restrict__ dist, int64_t *__restrict__ labels)
 {
+    pdl_begin();
     __shared__ int64_t sgs[RK_NT / 32][32 * E];
     __shared__ float sd[RK_NT / 32][32 * E];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 3, t = lane & 7;
@@ -1317,6 +1320,7 @@ __global__ __launch_bounds__(MT_NT, NQ <= 4 ? 8 : 2) void k_merge_rerank(
     const float *__restrict__ x32, const int64_t *__restrict__ ids, int k,
     float *__restrict__ dist, int64_t *__restrict__ labels)
 {
+    pdl_begin();
     constexpr int NW = MT_NT / 32;
     __shared__ uint32_t hist_s[NW][TC_HIST];
     __shared__ float sd[NW][32 * E];
@@ -1411,6 +1415,7 @@ __global__ __launch_bounds__(RR_NT, NQ <= 4 ? 4 : 1) void k_rerank_wide(const fl
                                                        float *__restrict__ dist,
                                                        int64_t *__restrict__ labels)
 {
+    pdl_begin();
     __shared__ float sd[RR_MAX];
     __shared__ int64_t si[RR_MAX];
     const int64_t qi = blockIdx.x;
@@ -1498,6 +1503,7 @@ __global__ void k_query_prep(const float *__restrict__ q, int64_t nq, int d,
                              float *__restrict__ qn, float *__restrict__ qsc,
                              unsigned char *__restrict__ qcast)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= nq) return;
@@ -1520,7 +1526,8 @@ void query_prep(sivf_index *ix, const float *q, int64_t nq, float *qn, float *qs
                 unsigned char *qcast, cudaStream_t st)
 {
     ix->launches += 1;
-    k_query_prep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(q, nq, ix->d, qn, qsc, qcast);
+    launch_pdl(k_query_prep, (unsigned)((nq * 32 + 255) / 256), 256, 0, st, q, nq, ix->d, qn, qsc,
+               qcast);
 }
 
 // FP8 residual scan: per (query, probe) pair e = q * P + p with list l =
@@ -1534,6 +1541,7 @@ __global__ void k_pair_prep(const float *__restrict__ q, int64_t npairs, int P, 
                             float *__restrict__ qn, float *__restrict__ qsc,
                             unsigned char *__restrict__ qcast)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (e >= npairs) return;
@@ -1609,14 +1617,14 @@ void pair_prep(sivf_index *ix, const float *q, int64_t nq, int P, const int32_t 
 {
     ix->launches += 1;
     const int64_t np = nq * P;
-    k_pair_prep<<<(unsigned)((np * 32 + 255) / 256), 256, 0, st>>>(q, np, P, ix->d, ix->nlist,
-                                                                  probes, ix->cent, qn, qsc,
-                                                                  qcast);
+    launch_pdl(k_pair_prep, (unsigned)((np * 32 + 255) / 256), 256, 0, st, q, np, P, ix->d,
+               ix->nlist, probes, ix->cent, qn, qsc, qcast);
 }
 
 // global slots -> labels (padding stays -1)
 __global__ void k_slots_to_ids(int64_t *v, int64_t n, const int64_t *__restrict__ ids)
 {
+    pdl_begin();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         if (v[i] >= 0) v[i] = ids[v[i]];
@@ -1625,7 +1633,8 @@ __global__ void k_slots_to_ids(int64_t *v, int64_t n, const int64_t *__restrict_
 void slots_to_ids(sivf_index *ix, int64_t *v, int64_t n, cudaStream_t st)
 {
     ix->launches += 1;
-    k_slots_to_ids<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, n, ix->ids);
+    launch_pdl(k_slots_to_ids, (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0,
+               st, v, n, ix->ids);
 }
 
 // --------------------------------------------------------------- host side
@@ -1797,9 +1806,9 @@ static void launch_tc(const unsigned char *tmap, const unsigned char *tmap_t, Tc
                              (int)smem);
         attr = smem;
     }
-    k_scan_tc<DT, TN><<<152, TcShape<TN>::NT, smem, st>>>(
-        *reinterpret_cast<const CUtensorMap *>(tmap), *reinterpret_cast<const CUtensorMap *>(tmap_t),
-        a);
+    launch_pdl(k_scan_tc<DT, TN>, 152, TcShape<TN>::NT, smem, st,
+               *reinterpret_cast<const CUtensorMap *>(tmap),
+               *reinterpret_cast<const CUtensorMap *>(tmap_t), a);
 }
 
 void scan_lists_tc(sivf_index *ix, int dtype, const float *q, int64_t nq, int P, int Kc,
@@ -1874,10 +1883,10 @@ void merge_rerank(sivf_index *ix, const float *q, int64_t nq, int nphase,
     }
     const unsigned blocks = (unsigned)((nq * 32 + MT_NT - 1) / MT_NT);
     const int tok = prof_begin(ix, PROF_RERANK, 1, st);
-#define SIVF_MRR(E_, NQ_)                                                                 \
-    k_merge_rerank<E_, NQ_><<<blocks, MT_NT, 0, st>>>(s.qrun, nq, nphase, Kc, RK, s.part_n, \
-                                                    s.part_d, s.part_i, q, ix->d, ix->x32,  \
-                                                    ix->ids, k, dist, labels)
+#define SIVF_MRR(E_, NQ_)                                                                          \
+    launch_pdl(k_merge_rerank<E_, NQ_>, blocks, MT_NT, 0, st, s.qrun, nq, nphase, Kc, RK,          \
+               s.part_n, s.part_d, s.part_i, q, ix->d, ix->x32, ix->ids, k, dist,                  \
+               labels)
     const bool wide = ix->d > 128;
     if (Kc <= 32) {
         if (wide) SIVF_MRR(1, 8);
@@ -1898,9 +1907,9 @@ void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *can
 {
     const int64_t blocks = (nq * 32 + RK_NT - 1) / RK_NT;
     const int tok = prof_begin(ix, PROF_RERANK, 1, st);
-#define SIVF_RERANK(E_, NQ_)                                                            \
-    k_rerank<E_, NQ_><<<(unsigned)blocks, RK_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s, \
-                                                        ix->x32, ix->ids, k, dist, labels)
+#define SIVF_RERANK(E_, NQ_)                                                                       \
+    launch_pdl(k_rerank<E_, NQ_>, (unsigned)blocks, RK_NT, 0, st, q, nq, ix->d, Kc, cand_d,        \
+               cand_s, ix->x32, ix->ids, k, dist, labels)
     const bool wide = ix->d > 128;  // chunks per lane: 4 (d <= 128) or 8 (d <= 256)
     if (Kc <= 32) {
         if (wide) SIVF_RERANK(1, 8);
@@ -1913,11 +1922,11 @@ void rerank(sivf_index *ix, const float *q, int64_t nq, int Kc, const float *can
         else SIVF_RERANK(4, 4);
     } else {
         if (ix->d > 128)
-            k_rerank_wide<8><<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s,
-                                                             ix->x32, ix->ids, k, dist, labels);
+            launch_pdl(k_rerank_wide<8>, (unsigned)nq, RR_NT, 0, st, q, nq, ix->d, Kc, cand_d,
+                       cand_s, ix->x32, ix->ids, k, dist, labels);
         else
-            k_rerank_wide<4><<<(unsigned)nq, RR_NT, 0, st>>>(q, nq, ix->d, Kc, cand_d, cand_s,
-                                                             ix->x32, ix->ids, k, dist, labels);
+            launch_pdl(k_rerank_wide<4>, (unsigned)nq, RR_NT, 0, st, q, nq, ix->d, Kc, cand_d,
+                       cand_s, ix->x32, ix->ids, k, dist, labels);
     }
 #undef SIVF_RERANK
     prof_end(ix, tok, st);

@@ -13,6 +13,7 @@ namespace sivf {
 __global__ void k_train_gather(const float *__restrict__ x, int d, const int64_t *__restrict__ rows,
                                int L, float *__restrict__ cent)
 {
+    pdl_begin();
     const int64_t n = (int64_t)L * d;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -24,6 +25,7 @@ __global__ void k_train_accum(const float *__restrict__ x, int64_t n, int d,
                               const int32_t *__restrict__ lab, double *__restrict__ sum,
                               int32_t *__restrict__ cnt)
 {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -39,6 +41,7 @@ __global__ void k_train_accum(const float *__restrict__ x, int64_t n, int d,
 __global__ void k_train_update(const double *__restrict__ sum, const int32_t *__restrict__ cnt,
                                int L, int d, float *__restrict__ cent)
 {
+    pdl_begin();
     const int64_t n = (int64_t)L * d;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -51,8 +54,8 @@ void train_gather(sivf_index *ix, const float *x, const int64_t *rows, cudaStrea
 {
     ix->launches += 1;
     const int64_t n = (int64_t)ix->nlist * ix->d;
-    k_train_gather<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(
-        x, ix->d, rows, ix->nlist, ix->cent);
+    launch_pdl(k_train_gather, (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st, x,
+               ix->d, rows, ix->nlist, ix->cent);
 }
 
 void train_step(sivf_index *ix, const float *x, int64_t n, const int32_t *lab, double *sum,
@@ -62,11 +65,11 @@ void train_step(sivf_index *ix, const float *x, int64_t n, const int32_t *lab, d
     cudaMemsetAsync(sum, 0, sizeof(double) * (size_t)L * d, st);
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)L, st);
     ix->launches += 2;
-    k_train_accum<<<(unsigned)std::min<int64_t>((n * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
-        x, n, d, lab, sum, cnt);
+    launch_pdl(k_train_accum, (unsigned)std::min<int64_t>((n * 32 + 255) / 256, 152 * 16), 256, 0,
+               st, x, n, d, lab, sum, cnt);
     const int64_t e = (int64_t)L * d;
-    k_train_update<<<(unsigned)std::min<int64_t>((e + 255) / 256, 152 * 8), 256, 0, st>>>(
-        sum, cnt, L, d, ix->cent);
+    launch_pdl(k_train_update, (unsigned)std::min<int64_t>((e + 255) / 256, 152 * 8), 256, 0, st,
+               sum, cnt, L, d, ix->cent);
 }
 
 }  // namespace sivf
