@@ -1312,8 +1312,11 @@ __global__ __launch_bounds__(RK_NT) void k_rerank(const float *__restrict__ q, i
 // rounds of four candidate rows per warp batch of the re-ranks that run with
 // more resident warps (fused merge + re-rank, wide re-rank)
 constexpr int RR_UNR = 2;
+// d <= 128: nine blocks of four warps per SM (at most 56 registers, no
+// spills), 5,472 resident warps, so 10,000 queries take two waves instead of
+// the three of eight blocks (0.062 -> 0.052 ms, same results)
 template <int E, int NQ>
-__global__ __launch_bounds__(MT_NT, NQ <= 4 ? 8 : 2) void k_merge_rerank(
+__global__ __launch_bounds__(MT_NT, NQ <= 4 ? 9 : 2) void k_merge_rerank(
     const int2 *__restrict__ qrun, int64_t nq, int nphase, int K, int RK,
     const int32_t *__restrict__ part_n, const float *__restrict__ part_d,
     const int64_t *__restrict__ part_i, const float *__restrict__ q, int d,
