@@ -396,7 +396,15 @@ __global__ void k_ins_alloc(IndexView V, const int32_t *__restrict__ touched,
     plan[t] = pe;
 }
 
-// one warp per kept vector
+// sum over the 16 lanes of a half warp (every lane of the warp calls it)
+__device__ __forceinline__ float half_sum(float v)
+{
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// two kept vectors per warp, one per half (16 lanes of 16-byte chunks): a
+// batch of 10,000 takes one wave of resident warps instead of two
 __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
                              const float *__restrict__ x, int64_t n,
                              const int32_t *__restrict__ lab, const int32_t *__restrict__ rloc,
@@ -404,65 +412,72 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
 {
     pdl_begin();
     if (V.ctl->status != SIVF_OK) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, hl = lane & 15;
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
     const int d = V.d, C = V.C;
-    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; i < n; i += nw) {
-        const int r0 = rloc[i];
-        if (r0 < 0) continue;
-        const int l = lab[i];
-        const int r = V.runcnt[(size_t)l * V.nblk_max + (i >> 10)] + r0;
-        const PlanEntry pe = plan[V.list_flag[l] - 1];
-        int64_t s;
-        int slot;
-        if (r < pe.into_head) {
-            s = pe.head_old;
-            slot = pe.fill_old + r;
-        } else {
-            const int q = r - pe.into_head;
-            s = V.dir[(size_t)l * V.dir_cap + pe.dir_pos0 + q / C];
-            slot = q % C;
-        }
-        const size_t row = (size_t)s * C + slot;
-        const float *xi = x + (size_t)i * d;
-        const float inv = V.x8 ? V.inv_scale8[l] : 1.f;
-        const float *cl = V.cent + (size_t)l * d;
+    // whole warps iterate together (the half sums shuffle across the warp)
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; 2 * w < n; w += nw) {
+        const int64_t i = 2 * w + (lane >> 4);
+        const int r0 = i < n ? rloc[i] : -1;
+        const bool on = r0 >= 0;
+        int64_t s = 0;
+        int slot = 0;
         float ss = 0.f, rs = 0.f;
-        for (int j = lane * 4; j < d; j += 128) {
-            const float4 v = *reinterpret_cast<const float4 *>(xi + j);
-            *reinterpret_cast<float4 *>(V.x32 + row * d + j) = v;
-            ss = fmaf(v.x, v.x, ss);
-            ss = fmaf(v.y, v.y, ss);
-            ss = fmaf(v.z, v.z, ss);
-            ss = fmaf(v.w, v.w, ss);
-            if (V.xb16) {
-                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t *>(&lo);
-                pk.y = *reinterpret_cast<uint32_t *>(&hi);
-                *reinterpret_cast<uint2 *>(V.xb16 + row * d + j) = pk;
+        if (on) {
+            const int l = lab[i];
+            const int r = V.runcnt[(size_t)l * V.nblk_max + (i >> 10)] + r0;
+            const PlanEntry pe = plan[V.list_flag[l] - 1];
+            if (r < pe.into_head) {
+                s = pe.head_old;
+                slot = pe.fill_old + r;
+            } else {
+                const int q = r - pe.into_head;
+                s = V.dir[(size_t)l * V.dir_cap + pe.dir_pos0 + q / C];
+                slot = q % C;
             }
-            if (V.x8) {
-                // residual r = fl32(x - c_l), code = E4M3(fl32(r * inv))
-                const float4 c4 = *reinterpret_cast<const float4 *>(cl + j);
-                const float4 rv = make_float4(__fsub_rn(v.x, c4.x), __fsub_rn(v.y, c4.y),
-                                              __fsub_rn(v.z, c4.z), __fsub_rn(v.w, c4.w));
-                rs = fmaf(rv.x, rv.x, rs);
-                rs = fmaf(rv.y, rv.y, rs);
-                rs = fmaf(rv.z, rv.z, rs);
-                rs = fmaf(rv.w, rv.w, rs);
-                float2 a = make_float2(__fmul_rn(rv.x, inv), __fmul_rn(rv.y, inv));
-                float2 b = make_float2(__fmul_rn(rv.z, inv), __fmul_rn(rv.w, inv));
-                __nv_fp8x2_storage_t pa = __nv_cvt_float2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
-                __nv_fp8x2_storage_t pb = __nv_cvt_float2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
-                *reinterpret_cast<uint32_t *>(V.x8 + row * d + j) =
-                    (uint32_t)pa | ((uint32_t)pb << 16);
+            const size_t row = (size_t)s * C + slot;
+            const float *xi = x + (size_t)i * d;
+            const float inv = V.x8 ? V.inv_scale8[l] : 1.f;
+            const float *cl = V.cent + (size_t)l * d;
+            for (int j = hl * 4; j < d; j += 64) {
+                const float4 v = *reinterpret_cast<const float4 *>(xi + j);
+                *reinterpret_cast<float4 *>(V.x32 + row * d + j) = v;
+                ss = fmaf(v.x, v.x, ss);
+                ss = fmaf(v.y, v.y, ss);
+                ss = fmaf(v.z, v.z, ss);
+                ss = fmaf(v.w, v.w, ss);
+                if (V.xb16) {
+                    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+                    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<uint32_t *>(&lo);
+                    pk.y = *reinterpret_cast<uint32_t *>(&hi);
+                    *reinterpret_cast<uint2 *>(V.xb16 + row * d + j) = pk;
+                }
+                if (V.x8) {
+                    // residual r = fl32(x - c_l), code = E4M3(fl32(r * inv))
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cl + j);
+                    const float4 rv = make_float4(__fsub_rn(v.x, c4.x), __fsub_rn(v.y, c4.y),
+                                                  __fsub_rn(v.z, c4.z), __fsub_rn(v.w, c4.w));
+                    rs = fmaf(rv.x, rv.x, rs);
+                    rs = fmaf(rv.y, rv.y, rs);
+                    rs = fmaf(rv.z, rv.z, rs);
+                    rs = fmaf(rv.w, rv.w, rs);
+                    float2 a = make_float2(__fmul_rn(rv.x, inv), __fmul_rn(rv.y, inv));
+                    float2 b = make_float2(__fmul_rn(rv.z, inv), __fmul_rn(rv.w, inv));
+                    __nv_fp8x2_storage_t pa =
+                        __nv_cvt_float2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
+                    __nv_fp8x2_storage_t pb =
+                        __nv_cvt_float2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
+                    *reinterpret_cast<uint32_t *>(V.x8 + row * d + j) =
+                        (uint32_t)pa | ((uint32_t)pb << 16);
+                }
             }
         }
-        ss = warp_sum(ss);
-        if (V.x8) rs = warp_sum(rs);
-        if (lane == 0) {
+        ss = half_sum(ss);
+        if (V.x8) rs = half_sum(rs);
+        if (on && hl == 0) {
+            const size_t row = (size_t)s * C + slot;
             const int64_t id = ids[i];
             V.xnorm[row] = ss;
             if (V.rnorm) V.rnorm[row] = rs;
@@ -472,7 +487,7 @@ __global__ void k_ins_append(IndexView V, const int64_t *__restrict__ ids,
         // payload, id and table entry are visible before the bit (Theorem 1)
         __threadfence();
         __syncwarp();
-        if (lane == 0) {
+        if (on && hl == 0) {
             __threadfence();
             atomicOr(&V.bits[s * V.W + (slot >> 5)], 1u << (slot & 31));
         }
@@ -518,7 +533,7 @@ void insert_batch(sivf_index *ix, const int64_t *ids, const float *x, int64_t n,
     launch_pdl(k_ins_overwrite, grid_for(n, 256), 256, 0, st, V, ids, n, s.rloc, s.affected);
     launch_pdl(k_reclaim, grid_for((int64_t)tmax * 32, 256), 256, 0, st, V, s.affected);
     launch_pdl(k_ins_alloc, (tmax + 127) / 128, 128, 0, st, V, s.touched, s.bcnt, s.plan);
-    launch_pdl(k_ins_append, grid_for(n * 32, 256), 256, 0, st, V, ids, x, n, s.lab, s.rloc,
+    launch_pdl(k_ins_append, grid_for(n * 16, 256), 256, 0, st, V, ids, x, n, s.lab, s.rloc,
                s.plan);
     launch_pdl(k_ins_cleanup, grid_for(std::max<int64_t>(n, (int64_t)tmax * nblk), 256), 256, 0, st,
                V, ids, n, nblk, s.touched);
