@@ -239,13 +239,31 @@ def run_reference(args):
     if rank != 0:
         return
     w = W.CONFIGS[args.workload]
-    nprobe = args.nprobe or 8
-    n_ins, n_del, n_q = 1000, 1000, 200
+    n_ins, n_del, n_q, n_cal = 1000, 1000, 200, 200
     steps = args.steps + args.warmup
-    cent, X, Q = make_data(w, (steps * n_ins) // w.step + 1, 0, 0)
+    cent, X, Q = make_data(w, (steps * n_ins) // w.step + 1, n_cal, 0)
     n_max = w.window + (steps * n_ins // w.step + 3) * w.step
     t0 = time.time()
-    r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps)
+    orc, _, _ = oracle_window(w, cent, X, n_max)
+    # nprobe by the sivf arm's rule: the smallest of the sweep whose
+    # recall@10 reaches 0.95 against the exact k nearest neighbours of
+    # sampled queries over the initial window (here the oracle's own IVF
+    # search against its brute force, on n_cal queries)
+    rec = {}
+    if args.nprobe:
+        nprobe = args.nprobe
+    else:
+        Qc = Q[-n_cal:]
+        _, gt = orc.exact_knn(Qc, w.k)
+        nprobe = NPROBES[-1]
+        for P in NPROBES:
+            _, got = orc.search(Qc, w.k, P)
+            rec[P] = float(np.mean([len(set(a) & set(b)) / w.k
+                                    for a, b in zip(got.tolist(), gt.tolist())]))
+            if rec[P] >= 0.95:
+                nprobe = P
+                break
+    r = oracle_sample(w, cent, X, Q, n_max, nprobe, n_ins, n_del, n_q, steps, o=orc)
     wall = time.time() - t0
     sample = (f"oracle index holding the full {w.window:,}-vector window (built with "
               f"{r['cores']} threads, untimed); per step {n_ins} inserts, {n_del} deletes "
@@ -259,6 +277,9 @@ def run_reference(args):
         "ms_per_step": round(float(np.mean(st)) * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(w, nprobe),
+        "recall_at_10": rec.get(nprobe), "recall_by_nprobe": rec,
+        "recall_truth": (f"the oracle's exact k nearest neighbours of {n_cal} sampled queries "
+                         "over the initial window" if rec else None),
         "components": {k: r[k] for k in ("search_qps", "insert_vec_s", "delete_vec_s",
                                            "p99_update_ms")},
         "cpu_baseline": {"value": round(val, 3), "unit": "queries/s", "cores": r["cores"],
