@@ -148,8 +148,8 @@ sivf_status sivf_set_centroids(sivf_index *index, const float *c, void *stream);
  * first-stage bound does not isolate one list is re-decided exactly.  The
  * single product is taken unless twice its bound at the largest centroid
  * norm, 4 gamma max ||c||^2 with gamma = 2 (2 u + u^2 + d 2^-22 (1 + u)^2),
- * u = 2^-8, exceeds half the median over lists of the squared distance from
- * a centroid to its nearest other centroid (FP32): then most rows would need
+ * u = 2^-8, exceeds the median over lists of the squared distance from a
+ * centroid to its nearest other centroid (FP32): then most rows would need
  * the re-decision and the split stage (a bound about 60x tighter) is taken.
  * Chosen by sivf_set_centroids, sivf_train and sivf_load.
  */

@@ -1399,15 +1399,16 @@ static double first_stage_rel(int d, int split)
 
 // Which first stage nearest-list assignment takes.  The single BF16 product
 // decides a row on its own when the row's second-nearest list is farther
-// than its nearest by more than twice the bound E <= gamma ||x|| ||c||
-// (gamma = 2 first_stage_rel); otherwise the row's candidates are recorded
-// and re-decided, and a row with more candidates than its records hold is
-// redone from every list.  For a point near its centroid that gap is about
-// the squared distance R^2 from the centroid to its nearest neighbour, so
-// when 2 E (taken at ||x|| = max ||c||) exceeds half the median R^2, most
-// rows would be undecided and the split first stage (bound about 60x
-// tighter) is taken instead.  Both give the same assignment.  Synchronizes
-// `st`.
+// than its nearest by more than twice the bound the fused stage uses,
+// E = 2 gamma ||x|| max ||c|| (gamma = 2 first_stage_rel, the bound on one
+// distance, doubled for safety); otherwise the row's candidates are
+// recorded and re-decided, and a row with more candidates than its records
+// hold is redone from every list.  For a point near its centroid that gap
+// is about the squared distance R^2 from the centroid to its nearest
+// neighbour, so when 2 E (taken at ||x|| = max ||c||) exceeds the median
+// R^2, most rows would be undecided and the split first stage (bound about
+// 60x tighter) is taken instead.  Both give the same assignment.
+// Synchronizes `st`.
 cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st)
 {
     ix->assign_split = false;
@@ -1429,8 +1430,8 @@ cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st)
     std::nth_element(g.begin(), g.begin() + L / 2, g.end());
     const double med = g[(size_t)L / 2];
     const double c2 = *std::max_element(cn.begin(), cn.end());
-    const double two_e = 4.0 * first_stage_rel(d, 1) * c2;
-    ix->assign_split = std::isfinite(med) && two_e > 0.5 * med;
+    const double e_max = 4.0 * first_stage_rel(d, 1) * c2;  // E at ||x|| = max ||c||
+    ix->assign_split = std::isfinite(med) && 2.0 * e_max > med;
     return cudaSuccess;
 }
 
