@@ -1421,7 +1421,9 @@ cudaError_t assign_stage_choose(sivf_index *ix, cudaStream_t st)
     ix->launches += 1;
     launch_pdl(k_cent_gap, (L * 32 + 127) / 128, 128, 0, st, ix->cent, L, d, gap2);
     std::vector<float> g((size_t)L), cn((size_t)L);
-    e = cudaMemcpyAsync(g.data(), gap2, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g.data(), gap2, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cn.data(), ix->cnorm, sizeof(float) * L, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(gap2, st);
