@@ -188,7 +188,8 @@ def oracle_window(w, cent, X, n_max):
     o.set_centroids(cent)
     t0 = time.time()
     for b in range(0, w.window, 100_000):
-        o.add(W.stream_ids(b, 100_000, n_max), X[b:b + 100_000])
+        n = min(100_000, w.window - b)
+        o.add(W.stream_ids(b, n, n_max), X[b:b + n])
     return o, cores, time.time() - t0
 
 
@@ -1004,8 +1005,9 @@ def main():
                    scan_dtypes=tuple(f for f in forms if f != "fp32"))
     g.set_centroids(torch.from_numpy(cent).to(dev))
     for b in range(0, w.window, 100_000):
-        g.add(torch.from_numpy(W.stream_ids(b, 100_000, n_max)).to(dev),
-              torch.from_numpy(X[b:b + 100_000]).to(dev))
+        n = min(100_000, w.window - b)
+        g.add(torch.from_numpy(W.stream_ids(b, n, n_max)).to(dev),
+              torch.from_numpy(X[b:b + n]).to(dev))
     g.sync()
 
     # per form: the smallest nprobe of the sweep whose recall@10 reaches
